@@ -1,0 +1,150 @@
+/*
+ * dpvo_ba.h -- C ABI of the B300-native differentiable Gauss-Newton bundle
+ * adjustment over the DPVO patch graph (Deep Patch Visual Odometry, Sec. 3.1
+ * "Differentiable Bundle Adjustment", Eq. 6; reprojection Eq. 2-3; damping in
+ * the Appendix "Bundle Adjustment Layer"; optimisation window Sec. 3.3).
+ *
+ * The layer minimises, over camera poses T (world->camera, SE(3)) and one
+ * inverse depth d_k per patch (its pixel centre held fixed),
+ *
+ *     sum_{(k,j) in edges}  || target_kj - omega_ij(T, P_k) ||^2_{diag(weight_kj)}
+ *
+ * where patch k is anchored in frame i = anchor[k] and omega_ij reprojects its
+ * centre (x_k, y_k) at inverse depth d_k from frame i into frame j (Eq. 2).
+ * Every iteration linearises the residuals, eliminates the inverse depths with
+ * the Schur complement, solves the reduced pose system by Cholesky with poses
+ * [0, t0) held fixed, back-substitutes the inverse depths and retracts
+ * T_a <- Exp(dxi_a) T_a (left increment, dxi = (v, w), translation first),
+ * d_k <- d_k + dd_k.  A damping lambda is added to every inverse-depth diagonal
+ * entry.  An edge takes part iff the third homogeneous coordinate of the
+ * reprojected centre exceeds z_min.
+ *
+ * Conventions for every entry point
+ *   - Return value: DPVO_BA_OK (0) or a negative DPVO_BA_E* code.  No call aborts,
+ *     traps or waits without a bound.
+ *   - Pointers inside dpvo_ba_problem are DEVICE pointers owned by the caller;
+ *     the library never frees them.  Arrays are dense, row-major, float32 or
+ *     int32 as stated, and must stay valid until the work on `stream` is done.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream unless stated otherwise.
+ *   - The handle owns its device workspace; calls that need more than it holds
+ *     grow it (a cudaMalloc outside any kernel).  dpvo_ba_reserve() grows it
+ *     ahead of time so that later solves allocate nothing.
+ *   - A handle is not thread-safe: serialise calls on one handle.
+ */
+#ifndef DPVO_BA_H
+#define DPVO_BA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define DPVO_BA_OK            0
+#define DPVO_BA_EINVAL      (-1)   /* bad argument (NULL, negative size, limit exceeded) */
+#define DPVO_BA_ENOMEM      (-2)   /* device allocation failed or memory budget exceeded */
+#define DPVO_BA_ECUDA       (-3)   /* a CUDA runtime call failed                         */
+#define DPVO_BA_ETIMEOUT    (-4)   /* a bounded wait ran out                             */
+#define DPVO_BA_EBUSY       (-5)   /* serving: no slot free and the call may not block   */
+#define DPVO_BA_ENOTFOUND   (-6)   /* serving: unknown session or ticket                 */
+
+/* ---- per-problem status bits (written to dpvo_ba_problem.status) -------- */
+#define DPVO_BA_STATUS_OK          0
+#define DPVO_BA_STATUS_NOT_SPD     1  /* reduced pose system not positive definite: pivot <= 0 or NaN */
+#define DPVO_BA_STATUS_BAD_INPUT   2  /* index out of range, unsorted edges, or a capacity exceeded   */
+#define DPVO_BA_STATUS_NONFINITE   4  /* a non-finite increment was produced                          */
+/* A problem whose status is not OK leaves its poses and patches as it found them. */
+
+/* ---- capacities of this build ------------------------------------------- */
+#define DPVO_BA_MAX_FRAMES       128  /* N per problem                                   */
+#define DPVO_BA_MAX_FREE          15  /* N - t0 per problem (reduced system <= 90 x 90)  */
+#define DPVO_BA_MAX_ITERS         16  /* Gauss-Newton iterations per solve               */
+
+/* Sizes of one problem. */
+typedef struct {
+    int32_t n_frames;   /* N >= 1                                                  */
+    int32_t n_patches;  /* P >= 0                                                  */
+    int32_t n_edges;    /* E >= 0                                                  */
+    int32_t t0;         /* poses [0, t0) fixed, [t0, N) free; 0 <= t0 <= N          */
+    int32_t n_iters;    /* Gauss-Newton iterations (2 in the paper, Sec. 3.3)       */
+    float fx, fy, cx, cy; /* pinhole intrinsics (Eq. 3)                             */
+} dpvo_ba_dims;
+
+/* Layer constants (Appendix "Bundle Adjustment Layer": damping 1e-4). */
+typedef struct {
+    float damping;          /* lambda added to each inverse-depth diagonal entry (1e-4)   */
+    float z_min;            /* edge active iff reprojected homogeneous depth > z_min (0.1)*/
+    size_t mem_budget_bytes;/* serving: device bytes sessions may hold (0 = 8 GiB)        */
+    int32_t max_sessions;   /* serving: resident sessions (0 = 256)                       */
+    int32_t reserved;
+} dpvo_ba_config;
+
+/* One problem's device arrays (caller-owned).
+ *   poses   [N][7]  tx ty tz qx qy qz qw, world->camera, unit quaternion.  IN/OUT.
+ *   patches [P][3]  x y d: pixel centre and inverse depth.  d is IN/OUT, x y are read.
+ *   anchor  [P]     source frame i_k of each patch, non-decreasing in k.
+ *   kk      [E]     patch of each edge, non-decreasing (edges grouped by patch).
+ *   jj      [E]     frame of each edge; strictly increasing within one patch.
+ *   target  [E][2]  2-D target pixel (the reprojection centre plus the flow revision).
+ *   weight  [E][2]  per-component confidence weight (the paper's Sigma, in (0,1)).
+ *   status  [1]     int32 DPVO_BA_STATUS_* bits written by solve (may be NULL).   */
+typedef struct {
+    float *poses;
+    float *patches;
+    const int32_t *anchor;
+    const int32_t *kk;
+    const int32_t *jj;
+    const float *target;
+    const float *weight;
+    int32_t *status;
+} dpvo_ba_problem;
+
+typedef struct dpvo_ba_handle dpvo_ba_handle;
+
+/* Create a handle on the current CUDA device.  cfg may be NULL (defaults above).
+ * Errors: EINVAL (out NULL), ECUDA, ENOMEM. */
+int dpvo_ba_create(const dpvo_ba_config *cfg, dpvo_ba_handle **out);
+
+/* Release the handle and its workspace (waits for the handle's own work). */
+int dpvo_ba_destroy(dpvo_ba_handle *h);
+
+/* Grow the workspace so that a solve of up to n_problems problems, none larger
+ * than *max_dims (frames, patches, edges, iterations; t0 is ignored), needs no
+ * further allocation.  Synchronous.  Errors: EINVAL, ENOMEM. */
+int dpvo_ba_reserve(dpvo_ba_handle *h, const dpvo_ba_dims *max_dims, int n_problems);
+
+/* Solve n_problems independent problems (dims[b], probs[b] host arrays of
+ * structs describing device data), n_iters Gauss-Newton iterations each (Sec.
+ * 3.1, Eq. 6).  n_problems == 1 is the plain form; larger batches are packed
+ * into the same launches.  Poses and inverse depths are updated in place;
+ * status bits written per problem.  Asynchronous on stream.
+ * Errors: EINVAL (NULL, sizes out of range, more than DPVO_BA_MAX_FREE free
+ * poses), ENOMEM, ECUDA.  Input-content errors (indices, ordering) are reported
+ * per problem as DPVO_BA_STATUS_BAD_INPUT, not as a return code. */
+int dpvo_ba_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
+                  int n_problems, void *stream);
+
+/* The same solve with every array in HOST memory (pageable or pinned): copies
+ * the inputs to the handle's device staging area, solves, copies poses,
+ * patches and status back, and synchronises before returning.  The pointers in
+ * hprobs are host pointers with the layouts above.  Errors: as dpvo_ba_solve. */
+int dpvo_ba_solve_host(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *hprobs,
+                       int n_problems, void *stream);
+
+/* Diagnostic: the reduced pose system of ONE linearisation at the given state
+ * (no update).  S_out [n][n] and v_out [n] are DEVICE float64 arrays with
+ * n = 6 (N - t0): S = B - E C^-1 E^T and v' = v - E C^-1 w (Sec. 3.1, Schur
+ * complement).  Asynchronous.  Errors: EINVAL, ENOMEM, ECUDA. */
+int dpvo_ba_reduced_system(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *prob,
+                           double *S_out, double *v_out, void *stream);
+
+/* Human-readable name of a return code. */
+const char *dpvo_ba_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPVO_BA_H */
