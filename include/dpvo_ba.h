@@ -141,6 +141,15 @@ int dpvo_ba_solve_host(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_b
 int dpvo_ba_reduced_system(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *prob,
                            double *S_out, double *v_out, void *stream);
 
+/* Diagnostic: after a solve on this handle (and before the next call on it),
+ * copy problem `index`'s state after iteration `iter` (0 = the input state,
+ * n_iters = the output) into HOST buffers: poses_out [N][7] float32 and
+ * depth_out [P] float32; and, for iter < n_iters, the FP64 pose increment of
+ * that iteration, dxi_out [N - t0][6] (v then w).  Any output may be NULL.
+ * Synchronises the device.  Errors: EINVAL (no such problem or iteration). */
+int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, float *depth_out,
+                    double *dxi_out);
+
 /* Human-readable name of a return code. */
 const char *dpvo_ba_strerror(int code);
 

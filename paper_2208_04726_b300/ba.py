@@ -1,0 +1,223 @@
+"""Python binding of the C ABI in ``include/dpvo_ba.h`` (ctypes; argument
+marshalling only -- every step of the solve runs in the CUDA library).
+
+The library must be built (``paper_2208_04726_b300.build``); there is no
+fallback: importing a missing or stale library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+# ---- C structs ---------------------------------------------------------------
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int32), ("n_patches", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("t0", ctypes.c_int32), ("n_iters", ctypes.c_int32),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("damping", ctypes.c_float), ("z_min", ctypes.c_float), ("mem_budget_bytes", ctypes.c_size_t),
+                ("max_sessions", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("poses", ctypes.c_void_p), ("patches", ctypes.c_void_p), ("anchor", ctypes.c_void_p),
+                ("kk", ctypes.c_void_p), ("jj", ctypes.c_void_p), ("target", ctypes.c_void_p),
+                ("weight", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
+STATUS_OK, STATUS_NOT_SPD, STATUS_BAD_INPUT, STATUS_NONFINITE = 0, 1, 2, 4
+MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 15, 16
+
+# Every symbol the header declares (checked by the CPU tests).
+EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solve", "dpvo_ba_solve_host",
+           "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_strerror"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the CUDA library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int
+    lib.dpvo_ba_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    lib.dpvo_ba_destroy.argtypes = [vp]
+    lib.dpvo_ba_reserve.argtypes = [vp, ctypes.POINTER(Dims), i32]
+    lib.dpvo_ba_solve.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), i32, vp]
+    lib.dpvo_ba_solve_host.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), i32, vp]
+    lib.dpvo_ba_reduced_system.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), vp, vp, vp]
+    lib.dpvo_ba_iterate.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.dpvo_ba_strerror.argtypes = [i32]
+    lib.dpvo_ba_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "dpvo_ba_strerror":
+            getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+class BAError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = load().dpvo_ba_strerror(code).decode()
+        super().__init__(f"{what}: {msg} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise BAError(code, what)
+
+
+# ---- problems -----------------------------------------------------------------
+
+
+@dataclass
+class BAProblem:
+    """Device tensors of one problem (layouts as in include/dpvo_ba.h)."""
+    poses: torch.Tensor      # [N, 7] float32, updated in place
+    patches: torch.Tensor    # [P, 3] float32, column 2 updated in place
+    anchor: torch.Tensor     # [P] int32
+    kk: torch.Tensor         # [E] int32
+    jj: torch.Tensor         # [E] int32
+    target: torch.Tensor     # [E, 2] float32
+    weight: torch.Tensor     # [E, 2] float32
+    intrinsics: Sequence[float]
+    t0: int
+    n_iters: int = 2
+    status: Optional[torch.Tensor] = None   # [1] int32
+
+    def dims(self) -> Dims:
+        fx, fy, cx, cy = (float(v) for v in self.intrinsics)
+        return Dims(self.poses.shape[0], self.patches.shape[0], self.kk.shape[0], int(self.t0),
+                    int(self.n_iters), fx, fy, cx, cy)
+
+    def cstruct(self) -> Problem:
+        for name in ("poses", "patches", "anchor", "kk", "jj", "target", "weight"):
+            t = getattr(self, name)
+            if not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+        if self.status is None:
+            self.status = torch.zeros(1, dtype=torch.int32, device=self.poses.device)
+        return Problem(self.poses.data_ptr(), self.patches.data_ptr(), self.anchor.data_ptr(),
+                       self.kk.data_ptr(), self.jj.data_ptr(), self.target.data_ptr(),
+                       self.weight.data_ptr(), self.status.data_ptr())
+
+
+def problem_from_scene(scene, device="cuda", n_iters=None) -> BAProblem:
+    """Copy a ``scenes.Scene`` (float32 / int32 arrays) to the device."""
+    f = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=device)
+    return BAProblem(
+        poses=f(scene.poses, torch.float32), patches=f(scene.patches, torch.float32),
+        anchor=f(scene.anchor, torch.int32), kk=f(scene.kk, torch.int32), jj=f(scene.jj, torch.int32),
+        target=f(scene.target, torch.float32), weight=f(scene.weight, torch.float32),
+        intrinsics=[float(v) for v in scene.intrinsics], t0=scene.t0,
+        n_iters=scene.n_iters if n_iters is None else n_iters)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Solver:
+    """A library handle (workspace + staging) on the current CUDA device."""
+
+    def __init__(self, damping: float = 1e-4, z_min: float = 0.1, mem_budget_bytes: int = 0,
+                 max_sessions: int = 0):
+        self.lib = load()
+        cfg = Config(damping, z_min, mem_budget_bytes, max_sessions, 0)
+        h = ctypes.c_void_p()
+        _check(self.lib.dpvo_ba_create(ctypes.byref(cfg), ctypes.byref(h)), "dpvo_ba_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dpvo_ba_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, max_frames: int, max_patches: int, max_edges: int, max_iters: int, n_problems: int):
+        d = Dims(max_frames, max_patches, max_edges, 0, max_iters, 1.0, 1.0, 0.0, 0.0)
+        _check(self.lib.dpvo_ba_reserve(self.h, ctypes.byref(d), n_problems), "dpvo_ba_reserve")
+
+    @staticmethod
+    def _arrays(problems: List[BAProblem]):
+        n = len(problems)
+        dims = (Dims * n)(*[p.dims() for p in problems])
+        probs = (Problem * n)(*[p.cstruct() for p in problems])
+        return n, dims, probs
+
+    def solve(self, problems: List[BAProblem], stream=None):
+        """Batched solve on device tensors (asynchronous on ``stream``)."""
+        n, dims, probs = self._arrays(problems)
+        _check(self.lib.dpvo_ba_solve(self.h, dims, probs, n, _stream_ptr(stream)), "dpvo_ba_solve")
+
+    def solve_arrays(self, dims, probs, n, stream=None):
+        """Solve with prebuilt ctypes arrays (no per-call marshalling)."""
+        _check(self.lib.dpvo_ba_solve(self.h, dims, probs, n, _stream_ptr(stream)), "dpvo_ba_solve")
+
+    def solve_host(self, scenes_np: List[dict], stream=None):
+        """Solve problems held in host numpy arrays (copied in and out by the library)."""
+        n = len(scenes_np)
+        dims = (Dims * n)()
+        probs = (Problem * n)()
+        keep = []
+        for b, s in enumerate(scenes_np):
+            fx, fy, cx, cy = (float(v) for v in s["intrinsics"])
+            dims[b] = Dims(s["poses"].shape[0], s["patches"].shape[0], s["kk"].shape[0], int(s["t0"]),
+                           int(s["n_iters"]), fx, fy, cx, cy)
+            arrs = [s[k] for k in ("poses", "patches", "anchor", "kk", "jj", "target", "weight", "status")]
+            for a in arrs:
+                assert a.flags["C_CONTIGUOUS"]
+            keep.append(arrs)
+            probs[b] = Problem(*[a.ctypes.data for a in arrs])
+        _check(self.lib.dpvo_ba_solve_host(self.h, dims, probs, n, _stream_ptr(stream)), "dpvo_ba_solve_host")
+
+    def reduced_system(self, problem: BAProblem, stream=None):
+        """(S, v') of one linearisation at the problem's current state, FP64 on the device."""
+        n6 = 6 * (problem.poses.shape[0] - problem.t0)
+        S = torch.empty((n6, n6), dtype=torch.float64, device=problem.poses.device)
+        v = torch.empty((n6,), dtype=torch.float64, device=problem.poses.device)
+        d = problem.dims()
+        p = problem.cstruct()
+        _check(self.lib.dpvo_ba_reduced_system(self.h, ctypes.byref(d), ctypes.byref(p), S.data_ptr(),
+                                               v.data_ptr(), _stream_ptr(stream)), "dpvo_ba_reduced_system")
+        return S, v
+
+    def iterate(self, index: int, it: int, n_frames: int, n_patches: int, t0: int):
+        """(poses [N,7] f32, depths [P] f32, dxi [N-t0,6] f64 or None) of problem ``index``
+        after iteration ``it`` of the last solve (host numpy arrays)."""
+        poses = np.empty((n_frames, 7), np.float32)
+        depth = np.empty((n_patches,), np.float32)
+        dxi = np.empty((n_frames - t0, 6), np.float64)
+        _check(self.lib.dpvo_ba_iterate(self.h, index, it, poses.ctypes.data, depth.ctypes.data,
+                                        dxi.ctypes.data), "dpvo_ba_iterate")
+        return poses, depth, dxi

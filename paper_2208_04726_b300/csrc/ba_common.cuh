@@ -1,0 +1,90 @@
+// Internal definitions shared by the bundle-adjustment kernels and the host API.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dpvo_ba.h"
+
+namespace dpvo {
+
+constexpr int kThreads = 256;          // block size of the linearise and solve kernels
+constexpr int kMaxWindow = 64;         // frames the edges of one patch chunk may span
+constexpr int kMaxFree = DPVO_BA_MAX_FREE;
+constexpr int kFlushEvery = 8;         // patches summed in FP32 before a compensated add
+constexpr int kMaxKSplit = 8;          // patch-parity split of the Schur accumulation
+
+// A run of consecutive patches that share one source frame (anchor).
+struct Chunk {
+    int k0, count;     // patches [k0, k0 + count)
+    int e0, e1;        // their edges [e0, e1)
+    int anchor;        // source frame of every patch in the chunk
+    int jlo, jhi;      // frames touched by the chunk's edges lie in [jlo, jhi]
+    int pad;
+};
+
+// Everything a kernel needs about one problem: caller arrays, sizes, workspace.
+struct Prob {
+    float *poses;            // [N][7] caller, IN/OUT
+    float *patches;          // [P][3] caller, d IN/OUT
+    const int32_t *anchor;   // [P]
+    const int32_t *kk;       // [E]
+    const int32_t *jj;       // [E]
+    const float *target;     // [E][2]
+    const float *weight;     // [E][2]
+    int32_t *status_user;    // [1] or null
+
+    int N, P, E, t0, iters, nf;
+    float fx, fy, cx, cy;
+    float damping, z_min;
+
+    int32_t *seg;            // [P + 1] first edge of each patch
+    Chunk *chunks;           // [max_chunks]
+    int32_t *n_chunks;       // [1]
+    int32_t *status;         // [1] DPVO_BA_STATUS_* bits
+    float *pose_it;          // [iters + 1][N][7] iterates
+    float *depth_it;         // [iters + 1][P]
+    double *dxi;             // [iters][nf][6] pose increments
+    double *partial;         // [n_items][ks][L] Schur partial sums
+    int max_chunks;
+    int n_items;             // linearise work items (CTAs) of this problem
+    int ks;                  // patch-parity split of the Schur accumulation
+    int L;                   // doubles per partial
+    int chunk_cap;           // patches per chunk at most
+    int win_cap;             // frames per chunk window at most
+};
+
+// One CTA of the linearise kernel: problem index and work-item index within it.
+struct Item {
+    int prob, item;
+};
+
+// Reduced-system layout.  The upper triangle of 6x6 pose blocks (a, b), a <= b,
+// is split into half-blocks ("strips") of 3 rows x 6 columns; the right-hand
+// side is one 6-entry strip per free pose.
+__host__ __device__ inline int n_block_pairs(int nf) { return nf * (nf + 1) / 2; }
+__host__ __device__ inline int n_strips(int nf) { return 2 * n_block_pairs(nf) + nf; }
+__host__ __device__ inline int partial_len(int nf) { return 18 * 2 * n_block_pairs(nf) + 6 * nf; }
+__host__ __device__ inline int k_split(int nf) {
+    int s = n_strips(nf);
+    if (s == 0) return 1;
+    int k = kThreads / s;
+    return k < 1 ? 1 : (k > kMaxKSplit ? kMaxKSplit : k);
+}
+
+// Decode the upper-triangle pair index of (a, b), a <= b.
+__host__ __device__ inline void decode_pair(int idx, int nf, int &a, int &b) {
+    a = 0;
+    while (idx >= nf - a) {
+        idx -= nf - a;
+        ++a;
+    }
+    b = a + idx;
+}
+
+// Index into the 21 packed entries of a symmetric 6x6 matrix.
+__host__ __device__ constexpr int sym6(int r, int c) {
+    return r <= c ? r * 6 - r * (r - 1) / 2 + (c - r) : c * 6 - c * (c - 1) / 2 + (r - c);
+}
+
+}  // namespace dpvo

@@ -1,0 +1,376 @@
+// Host side of the C ABI declared in include/dpvo_ba.h: argument checks,
+// workspace layout, descriptor upload and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "dpvo_ba.h"
+#include "ba_common.cuh"
+#include "kernels.cuh"
+
+using namespace dpvo;
+
+namespace {
+
+constexpr size_t kLinSmemBudget = 110 * 1024;   // leaves room for two CTAs per SM
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    std::vector<Prob> probs;       // workspace pointers hold offsets until rebased
+    std::vector<Item> items;
+    size_t bytes = 0, off_probs = 0, off_items = 0;
+    int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0;
+    size_t lin_smem = 0, solve_smem = 0;
+};
+
+int check_dims(const dpvo_ba_dims &d) {
+    if (d.n_frames < 1 || d.n_frames > DPVO_BA_MAX_FRAMES) return DPVO_BA_EINVAL;
+    if (d.n_patches < 0 || d.n_edges < 0) return DPVO_BA_EINVAL;
+    if (d.t0 < 0 || d.t0 > d.n_frames) return DPVO_BA_EINVAL;
+    if (d.n_frames - d.t0 > DPVO_BA_MAX_FREE) return DPVO_BA_EINVAL;
+    if (d.n_iters < 1 || d.n_iters > DPVO_BA_MAX_ITERS) return DPVO_BA_EINVAL;
+    if (!(d.fx > 0.f) || !(d.fy > 0.f)) return DPVO_BA_EINVAL;
+    return DPVO_BA_OK;
+}
+
+int check_problem(const dpvo_ba_dims &d, const dpvo_ba_problem &p) {
+    if (!p.poses) return DPVO_BA_EINVAL;
+    if (d.n_patches > 0 && (!p.patches || !p.anchor)) return DPVO_BA_EINVAL;
+    if (d.n_edges > 0 && (!p.kk || !p.jj || !p.target || !p.weight)) return DPVO_BA_EINVAL;
+    if (((uintptr_t)p.target & 7) || ((uintptr_t)p.weight & 7)) return DPVO_BA_EINVAL;
+    return DPVO_BA_OK;
+}
+
+Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_config &cfg) {
+    Layout L;
+    int n_max = 1;
+    for (int b = 0; b < n; ++b) {
+        n_max = std::max(n_max, dims[b].n_frames);
+        L.nf_max = std::max(L.nf_max, dims[b].n_frames - dims[b].t0);
+        L.iters_max = std::max(L.iters_max, dims[b].n_iters);
+    }
+    L.W_cap = std::min(n_max, kMaxWindow);
+    L.G_cap = 64;
+    while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max).bytes > kLinSmemBudget) L.G_cap -= 8;
+    L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max).bytes;
+    const int n6 = 6 * L.nf_max;
+    L.solve_smem = (size_t)n6 * (n6 + 1) * 8 + (size_t)n6 * 8 + 16;
+
+    const int target_ctas = 2 * num_sms;
+    size_t off = 0;
+    L.probs.resize(n);
+    for (int b = 0; b < n; ++b) {
+        const dpvo_ba_dims &d = dims[b];
+        Prob &p = L.probs[b];
+        std::memset(&p, 0, sizeof(Prob));
+        p.N = d.n_frames; p.P = d.n_patches; p.E = d.n_edges; p.t0 = d.t0; p.iters = d.n_iters;
+        p.nf = d.n_frames - d.t0;
+        p.fx = d.fx; p.fy = d.fy; p.cx = d.cx; p.cy = d.cy;
+        p.damping = cfg.damping; p.z_min = cfg.z_min;
+        p.chunk_cap = L.G_cap;
+        p.win_cap = L.W_cap;
+        p.max_chunks = (d.n_patches + L.G_cap - 1) / L.G_cap + d.n_frames;
+        p.ks = k_split(p.nf);
+        p.L = partial_len(p.nf);
+        int est_chunks = std::max(1, (d.n_patches + L.G_cap - 1) / L.G_cap);
+        int items = n >= target_ctas ? 1 : (target_ctas + n - 1) / n;
+        p.n_items = std::max(1, std::min(items, est_chunks));
+        // workspace offsets (rebased to device pointers later)
+        auto take = [&](size_t bytes) { size_t o = off; off = al256(off + bytes); return o; };
+        p.seg = (int32_t *)(uintptr_t)take((size_t)(d.n_patches + 1) * 4);
+        p.chunks = (Chunk *)(uintptr_t)take((size_t)p.max_chunks * sizeof(Chunk));
+        size_t ints = take(16);
+        p.n_chunks = (int32_t *)(uintptr_t)ints;
+        p.status = (int32_t *)(uintptr_t)(ints + 4);
+        p.pose_it = (float *)(uintptr_t)take((size_t)(d.n_iters + 1) * d.n_frames * 7 * 4);
+        p.depth_it = (float *)(uintptr_t)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
+        p.dxi = (double *)(uintptr_t)take((size_t)d.n_iters * p.nf * 6 * 8 + 8);
+        p.partial = (double *)(uintptr_t)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
+        for (int w = 0; w < p.n_items; ++w) L.items.push_back(Item{b, w});
+    }
+    L.off_probs = off;
+    off = al256(off + sizeof(Prob) * n);
+    L.off_items = off;
+    off = al256(off + sizeof(Item) * L.items.size());
+    L.bytes = off;
+    return L;
+}
+
+template <typename T>
+T *rebase(T *off, char *base) { return reinterpret_cast<T *>(base + (uintptr_t)off); }
+
+}  // namespace
+
+struct dpvo_ba_handle {
+    dpvo_ba_config cfg;
+    int device = 0;
+    int num_sms = 148;
+    char *ws = nullptr;
+    size_t ws_cap = 0;
+    char *stage = nullptr;          // pinned host staging for descriptors
+    size_t stage_cap = 0;
+    cudaEvent_t stage_done = nullptr;
+    bool stage_pending = false;
+    char *io = nullptr;             // device staging for dpvo_ba_solve_host
+    size_t io_cap = 0;
+    std::vector<Prob> last;         // descriptors of the last solve (for dpvo_ba_iterate)
+};
+
+static int grow_device(char **buf, size_t *cap, size_t need) {
+    if (need <= *cap) return DPVO_BA_OK;
+    if (*buf) {
+        if (cudaDeviceSynchronize() != cudaSuccess) return DPVO_BA_ECUDA;
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    size_t sz = need + need / 4;
+    if (cudaMalloc((void **)buf, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return DPVO_BA_ENOMEM;
+    }
+    *cap = sz;
+    return DPVO_BA_OK;
+}
+
+static int grow_stage(dpvo_ba_handle *h, size_t need) {
+    if (h->stage_pending) {
+        if (cudaEventSynchronize(h->stage_done) != cudaSuccess) return DPVO_BA_ECUDA;
+        h->stage_pending = false;
+    }
+    if (need <= h->stage_cap) return DPVO_BA_OK;
+    if (h->stage) cudaFreeHost(h->stage);
+    h->stage = nullptr;
+    h->stage_cap = 0;
+    if (cudaMallocHost((void **)&h->stage, need * 2) != cudaSuccess) {
+        cudaGetLastError();
+        return DPVO_BA_ENOMEM;
+    }
+    h->stage_cap = need * 2;
+    return DPVO_BA_OK;
+}
+
+static bool g_attr_set[64] = {false};
+
+static int set_kernel_attrs(int device) {
+    if (device >= 0 && device < 64 && g_attr_set[device]) return DPVO_BA_OK;
+    if (cudaFuncSetAttribute(linearize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (device >= 0 && device < 64) g_attr_set[device] = true;
+    return DPVO_BA_OK;
+}
+
+// Upload descriptors and run plan + iterations.  dims/probs host arrays.
+static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs, int n,
+                     cudaStream_t stream, double *S_out, double *v_out) {
+    Layout L = make_layout(dims, n, h->num_sms, h->cfg);
+    int rc = grow_device(&h->ws, &h->ws_cap, L.bytes);
+    if (rc) return rc;
+    const size_t desc_bytes = L.bytes - L.off_probs;
+    rc = grow_stage(h, desc_bytes);
+    if (rc) return rc;
+    for (int b = 0; b < n; ++b) {
+        Prob &p = L.probs[b];
+        const dpvo_ba_problem &q = probs[b];
+        p.poses = q.poses; p.patches = q.patches; p.anchor = q.anchor; p.kk = q.kk; p.jj = q.jj;
+        p.target = q.target; p.weight = q.weight; p.status_user = q.status;
+        p.seg = rebase(p.seg, h->ws);
+        p.chunks = rebase(p.chunks, h->ws);
+        p.n_chunks = rebase(p.n_chunks, h->ws);
+        p.status = rebase(p.status, h->ws);
+        p.pose_it = rebase(p.pose_it, h->ws);
+        p.depth_it = rebase(p.depth_it, h->ws);
+        p.dxi = rebase(p.dxi, h->ws);
+        p.partial = rebase(p.partial, h->ws);
+    }
+    h->last = L.probs;
+    std::memcpy(h->stage, L.probs.data(), sizeof(Prob) * n);
+    std::memcpy(h->stage + (L.off_items - L.off_probs), L.items.data(), sizeof(Item) * L.items.size());
+    if (cudaMemcpyAsync(h->ws + L.off_probs, h->stage, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaEventRecord(h->stage_done, stream) != cudaSuccess) return DPVO_BA_ECUDA;
+    h->stage_pending = true;
+
+    const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
+    const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
+    const int n_items = (int)L.items.size();
+    plan_kernel<<<n, kThreads, 0, stream>>>(d_probs);
+    if (S_out) {
+        linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, 0, L.W_cap, L.G_cap,
+                                                                     L.nf_max);
+        solve_kernel<<<n, kThreads, L.solve_smem, stream>>>(d_probs, 0, S_out, v_out);
+    } else {
+        for (int t = 0; t <= L.iters_max; ++t) {
+            linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap,
+                                                                         L.nf_max);
+            if (t < L.iters_max) solve_kernel<<<n, kThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
+    return DPVO_BA_OK;
+}
+
+extern "C" {
+
+int dpvo_ba_create(const dpvo_ba_config *cfg, dpvo_ba_handle **out) {
+    if (!out) return DPVO_BA_EINVAL;
+    *out = nullptr;
+    dpvo_ba_handle *h = new dpvo_ba_handle();
+    h->cfg.damping = 1e-4f;
+    h->cfg.z_min = 0.1f;
+    h->cfg.mem_budget_bytes = (size_t)8 << 30;
+    h->cfg.max_sessions = 256;
+    h->cfg.reserved = 0;
+    if (cfg) {
+        h->cfg = *cfg;
+        if (h->cfg.mem_budget_bytes == 0) h->cfg.mem_budget_bytes = (size_t)8 << 30;
+        if (h->cfg.max_sessions <= 0) h->cfg.max_sessions = 256;
+    }
+    if (!(h->cfg.damping >= 0.f) || !(h->cfg.z_min == h->cfg.z_min)) { delete h; return DPVO_BA_EINVAL; }
+    if (cudaGetDevice(&h->device) != cudaSuccess) { cudaGetLastError(); delete h; return DPVO_BA_ECUDA; }
+    if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        cudaGetLastError(); delete h; return DPVO_BA_ECUDA;
+    }
+    if (cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError(); delete h; return DPVO_BA_ECUDA;
+    }
+    if (set_kernel_attrs(h->device)) { cudaEventDestroy(h->stage_done); delete h; return DPVO_BA_ECUDA; }
+    *out = h;
+    return DPVO_BA_OK;
+}
+
+int dpvo_ba_destroy(dpvo_ba_handle *h) {
+    if (!h) return DPVO_BA_EINVAL;
+    cudaDeviceSynchronize();
+    if (h->ws) cudaFree(h->ws);
+    if (h->io) cudaFree(h->io);
+    if (h->stage) cudaFreeHost(h->stage);
+    if (h->stage_done) cudaEventDestroy(h->stage_done);
+    delete h;
+    return DPVO_BA_OK;
+}
+
+int dpvo_ba_reserve(dpvo_ba_handle *h, const dpvo_ba_dims *max_dims, int n_problems) {
+    if (!h || !max_dims || n_problems < 1) return DPVO_BA_EINVAL;
+    dpvo_ba_dims d = *max_dims;
+    d.t0 = std::max(0, d.n_frames - DPVO_BA_MAX_FREE);
+    if (int rc = check_dims(d)) return rc;
+    std::vector<dpvo_ba_dims> all(n_problems, d);
+    Layout L = make_layout(all.data(), n_problems, h->num_sms, h->cfg);
+    if (int rc = grow_device(&h->ws, &h->ws_cap, L.bytes)) return rc;
+    return grow_stage(h, L.bytes - L.off_probs);
+}
+
+int dpvo_ba_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs, int n_problems,
+                  void *stream) {
+    if (!h || !dims || !probs || n_problems < 1) return DPVO_BA_EINVAL;
+    for (int b = 0; b < n_problems; ++b) {
+        if (int rc = check_dims(dims[b])) return rc;
+        if (int rc = check_problem(dims[b], probs[b])) return rc;
+    }
+    return run_solve(h, dims, probs, n_problems, (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int dpvo_ba_reduced_system(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *prob,
+                           double *S_out, double *v_out, void *stream) {
+    if (!h || !dims || !prob || !S_out || !v_out) return DPVO_BA_EINVAL;
+    if (int rc = check_dims(*dims)) return rc;
+    if (int rc = check_problem(*dims, *prob)) return rc;
+    if (dims->n_frames == dims->t0) return DPVO_BA_EINVAL;
+    dpvo_ba_dims d = *dims;
+    d.n_iters = 1;
+    return run_solve(h, &d, prob, 1, (cudaStream_t)stream, S_out, v_out);
+}
+
+int dpvo_ba_solve_host(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *hp, int n_problems,
+                       void *stream_) {
+    if (!h || !dims || !hp || n_problems < 1) return DPVO_BA_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    std::vector<size_t> off(n_problems);
+    size_t total = 0;
+    for (int b = 0; b < n_problems; ++b) {
+        if (int rc = check_dims(dims[b])) return rc;
+        if (int rc = check_problem(dims[b], hp[b])) return rc;
+        const size_t N = dims[b].n_frames, P = dims[b].n_patches, E = dims[b].n_edges;
+        off[b] = total;
+        total += al256(N * 7 * 4) + al256(P * 3 * 4) + al256(P * 4) + 2 * al256(E * 4) + 2 * al256(E * 8) + 256;
+    }
+    if (int rc = grow_device(&h->io, &h->io_cap, total)) return rc;
+    std::vector<dpvo_ba_problem> dp(n_problems);
+    for (int b = 0; b < n_problems; ++b) {
+        const size_t N = dims[b].n_frames, P = dims[b].n_patches, E = dims[b].n_edges;
+        char *base = h->io + off[b];
+        size_t o = 0;
+        auto take = [&](size_t bytes) { char *p = base + o; o += al256(bytes); return p; };
+        dpvo_ba_problem &q = dp[b];
+        q.poses = (float *)take(N * 7 * 4);
+        q.patches = (float *)take(P * 3 * 4);
+        q.anchor = (const int32_t *)take(P * 4);
+        q.kk = (const int32_t *)take(E * 4);
+        q.jj = (const int32_t *)take(E * 4);
+        q.target = (const float *)take(E * 8);
+        q.weight = (const float *)take(E * 8);
+        q.status = (int32_t *)take(4);
+        cudaMemcpyAsync(q.poses, hp[b].poses, N * 7 * 4, cudaMemcpyHostToDevice, stream);
+        if (P) {
+            cudaMemcpyAsync(q.patches, hp[b].patches, P * 3 * 4, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync((void *)q.anchor, hp[b].anchor, P * 4, cudaMemcpyHostToDevice, stream);
+        }
+        if (E) {
+            cudaMemcpyAsync((void *)q.kk, hp[b].kk, E * 4, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync((void *)q.jj, hp[b].jj, E * 4, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync((void *)q.target, hp[b].target, E * 8, cudaMemcpyHostToDevice, stream);
+            cudaMemcpyAsync((void *)q.weight, hp[b].weight, E * 8, cudaMemcpyHostToDevice, stream);
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
+    if (int rc = run_solve(h, dims, dp.data(), n_problems, stream, nullptr, nullptr)) return rc;
+    for (int b = 0; b < n_problems; ++b) {
+        const size_t N = dims[b].n_frames, P = dims[b].n_patches;
+        cudaMemcpyAsync(hp[b].poses, dp[b].poses, N * 7 * 4, cudaMemcpyDeviceToHost, stream);
+        if (P) cudaMemcpyAsync(hp[b].patches, dp[b].patches, P * 3 * 4, cudaMemcpyDeviceToHost, stream);
+        if (hp[b].status) cudaMemcpyAsync(hp[b].status, dp[b].status, 4, cudaMemcpyDeviceToHost, stream);
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return DPVO_BA_ECUDA;
+    return DPVO_BA_OK;
+}
+
+int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, float *depth_out,
+                    double *dxi_out) {
+    if (!h || index < 0 || index >= (int)h->last.size()) return DPVO_BA_EINVAL;
+    const Prob &p = h->last[index];
+    if (iter < 0 || iter > p.iters) return DPVO_BA_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess) return DPVO_BA_ECUDA;
+    if (poses_out &&
+        cudaMemcpy(poses_out, p.pose_it + (size_t)iter * p.N * 7, (size_t)p.N * 7 * 4, cudaMemcpyDeviceToHost))
+        return DPVO_BA_ECUDA;
+    if (depth_out && p.P &&
+        cudaMemcpy(depth_out, p.depth_it + (size_t)iter * p.P, (size_t)p.P * 4, cudaMemcpyDeviceToHost))
+        return DPVO_BA_ECUDA;
+    if (dxi_out && iter < p.iters && p.nf &&
+        cudaMemcpy(dxi_out, p.dxi + (size_t)iter * p.nf * 6, (size_t)p.nf * 6 * 8, cudaMemcpyDeviceToHost))
+        return DPVO_BA_ECUDA;
+    return DPVO_BA_OK;
+}
+
+const char *dpvo_ba_strerror(int code) {
+    switch (code) {
+        case DPVO_BA_OK: return "ok";
+        case DPVO_BA_EINVAL: return "invalid argument";
+        case DPVO_BA_ENOMEM: return "out of device memory or over the memory budget";
+        case DPVO_BA_ECUDA: return "CUDA runtime error";
+        case DPVO_BA_ETIMEOUT: return "timed out";
+        case DPVO_BA_EBUSY: return "no serving slot free";
+        case DPVO_BA_ENOTFOUND: return "unknown session or ticket";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

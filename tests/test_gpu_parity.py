@@ -1,0 +1,207 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on seeded synthetic scenes.
+
+Sec. 3.1 Eq. 6: two Gauss-Newton iterations with the Schur complement; the
+oracle solves the dense normal equations instead.  Every test compares element
+by element (relative 2-norm per problem) on identical float32 inputs.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2208_04726_b300 import ba
+from paper_2208_04726_b300 import scenes as S
+from oracle import dense_gn as dg
+from oracle import schur
+from tests.gpu_util import (TOL_DEPTH, TOL_POSE, align_quats, end_to_end_errors, iteration_abs_errors,
+                            iteration_errors, rel, scene_at, solve_gpu)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    s = ba.Solver()
+    yield s
+    s.close()
+
+
+def test_reduced_system_matches_oracle_schur(solver):
+    for spec, seed in [(S.PLAIN_N8, 0), (S.WINDOW_N22, 1)]:
+        sc = S.make_scene(spec, seed)
+        prob = ba.problem_from_scene(sc)
+        Sg, vg = solver.reduced_system(prob)
+        torch.cuda.synchronize()
+        pr = dg.Problem.from_scene(sc)
+        Sr, vr = schur.reduced_system(pr, pr.T, pr.d)
+        assert rel(Sg.cpu().numpy(), Sr) < 2e-6
+        assert rel(vg.cpu().numpy(), vr) < 2e-6
+
+
+@pytest.mark.parametrize("spec,seed", [(S.PLAIN_N8, 3), (S.PLAIN_N8, 4), (S.WINDOW_N22, 5)])
+def test_each_iteration_matches_oracle_step(solver, spec, seed):
+    sc = S.make_scene(spec, seed)
+    probs = solve_gpu(solver, [sc])
+    assert int(probs[0].status.item()) == 0
+    for t, (e_xi, e_dd) in enumerate(iteration_errors(solver, sc, 0, sc.n_iters)):
+        assert e_xi < TOL_POSE, (t, e_xi)
+        assert e_dd < TOL_DEPTH, (t, e_dd)
+
+
+@pytest.mark.parametrize("spec,seed", [(S.PLAIN_N8, 6), (S.WINDOW_N22, 7)])
+def test_whole_solve_matches_oracle(solver, spec, seed):
+    sc = S.make_scene(spec, seed)
+    probs = solve_gpu(solver, [sc])
+    e_pose, e_depth, ref = end_to_end_errors(sc, probs[0])
+    assert e_pose < TOL_POSE and e_depth < TOL_DEPTH, (e_pose, e_depth)
+    # free-running second increment (the iterates differ by FP32 rounding)
+    _, _, dxi2 = solver.iterate(0, 1, sc.n_frames, sc.n_patches, sc.t0)
+    assert rel(dxi2, ref["dxi"][1]) < 1e-3
+
+
+def test_batched_mix_matches_solving_alone(solver):
+    """Problems of different shapes in one batch give the same results as
+    each problem solved by itself (the reduction order differs, so within
+    tolerance rather than bitwise)."""
+    specs = [S.PLAIN_N8, S.WINDOW_N22, dataclasses.replace(S.WINDOW_N22, patches_per_frame=48, radius=8),
+             dataclasses.replace(S.PLAIN_N8, n_frames=12, t0=4, radius=5)]
+    scenes = [S.make_scene(sp, 20 + i) for i, sp in enumerate(specs)]
+    alone = [solve_gpu(solver, [sc])[0] for sc in scenes]
+    mixed = solve_gpu(solver, scenes)
+    for a, m, sc in zip(alone, mixed, scenes):
+        assert int(m.status.item()) == 0
+        pa, pm = a.poses.cpu().numpy(), m.poses.cpu().numpy()
+        assert rel(pm[sc.t0:] - sc.poses[sc.t0:], pa[sc.t0:] - sc.poses[sc.t0:]) < 1e-5
+        da, dm = a.patches[:, 2].cpu().numpy(), m.patches[:, 2].cpu().numpy()
+        assert rel(dm - sc.patches[:, 2], da - sc.patches[:, 2]) < 1e-5
+    for i in range(len(scenes)):
+        for t, (e_xi, e_dd) in enumerate(iteration_errors(solver, scenes[i], i, scenes[i].n_iters)):
+            assert e_xi < TOL_POSE and e_dd < TOL_DEPTH, (i, t, e_xi, e_dd)
+
+
+def test_repeated_solves_are_bitwise_identical(solver):
+    sc = S.make_scene(S.WINDOW_N22, 30)
+    a = solve_gpu(solver, [sc])[0]
+    b = solve_gpu(solver, [sc])[0]
+    assert torch.equal(a.poses, b.poses) and torch.equal(a.patches, b.patches)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def _drop_edges(sc, frac, seed):
+    rng = np.random.default_rng(seed)
+    keep = rng.uniform(size=sc.n_edges) >= frac
+    return dataclasses.replace(sc, kk=sc.kk[keep], jj=sc.jj[keep], target=sc.target[keep],
+                               weight=sc.weight[keep], outlier=sc.outlier[keep], uv_true=sc.uv_true[keep])
+
+
+def test_ragged_graph_with_missing_edges_and_isolated_patches(solver):
+    sc = S.make_scene(dataclasses.replace(S.WINDOW_N22, patches_per_frame=37), 40)
+    sc = _drop_edges(sc, 0.3, 1)
+    # patch 5 loses every edge: its inverse depth must not move
+    keep = sc.kk != 5
+    sc = dataclasses.replace(sc, kk=sc.kk[keep], jj=sc.jj[keep], target=sc.target[keep], weight=sc.weight[keep],
+                             outlier=sc.outlier[keep], uv_true=sc.uv_true[keep])
+    probs = solve_gpu(solver, [sc])
+    assert int(probs[0].status.item()) == 0
+    for e_xi, e_dd in iteration_errors(solver, sc, 0, sc.n_iters):
+        assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
+    assert probs[0].patches[5, 2].item() == sc.patches[5, 2]
+
+
+def test_no_self_edges_and_uneven_frames(solver):
+    sc = S.make_scene(dataclasses.replace(S.PLAIN_N8, patches_per_frame=70, n_frames=9, t0=3), 41)
+    keep = sc.anchor[sc.kk] != sc.jj
+    sc = dataclasses.replace(sc, kk=sc.kk[keep], jj=sc.jj[keep], target=sc.target[keep], weight=sc.weight[keep],
+                             outlier=sc.outlier[keep], uv_true=sc.uv_true[keep])
+    solve_gpu(solver, [sc])
+    for e_xi, e_dd in iteration_errors(solver, sc, 0, 2):
+        assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
+
+
+def test_all_poses_fixed_updates_depths_only(solver):
+    sc = S.make_scene(dataclasses.replace(S.PLAIN_N8, t0=8), 42)
+    probs = solve_gpu(solver, [sc])
+    assert torch.equal(probs[0].poses.cpu(), torch.as_tensor(sc.poses))
+    ref = dg.solve_scene(sc)
+    d = probs[0].patches[:, 2].cpu().numpy()
+    assert rel(d - sc.patches[:, 2], ref["depths"] - sc.patches[:, 2]) < TOL_DEPTH
+
+
+@pytest.mark.parametrize("nf", [1, 15])
+def test_extreme_free_pose_counts(solver, nf):
+    spec = dataclasses.replace(S.PLAIN_N8, n_frames=17, patches_per_frame=24, radius=6, t0=17 - nf)
+    sc = S.make_scene(spec, 43 + nf)
+    probs = solve_gpu(solver, [sc])
+    assert int(probs[0].status.item()) == 0
+    for e_xi, e_dd in iteration_errors(solver, sc, 0, 2):
+        assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
+
+
+def test_more_iterations(solver):
+    """Five iterations: the first two match relatively; once the increments
+    reach the FP32 floor they are compared against the first increment."""
+    sc = S.make_scene(dataclasses.replace(S.PLAIN_N8, n_iters=5), 44)
+    solve_gpu(solver, [sc])
+    for e_xi, e_dd in iteration_errors(solver, sc, 0, 5)[:2]:
+        assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
+    for e_xi, e_dd in iteration_abs_errors(solver, sc, 0, 5):
+        assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
+
+
+def test_empty_graph_is_not_spd_and_leaves_state(solver):
+    sc = S.make_scene(S.PLAIN_N8, 45)
+    sc = dataclasses.replace(sc, kk=sc.kk[:0], jj=sc.jj[:0], target=sc.target[:0], weight=sc.weight[:0])
+    probs = solve_gpu(solver, [sc])
+    assert int(probs[0].status.item()) & ba.STATUS_NOT_SPD
+    assert torch.equal(probs[0].poses.cpu(), torch.as_tensor(sc.poses))
+    assert torch.equal(probs[0].patches.cpu(), torch.as_tensor(sc.patches))
+
+
+@pytest.mark.parametrize("breakage", ["unsorted_kk", "frame_out_of_range", "duplicate_edge", "anchor_order"])
+def test_bad_input_is_flagged_and_leaves_state(solver, breakage):
+    sc = S.make_scene(S.PLAIN_N8, 46)
+    kk, jj, anchor = sc.kk.copy(), sc.jj.copy(), sc.anchor.copy()
+    if breakage == "unsorted_kk":
+        kk[10], kk[500] = kk[500], kk[10]
+    elif breakage == "frame_out_of_range":
+        jj[7] = sc.n_frames
+    elif breakage == "duplicate_edge":
+        jj[9] = jj[8]
+    else:
+        anchor[3], anchor[400] = anchor[400], anchor[3]
+    bad = dataclasses.replace(sc, kk=kk, jj=jj, anchor=anchor)
+    good = S.make_scene(S.PLAIN_N8, 47)
+    probs = solve_gpu(solver, [bad, good])
+    assert int(probs[0].status.item()) == ba.STATUS_BAD_INPUT
+    assert torch.equal(probs[0].poses.cpu(), torch.as_tensor(sc.poses))
+    assert torch.equal(probs[0].patches.cpu(), torch.as_tensor(sc.patches))
+    # the good problem in the same batch is unaffected
+    assert int(probs[1].status.item()) == 0
+    for e_xi, e_dd in iteration_errors(solver, good, 1, 2):
+        assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
+
+
+def test_host_buffer_entry_point_matches_device_entry_point(solver):
+    sc = S.make_scene(S.PLAIN_N8, 48)
+    dev = solve_gpu(solver, [sc])[0]
+    h = dict(poses=sc.poses.copy(), patches=sc.patches.copy(), anchor=sc.anchor.copy(), kk=sc.kk.copy(),
+             jj=sc.jj.copy(), target=sc.target.copy(), weight=sc.weight.copy(),
+             status=np.zeros(1, np.int32), intrinsics=sc.intrinsics, t0=sc.t0, n_iters=sc.n_iters)
+    solver.solve_host([h])
+    assert h["status"][0] == 0
+    assert np.array_equal(h["poses"], dev.poses.cpu().numpy())
+    assert np.array_equal(h["patches"], dev.patches.cpu().numpy())
+
+
+def test_invalid_arguments_return_einval(solver):
+    sc = S.make_scene(S.PLAIN_N8, 49)
+    p = ba.problem_from_scene(sc)
+    with pytest.raises(ba.BAError) as e:
+        solver.solve([dataclasses.replace(p, t0=-1)])
+    assert e.value.code == ba.EINVAL
+    with pytest.raises(ba.BAError):
+        solver.solve([dataclasses.replace(p, t0=0, poses=torch.zeros(17, 7, device="cuda"))])   # 17 free > 15
