@@ -150,6 +150,17 @@ int dpvo_ba_reduced_system(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dp
 int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, float *depth_out,
                     double *dxi_out);
 
+/* Diagnostic timing.  While enabled (enable != 0), every solve records a CUDA
+ * event on its own stream before and after each kernel launch.
+ * dpvo_ba_timing() waits for the recorded events and writes, for each launch
+ * since the previous read (all solves, in order), the elapsed milliseconds
+ * (ms_out[i]) and the kernel (kind_out[i]: 0 plan, 1 linearise/Schur,
+ * 2 reduce/Cholesky/retract); it returns the number of launches written
+ * (<= cap) or a negative code, and starts a new record.  The record grows
+ * while enabled: read it regularly. */
+int dpvo_ba_set_timing(dpvo_ba_handle *h, int enable);
+int dpvo_ba_timing(dpvo_ba_handle *h, float *ms_out, int *kind_out, int cap);
+
 /* Human-readable name of a return code. */
 const char *dpvo_ba_strerror(int code);
 

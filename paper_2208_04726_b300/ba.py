@@ -42,7 +42,8 @@ MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 15, 16
 
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solve", "dpvo_ba_solve_host",
-           "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_strerror"]
+           "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_set_timing", "dpvo_ba_timing",
+           "dpvo_ba_strerror"]
 
 _lib = None
 
@@ -69,6 +70,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_solve_host.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), i32, vp]
     lib.dpvo_ba_reduced_system.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), vp, vp, vp]
     lib.dpvo_ba_iterate.argtypes = [vp, i32, i32, vp, vp, vp]
+    lib.dpvo_ba_set_timing.argtypes = [vp, i32]
+    lib.dpvo_ba_timing.argtypes = [vp, vp, vp, i32]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -221,3 +224,79 @@ class Solver:
         _check(self.lib.dpvo_ba_iterate(self.h, index, it, poses.ctypes.data, depth.ctypes.data,
                                         dxi.ctypes.data), "dpvo_ba_iterate")
         return poses, depth, dxi
+
+    def set_timing(self, enable: bool):
+        _check(self.lib.dpvo_ba_set_timing(self.h, int(bool(enable))), "dpvo_ba_set_timing")
+
+    def timing(self, cap: int = 4096):
+        """[(kind, ms)] of every launch since the last read (kind 0 plan,
+        1 linearise/Schur, 2 reduce/Cholesky/retract)."""
+        ms = np.zeros(cap, np.float32)
+        kinds = np.zeros(cap, np.int32)
+        n = self.lib.dpvo_ba_timing(self.h, ms.ctypes.data, kinds.ctypes.data, cap)
+        if n < 0:
+            raise BAError(n, "dpvo_ba_timing")
+        return [(int(kinds[i]), float(ms[i])) for i in range(n)]
+
+
+class PackedBatch:
+    """Many problems packed back to back in one tensor per array kind, with the
+    ctypes descriptor arrays built once.  ``where`` is "cuda" (device tensors),
+    "pinned" (page-locked host tensors, for the host-buffer entry point) or
+    "cpu".  ``initial_*`` keep copies of the starting poses and patches."""
+
+    KINDS = [("poses", torch.float32), ("patches", torch.float32), ("anchor", torch.int32), ("kk", torch.int32),
+             ("jj", torch.int32), ("target", torch.float32), ("weight", torch.float32)]
+
+    def __init__(self, scenes, where: str = "cuda", n_iters=None):
+        self.n = len(scenes)
+        self.where = where
+        dev = "cuda" if where == "cuda" else "cpu"
+        pin = where == "pinned"
+        self.flat = {}
+        self.offsets = {}
+        for name, dt in self.KINDS:
+            arrs = [np.ascontiguousarray(getattr(s, name)).reshape(-1) for s in scenes]
+            lens = np.array([a.shape[0] for a in arrs], np.int64)
+            self.offsets[name] = np.concatenate([[0], np.cumsum(lens)])
+            host = torch.from_numpy(np.concatenate(arrs)).to(dt)
+            if pin:
+                t = torch.empty(host.shape, dtype=dt, pin_memory=True)
+                t.copy_(host)
+            else:
+                t = host.to(dev)
+            self.flat[name] = t
+        if pin:
+            self.status = torch.zeros(self.n, dtype=torch.int32, pin_memory=True)
+        else:
+            self.status = torch.zeros(self.n, dtype=torch.int32, device=dev)
+        self.initial_poses = self.flat["poses"].clone()
+        self.initial_patches = self.flat["patches"].clone()
+        self.dims = (Dims * self.n)()
+        self.probs = (Problem * self.n)()
+        for b, s in enumerate(scenes):
+            fx, fy, cx, cy = (float(v) for v in s.intrinsics)
+            it = s.n_iters if n_iters is None else n_iters
+            self.dims[b] = Dims(s.n_frames, s.n_patches, s.n_edges, s.t0, it, fx, fy, cx, cy)
+            ptr = []
+            for name, dt in self.KINDS:
+                t = self.flat[name]
+                ptr.append(t.data_ptr() + int(self.offsets[name][b]) * t.element_size())
+            ptr.append(self.status.data_ptr() + 4 * b)
+            self.probs[b] = Problem(*ptr)
+        self.scenes = scenes
+
+    def view(self, name: str, b: int):
+        o = self.offsets[name]
+        return self.flat[name][o[b]:o[b + 1]]
+
+    def reset(self):
+        self.flat["poses"].copy_(self.initial_poses)
+        self.flat["patches"].copy_(self.initial_patches)
+
+    def subset(self, b: int):
+        """ctypes (dims, probs) arrays holding problem b alone."""
+        return (Dims * 1)(self.dims[b]), (Problem * 1)(self.probs[b])
+
+    def bytes_of(self, names) -> int:
+        return int(sum(self.flat[n].numel() * self.flat[n].element_size() for n in names))

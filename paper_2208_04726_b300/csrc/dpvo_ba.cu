@@ -117,7 +117,21 @@ struct dpvo_ba_handle {
     char *io = nullptr;             // device staging for dpvo_ba_solve_host
     size_t io_cap = 0;
     std::vector<Prob> last;         // descriptors of the last solve (for dpvo_ba_iterate)
+    bool timing = false;            // record events around launches
+    std::vector<cudaEvent_t> ev;    // event pool: (start, end) per timed launch
+    std::vector<int> ev_kind;       // kernel of each timed launch
+    int ev_used = 0;                // events recorded since the last read
 };
+
+static int timed_event(dpvo_ba_handle *h, cudaStream_t s) {
+    if (h->ev_used >= (int)h->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return DPVO_BA_ECUDA;
+        h->ev.push_back(e);
+    }
+    if (cudaEventRecord(h->ev[h->ev_used++], s) != cudaSuccess) return DPVO_BA_ECUDA;
+    return DPVO_BA_OK;
+}
 
 static int grow_device(char **buf, size_t *cap, size_t need) {
     if (need <= *cap) return DPVO_BA_OK;
@@ -201,16 +215,36 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
     const int n_items = (int)L.items.size();
-    plan_kernel<<<n, kThreads, 0, stream>>>(d_probs);
+    // with timing on, bracket each launch with a pair of events on `stream`
+    auto timed = [&](int kind, auto &&launch) -> int {
+        if (h->timing) {
+            if (int r = timed_event(h, stream)) return r;
+        }
+        launch();
+        if (h->timing) {
+            if (int r = timed_event(h, stream)) return r;
+            h->ev_kind.push_back(kind);
+        }
+        return DPVO_BA_OK;
+    };
+    if ((rc = timed(0, [&] { plan_kernel<<<n, kThreads, 0, stream>>>(d_probs); }))) return rc;
     if (S_out) {
         linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, 0, L.W_cap, L.G_cap,
                                                                      L.nf_max);
         solve_kernel<<<n, kThreads, L.solve_smem, stream>>>(d_probs, 0, S_out, v_out);
     } else {
         for (int t = 0; t <= L.iters_max; ++t) {
-            linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap,
-                                                                         L.nf_max);
-            if (t < L.iters_max) solve_kernel<<<n, kThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+            rc = timed(1, [&] {
+                linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap,
+                                                                             L.G_cap, L.nf_max);
+            });
+            if (rc) return rc;
+            if (t < L.iters_max) {
+                rc = timed(2, [&] {
+                    solve_kernel<<<n, kThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+                });
+                if (rc) return rc;
+            }
         }
     }
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
@@ -253,6 +287,7 @@ int dpvo_ba_destroy(dpvo_ba_handle *h) {
     if (h->io) cudaFree(h->io);
     if (h->stage) cudaFreeHost(h->stage);
     if (h->stage_done) cudaEventDestroy(h->stage_done);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     delete h;
     return DPVO_BA_OK;
 }
@@ -289,54 +324,94 @@ int dpvo_ba_reduced_system(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dp
     return run_solve(h, &d, prob, 1, (cudaStream_t)stream, S_out, v_out);
 }
 
+// Copies for dpvo_ba_solve_host.  Device staging keeps each array kind of
+// all problems back to back; runs of problems whose host arrays are also back
+// to back move in one cudaMemcpyAsync.
+namespace {
+struct KindCopy {
+    size_t dev_off;                 // start of this kind's region in h->io
+    std::vector<size_t> pos;        // byte offset of problem b in the region
+    std::vector<size_t> bytes;      // bytes of problem b
+};
+
+int copy_runs(char *dev_base, const KindCopy &k, const std::vector<char *> &host, cudaMemcpyKind dir,
+              cudaStream_t s) {
+    const size_t n = host.size();
+    size_t b = 0;
+    while (b < n) {
+        size_t e = b + 1, len = k.bytes[b];
+        while (e < n && host[e] == host[e - 1] + k.bytes[e - 1]) { len += k.bytes[e]; ++e; }
+        if (len) {
+            char *d = dev_base + k.dev_off + k.pos[b];
+            cudaError_t r = dir == cudaMemcpyHostToDevice ? cudaMemcpyAsync(d, host[b], len, dir, s)
+                                                          : cudaMemcpyAsync(host[b], d, len, dir, s);
+            if (r != cudaSuccess) return DPVO_BA_ECUDA;
+        }
+        b = e;
+    }
+    return DPVO_BA_OK;
+}
+}  // namespace
+
 int dpvo_ba_solve_host(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *hp, int n_problems,
                        void *stream_) {
     if (!h || !dims || !hp || n_problems < 1) return DPVO_BA_EINVAL;
     cudaStream_t stream = (cudaStream_t)stream_;
-    std::vector<size_t> off(n_problems);
-    size_t total = 0;
     for (int b = 0; b < n_problems; ++b) {
         if (int rc = check_dims(dims[b])) return rc;
         if (int rc = check_problem(dims[b], hp[b])) return rc;
-        const size_t N = dims[b].n_frames, P = dims[b].n_patches, E = dims[b].n_edges;
-        off[b] = total;
-        total += al256(N * 7 * 4) + al256(P * 3 * 4) + al256(P * 4) + 2 * al256(E * 4) + 2 * al256(E * 8) + 256;
+    }
+    // kinds: 0 poses, 1 patches, 2 anchor, 3 kk, 4 jj, 5 target, 6 weight, 7 status
+    const int NK = 8;
+    KindCopy k[NK];
+    size_t total = 0;
+    for (int q = 0; q < NK; ++q) {
+        k[q].dev_off = total;
+        size_t pos = 0;
+        for (int b = 0; b < n_problems; ++b) {
+            const size_t N = dims[b].n_frames, P = dims[b].n_patches, E = dims[b].n_edges;
+            const size_t sz[NK] = {N * 28, P * 12, P * 4, E * 4, E * 4, E * 8, E * 8, 4};
+            k[q].pos.push_back(pos);
+            k[q].bytes.push_back(sz[q]);
+            pos += sz[q];
+        }
+        total = al256(total + pos);
     }
     if (int rc = grow_device(&h->io, &h->io_cap, total)) return rc;
     std::vector<dpvo_ba_problem> dp(n_problems);
+    std::vector<char *> host[NK];
     for (int b = 0; b < n_problems; ++b) {
-        const size_t N = dims[b].n_frames, P = dims[b].n_patches, E = dims[b].n_edges;
-        char *base = h->io + off[b];
-        size_t o = 0;
-        auto take = [&](size_t bytes) { char *p = base + o; o += al256(bytes); return p; };
-        dpvo_ba_problem &q = dp[b];
-        q.poses = (float *)take(N * 7 * 4);
-        q.patches = (float *)take(P * 3 * 4);
-        q.anchor = (const int32_t *)take(P * 4);
-        q.kk = (const int32_t *)take(E * 4);
-        q.jj = (const int32_t *)take(E * 4);
-        q.target = (const float *)take(E * 8);
-        q.weight = (const float *)take(E * 8);
-        q.status = (int32_t *)take(4);
-        cudaMemcpyAsync(q.poses, hp[b].poses, N * 7 * 4, cudaMemcpyHostToDevice, stream);
-        if (P) {
-            cudaMemcpyAsync(q.patches, hp[b].patches, P * 3 * 4, cudaMemcpyHostToDevice, stream);
-            cudaMemcpyAsync((void *)q.anchor, hp[b].anchor, P * 4, cudaMemcpyHostToDevice, stream);
-        }
-        if (E) {
-            cudaMemcpyAsync((void *)q.kk, hp[b].kk, E * 4, cudaMemcpyHostToDevice, stream);
-            cudaMemcpyAsync((void *)q.jj, hp[b].jj, E * 4, cudaMemcpyHostToDevice, stream);
-            cudaMemcpyAsync((void *)q.target, hp[b].target, E * 8, cudaMemcpyHostToDevice, stream);
-            cudaMemcpyAsync((void *)q.weight, hp[b].weight, E * 8, cudaMemcpyHostToDevice, stream);
-        }
+        auto dev = [&](int q) { return h->io + k[q].dev_off + k[q].pos[b]; };
+        dp[b].poses = (float *)dev(0);
+        dp[b].patches = (float *)dev(1);
+        dp[b].anchor = (const int32_t *)dev(2);
+        dp[b].kk = (const int32_t *)dev(3);
+        dp[b].jj = (const int32_t *)dev(4);
+        dp[b].target = (const float *)dev(5);
+        dp[b].weight = (const float *)dev(6);
+        dp[b].status = (int32_t *)dev(7);
+        host[0].push_back((char *)hp[b].poses);
+        host[1].push_back((char *)hp[b].patches);
+        host[2].push_back((char *)hp[b].anchor);
+        host[3].push_back((char *)hp[b].kk);
+        host[4].push_back((char *)hp[b].jj);
+        host[5].push_back((char *)hp[b].target);
+        host[6].push_back((char *)hp[b].weight);
+        host[7].push_back((char *)hp[b].status);
     }
-    if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
+    for (int q = 0; q < 7; ++q)
+        if (int rc = copy_runs(h->io, k[q], host[q], cudaMemcpyHostToDevice, stream)) return rc;
     if (int rc = run_solve(h, dims, dp.data(), n_problems, stream, nullptr, nullptr)) return rc;
-    for (int b = 0; b < n_problems; ++b) {
-        const size_t N = dims[b].n_frames, P = dims[b].n_patches;
-        cudaMemcpyAsync(hp[b].poses, dp[b].poses, N * 7 * 4, cudaMemcpyDeviceToHost, stream);
-        if (P) cudaMemcpyAsync(hp[b].patches, dp[b].patches, P * 3 * 4, cudaMemcpyDeviceToHost, stream);
-        if (hp[b].status) cudaMemcpyAsync(hp[b].status, dp[b].status, 4, cudaMemcpyDeviceToHost, stream);
+    for (int q : {0, 1})
+        if (int rc = copy_runs(h->io, k[q], host[q], cudaMemcpyDeviceToHost, stream)) return rc;
+    bool all_status = true;
+    for (int b = 0; b < n_problems; ++b) all_status = all_status && hp[b].status;
+    if (all_status) {
+        if (int rc = copy_runs(h->io, k[7], host[7], cudaMemcpyDeviceToHost, stream)) return rc;
+    } else {
+        for (int b = 0; b < n_problems; ++b)
+            if (hp[b].status && cudaMemcpyAsync(hp[b].status, dp[b].status, 4, cudaMemcpyDeviceToHost, stream))
+                return DPVO_BA_ECUDA;
     }
     if (cudaStreamSynchronize(stream) != cudaSuccess) return DPVO_BA_ECUDA;
     return DPVO_BA_OK;
@@ -358,6 +433,31 @@ int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, fl
         cudaMemcpy(dxi_out, p.dxi + (size_t)iter * p.nf * 6, (size_t)p.nf * 6 * 8, cudaMemcpyDeviceToHost))
         return DPVO_BA_ECUDA;
     return DPVO_BA_OK;
+}
+
+int dpvo_ba_set_timing(dpvo_ba_handle *h, int enable) {
+    if (!h) return DPVO_BA_EINVAL;
+    h->timing = enable != 0;
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    return DPVO_BA_OK;
+}
+
+int dpvo_ba_timing(dpvo_ba_handle *h, float *ms_out, int *kind_out, int cap) {
+    if (!h || cap < 0) return DPVO_BA_EINVAL;
+    const int launches = (int)h->ev_kind.size();
+    if (launches == 0) return 0;
+    if (cudaEventSynchronize(h->ev[h->ev_used - 1]) != cudaSuccess) return DPVO_BA_ECUDA;
+    const int n = std::min(cap, launches);
+    for (int i = 0; i < n; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) != cudaSuccess) return DPVO_BA_ECUDA;
+        if (ms_out) ms_out[i] = ms;
+        if (kind_out) kind_out[i] = h->ev_kind[i];
+    }
+    h->ev_used = 0;
+    h->ev_kind.clear();
+    return n;
 }
 
 const char *dpvo_ba_strerror(int code) {
