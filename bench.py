@@ -1,0 +1,410 @@
+"""Benchmark: bundle-adjustment solves per second on the sliding-window workload.
+
+Workload (one "step"): one batched solve of B problems of the sliding-window
+shape -- 22 buffered frames, 96 patches per frame (2112 patches), every patch
+connected to the frames within +-13 of its source frame (39,552 edges), the
+last 10 poses free, 2 Gauss-Newton iterations -- through the C ABI on device
+buffers.  B = 256 by default, so one step's inputs (~250 MB) exceed the 126 MB
+L2 and every iteration re-reads them from HBM.  Inputs are seeded synthetic
+scenes (paper_2208_04726_b300/scenes.py).
+
+Also measured and reported on the same JSON line:
+  plain     the same problems solved one per call, back to back (latency p50/p99)
+  e2e       the batched solve through the host-buffer entry point, host<->device
+            copies of every step's inputs and results inside the timed region
+  roofline  the linearise/Schur kernel against the FP32-ALU or HBM roofline
+  parity    sampled problems of the first timed-configuration solve vs the FP64 oracle
+  cpu_baseline  the FP64 oracle timed on this host's cores on a bounded sample
+
+``--impl reference`` times the FP64 oracle (the reference arm) instead.
+Launch: ``python bench.py --gpus N --steps K --warmup W`` (torchrun for N > 1,
+one replica per GPU, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "BA solves/s (2 GN iters) + p50/p99 latency, batched vs plain, at ≤1e-4 vs FP64"
+WORKLOAD = ("sliding window: N=22 frames, 96 patches/frame (2112 patches), radius 13 (39552 edges), "
+            "last 10 poses free, 2 GN iterations")
+PEAK_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--distinct", type=int, default=64, help="distinct seeded scenes, tiled to --batch")
+    ap.add_argument("--plain", type=int, default=200, help="one-problem solves timed for the plain form")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--parity-samples", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- work accounting
+
+def algorithmic_work(scene):
+    """Algorithmic FP32 flops and HBM bytes of one linearise/Schur pass over a
+    problem: 200 flops and 24 bytes per edge (projection, residual, Jacobians,
+    weighted products; kk, jj, target, weight), 20 bytes per patch, and per
+    patch 36 f (f + 1) + 12 f flops for its upper-triangle Schur blocks and
+    right-hand side, f = free poses the patch touches."""
+    i = scene.anchor[scene.kk]
+    nonself = i != scene.jj
+    E = int(nonself.sum())
+    t0 = scene.t0
+    f = np.zeros(scene.n_patches, np.int64)
+    m = nonself & (scene.jj >= t0)
+    np.add.at(f, scene.kk[m], 1)
+    f += ((scene.anchor >= t0) & np.isin(np.arange(scene.n_patches), scene.kk[nonself])).astype(np.int64)
+    flops = 200.0 * E + float(np.sum(36 * f * (f + 1) + 12 * f))
+    bytes_ = 24.0 * scene.n_edges + 20.0 * scene.n_patches
+    return flops, bytes_
+
+
+def traffic_from_profiles(kernel_source_sha):
+    """DRAM bytes per launch per problem from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "linearize_window_n22.md")
+    if not os.path.exists(path):
+        return None
+    sha, val = None, None
+    for line in open(path):
+        if line.startswith("kernel_source_sha1:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch_per_problem:"):
+            val = float(line.split(":", 1)[1].strip())
+    return val if (sha == kernel_source_sha and val is not None) else None
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2208_04726_b300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_2208_04726_b300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+# --------------------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2208_04726_b300 import scenes as S
+    from oracle import dense_gn as dg
+    scenes = [S.make_scene(S.WINDOW_N22, 1000 + s) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        dg.solve_scene(scenes[s])
+    t = time.perf_counter()
+    for s in range(args.steps):
+        dg.solve_scene(scenes[args.warmup + s])
+    el = time.perf_counter() - t
+    value = args.steps / el
+    cores = oracle_threads()
+    sample = "one sliding-window problem per step (dense FP64 oracle, 2 GN iterations)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    from paper_2208_04726_b300 import ba
+    from paper_2208_04726_b300 import scenes as S
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # ---- workload: distinct seeded scenes tiled to the batch size
+    base = 10_000 * (rank + 1)
+    distinct = [S.make_scene(S.WINDOW_N22, base + s) for s in range(min(args.distinct, args.batch))]
+    scenes = [distinct[b % len(distinct)] for b in range(args.batch)]
+    B = len(scenes)
+    batch = ba.PackedBatch(scenes, "cuda")
+    solver = ba.Solver()
+    solver.reserve(22, 2112, 39552, 2, B)
+
+    # ---- first solve from the initial state: full-size parity on sampled problems
+    solver.solve_arrays(batch.dims, batch.probs, B, stream)
+    torch.cuda.synchronize()
+    statuses = batch.status.cpu().numpy()
+    parity = None
+    cpu_baseline = None
+    if rank == 0 and args.parity_samples > 0:
+        from oracle import dense_gn as dg
+        idx = sorted(set([0, B - 1] + list(range(1, B - 1, max(1, B // max(1, args.parity_samples))))))[
+            :args.parity_samples]
+        errs_p, errs_d = [], []
+        t_or = 0.0
+        for b in idx:
+            sc = scenes[b]
+            t = time.perf_counter()
+            ref = dg.solve_scene(sc)
+            t_or += time.perf_counter() - t
+            poses = batch.view("poses", b).view(-1, 7).cpu().numpy().astype(np.float64)
+            poses[:, 3:] *= np.sign((poses[:, 3:] * ref["poses"][:, 3:]).sum(1))[:, None]
+            p0 = sc.poses.astype(np.float64).copy()
+            p0[:, 3:] *= np.sign((p0[:, 3:] * ref["poses"][:, 3:]).sum(1))[:, None]
+            t0 = sc.t0
+            errs_p.append(float(np.linalg.norm(poses[t0:] - ref["poses"][t0:]) /
+                                np.linalg.norm(ref["poses"][t0:] - p0[t0:])))
+            d = batch.view("patches", b).view(-1, 3)[:, 2].cpu().numpy().astype(np.float64)
+            errs_d.append(float(np.linalg.norm(d - ref["depths"]) /
+                                np.linalg.norm(ref["depths"] - sc.patches[:, 2])))
+        parity = {"problems_checked": idx, "pose_update_rel_err_max": max(errs_p),
+                  "depth_update_rel_err_max": max(errs_d), "tolerance": 1e-4,
+                  "statuses_nonzero": int((statuses != 0).sum())}
+        cpu_baseline = {"value": len(idx) / t_or, "unit": "solves/s", "cores": oracle_threads(), "kind": "oracle",
+                        "sample": f"{len(idx)} sliding-window problems of this batch, dense FP64 oracle, "
+                                  f"2 GN iterations each ({t_or:.1f} s)"}
+
+    # ---- warm-up
+    for _ in range(max(3, args.warmup)):
+        solver.solve_arrays(batch.dims, batch.probs, B, stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K batched solves, per-launch events on the launching stream
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    solver.set_timing(True)
+    solver.timing()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            solver.solve_arrays(batch.dims, batch.probs, B, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = solver.timing(cap=16 * args.steps + 64)
+    solver.set_timing(False)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    n_launch_per_solve = 1 + 3 + 2
+    value = world * B * args.steps / (elapsed_ms / 1e3)
+
+    # per-kernel times: per solve [plan, lin t0, solve, lin t1, solve, lin t2 (back-substitution only)]
+    lin_full, lin_bs, sol, plan = [], [], [], []
+    for s in range(len(launches) // n_launch_per_solve):
+        seq = launches[s * n_launch_per_solve:(s + 1) * n_launch_per_solve]
+        plan.append(seq[0][1]); lin_full += [seq[1][1], seq[3][1]]; sol += [seq[2][1], seq[4][1]]
+        lin_bs.append(seq[5][1])
+    kern = {"plan_ms": float(np.mean(plan)), "linearize_schur_ms": float(np.mean(lin_full)),
+            "backsub_final_ms": float(np.mean(lin_bs)), "reduce_cholesky_ms": float(np.mean(sol))}
+    step_ms = elapsed_ms / args.steps
+    kern["share_linearize_schur"] = 2 * kern["linearize_schur_ms"] / step_ms
+    kern["share_reduce_cholesky"] = 2 * kern["reduce_cholesky_ms"] / step_ms
+
+    hbm_peak, hbm_src = load_peaks()
+    flops_p, bytes_p = zip(*[algorithmic_work(sc) for sc in distinct])
+    flops = float(np.mean(flops_p)) * B
+    bytes_ = float(np.mean(bytes_p)) * B
+    t_lin = kern["linearize_schur_ms"] / 1e3
+    alu_time, hbm_time = flops / (PEAK_ALU_TFLOPS * 1e12), bytes_ / (hbm_peak * 1e9)
+    traffic_pp = traffic_from_profiles(kernel_sha())
+    if alu_time >= hbm_time:
+        achieved = flops / t_lin / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_ALU_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / PEAK_ALU_TFLOPS, "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2032 MHz"}
+    else:
+        achieved = bytes_ / t_lin / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": hbm_src}
+    roof["kernel"] = "linearize_kernel (back-substitution + linearisation + Schur, one launch per GN iteration)"
+    roof["traffic"] = traffic_pp * B if traffic_pp is not None else None
+    roof["algorithmic_per_launch"] = {"flops": flops, "bytes": bytes_}
+    roof["hbm_gbs_achieved"] = bytes_ / t_lin / 1e9
+    roof["hbm_frac_of_measured"] = roof["hbm_gbs_achieved"] / hbm_peak
+
+    # batched per-solve latency: every solve of a step completes with the step
+    step_times = []
+    for s in range(len(launches) // n_launch_per_solve):
+        step_times.append(sum(x[1] for x in launches[s * n_launch_per_solve:(s + 1) * n_launch_per_solve]))
+
+    # ---- plain form: one problem per call, back to back
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.plain)]
+    subsets = [batch.subset(b % B) for b in range(args.plain)]
+    for d_, p_ in subsets[:5]:
+        solver.solve_arrays(d_, p_, 1, stream)
+    torch.cuda.synchronize()
+    tp0 = torch.cuda.Event(enable_timing=True); tp1 = torch.cuda.Event(enable_timing=True)
+    tp0.record(stream)
+    for (a, b_), (d_, p_) in zip(ev, subsets):
+        a.record(stream)
+        solver.solve_arrays(d_, p_, 1, stream)
+        b_.record(stream)
+    tp1.record(stream)
+    torch.cuda.synchronize()
+    plain_lat = np.array([a.elapsed_time(b_) for a, b_ in ev])
+    plain_value = args.plain / (tp0.elapsed_time(tp1) / 1e3)
+
+    # ---- end to end through the host-buffer entry point
+    hbatch = ba.PackedBatch(scenes, "pinned")
+    h2d = hbatch.bytes_of([k for k, _ in ba.PackedBatch.KINDS])
+    d2h = hbatch.bytes_of(["poses", "patches"]) + 4 * B
+    hstream = torch.cuda.current_stream()
+    lib = solver.lib
+    for _ in range(2):
+        rc = lib.dpvo_ba_solve_host(solver.h, hbatch.dims, hbatch.probs, B, hstream.cuda_stream)
+        assert rc == 0, rc
+    if world > 1:
+        dist.barrier()
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        rc = lib.dpvo_ba_solve_host(solver.h, hbatch.dims, hbatch.probs, B, hstream.cuda_stream)
+        assert rc == 0, rc
+    e2e_s = time.perf_counter() - t
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * B * args.e2e_steps / e2e_s
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (edges, reductions, Schur) + f64 (Cholesky, solve, retraction)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_per_step": B, "distinct_scenes": len(distinct),
+                       "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush)",
+                       "input_bytes_per_step": int(batch.bytes_of([k for k, _ in ba.PackedBatch.KINDS])),
+                       "state": "poses and depths carried from step to step"},
+            "batched": {"solves_per_s": value, "latency_ms_p50": float(np.percentile(step_times, 50)),
+                        "latency_ms_p99": float(np.percentile(step_times, 99))},
+            "plain": {"solves_per_s": plain_value, "latency_ms_p50": float(np.percentile(plain_lat, 50)),
+                      "latency_ms_p99": float(np.percentile(plain_lat, 99)), "solves": args.plain},
+            "kernels": kern,
+            "roofline": roof,
+            "parity": parity,
+            "cpu_baseline": cpu_baseline,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": args.e2e_steps, "api": "dpvo_ba_solve_host (pinned host buffers)"},
+            "gpu_launches": world * n_launch_per_solve * args.steps,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
