@@ -161,6 +161,33 @@ int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, fl
 int dpvo_ba_set_timing(dpvo_ba_handle *h, int enable);
 int dpvo_ba_timing(dpvo_ba_handle *h, float *ms_out, int *kind_out, int cap);
 
+/* Allocation-free solve of ONE problem (the paper has no counterpart: this is
+ * a deployment entry point).  For callers that may not allocate device memory
+ * while running -- fixed-budget embedded pipelines, processes whose device
+ * memory is owned by another allocator, real-time loops that cannot take
+ * cudaMalloc's device synchronisation -- it needs no handle and makes no host
+ * or device allocation.  Its workspace is a fixed 8 MiB device array inside
+ * this library, held by every GPU that loads the library until the process
+ * exits.  Arguments as for dpvo_ba_solve with n_problems == 1 (cfg may be NULL
+ * for the defaults); results are the same as dpvo_ba_solve's.
+ *   - The first call on each device does a one-time set-up there (it looks up
+ *     the array's device address and sets kernel attributes); make that first
+ *     call before any stream capture, with the device current.
+ *   - All calls in the process share the one array and it keeps the previous
+ *     call's contents (every call rewrites what it reads).  Calls whose work
+ *     overlaps on the GPU -- on different streams, or from several host
+ *     threads -- race on it and corrupt each other: serialise them.
+ *   - Returns DPVO_BA_EINVAL, launching nothing, when the problem's workspace
+ *     exceeds the array.  The workspace grows with the patch count (one
+ *     64-patch work item per CTA, up to two CTAs per SM, each with its own
+ *     partial reduced system) and with the square of the free-pose count: an
+ *     8-frame problem of 512 patches needs 0.25 MiB, a 22-frame window of 2112
+ *     patches with 10 free poses 1.07 MiB, a 32-frame window of 3072 patches
+ *     with 10 free poses 1.55 MiB.
+ * Errors: EINVAL, ECUDA. */
+int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_dims *dims, const dpvo_ba_problem *prob,
+                          void *stream);
+
 /* Human-readable name of a return code. */
 const char *dpvo_ba_strerror(int code);
 

@@ -43,7 +43,7 @@ MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 15, 16
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solve", "dpvo_ba_solve_host",
            "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_set_timing", "dpvo_ba_timing",
-           "dpvo_ba_strerror"]
+           "dpvo_ba_solve_noalloc", "dpvo_ba_strerror"]
 
 _lib = None
 
@@ -72,6 +72,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_iterate.argtypes = [vp, i32, i32, vp, vp, vp]
     lib.dpvo_ba_set_timing.argtypes = [vp, i32]
     lib.dpvo_ba_timing.argtypes = [vp, vp, vp, i32]
+    lib.dpvo_ba_solve_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Dims), ctypes.POINTER(Problem), vp]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:

@@ -474,3 +474,109 @@ const char *dpvo_ba_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Allocation-free single-problem solve.
+//
+// Some callers may not allocate device memory once they are running: a VO
+// pipeline on an embedded GPU whose memory is fixed at start-up, a process
+// whose device memory belongs to another allocator (a framework's caching
+// allocator or a pre-sized pool), or a real-time frame loop that cannot take
+// cudaMalloc's implicit device synchronisation.  dpvo_ba_solve_noalloc()
+// serves them: its workspace lives in the fixed array below, which every GPU
+// that loads this library holds until the process exits.  It makes no host or
+// device allocation: the layout of its one problem is computed on the stack,
+// and its descriptors reach the device as kernel arguments.
+// ----------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB per device
+}
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Per-device set-up, done by the first call on each device: the device address
+// of g_noalloc_scratch (the host-side name is only a stand-in for it) and the
+// SM count.
+static char *g_noalloc_base[64] = {nullptr};
+static int g_noalloc_sms[64] = {0};
+
+__global__ void noalloc_descriptors_kernel(Prob p, int n_items, Prob *dst_prob, Item *dst_items) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dst_prob = p;
+    for (int w = threadIdx.x; w < n_items; w += blockDim.x) dst_items[w] = Item{0, w};
+}
+
+extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_dims *dims,
+                                     const dpvo_ba_problem *prob, void *stream_) {
+    if (!dims || !prob) return DPVO_BA_EINVAL;
+    if (int rc = check_dims(*dims)) return rc;
+    if (int rc = check_problem(*dims, *prob)) return rc;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DPVO_BA_ECUDA; }
+    if (dev < 0 || dev >= 64) return DPVO_BA_EINVAL;
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DPVO_BA_ECUDA;
+        }
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return DPVO_BA_ECUDA;
+        }
+        if (set_kernel_attrs(dev)) return DPVO_BA_ECUDA;
+        g_noalloc_sms[dev] = sms;
+        g_noalloc_base[dev] = (char *)p;
+    }
+    const float damping = cfg ? cfg->damping : 1e-4f;
+    const float z_min = cfg ? cfg->z_min : 0.1f;
+    if (!(damping >= 0.f) || !(z_min == z_min)) return DPVO_BA_EINVAL;
+
+    // layout of one problem (same formulas as the handle path), on the stack
+    const dpvo_ba_dims &d = *dims;
+    const int nf = d.n_frames - d.t0;
+    const int W_cap = std::min(d.n_frames, kMaxWindow);
+    int G_cap = 64;
+    while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf).bytes > kLinSmemBudget) G_cap -= 8;
+    const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf).bytes;
+    const size_t solve_smem = (size_t)(6 * nf) * (6 * nf + 1) * 8 + (size_t)(6 * nf) * 8 + 16;
+    Prob p;
+    std::memset(&p, 0, sizeof(Prob));
+    p.poses = prob->poses; p.patches = prob->patches; p.anchor = prob->anchor; p.kk = prob->kk;
+    p.jj = prob->jj; p.target = prob->target; p.weight = prob->weight; p.status_user = prob->status;
+    p.N = d.n_frames; p.P = d.n_patches; p.E = d.n_edges; p.t0 = d.t0; p.iters = d.n_iters; p.nf = nf;
+    p.fx = d.fx; p.fy = d.fy; p.cx = d.cx; p.cy = d.cy;
+    p.damping = damping; p.z_min = z_min;
+    p.chunk_cap = G_cap;
+    p.win_cap = W_cap;
+    p.max_chunks = (d.n_patches + G_cap - 1) / G_cap + d.n_frames;
+    p.ks = k_split(nf);
+    p.L = partial_len(nf);
+    const int est_chunks = std::max(1, (d.n_patches + G_cap - 1) / G_cap);
+    p.n_items = std::max(1, std::min(2 * g_noalloc_sms[dev], est_chunks));
+    char *base = g_noalloc_base[dev];
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char *q = base + off; off = al256(off + bytes); return q; };
+    p.seg = (int32_t *)take((size_t)(d.n_patches + 1) * 4);
+    p.chunks = (Chunk *)take((size_t)p.max_chunks * sizeof(Chunk));
+    char *ints = take(16);
+    p.n_chunks = (int32_t *)ints;
+    p.status = (int32_t *)(ints + 4);
+    p.pose_it = (float *)take((size_t)(d.n_iters + 1) * d.n_frames * 7 * 4);
+    p.depth_it = (float *)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
+    p.dxi = (double *)take((size_t)d.n_iters * nf * 6 * 8 + 8);
+    p.partial = (double *)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
+    Prob *d_prob = (Prob *)take(sizeof(Prob));
+    Item *d_items = (Item *)take(sizeof(Item) * p.n_items);
+    if (off > kNoAllocScratchBytes) return DPVO_BA_EINVAL;   // problem too large for the fixed scratch
+
+    noalloc_descriptors_kernel<<<1, kThreads, 0, stream>>>(p, p.n_items, d_prob, d_items);
+    plan_kernel<<<1, kThreads, 0, stream>>>(d_prob);
+    for (int t = 0; t <= d.n_iters; ++t) {
+        linearize_kernel<<<p.n_items, kThreads, lin_smem, stream>>>(d_prob, d_items, t, W_cap, G_cap, nf);
+        if (t < d.n_iters) solve_kernel<<<1, kThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
+    }
+    if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
+    return DPVO_BA_OK;
+}
