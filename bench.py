@@ -4,8 +4,9 @@ Workload (one "step"): one batched solve of B problems of the sliding-window
 shape -- 22 buffered frames, 96 patches per frame (2112 patches), every patch
 connected to the frames within +-13 of its source frame (39,552 edges), the
 last 10 poses free, 2 Gauss-Newton iterations -- through the C ABI on device
-buffers.  B = 256 by default, so one step's inputs (~250 MB) exceed the 126 MB
-L2 and every iteration re-reads them from HBM.  Inputs are seeded synthetic
+buffers.  B = two problems per SM by default (296 on a B300: one work item per
+problem fills exactly one wave), so one step's inputs (~290 MB) exceed the
+126 MB L2 and every iteration re-reads them from HBM.  Inputs are seeded synthetic
 scenes (paper_2208_04726_b300/scenes.py).
 
 Also measured and reported on the same JSON line:
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=0, help="problems per step (0: two per SM)")
     ap.add_argument("--distinct", type=int, default=64, help="distinct seeded scenes, tiled to --batch")
     ap.add_argument("--plain", type=int, default=200, help="one-problem solves timed for the plain form")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -227,8 +228,9 @@ def main():
 
     # ---- workload: distinct seeded scenes tiled to the batch size
     base = 10_000 * (rank + 1)
-    distinct = [S.make_scene(S.WINDOW_N22, base + s) for s in range(min(args.distinct, args.batch))]
-    scenes = [distinct[b % len(distinct)] for b in range(args.batch)]
+    n_batch = args.batch if args.batch > 0 else 2 * torch.cuda.get_device_properties(dev).multi_processor_count
+    distinct = [S.make_scene(S.WINDOW_N22, base + s) for s in range(min(args.distinct, n_batch))]
+    scenes = [distinct[b % len(distinct)] for b in range(n_batch)]
     B = len(scenes)
     batch = ba.PackedBatch(scenes, "cuda")
     solver = ba.Solver()

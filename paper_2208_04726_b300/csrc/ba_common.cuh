@@ -11,7 +11,7 @@ namespace dpvo {
 constexpr int kThreads = 256;          // block size of the linearise and solve kernels
 constexpr int kMaxWindow = 64;         // frames the edges of one patch chunk may span
 constexpr int kMaxFree = DPVO_BA_MAX_FREE;
-constexpr int kFlushEvery = 8;         // patches summed in FP32 before a compensated add
+constexpr int kFlushEvery = 16;        // patches summed in FP32 before a compensated add
 constexpr int kMaxKSplit = 8;          // patch-parity split of the Schur accumulation
 
 // A run of consecutive patches that share one source frame (anchor).

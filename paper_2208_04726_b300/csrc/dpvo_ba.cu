@@ -22,7 +22,7 @@ struct Layout {
     std::vector<Prob> probs;       // workspace pointers hold offsets until rebased
     std::vector<Item> items;
     size_t bytes = 0, off_probs = 0, off_items = 0;
-    int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0;
+    int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0, n_max = 1;
     size_t lin_smem = 0, solve_smem = 0;
 };
 
@@ -52,10 +52,11 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         L.nf_max = std::max(L.nf_max, dims[b].n_frames - dims[b].t0);
         L.iters_max = std::max(L.iters_max, dims[b].n_iters);
     }
+    L.n_max = n_max;
     L.W_cap = std::min(n_max, kMaxWindow);
     L.G_cap = 64;
-    while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max).bytes > kLinSmemBudget) L.G_cap -= 8;
-    L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max).bytes;
+    while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max).bytes > kLinSmemBudget) L.G_cap -= 8;
+    L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max).bytes;
     const int n6 = 6 * L.nf_max;
     L.solve_smem = (size_t)n6 * (n6 + 1) * 8 + (size_t)n6 * 8 + 16;
 
@@ -230,18 +231,18 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     if ((rc = timed(0, [&] { plan_kernel<<<n, kThreads, 0, stream>>>(d_probs); }))) return rc;
     if (S_out) {
         linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, 0, L.W_cap, L.G_cap,
-                                                                     L.nf_max);
-        solve_kernel<<<n, kThreads, L.solve_smem, stream>>>(d_probs, 0, S_out, v_out);
+                                                                     L.nf_max, L.n_max);
+        solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, 0, S_out, v_out);
     } else {
         for (int t = 0; t <= L.iters_max; ++t) {
             rc = timed(1, [&] {
                 linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap,
-                                                                             L.G_cap, L.nf_max);
+                                                                             L.G_cap, L.nf_max, L.n_max);
             });
             if (rc) return rc;
             if (t < L.iters_max) {
                 rc = timed(2, [&] {
-                    solve_kernel<<<n, kThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+                    solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
                 });
                 if (rc) return rc;
             }
@@ -538,8 +539,8 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     const int nf = d.n_frames - d.t0;
     const int W_cap = std::min(d.n_frames, kMaxWindow);
     int G_cap = 64;
-    while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf).bytes > kLinSmemBudget) G_cap -= 8;
-    const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf).bytes;
+    while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf, d.n_frames).bytes > kLinSmemBudget) G_cap -= 8;
+    const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf, d.n_frames).bytes;
     const size_t solve_smem = (size_t)(6 * nf) * (6 * nf + 1) * 8 + (size_t)(6 * nf) * 8 + 16;
     Prob p;
     std::memset(&p, 0, sizeof(Prob));
@@ -574,8 +575,9 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     noalloc_descriptors_kernel<<<1, kThreads, 0, stream>>>(p, p.n_items, d_prob, d_items);
     plan_kernel<<<1, kThreads, 0, stream>>>(d_prob);
     for (int t = 0; t <= d.n_iters; ++t) {
-        linearize_kernel<<<p.n_items, kThreads, lin_smem, stream>>>(d_prob, d_items, t, W_cap, G_cap, nf);
-        if (t < d.n_iters) solve_kernel<<<1, kThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
+        linearize_kernel<<<p.n_items, kThreads, lin_smem, stream>>>(d_prob, d_items, t, W_cap, G_cap, nf,
+                                                                     d.n_frames);
+        if (t < d.n_iters) solve_kernel<<<1, kSolveThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
     }
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
     return DPVO_BA_OK;

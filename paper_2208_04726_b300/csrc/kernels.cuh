@@ -167,20 +167,37 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__
             ch.e0 = pr.seg[k];
             ch.e1 = pr.seg[k + sz];
             ch.anchor = i;
-            int jlo = i, jhi = i;
-            for (int q = k; q < k + sz; ++q) {
-                const int s0 = pr.seg[q], s1 = pr.seg[q + 1];
-                if (s1 > s0) {
-                    jlo = min(jlo, (int)pr.jj[s0]);
-                    jhi = max(jhi, (int)pr.jj[s1 - 1]);
-                }
-            }
-            ch.jlo = jlo;
-            ch.jhi = jhi;
+            ch.jlo = i;          // window filled in below, one warp per chunk
+            ch.jhi = i;
             ch.pad = 0;
-            if (jhi - jlo + 1 > pr.win_cap) atomicOr(&s_bad, 1);
             pr.chunks[s_choff[i] + c] = ch;
             k += sz;
+        }
+    }
+    __syncthreads();
+    // frame window [jlo, jhi] of each chunk: edges of a patch are sorted by
+    // frame, so its first and last edges bound it
+    const int lane = tid & 31, warp = tid >> 5;
+    const int n_built = s_bad ? 0 : s_choff[N];    // 0 if the chunk table overflowed
+    for (int c = warp; c < n_built; c += kThreads / 32) {
+        Chunk ch = pr.chunks[c];
+        int jlo = ch.anchor, jhi = ch.anchor;
+        for (int q = ch.k0 + lane; q < ch.k0 + ch.count; q += 32) {
+            const int s0 = pr.seg[q], s1 = pr.seg[q + 1];
+            if (s1 > s0) {
+                jlo = min(jlo, (int)pr.jj[s0]);
+                jhi = max(jhi, (int)pr.jj[s1 - 1]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            jlo = min(jlo, __shfl_xor_sync(0xffffffffu, jlo, o));
+            jhi = max(jhi, __shfl_xor_sync(0xffffffffu, jhi, o));
+        }
+        if (lane == 0) {
+            pr.chunks[c].jlo = jlo;
+            pr.chunks[c].jhi = jhi;
+            if (jhi - jlo + 1 > pr.win_cap) atomicOr(&s_bad, 1);
         }
     }
     __syncthreads();
@@ -191,37 +208,54 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__
 }
 
 // ----------------------------------------------------------------------------
-// linearize_kernel shared-memory carve-up (sizes depend on the batch's window
-// and chunk caps, and on the largest number of free poses).
+// linearize_kernel shared memory.  Sizes depend on the batch's frame-window
+// cap W, chunk cap G and largest free-pose count.
 // ----------------------------------------------------------------------------
 struct LinSmem {
-    int W, G, ES;  // window cap, chunk cap, E-column stride
-    size_t off_tw, off_sc4, off_sc1, off_ec, off_rel, off_adj, off_mc, off_aj, off_bii, off_pd, off_zk, off_dx;
+    int W, G, Gs, ES, EC;  // window cap, chunk cap, odd slot stride, E-column stride, edge capacity
+    size_t off_pose, off_rjj, off_rtg, off_rwt, off_rpx, off_rpy, off_rdep, off_rseg, off_idx, off_sc4, off_sc1,
+        off_ec, off_mp, off_relo, off_reln, off_adj, off_mc, off_aj, off_bp, off_bii, off_pd, off_zk, off_ps, off_dx;
     size_t bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max) {
+__host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int n_max) {
     LinSmem s;
-    s.W = W; s.G = G;
-    int es = 6 * nf_max + 2;
-    if ((es & 1) == 0) es += 1;
+    s.W = W;
+    s.G = G;
+    s.Gs = G | 1;
+    // E_k row: frame f at floats 8f..8f+7 laid out [v0 v1 v2 _ v3 v4 v5 _],
+    // then C_k^-1/2 w_k; the stride is an odd multiple of 4 floats
+    const int es = 8 * nf_max + 4;
     s.ES = es;
+    s.EC = W * G;
+    const size_t slots = (size_t)W * s.Gs;
     size_t o = 0;
-    size_t tw = (size_t)W * G * 16, mp = (size_t)kThreads * 27 * 4;
-    s.off_tw = o;  o = align16(o + (tw > mp ? tw : mp));
-    s.off_sc4 = o; o = align16(o + (size_t)W * G * 16);
-    s.off_sc1 = o; o = align16(o + (size_t)W * G * 4);
-    s.off_ec = o;  o = align16(o + (size_t)G * es * 4);
-    s.off_rel = o; o = align16(o + (size_t)W * 12 * 4);
-    s.off_adj = o; o = align16(o + (size_t)W * 36 * 4);
-    s.off_mc = o;  o = align16(o + (size_t)W * 27 * 4);
-    s.off_aj = o;  o = align16(o + (size_t)W * 42 * 4);
-    s.off_bii = o; o = align16(o + 42 * 4);
-    s.off_pd = o;  o = align16(o + (size_t)G * 16);
-    s.off_zk = o;  o = align16(o + (size_t)G * 16);
-    s.off_dx = o;  o = align16(o + kMaxFree * 6 * 4);
+    s.off_pose = o; o = align16(o + 2 * (size_t)n_max * 7 * 4);
+    s.off_rjj = o;  o = align16(o + (size_t)s.EC * 4);
+    s.off_rtg = o;  o = align16(o + (size_t)s.EC * 8);
+    s.off_rwt = o;  o = align16(o + (size_t)s.EC * 8);
+    s.off_rpx = o;  o = align16(o + (size_t)G * 4);
+    s.off_rpy = o;  o = align16(o + (size_t)G * 4);
+    s.off_rdep = o; o = align16(o + (size_t)G * 4);
+    s.off_rseg = o; o = align16(o + (size_t)(G + 1) * 4);
+    s.off_idx = o;  o = align16(o + slots * 2);
+    s.off_sc4 = o;  o = align16(o + slots * 16);
+    s.off_sc1 = o;  o = align16(o + slots * 4);
+    s.off_ec = o;   o = align16(o + (size_t)G * es * 4);
+    s.off_mp = o;   o = align16(o + (size_t)kThreads * 27 * 4);
+    s.off_relo = o; o = align16(o + (size_t)W * 12 * 4);
+    s.off_reln = o; o = align16(o + (size_t)W * 12 * 4);
+    s.off_adj = o;  o = align16(o + (size_t)W * 36 * 4);
+    s.off_mc = o;   o = align16(o + (size_t)W * 27 * 4);
+    s.off_aj = o;   o = align16(o + (size_t)W * 42 * 4);
+    s.off_bp = o;   o = align16(o + (size_t)W * 42 * 4);
+    s.off_bii = o;  o = align16(o + 42 * 4);
+    s.off_pd = o;   o = align16(o + (size_t)G * 16);
+    s.off_zk = o;   o = align16(o + (size_t)G * 16);
+    s.off_ps = o;   o = align16(o + (size_t)G * 8 * 4);
+    s.off_dx = o;   o = align16(o + kMaxFree * 6 * 4);
     s.bytes = o;
     return s;
 }
@@ -234,15 +268,60 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float blk) {
     s = t;
 }
 
-// Compute relative poses (and adjoints) of the chunk's window frames w.r.t.
-// the anchor at the pose set `poses`.
+// Asynchronous global -> shared copies (completed by cp_async_wait_all + a barrier).
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Start copying one chunk's inputs -- frames, targets and weights of its
+// edges, its patches' centres and inverse depths, its patch -> edge offsets --
+// into the staging buffers.
+__device__ __forceinline__ void prefetch_chunk(const Prob &pr, const Chunk &ch, const float *depth_src, int *rjj,
+                                               float2 *rtg, float2 *rwt, float *rpx, float *rpy, float *rdep,
+                                               int *rseg, const Chunk *desc_src, Chunk *desc_dst) {
+    if (desc_src && threadIdx.x < 8)   // the descriptor of the chunk after this one
+        cp_async4(reinterpret_cast<int *>(desc_dst) + threadIdx.x, reinterpret_cast<const int *>(desc_src) + threadIdx.x);
+    const float2 *tg = reinterpret_cast<const float2 *>(pr.target);
+    const float2 *wt = reinterpret_cast<const float2 *>(pr.weight);
+    const int ne = ch.e1 - ch.e0;
+    for (int q = threadIdx.x; q < ne; q += kThreads) {
+        const int e = ch.e0 + q;
+        cp_async4(rjj + q, pr.jj + e);
+        cp_async8(rtg + q, tg + e);
+        cp_async8(rwt + q, wt + e);
+    }
+    for (int q = threadIdx.x; q < ch.count; q += kThreads) {
+        const int k = ch.k0 + q;
+        cp_async4(rpx + q, pr.patches + 3 * k);
+        cp_async4(rpy + q, pr.patches + 3 * k + 1);
+        cp_async4(rdep + q, depth_src + k);
+    }
+    for (int q = threadIdx.x; q <= ch.count; q += kThreads) cp_async4(rseg + q, pr.seg + ch.k0 + q);
+    cp_async_commit();
+}
+
+// Relative poses of the window frames w.r.t. the anchor (and their adjoints).
 __device__ __forceinline__ void window_poses(const float *poses, int anchor, int jlo, int W, float *rel,
                                              float *adj) {
     for (int jl = threadIdx.x; jl < W; jl += kThreads) {
         float *R = rel + jl * 12;
         relative_pose(poses + 7 * anchor, poses + 7 * (jlo + jl), R, R + 9);
-        adjoint6(R, R + 9, adj + jl * 36);
+        if (adj) adjoint6(R, R + 9, adj + jl * 36);
     }
+}
+
+// Sum of 4 consecutive lanes' values (fixed order), broadcast to all four.
+__device__ __forceinline__ float quad_sum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    return v;
 }
 
 // ----------------------------------------------------------------------------
@@ -250,10 +329,14 @@ __device__ __forceinline__ void window_poses(const float *poses, int anchor, int
 // t = iteration.  For t < iters: back-substitute iteration t-1 (if t > 0), then
 // linearise at iterate t and accumulate the Schur partial.  For t == iters:
 // back-substitute the last iteration and write the caller's outputs.
+// A chunk's inputs are copied into shared memory asynchronously while the
+// previous chunk is still being reduced.  Consecutive chunks with the same
+// anchor and frame window form a group that shares its window poses and its
+// pose-pair blocks.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restrict__ probs,
+__global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__restrict__ probs,
                                                              const Item *__restrict__ items, int t,
-                                                             int W_cap, int G_cap, int nf_max) {
+                                                             int W_cap, int G_cap, int nf_max, int n_max) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
@@ -268,35 +351,48 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
         if (st != 0) return;
     }
 
-    const LinSmem L = lin_smem_layout(W_cap, G_cap, nf_max);
-    float4 *tw = reinterpret_cast<float4 *>(smem + L.off_tw);
-    float *Mp = reinterpret_cast<float *>(smem + L.off_tw);   // aliases tw after the edge pass
+    const LinSmem L = lin_smem_layout(W_cap, G_cap, nf_max, n_max);
+    float *spo = reinterpret_cast<float *>(smem + L.off_pose);        // old-state poses
+    float *spn = spo + n_max * 7;                                       // new-state poses
+    int *rjj = reinterpret_cast<int *>(smem + L.off_rjj);
+    float2 *rtg = reinterpret_cast<float2 *>(smem + L.off_rtg);
+    float2 *rwt = reinterpret_cast<float2 *>(smem + L.off_rwt);
+    float *rpx = reinterpret_cast<float *>(smem + L.off_rpx);
+    float *rpy = reinterpret_cast<float *>(smem + L.off_rpy);
+    float *rdep = reinterpret_cast<float *>(smem + L.off_rdep);
+    int *rseg = reinterpret_cast<int *>(smem + L.off_rseg);
+    short *sidx = reinterpret_cast<short *>(smem + L.off_idx);
     float4 *sc4 = reinterpret_cast<float4 *>(smem + L.off_sc4);
     float *sc1 = reinterpret_cast<float *>(smem + L.off_sc1);
     float *Ec = reinterpret_cast<float *>(smem + L.off_ec);
-    float *rel = reinterpret_cast<float *>(smem + L.off_rel);
+    float *Mp = reinterpret_cast<float *>(smem + L.off_mp);
+    float *relo = reinterpret_cast<float *>(smem + L.off_relo);
+    float *reln = reinterpret_cast<float *>(smem + L.off_reln);
     float *adj = reinterpret_cast<float *>(smem + L.off_adj);
     float *Mc = reinterpret_cast<float *>(smem + L.off_mc);
     float *Aj = reinterpret_cast<float *>(smem + L.off_aj);
+    float *Bp = reinterpret_cast<float *>(smem + L.off_bp);
     float *Bii = reinterpret_cast<float *>(smem + L.off_bii);
     float4 *pd = reinterpret_cast<float4 *>(smem + L.off_pd);
     float4 *zk = reinterpret_cast<float4 *>(smem + L.off_zk);
+    float *ps = reinterpret_cast<float *>(smem + L.off_ps);
     float *dxs = reinterpret_cast<float *>(smem + L.off_dx);
-    const int Gs = G_cap, ES = L.ES;
+    const int Gs = L.Gs, ES = L.ES;
 
     const int N = pr.N, t0 = pr.t0, nf = pr.nf;
     const float fx = pr.fx, fy = pr.fy, cx = pr.cx, cy = pr.cy, z_min = pr.z_min, lam = pr.damping;
+    const float ifx = 1.0f / fx, ify = 1.0f / fy;
     const float *pose_old = pr.pose_it + (size_t)(t > 0 ? t - 1 : 0) * N * 7;
     const float *pose_new = pr.pose_it + (size_t)t * N * 7;
     const float *depth_old = pr.depth_it + (size_t)(t > 0 ? t - 1 : 0) * pr.P;
     float *depth_new = pr.depth_it + (size_t)t * pr.P;
+    const float *depth_src = do_bs ? depth_old : depth_new;
 
-    // Work-item chunk range.
     const int nch = *pr.n_chunks;
     const int c_begin = (int)(((long long)itm.item * nch) / pr.n_items);
     const int c_end = (int)(((long long)(itm.item + 1) * nch) / pr.n_items);
 
-    // Strip ownership for the Schur accumulation.
+    // strip ownership of the Schur accumulation
     const int nbp = n_block_pairs(nf);
     const int nbs = 2 * nbp;
     const int nst = nbs + nf;
@@ -318,74 +414,119 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
 #pragma unroll
     for (int q = 0; q < 18; ++q) { acc_s[q] = 0.f; acc_c[q] = 0.f; blk[q] = 0.f; }
 
+    for (int q = tid; q < N * 7; q += kThreads) {
+        spo[q] = pose_old[q];
+        spn[q] = pose_new[q];
+    }
     if (do_bs) {
         const double *dx = pr.dxi + (size_t)(t - 1) * nf * 6;
         for (int q = tid; q < nf * 6; q += kThreads) dxs[q] = (float)dx[q];
     }
 
-    __shared__ Chunk s_ch;
-    for (int c = c_begin; c < c_end; ++c) {
-        if (tid == 0) s_ch = pr.chunks[c];
+    __shared__ __align__(16) Chunk s_ch[2];
+    if (c_begin < c_end) {
+        if (tid == 0) s_ch[0] = pr.chunks[c_begin];
         __syncthreads();
-        const int k0 = s_ch.k0, cnt = s_ch.count, e0 = s_ch.e0, e1 = s_ch.e1;
-        const int anc = s_ch.anchor, jlo = s_ch.jlo;
-        const int W = s_ch.jhi - jlo + 1;
+        prefetch_chunk(pr, s_ch[0], depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
+                       c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1]);
+    }
+    int cur = 0;
+    bool group_open = false;   // the previous chunk continues into this one
+
+    for (int c = c_begin; c < c_end; ++c) {
+        const Chunk ch = s_ch[cur];
+        const bool have_next = c + 1 < c_end;
+        cp_async_wait_all();
+        __syncthreads();                                   // this chunk's inputs are in shared memory
+        Chunk nx = ch;
+        if (have_next) nx = s_ch[cur ^ 1];
+        const bool group_next = have_next && nx.anchor == ch.anchor && nx.jlo == ch.jlo && nx.jhi == ch.jhi;
+        const int k0 = ch.k0, cnt = ch.count, e0 = ch.e0;
+        const int anc = ch.anchor, jlo = ch.jlo;
+        const int W = ch.jhi - jlo + 1;
         const bool anc_free = anc >= t0;
         const int NG = kThreads / W;
-        const int my_jl = tid % W, my_g = tid / W;
+        const int my_g = tid % NG, my_jl = tid / NG;       // consecutive lanes: consecutive patches of one frame
         const int my_j = jlo + my_jl;
-        const bool edge_thread = my_g < NG;
+        const bool edge_thread = my_jl < W;
 
-        // -- stage: clear slots, load edges transposed to [frame][patch], patch data
-        for (int q = tid; q < W * Gs; q += kThreads) tw[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int p = tid; p < cnt; p += kThreads) {
-            const int k = k0 + p;
-            const float x = pr.patches[3 * k], y = pr.patches[3 * k + 1];
-            pd[p] = make_float4((x - cx) / fx, (y - cy) / fy, do_bs ? depth_old[k] : depth_new[k], 0.f);
-        }
-        window_poses(do_bs ? pose_old : pose_new, anc, jlo, W, rel, adj);
-        __syncthreads();
+        // -- (0) slot -> edge table, patch data, window poses, cleared E columns.
+        // Thread (p = tid mod 64, jl = tid / 64 + 4 i) for the slots.
         {
-            const float2 *tg = reinterpret_cast<const float2 *>(pr.target);
-            const float2 *wt = reinterpret_cast<const float2 *>(pr.weight);
-            for (int e = e0 + tid; e < e1; e += kThreads) {
-                const int p = pr.kk[e] - k0, jl = pr.jj[e] - jlo;
-                const float2 a = tg[e], w = wt[e];
-                tw[jl * Gs + p] = make_float4(a.x, a.y, w.x, w.y);
+            const int p = tid & 63;
+            if (p < cnt) {
+                const int a = rseg[p] - e0, b = rseg[p + 1] - e0;
+                int jf = 0, jz = -1;
+                bool contig = true;
+                if (b > a) {
+                    jf = rjj[a];
+                    jz = rjj[b - 1];
+                    contig = jz - jf + 1 == b - a;         // frames of this patch are contiguous
+                }
+                for (int jl = tid >> 6; jl < W; jl += kThreads / 64) {
+                    const int j = jlo + jl;
+                    int idx = -1;
+                    if (j >= jf && j <= jz) {
+                        if (contig) {
+                            idx = a + (j - jf);
+                        } else {
+                            int lo = a, hi = b - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (rjj[mid] < j) lo = mid + 1; else hi = mid;
+                            }
+                            if (rjj[lo] == j) idx = lo;
+                        }
+                    }
+                    sidx[jl * Gs + p] = (short)idx;
+                }
+                if (do_lin)   // E columns of free frames outside the window are zero
+                    for (int f = tid >> 6; f < nf; f += kThreads / 64) {
+                        const int fr = t0 + f;
+                        if (fr < jlo || fr > ch.jhi) {
+                            float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * f);
+                            e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            e4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
+                if (tid < 64) {
+                    const float px = (rpx[p] - cx) * ifx, py = (rpy[p] - cy) * ify, d = rdep[p];
+                    pd[p] = make_float4(px, py, d, 0.f);
+                    if (do_bs && anc_free) {
+                        // z_k = d dxi_i,v + dxi_i,w x pbar, for the anchor term of the back-substitution
+                        const float *di = dxs + 6 * (anc - t0);
+                        zk[p] = make_float4(fmaf(d, di[0], di[4] - di[5] * py), fmaf(d, di[1], di[5] * px - di[3]),
+                                            fmaf(d, di[2], di[3] * py - di[4] * px), 0.f);
+                    }
+                }
             }
         }
-        if (do_bs && anc_free) {
-            // z_k = d dxi_i,v + dxi_i,w x pbar for the anchor term of the back-substitution
-            const float *di = dxs + 6 * (anc - t0);
-            for (int p = tid; p < cnt; p += kThreads) {
-                const float4 q = pd[p];
-                const float px = q.x, py = q.y, pz = 1.f, d = q.z;
-                zk[p] = make_float4(fmaf(d, di[0], di[4] * pz - di[5] * py),
-                                    fmaf(d, di[1], di[5] * px - di[3] * pz),
-                                    fmaf(d, di[2], di[3] * py - di[4] * px), 0.f);
-            }
+        if (!group_open) {
+            if (do_bs) window_poses(spo, anc, jlo, W, relo, nullptr);
+            if (do_lin) window_poses(spn, anc, jlo, W, reln, adj);
         }
         __syncthreads();
 
         // -- (a) back-substitution of the previous iteration at the old state
         if (do_bs) {
             if (edge_thread) {
-                const float *R = rel + my_jl * 12;
                 float Rr[12];
 #pragma unroll
-                for (int q = 0; q < 12; ++q) Rr[q] = R[q];
+                for (int q = 0; q < 12; ++q) Rr[q] = relo[my_jl * 12 + q];
                 const bool jfree = my_j >= t0 && my_j != anc;
-                const float *dj = dxs + 6 * (my_j - t0);
+                const float *dj = dxs + 6 * (jfree ? my_j - t0 : 0);
                 for (int p = my_g; p < cnt; p += NG) {
                     const int slot = my_jl * Gs + p;
-                    const float4 tv = tw[slot];
+                    const int ei = sidx[slot];
                     float Ce = 0.f, we = 0.f, se = 0.f;
-                    if (my_j != anc && (tv.z != 0.f || tv.w != 0.f)) {
+                    if (ei >= 0 && my_j != anc) {
+                        const float2 tv = rtg[ei], wv = rwt[ei];
                         const float4 q = pd[p];
                         EdgeLin E;
-                        if (edge_linearize(Rr, Rr + 9, q.x, q.y, q.z, tv.x, tv.y, fx, fy, cx, cy, z_min, E)) {
+                        if ((wv.x != 0.f || wv.y != 0.f) &&
+                            edge_linearize(Rr, Rr + 9, q.x, q.y, q.z, tv.x, tv.y, fx, fy, cx, cy, z_min, E)) {
                             float wjd0, wjd1;
-                            depth_terms(E, tv.z, tv.w, wjd0, wjd1, Ce, we);
+                            depth_terms(E, wv.x, wv.y, wjd0, wjd1, Ce, we);
                             if (jfree) {
 #pragma unroll
                                 for (int m = 0; m < 6; ++m) se = fmaf(fmaf(E.j1[m], wjd1, E.j0[m] * wjd0), dj[m], se);
@@ -402,53 +543,71 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
                 }
             }
             __syncthreads();
-            for (int p = tid; p < cnt; p += kThreads) {
-                float C = lam, w = 0.f, s = 0.f;
-                for (int jl = 0; jl < W; ++jl) {
-                    const float4 v = sc4[jl * Gs + p];
-                    C += v.x;
-                    w += v.y;
-                    s += v.z;
+            {   // per-patch sums over the window by four lanes, then dd_k = (w_k - e_k . dxi) / C_k
+                const int p = tid >> 2, sub = tid & 3;
+                float C = sub == 0 ? lam : 0.f, w = 0.f, s = 0.f;
+                if (p < cnt)
+                    for (int jl = sub; jl < W; jl += 4) {
+                        const float4 v = sc4[jl * Gs + p];
+                        C += v.x;
+                        w += v.y;
+                        s += v.z;
+                    }
+                C = quad_sum(C);
+                w = quad_sum(w);
+                s = quad_sum(s);
+                if (sub == 0 && p < cnt) {
+                    const float dnew = pd[p].z + (w - s) / C;
+                    pd[p].z = dnew;
+                    depth_new[k0 + p] = dnew;
+                    if (final_pass) pr.patches[3 * (k0 + p) + 2] = dnew;
                 }
-                const float dnew = pd[p].z + (w - s) / C;
-                pd[p].z = dnew;
-                depth_new[k0 + p] = dnew;
-                if (final_pass) pr.patches[3 * (k0 + p) + 2] = dnew;
             }
-            if (do_lin) window_poses(pose_new, anc, jlo, W, rel, adj);
+            if (!do_lin) {
+                // the staging buffers are free: start the next chunk's copies
+                if (have_next)
+                    prefetch_chunk(pr, nx, depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
+                                   c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur]);
+                group_open = group_next;
+                cur ^= 1;
+                continue;
+            }
             __syncthreads();
         }
-        if (!do_lin) continue;
 
-        // -- (b) linearise at the new state
-        for (int q = tid; q < cnt * ES; q += kThreads) Ec[q] = 0.f;
-        __syncthreads();
-        float M[21], V[6];
-#pragma unroll
-        for (int q = 0; q < 21; ++q) M[q] = 0.f;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) V[q] = 0.f;
+        // -- (b) linearise at the new state.  Each edge thread keeps its frame
+        // sums (M_j, v_j) in its own Mp slot between the chunks of a group.
         if (edge_thread) {
-            const float *R = rel + my_jl * 12;
+            float M[21], V[6];
+            {
+                const float *mp = Mp + (size_t)tid * 27;
+#pragma unroll
+                for (int q = 0; q < 21; ++q) M[q] = group_open ? mp[q] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) V[q] = group_open ? mp[21 + q] : 0.f;
+            }
             float Rr[12];
 #pragma unroll
-            for (int q = 0; q < 12; ++q) Rr[q] = R[q];
+            for (int q = 0; q < 12; ++q) Rr[q] = reln[my_jl * 12 + q];
             const bool jfree = my_j >= t0 && my_j != anc;
-            const int fj = my_j - t0;
+            const int fj = jfree ? my_j - t0 : 0;
             for (int p = my_g; p < cnt; p += NG) {
                 const int slot = my_jl * Gs + p;
-                const float4 tv = tw[slot];
+                const int ei = sidx[slot];
                 float Ce = 0.f, we = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
-                if (my_j != anc && (tv.z != 0.f || tv.w != 0.f)) {
+                float4 elo = make_float4(0.f, 0.f, 0.f, 0.f), ehi = elo;
+                if (ei >= 0 && my_j != anc) {
+                    const float2 tv = rtg[ei], wv = rwt[ei];
                     const float4 q = pd[p];
                     EdgeLin E;
-                    if (edge_linearize(Rr, Rr + 9, q.x, q.y, q.z, tv.x, tv.y, fx, fy, cx, cy, z_min, E)) {
+                    if ((wv.x != 0.f || wv.y != 0.f) &&
+                        edge_linearize(Rr, Rr + 9, q.x, q.y, q.z, tv.x, tv.y, fx, fy, cx, cy, z_min, E)) {
                         float wjd0, wjd1;
-                        depth_terms(E, tv.z, tv.w, wjd0, wjd1, Ce, we);
+                        depth_terms(E, wv.x, wv.y, wjd0, wjd1, Ce, we);
                         anchor_terms(E, Rr, wjd0, wjd1, Y0, Y1, Y2);
                         float wj0[6], wj1[6];
 #pragma unroll
-                        for (int m = 0; m < 6; ++m) { wj0[m] = tv.z * E.j0[m]; wj1[m] = tv.w * E.j1[m]; }
+                        for (int m = 0; m < 6; ++m) { wj0[m] = wv.x * E.j0[m]; wj1[m] = wv.y * E.j1[m]; }
                         // B_jj += J_j^T W J_j (the zero entries j0[1], j1[0] skipped)
 #pragma unroll
                         for (int r = 0; r < 6; ++r)
@@ -467,120 +626,139 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
                             if (m != 0) vv = fmaf(wj1[m], E.r1, vv);
                             V[m] = vv;
                         }
-                        if (jfree) {
-                            float *e = Ec + p * ES + 6 * fj;
-                            e[0] = wj0[0] * E.jd0;
-                            e[1] = wj1[1] * E.jd1;
-#pragma unroll
-                            for (int m = 2; m < 6; ++m) e[m] = fmaf(wj1[m], E.jd1, wj0[m] * E.jd0);
-                        }
+                        elo = make_float4(wj0[0] * E.jd0, wj1[1] * E.jd1, fmaf(wj1[2], E.jd1, wj0[2] * E.jd0), 0.f);
+                        ehi = make_float4(fmaf(wj1[3], E.jd1, wj0[3] * E.jd0), fmaf(wj1[4], E.jd1, wj0[4] * E.jd0),
+                                          fmaf(wj1[5], E.jd1, wj0[5] * E.jd0), 0.f);
                     }
+                }
+                if (jfree) {   // e_jk = J_j^T W J_d (zero for a missing or inactive edge)
+                    float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * fj);
+                    e4[0] = elo;
+                    e4[1] = ehi;
                 }
                 sc4[slot] = make_float4(Ce, we, Y0, Y1);
                 sc1[slot] = Y2;
             }
-        }
-        __syncthreads();   // tw no longer read: Mp may overwrite it
-        if (edge_thread) {
-            float *mp = Mp + (size_t)(my_g * W + my_jl) * 27;
+            float *mp = Mp + (size_t)tid * 27;
 #pragma unroll
             for (int q = 0; q < 21; ++q) mp[q] = M[q];
 #pragma unroll
             for (int q = 0; q < 6; ++q) mp[21 + q] = V[q];
         }
-        // per-patch finalisation: C_k, w_k, anchor column, scaling by C_k^-1/2
-        for (int p = tid; p < cnt; p += kThreads) {
-            float C = lam, w = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
-            for (int jl = 0; jl < W; ++jl) {
-                const float4 v = sc4[jl * Gs + p];
-                C += v.x;
-                w += v.y;
-                Y0 += v.z;
-                Y1 += v.w;
-                Y2 += sc1[jl * Gs + p];
+        __syncthreads();
+        // the staging buffers are free: start the next chunk's copies
+        if (have_next)
+            prefetch_chunk(pr, nx, depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
+                           c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur]);
+        {   // per-patch sums over the window by four lanes: C_k, w_k, Y; then
+            // C_k^-1/2, C_k^-1/2 w_k and the anchor column e_ik = -[d Y; pbar x Y]
+            const int p = tid >> 2, sub = tid & 3;
+            float C = sub == 0 ? lam : 0.f, w = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
+            if (p < cnt)
+                for (int jl = sub; jl < W; jl += 4) {
+                    const float4 v = sc4[jl * Gs + p];
+                    C += v.x;
+                    w += v.y;
+                    Y0 += v.z;
+                    Y1 += v.w;
+                    Y2 += sc1[jl * Gs + p];
+                }
+            C = quad_sum(C);
+            w = quad_sum(w);
+            Y0 = quad_sum(Y0);
+            Y1 = quad_sum(Y1);
+            Y2 = quad_sum(Y2);
+            if (p < cnt) {
+                float *e = Ec + p * ES;
+                if (sub == 0) {
+                    const float sq = sqrtf(1.0f / C);
+                    ps[p * 8] = sq;
+                    e[8 * nf] = sq * w;
+                } else if (anc_free && sub < 3) {
+                    const float4 qd = pd[p];
+                    const float d = qd.z, px = qd.x, py = qd.y;
+                    float4 *ei = reinterpret_cast<float4 *>(e + 8 * (anc - t0));
+                    if (sub == 1) ei[0] = make_float4(-d * Y0, -d * Y1, -d * Y2, 0.f);
+                    else                                   // -(pbar x Y), pbar = (px, py, 1)
+                        ei[1] = make_float4(-(py * Y2 - Y1), -(Y0 - px * Y2), -(px * Y1 - py * Y0), 0.f);
+                }
             }
-            float *e = Ec + p * ES;
-            if (anc_free) {
-                const float4 q = pd[p];
-                const float d = q.z, px = q.x, py = q.y;
-                float *ei = e + 6 * (anc - t0);
-                ei[0] = -d * Y0;
-                ei[1] = -d * Y1;
-                ei[2] = -d * Y2;
-                ei[3] = -(py * Y2 - Y1);          // -(pbar x Y), pbar = (px, py, 1)
-                ei[4] = -(Y0 - px * Y2);
-                ei[5] = -(px * Y1 - py * Y0);
-            }
-            const float sq = sqrtf(1.0f / C);
-            for (int m = 0; m < 6 * nf; ++m) e[m] *= sq;
-            e[6 * nf] = sq * w;
         }
         __syncthreads();
-        // combine the per-thread frame sums (M_j, v_j) over patch groups, compensated
-        for (int q = tid; q < W * 27; q += kThreads) {
-            const int jl = q / 27, m = q % 27;
-            float s = 0.f, cc = 0.f;
-            for (int g = 0; g < NG; ++g) kahan_add(s, cc, Mp[(size_t)(g * W + jl) * 27 + m]);
-            Mc[jl * 27 + m] = s - cc;
+        if (!group_next) {
+            // combine the per-thread frame sums (M_j, v_j) over patch groups, compensated
+            for (int q = tid; q < W * 27; q += kThreads) {
+                const int jl = q / 27, m = q - jl * 27;
+                float s = 0.f, cc = 0.f;
+                for (int g = 0; g < NG; ++g) kahan_add(s, cc, Mp[(size_t)(jl * NG + g) * 27 + m]);
+                Mc[jl * 27 + m] = s - cc;
+            }
+        }
+        {   // E_k (pose columns) scaled by C_k^-1/2
+            const int n4 = 2 * nf;
+            for (int p = tid >> 6; p < cnt; p += kThreads / 64) {
+                const float sq = ps[p * 8];
+                float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES);
+                for (int m = tid & 63; m < n4; m += 64) {
+                    float4 v = e4[m];
+                    v.x *= sq; v.y *= sq; v.z *= sq;
+                    e4[m] = v;
+                }
+            }
         }
         __syncthreads();
-        // pose-pair blocks that involve the anchor:
-        //   B_ij = -Ad_ij^T M_j,  B_ii = sum_j Ad_ij^T M_j Ad_ij,  v_i = -sum_j Ad_ij^T v_j
-        if (anc_free) {
+        if (!group_next && anc_free) {
+            // pose-pair blocks involving the anchor, per window frame j:
+            //   B_ij = -Ad_ij^T M_j,  B_ii += Ad_ij^T M_j Ad_ij,  v_i += -Ad_ij^T v_j
             for (int q = tid; q < W * 6; q += kThreads) {
-                const int jl = q / 6, r = q % 6;
+                const int jl = q / 6, r = q - jl * 6;
                 const float *Ad = adj + jl * 36;
                 const float *Mj = Mc + jl * 27;
                 float *A = Aj + jl * 42;
+                float *B = Bp + jl * 42;
+                const bool self = jlo + jl == anc;
+                float row[6];
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) {
                     float s = 0.f;
 #pragma unroll
                     for (int m = 0; m < 6; ++m) s = fmaf(Ad[6 * m + r], Mj[sym6(m, cc)], s);
+                    row[cc] = s;
                     A[6 * r + cc] = s;
                 }
                 float s = 0.f;
 #pragma unroll
                 for (int m = 0; m < 6; ++m) s = fmaf(Ad[6 * m + r], Mj[21 + m], s);
                 A[36 + r] = -s;
+                B[36 + r] = self ? 0.f : -s;
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) {
+                    float b = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) b = fmaf(row[m], Ad[6 * m + cc], b);
+                    B[6 * r + cc] = self ? 0.f : b;
+                }
             }
             __syncthreads();
             if (tid < 42) {
                 float s = 0.f, cc = 0.f;
-                if (tid < 36) {
-                    const int r = tid / 6, col = tid % 6;
-                    for (int jl = 0; jl < W; ++jl) {
-                        if (jlo + jl == anc) continue;
-                        const float *A = Aj + jl * 42;
-                        const float *Ad = adj + jl * 36;
-                        float v = 0.f;
-#pragma unroll
-                        for (int m = 0; m < 6; ++m) v = fmaf(A[6 * r + m], Ad[6 * m + col], v);
-                        kahan_add(s, cc, v);
-                    }
-                } else {
-                    const int r = tid - 36;
-                    for (int jl = 0; jl < W; ++jl) {
-                        if (jlo + jl == anc) continue;
-                        kahan_add(s, cc, Aj[jl * 42 + 36 + r]);
-                    }
-                }
+                for (int jl = 0; jl < W; ++jl) kahan_add(s, cc, Bp[jl * 42 + tid]);
                 Bii[tid] = s - cc;
             }
             __syncthreads();
         }
 
-        // -- (c) Schur accumulation over the chunk's patches, then the B blocks
+        // -- (c) Schur accumulation over the chunk's patches, then the group's B blocks
         if (owns) {
             int since = 0;
             if (!is_vstrip) {
                 for (int p = my_ks; p < cnt; p += KS) {
                     const float *e = Ec + p * ES;
-                    float ea[3], eb[6];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) ea[r] = e[6 * sa + 3 * sh + r];
-#pragma unroll
-                    for (int cc = 0; cc < 6; ++cc) eb[cc] = e[6 * sb + cc];
+                    const float4 a4 = *reinterpret_cast<const float4 *>(e + 8 * sa + 4 * sh);
+                    const float4 b0 = *reinterpret_cast<const float4 *>(e + 8 * sb);
+                    const float4 b1 = *reinterpret_cast<const float4 *>(e + 8 * sb + 4);
+                    const float ea[3] = {a4.x, a4.y, a4.z};
+                    const float eb[6] = {b0.x, b0.y, b0.z, b1.x, b1.y, b1.z};
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -594,9 +772,12 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
             } else {
                 for (int p = my_ks; p < cnt; p += KS) {
                     const float *e = Ec + p * ES;
-                    const float sw = e[6 * nf];
+                    const float sw = e[8 * nf];
+                    const float4 a0 = *reinterpret_cast<const float4 *>(e + 8 * sa);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(e + 8 * sa + 4);
+                    const float ea[6] = {a0.x, a0.y, a0.z, a1.x, a1.y, a1.z};
 #pragma unroll
-                    for (int cc = 0; cc < 6; ++cc) blk[cc] = fmaf(-e[6 * sa + cc], sw, blk[cc]);
+                    for (int cc = 0; cc < 6; ++cc) blk[cc] = fmaf(-ea[cc], sw, blk[cc]);
                     if (++since == kFlushEvery) {
 #pragma unroll
                         for (int q = 0; q < 6; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
@@ -606,7 +787,7 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
             }
 #pragma unroll
             for (int q = 0; q < 18; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
-            if (my_ks == 0) {
+            if (my_ks == 0 && !group_next) {
                 const int fa = t0 + sa, fb = t0 + sb;
                 const int ja = fa - jlo, jb = fb - jlo;
                 const bool a_in = ja >= 0 && ja < W, b_in = jb >= 0 && jb < W;
@@ -659,7 +840,10 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
             }
         }
         __syncthreads();
+        group_open = group_next;
+        cur ^= 1;
     }
+    cp_async_wait_all();
 
     // write this CTA's partial of (S, v')
     if (owns) {
@@ -680,16 +864,28 @@ __global__ void __launch_bounds__(kThreads) linearize_kernel(const Prob *__restr
 }
 
 // ----------------------------------------------------------------------------
-// solve_kernel: one CTA per problem.  Sums the Schur partials in FP64, factors
-// S = L L^T (FP64, right-looking, in shared memory), solves S dxi = v', and
-// retracts the free poses.  If S_out is non-null, writes (S, v') there instead
-// and changes nothing else.
+// solve_kernel: one CTA of kSolveThreads per problem.  Sums the Schur partials
+// in FP64 (fixed order), factors the reduced pose system by Cholesky in its
+// square-root-free form S = U D^-1 U^T (U lower, D = diag U) with the right-
+// hand side eliminated alongside, back-substitutes for the pose increments and
+// retracts the free poses in FP64.  A pivot <= 0 or NaN marks the problem
+// NOT_SPD.  If S_out is non-null, writes (S, v') there instead and changes
+// nothing else.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) solve_kernel(const Prob *__restrict__ probs, int t,
-                                                         double *S_out, double *v_out) {
+constexpr int kSolveThreads = 256;
+
+__device__ __forceinline__ double shfl_double(double x, int src) {
+    int lo = __double2loint(x), hi = __double2hiint(x);
+    lo = __shfl_sync(0xffffffffu, lo, src);
+    hi = __shfl_sync(0xffffffffu, hi, src);
+    return __hiloint2double(hi, lo);
+}
+
+__global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__restrict__ probs, int t,
+                                                              double *S_out, double *v_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Prob &pr = probs[blockIdx.x];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (t >= pr.iters) return;
     const int N = pr.N, t0 = pr.t0, nf = pr.nf, n = 6 * nf;
     const float *pose_cur = pr.pose_it + (size_t)t * N * 7;
@@ -700,8 +896,8 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(const Prob *__restrict_
     __syncthreads();
     if (s_flag != 0 || nf == 0) {
         if (S_out == nullptr) {
-            for (int q = tid; q < N * 7; q += kThreads) pose_next[q] = pose_cur[q];
-            for (int q = tid; q < nf * 6; q += kThreads) dxi[q] = 0.0;
+            for (int q = tid; q < N * 7; q += kSolveThreads) pose_next[q] = pose_cur[q];
+            for (int q = tid; q < nf * 6; q += kSolveThreads) dxi[q] = 0.0;
         }
         return;
     }
@@ -711,14 +907,23 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(const Prob *__restrict_
 
     // FP64 sum of the partials in a fixed order (deterministic)
     const int Lp = pr.L, nparts = pr.n_items * pr.ks, nbs = 2 * n_block_pairs(nf);
-    for (int q = tid; q < Lp; q += kThreads) {
+    for (int q = tid; q < Lp; q += kSolveThreads) {
         double acc = 0.0;
-        for (int part = 0; part < nparts; ++part) acc += pr.partial[(size_t)part * Lp + q];
+        const double *src = pr.partial + q;
+        int part = 0;
+        for (; part + 8 <= nparts; part += 8) {     // eight loads in flight, summed in order
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = src[(size_t)(part + u) * Lp];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += x[u];
+        }
+        for (; part < nparts; ++part) acc += src[(size_t)part * Lp];
         if (q < 18 * nbs) {
-            const int s = q / 18, e = q % 18;
+            const int st = q / 18, e = q - 18 * st;
             int a, b;
-            decode_pair(s >> 1, nf, a, b);
-            const int row = 6 * a + 3 * (s & 1) + e / 6, col = 6 * b + e % 6;
+            decode_pair(st >> 1, nf, a, b);
+            const int row = 6 * a + 3 * (st & 1) + e / 6, col = 6 * b + e % 6;
             S[row * ld + col] = acc;
             if (a != b) S[col * ld + row] = acc;
         } else {
@@ -727,58 +932,57 @@ __global__ void __launch_bounds__(kThreads) solve_kernel(const Prob *__restrict_
     }
     __syncthreads();
     if (S_out != nullptr) {
-        for (int q = tid; q < n * n; q += kThreads) S_out[q] = S[(q / n) * ld + q % n];
-        for (int q = tid; q < n; q += kThreads) v_out[q] = v[q];
+        for (int q = tid; q < n * n; q += kSolveThreads) S_out[q] = S[(q / n) * ld + q % n];
+        for (int q = tid; q < n; q += kSolveThreads) v_out[q] = v[q];
         return;
     }
-    // Cholesky, lower triangle, in place
+    // right-looking elimination of the lower triangle: thread (ty, tx) of a
+    // 16 x 16 grid updates rows i = ty mod 16, columns k = tx mod 16
+    const int ty = tid >> 4, tx = tid & 15;
     for (int j = 0; j < n; ++j) {
-        if (tid == 0) {
-            const double piv = S[j * ld + j];
-            if (!(piv > 0.0)) s_flag = DPVO_BA_STATUS_NOT_SPD;
-            else S[j * ld + j] = sqrt(piv);
+        const double piv = S[j * ld + j];
+        if (!(piv > 0.0)) {
+            if (tid == 0) s_flag = DPVO_BA_STATUS_NOT_SPD;
+            break;
         }
-        __syncthreads();
-        if (s_flag) break;
-        const double djj = S[j * ld + j];
-        for (int i = j + 1 + tid; i < n; i += kThreads) S[i * ld + j] /= djj;
-        __syncthreads();
-        const int m = n - j - 1;
-        for (int q = tid; q < m * m; q += kThreads) {
-            const int ii = q / m, kk = q % m;
-            if (kk <= ii) S[(j + 1 + ii) * ld + j + 1 + kk] -= S[(j + 1 + ii) * ld + j] * S[(j + 1 + kk) * ld + j];
+        double ip = 0.0;
+        if (lane == 0) ip = 1.0 / piv;
+        ip = shfl_double(ip, 0);
+        const double vj = v[j];
+        for (int i = j + 1 + ty; i < n; i += 16) {
+            const double lij = S[i * ld + j] * ip;
+            double *row = S + i * ld;
+#pragma unroll 4
+            for (int k = j + 1 + tx; k <= i; k += 16) row[k] -= lij * S[k * ld + j];
+            if (tx == 0) v[i] -= lij * vj;
         }
         __syncthreads();
     }
-    if (!s_flag) {
-        // L y = v'
-        for (int j = 0; j < n; ++j) {
-            if (tid == 0) v[j] /= S[j * ld + j];
-            __syncthreads();
-            for (int i = j + 1 + tid; i < n; i += kThreads) v[i] -= S[i * ld + j] * v[j];
-            __syncthreads();
-        }
-        // L^T x = y
+    __syncthreads();
+    if (!s_flag && tid < 32) {
+        // U^T x = v' (back substitution, one warp): x_j = v_j / U_jj, v_i -= U_ji x_j
         for (int j = n - 1; j >= 0; --j) {
-            if (tid == 0) v[j] /= S[j * ld + j];
-            __syncthreads();
-            for (int i = tid; i < j; i += kThreads) v[i] -= S[j * ld + i] * v[j];
-            __syncthreads();
+            double xj = 0.0;
+            if (lane == 0) xj = v[j] / S[j * ld + j];
+            xj = shfl_double(xj, 0);
+            for (int i = lane; i < j; i += 32) v[i] -= S[j * ld + i] * xj;
+            __syncwarp();
+            if (lane == 0) v[j] = xj;
+            __syncwarp();
         }
-        if (tid == 0) {
-            for (int q = 0; q < n; ++q)
-                if (!isfinite(v[q])) s_flag = DPVO_BA_STATUS_NONFINITE;
-        }
-        __syncthreads();
+        bool bad = false;
+        for (int q = lane; q < n; q += 32) bad |= !isfinite(v[q]);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) s_flag = DPVO_BA_STATUS_NONFINITE;
     }
+    __syncthreads();
     if (s_flag) {
         if (tid == 0) *pr.status = s_flag;
-        for (int q = tid; q < N * 7; q += kThreads) pose_next[q] = pose_cur[q];
-        for (int q = tid; q < nf * 6; q += kThreads) dxi[q] = 0.0;
+        for (int q = tid; q < N * 7; q += kSolveThreads) pose_next[q] = pose_cur[q];
+        for (int q = tid; q < nf * 6; q += kSolveThreads) dxi[q] = 0.0;
         return;
     }
-    for (int q = tid; q < n; q += kThreads) dxi[q] = v[q];
-    for (int a = tid; a < N; a += kThreads) {
+    for (int q = tid; q < n; q += kSolveThreads) dxi[q] = v[q];
+    for (int a = tid; a < N; a += kSolveThreads) {
         if (a >= t0) se3_left_update(v + 6 * (a - t0), pose_cur + 7 * a, pose_next + 7 * a);
         else
             for (int q = 0; q < 7; ++q) pose_next[7 * a + q] = pose_cur[7 * a + q];
