@@ -134,6 +134,32 @@ int dpvo_ba_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_pro
 int dpvo_ba_solve_host(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *hprobs,
                        int n_problems, void *stream);
 
+/* Gradient buffers of one problem for dpvo_ba_backward (DEVICE pointers, caller-owned).
+ *   dL_dposes  [N][7]  dL/d(final poses), same layout as the poses      (read)
+ *   dL_ddepth  [P]     dL/d(final inverse depths)                        (read)
+ *   dL_dtarget [E][2]  dL/d(targets)                                     (written)
+ *   dL_dweight [E][2]  dL/d(weights)                                     (written)            */
+typedef struct {
+    const float *dL_dposes;
+    const float *dL_ddepth;
+    float *dL_dtarget;
+    float *dL_dweight;
+} dpvo_ba_grads;
+
+/* Backward pass of the layer (Sec. 3.1: gradients are propagated through the
+ * Gauss-Newton iterations).  probs[b] describes the problem's state at the
+ * START of the forward solve; it is read, never modified.  The forward
+ * iterations are recomputed (only the small per-iteration states, increments
+ * and FP64 reduced-system factors are kept in the workspace), then the
+ * adjoint runs back through every iteration: retraction (SE(3) left
+ * Jacobian), linear solve (Schur complement with the kept factor), and the
+ * per-edge residual and Jacobian terms including the Jacobian's own
+ * derivative.  Inactive edges and self edges get zero gradient; a problem
+ * whose status is not OK gets zero gradients.  Asynchronous on stream.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int dpvo_ba_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
+                     const dpvo_ba_grads *grads, int n_problems, void *stream);
+
 /* Diagnostic: the reduced pose system of ONE linearisation at the given state
  * (no update).  S_out [n][n] and v_out [n] are DEVICE float64 arrays with
  * n = 6 (N - t0): S = B - E C^-1 E^T and v' = v - E C^-1 w (Sec. 3.1, Schur

@@ -30,6 +30,11 @@ class Config(ctypes.Structure):
                 ("max_sessions", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class Grads(ctypes.Structure):
+    _fields_ = [("dL_dposes", ctypes.c_void_p), ("dL_ddepth", ctypes.c_void_p), ("dL_dtarget", ctypes.c_void_p),
+                ("dL_dweight", ctypes.c_void_p)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("poses", ctypes.c_void_p), ("patches", ctypes.c_void_p), ("anchor", ctypes.c_void_p),
                 ("kk", ctypes.c_void_p), ("jj", ctypes.c_void_p), ("target", ctypes.c_void_p),
@@ -43,7 +48,7 @@ MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 15, 16
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solve", "dpvo_ba_solve_host",
            "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_set_timing", "dpvo_ba_timing",
-           "dpvo_ba_solve_noalloc", "dpvo_ba_strerror"]
+           "dpvo_ba_solve_noalloc", "dpvo_ba_backward", "dpvo_ba_strerror"]
 
 _lib = None
 
@@ -73,6 +78,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_set_timing.argtypes = [vp, i32]
     lib.dpvo_ba_timing.argtypes = [vp, vp, vp, i32]
     lib.dpvo_ba_solve_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Dims), ctypes.POINTER(Problem), vp]
+    lib.dpvo_ba_backward.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), ctypes.POINTER(Grads), i32, vp]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -239,6 +245,19 @@ class Solver:
             raise BAError(n, "dpvo_ba_timing")
         return [(int(kinds[i]), float(ms[i])) for i in range(n)]
 
+    def backward(self, problems: List[BAProblem], dL_dposes: List[torch.Tensor], dL_ddepth: List[torch.Tensor],
+                 stream=None):
+        """dL/dtarget and dL/dweight of every problem, given the gradients of a loss
+        w.r.t. the final poses [N, 7] and final inverse depths [P].  ``problems``
+        hold the state at the START of the forward solve (not modified)."""
+        n, dims, probs = self._arrays(problems)
+        gts = [torch.empty_like(p.target) for p in problems]
+        gws = [torch.empty_like(p.weight) for p in problems]
+        keep = [t.contiguous() for t in dL_dposes] + [t.contiguous() for t in dL_ddepth]
+        gr = (Grads * n)(*[Grads(keep[b].data_ptr(), keep[n + b].data_ptr(), gts[b].data_ptr(), gws[b].data_ptr())
+                           for b in range(n)])
+        _check(self.lib.dpvo_ba_backward(self.h, dims, probs, gr, n, _stream_ptr(stream)), "dpvo_ba_backward")
+        return gts, gws
 
 class PackedBatch:
     """Many problems packed back to back in one tensor per array kind, with the
@@ -301,3 +320,46 @@ class PackedBatch:
 
     def bytes_of(self, names) -> int:
         return int(sum(self.flat[n].numel() * self.flat[n].element_size() for n in names))
+
+_default_solver = None
+
+
+def default_solver() -> Solver:
+    global _default_solver
+    if _default_solver is None:
+        _default_solver = Solver()
+    return _default_solver
+
+
+class DPVOBAFunction(torch.autograd.Function):
+    """Differentiable bundle-adjustment layer: (poses, patches, target, weight)
+    -> (final poses, final patches), differentiable w.r.t. the targets and the
+    weights (the flow revisions and confidences of the update operator).
+
+    apply(poses [N,7], patches [P,3], target [E,2], weight [E,2], anchor, kk, jj,
+          intrinsics (fx, fy, cx, cy), t0, n_iters=2, solver=None)
+    """
+
+    @staticmethod
+    def forward(ctx, poses, patches, target, weight, anchor, kk, jj, intrinsics, t0, n_iters=2, solver=None):
+        solver = solver or default_solver()
+        out_poses = poses.detach().clone().contiguous()
+        out_patches = patches.detach().clone().contiguous()
+        prob = BAProblem(out_poses, out_patches, anchor.contiguous(), kk.contiguous(), jj.contiguous(),
+                         target.detach().contiguous(), weight.detach().contiguous(), intrinsics, t0, n_iters)
+        solver.solve([prob])
+        ctx.save_for_backward(poses.detach().contiguous(), patches.detach().contiguous(),
+                              target.detach().contiguous(), weight.detach().contiguous(), anchor, kk, jj)
+        ctx.meta = (intrinsics, t0, n_iters, solver)
+        return out_poses, out_patches
+
+    @staticmethod
+    def backward(ctx, g_poses, g_patches):
+        poses, patches, target, weight, anchor, kk, jj = ctx.saved_tensors
+        intrinsics, t0, n_iters, solver = ctx.meta
+        prob = BAProblem(poses, patches, anchor, kk, jj, target, weight, intrinsics, t0, n_iters)
+        if g_poses is None:
+            g_poses = torch.zeros_like(poses)
+        g_depth = g_patches[:, 2].contiguous() if g_patches is not None else torch.zeros_like(patches[:, 2])
+        gts, gws = solver.backward([prob], [g_poses.contiguous()], [g_depth])
+        return None, None, gts[0], gws[0], None, None, None, None, None, None, None

@@ -46,6 +46,20 @@ struct Prob {
     float *depth_it;         // [iters + 1][P]
     double *dxi;             // [iters][nf][6] pose increments
     double *partial;         // [n_items][ks][L] Schur partial sums
+    // backward (adjoint) state; null / zero for a plain solve
+    int store_factor;        // keep the factored reduced system of every iteration
+    int no_writeback;        // leave the caller's poses and patches untouched
+    double *ufac;            // [iters][n (n + 1) / 2] factor U (lower, row-major) of each iteration
+    const float *dL_dposes;  // [N][7] gradient of the loss w.r.t. the final poses
+    const float *dL_ddepth;  // [P] gradient w.r.t. the final inverse depths
+    float *dL_dtarget;       // [E][2] output
+    float *dL_dweight;       // [E][2] output
+    double *eps;             // [N][6] pose gradient (left-perturbation coordinates)
+    double *dxibar;          // [nf][6] gradient w.r.t. the pose increment of the current iteration
+    double *yxi;             // [nf][6] adjoint solution, pose part
+    float *dbar;             // [P] gradient w.r.t. the inverse depths of the current state
+    double *pgrad;           // [n_items][N][6] per-CTA pose-gradient partial sums
+
     int max_chunks;
     int n_items;             // linearise work items (CTAs) of this problem
     int ks;                  // patch-parity split of the Schur accumulation

@@ -9,6 +9,7 @@
 #include "dpvo_ba.h"
 #include "ba_common.cuh"
 #include "kernels.cuh"
+#include "backward.cuh"
 
 using namespace dpvo;
 
@@ -44,7 +45,7 @@ int check_problem(const dpvo_ba_dims &d, const dpvo_ba_problem &p) {
     return DPVO_BA_OK;
 }
 
-Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_config &cfg) {
+Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_config &cfg, bool adjoint = false) {
     Layout L;
     int n_max = 1;
     for (int b = 0; b < n; ++b) {
@@ -90,6 +91,17 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.depth_it = (float *)(uintptr_t)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
         p.dxi = (double *)(uintptr_t)take((size_t)d.n_iters * p.nf * 6 * 8 + 8);
         p.partial = (double *)(uintptr_t)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
+        if (adjoint) {
+            const size_t n6 = 6 * (size_t)p.nf;
+            p.store_factor = 1;
+            p.no_writeback = 1;
+            p.ufac = (double *)(uintptr_t)take((size_t)d.n_iters * (n6 * (n6 + 1) / 2) * 8 + 8);
+            p.eps = (double *)(uintptr_t)take((size_t)d.n_frames * 6 * 8);
+            p.dxibar = (double *)(uintptr_t)take(n6 * 8 + 8);
+            p.yxi = (double *)(uintptr_t)take(n6 * 8 + 8);
+            p.dbar = (float *)(uintptr_t)take((size_t)d.n_patches * 4 + 4);
+            p.pgrad = (double *)(uintptr_t)take((size_t)p.n_items * d.n_frames * 6 * 8);
+        }
         for (int w = 0; w < p.n_items; ++w) L.items.push_back(Item{b, w});
     }
     L.off_probs = off;
@@ -178,6 +190,9 @@ static int set_kernel_attrs(int device) {
     if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
         return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(bw_edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess)
+        return DPVO_BA_ECUDA;
     if (device >= 0 && device < 64) g_attr_set[device] = true;
     return DPVO_BA_OK;
 }
@@ -231,13 +246,13 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     if ((rc = timed(0, [&] { plan_kernel<<<n, kThreads, 0, stream>>>(d_probs); }))) return rc;
     if (S_out) {
         linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, 0, L.W_cap, L.G_cap,
-                                                                     L.nf_max, L.n_max);
+                                                                     L.nf_max, L.n_max, 0);
         solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, 0, S_out, v_out);
     } else {
         for (int t = 0; t <= L.iters_max; ++t) {
             rc = timed(1, [&] {
                 linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap,
-                                                                             L.G_cap, L.nf_max, L.n_max);
+                                                                             L.G_cap, L.nf_max, L.n_max, 0);
             });
             if (rc) return rc;
             if (t < L.iters_max) {
@@ -252,7 +267,84 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     return DPVO_BA_OK;
 }
 
+// Forward with the factors kept and the caller's state untouched, then the
+// adjoint iterations from the last one back to the first.
+static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
+                        const dpvo_ba_grads *grads, int n, cudaStream_t stream) {
+    Layout L = make_layout(dims, n, h->num_sms, h->cfg, true);
+    int rc = grow_device(&h->ws, &h->ws_cap, L.bytes);
+    if (rc) return rc;
+    const size_t desc_bytes = L.bytes - L.off_probs;
+    rc = grow_stage(h, desc_bytes);
+    if (rc) return rc;
+    for (int b = 0; b < n; ++b) {
+        Prob &p = L.probs[b];
+        const dpvo_ba_problem &q = probs[b];
+        p.poses = q.poses; p.patches = q.patches; p.anchor = q.anchor; p.kk = q.kk; p.jj = q.jj;
+        p.target = q.target; p.weight = q.weight; p.status_user = q.status;
+        p.dL_dposes = grads[b].dL_dposes;
+        p.dL_ddepth = grads[b].dL_ddepth;
+        p.dL_dtarget = grads[b].dL_dtarget;
+        p.dL_dweight = grads[b].dL_dweight;
+        p.seg = rebase(p.seg, h->ws);
+        p.chunks = rebase(p.chunks, h->ws);
+        p.n_chunks = rebase(p.n_chunks, h->ws);
+        p.status = rebase(p.status, h->ws);
+        p.pose_it = rebase(p.pose_it, h->ws);
+        p.depth_it = rebase(p.depth_it, h->ws);
+        p.dxi = rebase(p.dxi, h->ws);
+        p.partial = rebase(p.partial, h->ws);
+        p.ufac = rebase(p.ufac, h->ws);
+        p.eps = rebase(p.eps, h->ws);
+        p.dxibar = rebase(p.dxibar, h->ws);
+        p.yxi = rebase(p.yxi, h->ws);
+        p.dbar = rebase(p.dbar, h->ws);
+        p.pgrad = rebase(p.pgrad, h->ws);
+    }
+    h->last = L.probs;
+    std::memcpy(h->stage, L.probs.data(), sizeof(Prob) * n);
+    std::memcpy(h->stage + (L.off_items - L.off_probs), L.items.data(), sizeof(Item) * L.items.size());
+    if (cudaMemcpyAsync(h->ws + L.off_probs, h->stage, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaEventRecord(h->stage_done, stream) != cudaSuccess) return DPVO_BA_ECUDA;
+    h->stage_pending = true;
+    const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
+    const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
+    const int n_items = (int)L.items.size();
+    const size_t bw_smem = bw_smem_layout(L.W_cap, L.G_cap, L.n_max).bytes;
+    plan_kernel<<<n, kThreads, 0, stream>>>(d_probs);
+    for (int t = 0; t <= L.iters_max; ++t) {
+        linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap,
+                                                                     L.nf_max, L.n_max, 0);
+        if (t < L.iters_max) solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+    }
+    bw_init_kernel<<<n, kThreads, 0, stream>>>(d_probs);
+    for (int t = L.iters_max - 1; t >= 0; --t) {
+        bw_retract_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
+        linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap,
+                                                                     L.nf_max, L.n_max, 1);
+        bw_solve_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
+        bw_edge_kernel<<<n_items, kThreads, bw_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap, L.n_max);
+    }
+    if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
+    return DPVO_BA_OK;
+}
+
 extern "C" {
+
+int dpvo_ba_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
+                     const dpvo_ba_grads *grads, int n_problems, void *stream) {
+    if (!h || !dims || !probs || !grads || n_problems < 1) return DPVO_BA_EINVAL;
+    for (int b = 0; b < n_problems; ++b) {
+        if (int rc = check_dims(dims[b])) return rc;
+        if (int rc = check_problem(dims[b], probs[b])) return rc;
+        const dpvo_ba_grads &g = grads[b];
+        if (!g.dL_dposes || (dims[b].n_patches > 0 && !g.dL_ddepth) ||
+            (dims[b].n_edges > 0 && (!g.dL_dtarget || !g.dL_dweight)))
+            return DPVO_BA_EINVAL;
+    }
+    return run_backward(h, dims, probs, grads, n_problems, (cudaStream_t)stream);
+}
 
 int dpvo_ba_create(const dpvo_ba_config *cfg, dpvo_ba_handle **out) {
     if (!out) return DPVO_BA_EINVAL;
@@ -576,7 +668,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     plan_kernel<<<1, kThreads, 0, stream>>>(d_prob);
     for (int t = 0; t <= d.n_iters; ++t) {
         linearize_kernel<<<p.n_items, kThreads, lin_smem, stream>>>(d_prob, d_items, t, W_cap, G_cap, nf,
-                                                                     d.n_frames);
+                                                                     d.n_frames, 0);
         if (t < d.n_iters) solve_kernel<<<1, kSolveThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
     }
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;

@@ -336,15 +336,19 @@ __device__ __forceinline__ float quad_sum(float v) {
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__restrict__ probs,
                                                              const Item *__restrict__ items, int t,
-                                                             int W_cap, int G_cap, int nf_max, int n_max) {
+                                                             int W_cap, int G_cap, int nf_max, int n_max,
+                                                             int adjoint_rhs) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
     const int tid = threadIdx.x;
     if (t > pr.iters) return;
-    const bool do_bs = t > 0;
+    // adjoint_rhs: linearise at iterate t only and accumulate the pose part of
+    // E C^-1 dbar (dbar = gradient w.r.t. the inverse depths) into the
+    // right-hand-side strips, for the adjoint solve of iteration t
+    const bool do_bs = t > 0 && !adjoint_rhs;
     const bool do_lin = t < pr.iters;
-    const bool final_pass = t == pr.iters;
+    const bool final_pass = t == pr.iters && !adjoint_rhs;
     {
         const int st = *pr.status;
         if (final_pass && itm.item == 0 && tid == 0 && pr.status_user) *pr.status_user = st;
@@ -399,8 +403,8 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     const int KS = pr.ks;
     const int my_strip = nst > 0 ? tid % nst : 0;
     const int my_ks = nst > 0 ? tid / nst : KS;
-    const bool owns = do_lin && nst > 0 && my_ks < KS;
     const bool is_vstrip = my_strip >= nbs;
+    const bool owns = do_lin && nst > 0 && my_ks < KS && (is_vstrip || !adjoint_rhs);
     int sa = 0, sb = 0, sh = 0;
     if (owns) {
         if (!is_vstrip) {
@@ -560,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     const float dnew = pd[p].z + (w - s) / C;
                     pd[p].z = dnew;
                     depth_new[k0 + p] = dnew;
-                    if (final_pass) pr.patches[3 * (k0 + p) + 2] = dnew;
+                    if (final_pass && !pr.no_writeback) pr.patches[3 * (k0 + p) + 2] = dnew;
                 }
             }
             if (!do_lin) {
@@ -673,7 +677,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 if (sub == 0) {
                     const float sq = sqrtf(1.0f / C);
                     ps[p * 8] = sq;
-                    e[8 * nf] = sq * w;
+                    e[8 * nf] = sq * (adjoint_rhs ? pr.dbar[k0 + p] : w);
                 } else if (anc_free && sub < 3) {
                     const float4 qd = pd[p];
                     const float d = qd.z, px = qd.x, py = qd.y;
@@ -685,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
         }
         __syncthreads();
-        if (!group_next) {
+        if (!group_next && !adjoint_rhs) {
             // combine the per-thread frame sums (M_j, v_j) over patch groups, compensated
             for (int q = tid; q < W * 27; q += kThreads) {
                 const int jl = q / 27, m = q - jl * 27;
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
         }
         __syncthreads();
-        if (!group_next && anc_free) {
+        if (!group_next && anc_free && !adjoint_rhs) {
             // pose-pair blocks involving the anchor, per window frame j:
             //   B_ij = -Ad_ij^T M_j,  B_ii += Ad_ij^T M_j Ad_ij,  v_i += -Ad_ij^T v_j
             for (int q = tid; q < W * 6; q += kThreads) {
@@ -787,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
 #pragma unroll
             for (int q = 0; q < 18; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
-            if (my_ks == 0 && !group_next) {
+            if (my_ks == 0 && !group_next && !adjoint_rhs) {
                 const int fa = t0 + sa, fb = t0 + sb;
                 const int ja = fa - jlo, jb = fb - jlo;
                 const bool a_in = ja >= 0 && ja < W, b_in = jb >= 0 && jb < W;
@@ -858,7 +862,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             for (int q = 0; q < 6; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
         }
     }
-    if (final_pass && itm.item == 0) {
+    if (final_pass && itm.item == 0 && !pr.no_writeback) {
         for (int q = tid; q < N * 7; q += kThreads) pr.poses[q] = pose_new[q];
     }
 }
@@ -959,6 +963,13 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         __syncthreads();
     }
     __syncthreads();
+    if (!s_flag && pr.store_factor) {   // keep U for the adjoint solve
+        double *u = pr.ufac + (size_t)t * (n * (n + 1) / 2);
+        for (int q = tid; q < n * n; q += kSolveThreads) {
+            const int i = q / n, k = q - i * n;
+            if (k <= i) u[i * (i + 1) / 2 + k] = S[i * ld + k];
+        }
+    }
     if (!s_flag && tid < 32) {
         // U^T x = v' (back substitution, one warp): x_j = v_j / U_jj, v_i -= U_ji x_j
         for (int j = n - 1; j >= 0; --j) {
