@@ -160,6 +160,57 @@ typedef struct {
 int dpvo_ba_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
                      const dpvo_ba_grads *grads, int n_problems, void *stream);
 
+/* ---- serving: many concurrent VO sessions, continuously batched ----------
+ * (The paper's VO system runs one bundle adjustment per frame, Sec. 3.3; these
+ * calls serve many such streams from one GPU.)  A session keeps one problem's
+ * graph and state resident in device memory owned by the library; each request
+ * brings new targets and weights (host memory) for one session and runs
+ * n_iters Gauss-Newton iterations on the session's current state.  A
+ * scheduler thread packs every pending request into the next batched solve as
+ * soon as one of max_in_flight launch slots is free, so requests that arrive
+ * while a batch runs join the next batch and batches overlap on the device.
+ * Sessions are admitted against cfg.mem_budget_bytes (their resident arrays;
+ * the slots' workspaces are reserved at start and not counted).  A session
+ * takes one request at a time.  Every wait is bounded; none traps. */
+
+/* Start the scheduler.  max_dims bounds every session's sizes (as for
+ * dpvo_ba_reserve); max_batch requests per launch; 1..8 launch slots.
+ * Errors: EINVAL, EBUSY (already started), ENOMEM. */
+int dpvo_ba_serve_start(dpvo_ba_handle *h, const dpvo_ba_dims *max_dims, int max_batch, int max_in_flight);
+
+/* Stop the scheduler, wait for the launches in flight, close every session.
+ * Also done by dpvo_ba_destroy. */
+int dpvo_ba_serve_stop(dpvo_ba_handle *h);
+
+/* Open a session from HOST arrays (layouts of dpvo_ba_problem; status unused).
+ * The data are copied; the caller may free them on return.  EBUSY when the
+ * session does not fit in the remaining memory budget (not admitted: retry
+ * after closing another).  Errors: EINVAL, EBUSY, ENOMEM, ECUDA. */
+int dpvo_ba_session_open(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *host_problem,
+                         int64_t *session_id);
+
+/* Close a session once its request (if any) has finished (waits up to 10 s:
+ * ETIMEOUT) and release its memory.  Errors: EINVAL, ENOTFOUND, ETIMEOUT. */
+int dpvo_ba_session_close(dpvo_ba_handle *h, int64_t session_id);
+
+/* Copy a session's current poses [N][7] and patches [P][3] to HOST memory (either
+ * may be NULL); waits up to 10 s for its request to finish.  Synchronous. */
+int dpvo_ba_session_read(dpvo_ba_handle *h, int64_t session_id, float *poses_out, float *patches_out);
+
+/* Queue a request on a session: target and weight are HOST arrays [E][2],
+ * copied before the call returns.  EBUSY if the session's previous request has
+ * not finished.  Errors: EINVAL, ENOTFOUND, EBUSY. */
+int dpvo_ba_submit(dpvo_ba_handle *h, int64_t session_id, const float *target, const float *weight,
+                   uint64_t *ticket);
+
+/* Non-blocking: DPVO_BA_OK and the request's status bits and latency (submit to
+ * completion on the device, milliseconds) when done -- a ticket is collected
+ * once; EBUSY while pending; ENOTFOUND for an unknown or collected ticket. */
+int dpvo_ba_poll(dpvo_ba_handle *h, uint64_t ticket, int32_t *status, double *latency_ms);
+
+/* Blocking form of dpvo_ba_poll, bounded by timeout_ms (ETIMEOUT). */
+int dpvo_ba_wait(dpvo_ba_handle *h, uint64_t ticket, int timeout_ms, int32_t *status, double *latency_ms);
+
 /* Diagnostic: the reduced pose system of ONE linearisation at the given state
  * (no update).  S_out [n][n] and v_out [n] are DEVICE float64 arrays with
  * n = 6 (N - t0): S = B - E C^-1 E^T and v' = v - E C^-1 w (Sec. 3.1, Schur

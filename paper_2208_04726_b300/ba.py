@@ -48,7 +48,9 @@ MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 15, 16
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solve", "dpvo_ba_solve_host",
            "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_set_timing", "dpvo_ba_timing",
-           "dpvo_ba_solve_noalloc", "dpvo_ba_backward", "dpvo_ba_strerror"]
+           "dpvo_ba_solve_noalloc", "dpvo_ba_backward", "dpvo_ba_serve_start",
+           "dpvo_ba_serve_stop", "dpvo_ba_session_open", "dpvo_ba_session_close", "dpvo_ba_session_read",
+           "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror"]
 
 _lib = None
 
@@ -79,6 +81,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_timing.argtypes = [vp, vp, vp, i32]
     lib.dpvo_ba_solve_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Dims), ctypes.POINTER(Problem), vp]
     lib.dpvo_ba_backward.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), ctypes.POINTER(Grads), i32, vp]
+    i64, u64p = ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)
+    lib.dpvo_ba_serve_start.argtypes = [vp, ctypes.POINTER(Dims), i32, i32]
+    lib.dpvo_ba_serve_stop.argtypes = [vp]
+    lib.dpvo_ba_session_open.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem), ctypes.POINTER(i64)]
+    lib.dpvo_ba_session_close.argtypes = [vp, i64]
+    lib.dpvo_ba_session_read.argtypes = [vp, i64, vp, vp]
+    lib.dpvo_ba_submit.argtypes = [vp, i64, vp, vp, u64p]
+    lib.dpvo_ba_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
+    lib.dpvo_ba_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_double)]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -258,6 +270,62 @@ class Solver:
                            for b in range(n)])
         _check(self.lib.dpvo_ba_backward(self.h, dims, probs, gr, n, _stream_ptr(stream)), "dpvo_ba_backward")
         return gts, gws
+
+    # ---- serving --------------------------------------------------------------
+    def serve_start(self, max_frames: int, max_patches: int, max_edges: int, max_iters: int = 2,
+                    max_batch: int = 64, max_in_flight: int = 2):
+        d = Dims(max_frames, max_patches, max_edges, 0, max_iters, 1.0, 1.0, 0.0, 0.0)
+        _check(self.lib.dpvo_ba_serve_start(self.h, ctypes.byref(d), max_batch, max_in_flight), "dpvo_ba_serve_start")
+
+    def serve_stop(self):
+        _check(self.lib.dpvo_ba_serve_stop(self.h), "dpvo_ba_serve_stop")
+
+    def session_open(self, scene, n_iters=None) -> int:
+        """Open a session from a scenes.Scene (host arrays copied to the device)."""
+        fx, fy, cx, cy = (float(v) for v in scene.intrinsics)
+        it = scene.n_iters if n_iters is None else n_iters
+        d = Dims(scene.n_frames, scene.n_patches, scene.n_edges, scene.t0, it, fx, fy, cx, cy)
+        arrs = [np.ascontiguousarray(a) for a in (scene.poses, scene.patches, scene.anchor, scene.kk, scene.jj,
+                                                   scene.target, scene.weight)]
+        p = Problem(*[a.ctypes.data for a in arrs], None)
+        sid = ctypes.c_int64()
+        rc = self.lib.dpvo_ba_session_open(self.h, ctypes.byref(d), ctypes.byref(p), ctypes.byref(sid))
+        _check(rc, "dpvo_ba_session_open")
+        return sid.value
+
+    def session_close(self, sid: int):
+        _check(self.lib.dpvo_ba_session_close(self.h, sid), "dpvo_ba_session_close")
+
+    def session_read(self, sid: int, n_frames: int, n_patches: int):
+        poses = np.empty((n_frames, 7), np.float32)
+        patches = np.empty((n_patches, 3), np.float32)
+        _check(self.lib.dpvo_ba_session_read(self.h, sid, poses.ctypes.data, patches.ctypes.data),
+               "dpvo_ba_session_read")
+        return poses, patches
+
+    def submit(self, sid: int, target: np.ndarray, weight: np.ndarray) -> int:
+        t = np.ascontiguousarray(target, np.float32)
+        w = np.ascontiguousarray(weight, np.float32)
+        tk = ctypes.c_uint64()
+        _check(self.lib.dpvo_ba_submit(self.h, sid, t.ctypes.data, w.ctypes.data, ctypes.byref(tk)), "dpvo_ba_submit")
+        return tk.value
+
+    def poll(self, ticket: int):
+        """(done, status, latency_ms)."""
+        st, lat = ctypes.c_int32(), ctypes.c_double()
+        rc = self.lib.dpvo_ba_poll(self.h, ticket, ctypes.byref(st), ctypes.byref(lat))
+        if rc == EBUSY:
+            return False, None, None
+        _check(rc, "dpvo_ba_poll")
+        return True, st.value, lat.value
+
+    def wait(self, ticket: int, timeout_ms: int = 10000):
+        """(status, latency_ms); raises BAError(ETIMEOUT) when the bound runs out."""
+        st, lat = ctypes.c_int32(), ctypes.c_double()
+        _check(self.lib.dpvo_ba_wait(self.h, ticket, timeout_ms, ctypes.byref(st), ctypes.byref(lat)), "dpvo_ba_wait")
+        return st.value, lat.value
+
+
 
 class PackedBatch:
     """Many problems packed back to back in one tensor per array kind, with the

@@ -10,6 +10,7 @@
 #include "ba_common.cuh"
 #include "kernels.cuh"
 #include "backward.cuh"
+#include "serve.cuh"
 
 using namespace dpvo;
 
@@ -134,6 +135,7 @@ struct dpvo_ba_handle {
     std::vector<cudaEvent_t> ev;    // event pool: (start, end) per timed launch
     std::vector<int> ev_kind;       // kernel of each timed launch
     int ev_used = 0;                // events recorded since the last read
+    dpvo_serve::Server *srv = nullptr;   // serving runtime, if started
 };
 
 static int timed_event(dpvo_ba_handle *h, cudaStream_t s) {
@@ -267,6 +269,8 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     return DPVO_BA_OK;
 }
 
+static int serve_stop_impl(dpvo_ba_handle *h);
+
 // Forward with the factors kept and the caller's state untouched, then the
 // adjoint iterations from the last one back to the first.
 static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
@@ -375,6 +379,7 @@ int dpvo_ba_create(const dpvo_ba_config *cfg, dpvo_ba_handle **out) {
 
 int dpvo_ba_destroy(dpvo_ba_handle *h) {
     if (!h) return DPVO_BA_EINVAL;
+    serve_stop_impl(h);
     cudaDeviceSynchronize();
     if (h->ws) cudaFree(h->ws);
     if (h->io) cudaFree(h->io);
@@ -567,6 +572,342 @@ const char *dpvo_ba_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Serving runtime (see serve.cuh).
+// ----------------------------------------------------------------------------
+using dpvo_serve::Clock;
+using dpvo_serve::Server;
+using dpvo_serve::Session;
+using dpvo_serve::Slot;
+using dpvo_serve::Ticket;
+
+static size_t session_bytes(const dpvo_ba_dims &d) {
+    const size_t N = d.n_frames, P = d.n_patches, E = d.n_edges;
+    return al256(N * 28) + al256(P * 12) + al256(P * 4) + 2 * al256(E * 4) + 2 * al256(E * 8) + 256;
+}
+
+static void CUDART_CB serve_batch_done(void *arg) {
+    Slot *slot = static_cast<Slot *>(arg);
+    Server *srv = slot->srv;
+    const auto now = Clock::now();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    for (uint64_t tk : slot->batch) {
+        auto it = srv->tickets.find(tk);
+        if (it == srv->tickets.end()) continue;
+        Ticket &t = it->second;
+        auto ss = srv->sessions.find(t.session);
+        if (ss != srv->sessions.end()) {
+            t.status = *ss->second->pinned_status;
+            ss->second->busy = false;
+        }
+        t.done = true;
+        t.done_at = now;
+    }
+    slot->batch.clear();
+    slot->busy = false;
+    srv->cv.notify_all();
+}
+
+static void serve_loop(Server *srv) {
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (!srv->stop) {
+        Slot *slot = nullptr;
+        for (Slot *s : srv->slots)
+            if (!s->busy) { slot = s; break; }
+        if (!slot || srv->pending.empty()) {
+            srv->cv.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+        std::vector<uint64_t> batch;
+        while (!srv->pending.empty() && (int)batch.size() < srv->max_batch) {
+            batch.push_back(srv->pending.front());
+            srv->pending.pop_front();
+        }
+        std::vector<dpvo_ba_dims> dims;
+        std::vector<dpvo_ba_problem> probs;
+        std::vector<Session *> ss;
+        for (uint64_t tk : batch) {
+            Session *s = srv->sessions[srv->tickets[tk].session];
+            dims.push_back(s->dims);
+            probs.push_back(s->dev);
+            ss.push_back(s);
+        }
+        slot->busy = true;
+        slot->batch = batch;
+        lk.unlock();
+        int rc = DPVO_BA_OK;
+        for (Session *s : ss) {
+            const size_t E = s->dims.n_edges;
+            if (E && (cudaMemcpyAsync((void *)s->dev.target, s->pinned_tw, E * 8, cudaMemcpyHostToDevice, slot->stream) ||
+                      cudaMemcpyAsync((void *)s->dev.weight, s->pinned_tw + 2 * E, E * 8, cudaMemcpyHostToDevice,
+                                      slot->stream)))
+                rc = DPVO_BA_ECUDA;
+        }
+        if (!rc) rc = run_solve(slot->h, dims.data(), probs.data(), (int)ss.size(), slot->stream, nullptr, nullptr);
+        for (Session *s : ss)
+            if (cudaMemcpyAsync(s->pinned_status, s->dev.status, 4, cudaMemcpyDeviceToHost, slot->stream)) rc = DPVO_BA_ECUDA;
+        if (cudaLaunchHostFunc(slot->stream, serve_batch_done, slot) != cudaSuccess) rc = DPVO_BA_ECUDA;
+        lk.lock();
+        if (rc) {
+            // could not launch: fail the batch's tickets on the host, free the slot
+            srv->launch_error = rc;
+            for (uint64_t tk : batch) {
+                Ticket &t = srv->tickets[tk];
+                t.done = true;
+                t.done_at = Clock::now();
+                t.status = DPVO_BA_STATUS_BAD_INPUT;
+                auto it = srv->sessions.find(t.session);
+                if (it != srv->sessions.end()) it->second->busy = false;
+            }
+            slot->batch.clear();
+            slot->busy = false;
+            srv->cv.notify_all();
+        }
+    }
+}
+
+static int serve_stop_impl(dpvo_ba_handle *h);
+
+extern "C" int dpvo_ba_serve_start(dpvo_ba_handle *h, const dpvo_ba_dims *max_dims, int max_batch, int max_in_flight) {
+    if (!h || !max_dims || max_batch < 1 || max_in_flight < 1 || max_in_flight > 8) return DPVO_BA_EINVAL;
+    if (h->srv) return DPVO_BA_EBUSY;
+    Server *srv = new Server();
+    srv->owner = h;
+    srv->device = h->device;
+    srv->max_batch = max_batch;
+    srv->budget = h->cfg.mem_budget_bytes;
+    h->srv = srv;
+    for (int i = 0; i < max_in_flight; ++i) {
+        Slot *slot = new Slot();
+        slot->srv = srv;
+        srv->slots.push_back(slot);
+        if (dpvo_ba_create(&h->cfg, &slot->h) != DPVO_BA_OK ||
+            cudaStreamCreateWithFlags(&slot->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            dpvo_ba_reserve(slot->h, max_dims, max_batch) != DPVO_BA_OK) {
+            serve_stop_impl(h);
+            return DPVO_BA_ENOMEM;
+        }
+    }
+    srv->running = true;
+    srv->thread = std::thread(serve_loop, srv);
+    return DPVO_BA_OK;
+}
+
+static int serve_stop_impl(dpvo_ba_handle *h) {
+    Server *srv = h->srv;
+    if (!srv) return DPVO_BA_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        srv->cv.notify_all();
+    }
+    if (srv->thread.joinable()) srv->thread.join();
+    for (Slot *slot : srv->slots) {
+        if (slot->stream) {
+            cudaStreamSynchronize(slot->stream);
+            cudaStreamDestroy(slot->stream);
+        }
+        if (slot->h) dpvo_ba_destroy(slot->h);
+        delete slot;
+    }
+    for (auto &kv : srv->sessions) {
+        Session *s = kv.second;
+        if (s->mem) cudaFree(s->mem);
+        if (s->pinned_tw) cudaFreeHost(s->pinned_tw);
+        delete s;
+    }
+    delete srv;
+    h->srv = nullptr;
+    return DPVO_BA_OK;
+}
+
+extern "C" int dpvo_ba_serve_stop(dpvo_ba_handle *h) {
+    if (!h) return DPVO_BA_EINVAL;
+    return serve_stop_impl(h);
+}
+
+extern "C" int dpvo_ba_session_open(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *hp,
+                                    int64_t *session_id) {
+    if (!h || !h->srv || !dims || !hp || !session_id) return DPVO_BA_EINVAL;
+    if (int rc = check_dims(*dims)) return rc;
+    if (int rc = check_problem(*dims, *hp)) return rc;
+    Server *srv = h->srv;
+    const size_t bytes = session_bytes(*dims);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->used_bytes + bytes > srv->budget) return DPVO_BA_EBUSY;   // not admitted: over the budget
+        srv->used_bytes += bytes;
+    }
+    Session *s = new Session();
+    s->dims = *dims;
+    s->bytes = bytes;
+    const size_t N = dims->n_frames, P = dims->n_patches, E = dims->n_edges;
+    int rc = DPVO_BA_OK;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) rc = DPVO_BA_ECUDA;
+    if (!rc && cudaMallocAsync((void **)&s->mem, bytes, st) != cudaSuccess) rc = DPVO_BA_ENOMEM;
+    if (!rc && cudaMallocHost((void **)&s->pinned_tw, E * 16 + 16) != cudaSuccess) rc = DPVO_BA_ENOMEM;
+    if (!rc) {
+        s->pinned_status = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(s->pinned_tw) + E * 16);
+        size_t o = 0;
+        auto take = [&](size_t b) { char *p = s->mem + o; o += al256(b); return p; };
+        s->dev.poses = (float *)take(N * 28);
+        s->dev.patches = (float *)take(P * 12);
+        s->dev.anchor = (const int32_t *)take(P * 4);
+        s->dev.kk = (const int32_t *)take(E * 4);
+        s->dev.jj = (const int32_t *)take(E * 4);
+        s->dev.target = (const float *)take(E * 8);
+        s->dev.weight = (const float *)take(E * 8);
+        s->dev.status = (int32_t *)take(4);
+        cudaMemcpyAsync(s->dev.poses, hp->poses, N * 28, cudaMemcpyHostToDevice, st);
+        if (P) {
+            cudaMemcpyAsync(s->dev.patches, hp->patches, P * 12, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync((void *)s->dev.anchor, hp->anchor, P * 4, cudaMemcpyHostToDevice, st);
+        }
+        if (E) {
+            cudaMemcpyAsync((void *)s->dev.kk, hp->kk, E * 4, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync((void *)s->dev.jj, hp->jj, E * 4, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync((void *)s->dev.target, hp->target, E * 8, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync((void *)s->dev.weight, hp->weight, E * 8, cudaMemcpyHostToDevice, st);
+        }
+        cudaMemsetAsync(s->dev.status, 0, 4, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = DPVO_BA_ECUDA;
+    }
+    if (st) cudaStreamDestroy(st);
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (rc) {
+        cudaGetLastError();
+        if (s->mem) cudaFree(s->mem);
+        if (s->pinned_tw) cudaFreeHost(s->pinned_tw);
+        delete s;
+        srv->used_bytes -= bytes;
+        return rc;
+    }
+    s->id = srv->next_session++;
+    srv->sessions[s->id] = s;
+    *session_id = s->id;
+    return DPVO_BA_OK;
+}
+
+static Session *find_idle_session(Server *srv, int64_t id, std::unique_lock<std::mutex> &lk, int timeout_ms,
+                                  int *rc) {
+    auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        auto it = srv->sessions.find(id);
+        if (it == srv->sessions.end()) { *rc = DPVO_BA_ENOTFOUND; return nullptr; }
+        if (!it->second->busy) { *rc = DPVO_BA_OK; return it->second; }
+        if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout) { *rc = DPVO_BA_ETIMEOUT; return nullptr; }
+    }
+}
+
+extern "C" int dpvo_ba_session_close(dpvo_ba_handle *h, int64_t session_id) {
+    if (!h || !h->srv) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    int rc;
+    Session *s = find_idle_session(srv, session_id, lk, 10000, &rc);
+    if (!s) return rc;
+    srv->sessions.erase(session_id);
+    srv->used_bytes -= s->bytes;
+    lk.unlock();
+    cudaFree(s->mem);
+    cudaFreeHost(s->pinned_tw);
+    delete s;
+    return DPVO_BA_OK;
+}
+
+extern "C" int dpvo_ba_session_read(dpvo_ba_handle *h, int64_t session_id, float *poses_out, float *patches_out) {
+    if (!h || !h->srv) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    int rc;
+    Session *s = find_idle_session(srv, session_id, lk, 10000, &rc);
+    if (!s) return rc;
+    s->busy = true;        // hold it while copying
+    lk.unlock();
+    if (poses_out && cudaMemcpy(poses_out, s->dev.poses, (size_t)s->dims.n_frames * 28, cudaMemcpyDeviceToHost))
+        rc = DPVO_BA_ECUDA;
+    if (patches_out && s->dims.n_patches &&
+        cudaMemcpy(patches_out, s->dev.patches, (size_t)s->dims.n_patches * 12, cudaMemcpyDeviceToHost))
+        rc = DPVO_BA_ECUDA;
+    lk.lock();
+    s->busy = false;
+    srv->cv.notify_all();
+    return rc;
+}
+
+extern "C" int dpvo_ba_submit(dpvo_ba_handle *h, int64_t session_id, const float *target, const float *weight,
+                              uint64_t *ticket) {
+    if (!h || !h->srv || !ticket) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    Session *s;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->sessions.find(session_id);
+        if (it == srv->sessions.end()) return DPVO_BA_ENOTFOUND;
+        s = it->second;
+        if (s->busy) return DPVO_BA_EBUSY;   // one request per session at a time
+        s->busy = true;
+    }
+    const size_t E = s->dims.n_edges;
+    if (E && (!target || !weight)) {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        s->busy = false;
+        return DPVO_BA_EINVAL;
+    }
+    if (E) {
+        std::memcpy(s->pinned_tw, target, E * 8);
+        std::memcpy(s->pinned_tw + 2 * E, weight, E * 8);
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const uint64_t t = srv->next_ticket++;
+    Ticket tk;
+    tk.session = session_id;
+    tk.submitted = Clock::now();
+    srv->tickets[t] = tk;
+    srv->pending.push_back(t);
+    srv->cv.notify_all();
+    *ticket = t;
+    return DPVO_BA_OK;
+}
+
+static int collect(Server *srv, uint64_t ticket, int32_t *status, double *latency_ms) {
+    auto it = srv->tickets.find(ticket);
+    const Ticket &t = it->second;
+    if (status) *status = t.status;
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(t.done_at - t.submitted).count();
+    srv->tickets.erase(it);
+    return DPVO_BA_OK;
+}
+
+extern "C" int dpvo_ba_poll(dpvo_ba_handle *h, uint64_t ticket, int32_t *status, double *latency_ms) {
+    if (!h || !h->srv) return DPVO_BA_EINVAL;
+    std::lock_guard<std::mutex> lk(h->srv->mu);
+    auto it = h->srv->tickets.find(ticket);
+    if (it == h->srv->tickets.end()) return DPVO_BA_ENOTFOUND;
+    if (!it->second.done) return DPVO_BA_EBUSY;
+    return collect(h->srv, ticket, status, latency_ms);
+}
+
+extern "C" int dpvo_ba_wait(dpvo_ba_handle *h, uint64_t ticket, int timeout_ms, int32_t *status,
+                            double *latency_ms) {
+    if (!h || !h->srv || timeout_ms < 0) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        auto it = srv->tickets.find(ticket);
+        if (it == srv->tickets.end()) return DPVO_BA_ENOTFOUND;
+        if (it->second.done) return collect(srv, ticket, status, latency_ms);
+        if (srv->cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+            auto it2 = srv->tickets.find(ticket);
+            if (it2 != srv->tickets.end() && it2->second.done) return collect(srv, ticket, status, latency_ms);
+            return DPVO_BA_ETIMEOUT;
+        }
+    }
+}
 
 // ----------------------------------------------------------------------------
 // Allocation-free single-problem solve.
