@@ -16,6 +16,9 @@ Also measured and reported on the same JSON line:
   roofline  the linearise/Schur kernel against the FP32-ALU or HBM roofline
   parity    sampled problems of the first timed-configuration solve vs the FP64 oracle
   cpu_baseline  the FP64 oracle timed on this host's cores on a bounded sample
+  serving   256 VO sessions (uneven shapes) with device-resident state, Poisson
+            requests at 2000/s: p50/p99 latency and solves/s, continuous
+            batching vs one launch per solve, plus a saturated closed loop
 
 ``--impl reference`` times the FP64 oracle (the reference arm) instead.
 Launch: ``python bench.py --gpus N --steps K --warmup W`` (torchrun for N > 1,
@@ -53,6 +56,7 @@ def parse():
     ap.add_argument("--plain", type=int, default=200, help="one-problem solves timed for the plain form")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--parity-samples", type=int, default=2)
+    ap.add_argument("--serving", type=int, default=1, help="run the serving measurement (Poisson sessions)")
     return ap.parse_args()
 
 
@@ -205,6 +209,83 @@ def run_reference(args, world, rank):
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+# --------------------------------------------------------------------- serving
+
+def serving_bench(n_sessions=256, distinct=32, rate=2000.0, duration=2.0, saturate=1.0, seed=0):
+    """Poisson open loop (rate requests/s over n_sessions) and a saturated
+    closed loop, for continuous batching and for one launch per solve.
+    Latency is the library's (submit to completion on the device)."""
+    import time as _t
+    from paper_2208_04726_b300 import ba
+    from paper_2208_04726_b300 import scenes as S
+    mix = S.make_serving_mix(distinct, base_seed=seed)
+    reqs = [[S.refresh_factors(sc, 10_000 + 10 * i + r) for r in range(3)] for i, sc in enumerate(mix)]
+    sess_of = [b % distinct for b in range(n_sessions)]
+    max_n = max(sc.n_frames for sc in mix)
+    max_p = max(sc.n_patches for sc in mix)
+    max_e = max(sc.n_edges for sc in mix)
+    out = {"sessions": n_sessions, "distinct_shapes": distinct, "poisson_rate": rate,
+           "workload": "N~U{8..32} frames, {48,64,96} patches/frame, radius U{8..13}, last min(10, N-2) poses free, "
+                       "2 GN iterations, fresh targets and weights per request"}
+    for mode, (mb, mif) in (("batched", (n_sessions, 2)), ("plain", (1, 1))):
+        srv = ba.Solver()
+        srv.serve_start(max_n, max_p, max_e, 2, max_batch=mb, max_in_flight=mif)
+        sids = [srv.session_open(mix[sess_of[b]]) for b in range(n_sessions)]
+
+        def request(b, k):
+            r = reqs[sess_of[b]][k % 3]
+            return srv.submit(sids[b], r.target, r.weight)
+
+        for b in range(n_sessions):                     # warm-up: one request per session
+            srv.wait(request(b, 0), 60000)
+        rng = np.random.default_rng(1)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * duration * 1.5) + 10))
+        arrivals = arrivals[arrivals < duration]
+        who = rng.integers(0, n_sessions, size=arrivals.shape[0])
+        busy = {}                                       # session -> ticket
+        queued = {b: [] for b in range(n_sessions)}     # arrivals waiting for their session
+        lat, k, done = [], 0, 0
+        t0 = _t.perf_counter()
+        while done < arrivals.shape[0]:
+            now = _t.perf_counter() - t0
+            while k < arrivals.shape[0] and arrivals[k] <= now:
+                b = int(who[k])
+                if b in busy:
+                    queued[b].append(k)
+                else:
+                    busy[b] = request(b, k)
+                k += 1
+            for b, tk in list(busy.items()):
+                ok, st, ms = srv.poll(tk)
+                if ok:
+                    lat.append(ms)
+                    done += 1
+                    del busy[b]
+                    if queued[b]:
+                        busy[b] = request(b, queued[b].pop(0))
+        elapsed = _t.perf_counter() - t0
+        res = {"latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+               "completed": done, "solves_per_s": done / elapsed}
+        # saturated closed loop: every session resubmits as soon as its request finishes
+        busy = {b: request(b, 1) for b in range(n_sessions)}
+        cnt = 0
+        t0 = _t.perf_counter()
+        while _t.perf_counter() - t0 < saturate:
+            for b, tk in list(busy.items()):
+                ok, st, ms = srv.poll(tk)
+                if ok:
+                    cnt += 1
+                    busy[b] = request(b, cnt)
+        el = _t.perf_counter() - t0
+        for tk in busy.values():
+            srv.wait(tk, 60000)
+        res["saturated_solves_per_s"] = cnt / el
+        out[mode] = res
+        srv.serve_stop()
+        srv.close()
+    return out
 
 
 # --------------------------------------------------------------------- our arm
@@ -379,6 +460,8 @@ def main():
         e2e_s = float(tt.item())
     e2e_value = world * B * args.e2e_steps / e2e_s
 
+    serving = serving_bench() if (rank == 0 and args.serving) else None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -399,6 +482,7 @@ def main():
             "cpu_baseline": cpu_baseline,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": args.e2e_steps, "api": "dpvo_ba_solve_host (pinned host buffers)"},
+            "serving": serving,
             "gpu_launches": world * n_launch_per_solve * args.steps,
             "clocks": clocks.summary(),
         }
