@@ -46,6 +46,7 @@ struct Prob {
     float *depth_it;         // [iters + 1][P]
     double *dxi;             // [iters][nf][6] pose increments
     double *partial;         // [n_items][ks][L] Schur partial sums
+    float *erow;             // [P][erow_len(nf)] scaled Schur row of each patch, last linearisation
     // backward (adjoint) state; null / zero for a plain solve
     int store_factor;        // keep the factored reduced system of every iteration
     int no_writeback;        // leave the caller's poses and patches untouched
@@ -67,6 +68,18 @@ struct Prob {
     int chunk_cap;           // patches per chunk at most
     int win_cap;             // frames per chunk window at most
 };
+
+// Stored Schur row of a patch, written when it is linearised and read by the
+// back-substitution of that iteration: the pose columns C_k^-1/2 e_k (6 nf
+// floats, frame-major), then C_k^-1/2 w_k and C_k^-1/2, zero-padded to a
+// multiple of 4 floats so that every row starts on a 16-byte boundary.
+__host__ __device__ inline int erow_len(int nf) { return (6 * nf + 2 + 3) & ~3; }
+// Row stride of the rows staged in shared memory: congruent to 16 mod 32
+// floats, so the 16-byte loads of two rows by 4 lanes each fall in disjoint banks.
+__host__ __device__ inline int erow_smem_stride(int nf) {
+    const int rs = erow_len(nf);
+    return rs + ((16 - rs % 32) + 32) % 32;
+}
 
 // One CTA of the linearise kernel: problem index and work-item index within it.
 struct Item {

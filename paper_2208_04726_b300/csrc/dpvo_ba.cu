@@ -92,6 +92,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.depth_it = (float *)(uintptr_t)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
         p.dxi = (double *)(uintptr_t)take((size_t)d.n_iters * p.nf * 6 * 8 + 8);
         p.partial = (double *)(uintptr_t)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
+        p.erow = (float *)(uintptr_t)take((size_t)d.n_patches * erow_len(p.nf) * 4 + 16);
         if (adjoint) {
             const size_t n6 = 6 * (size_t)p.nf;
             p.store_factor = 1;
@@ -221,6 +222,7 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         p.depth_it = rebase(p.depth_it, h->ws);
         p.dxi = rebase(p.dxi, h->ws);
         p.partial = rebase(p.partial, h->ws);
+        p.erow = rebase(p.erow, h->ws);
     }
     h->last = L.probs;
     std::memcpy(h->stage, L.probs.data(), sizeof(Prob) * n);
@@ -298,6 +300,7 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
         p.depth_it = rebase(p.depth_it, h->ws);
         p.dxi = rebase(p.dxi, h->ws);
         p.partial = rebase(p.partial, h->ws);
+        p.erow = rebase(p.erow, h->ws);
         p.ufac = rebase(p.ufac, h->ws);
         p.eps = rebase(p.eps, h->ws);
         p.dxibar = rebase(p.dxibar, h->ws);
@@ -1001,6 +1004,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.depth_it = (float *)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
     p.dxi = (double *)take((size_t)d.n_iters * nf * 6 * 8 + 8);
     p.partial = (double *)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
+    p.erow = (float *)take((size_t)d.n_patches * erow_len(nf) * 4 + 16);
     Prob *d_prob = (Prob *)take(sizeof(Prob));
     Item *d_items = (Item *)take(sizeof(Item) * p.n_items);
     if (off > kNoAllocScratchBytes) return DPVO_BA_EINVAL;   // problem too large for the fixed scratch

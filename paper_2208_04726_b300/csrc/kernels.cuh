@@ -6,15 +6,18 @@
 //   linearize_kernel  once per iteration (and once more at the end): for each
 //                     chunk of patches that share a source frame,
 //                       (a) back-substitutes the previous iteration's inverse-
-//                           depth increments dd_k = (w_k - e_k^T dxi) / C_k,
+//                           depth increments dd_k = (w_k - e_k^T dxi) / C_k
+//                           from the patch's stored scaled Schur row,
 //                       (b) linearises every edge at the new state (Eq. 2-3
 //                           reprojection, residual, pose-j / inverse-depth
 //                           Jacobians) and reduces the pose-pair blocks
 //                           B_jj += J_j^T W J_j by frame,
 //                       (c) accumulates the Schur complement
 //                           S = B - sum_k E_k C_k^-1 E_k^T, v' = v - sum_k E_k C_k^-1 w_k
-//                           over the free poses, with compensated sums,
-//                     and writes one FP64 partial of (S, v') per CTA.
+//                           over the free poses, with compensated sums, and
+//                           stores each patch's row C_k^-1/2 (e_k, w_k, 1),
+//                     and writes one FP64 partial of (S, v') per CTA.  The
+//                     last launch only back-substitutes, per patch.
 //   solve_kernel      once per iteration: sums the partials in FP64, factorises
 //                     S = L L^T in FP64 (pivot check -> NOT_SPD), solves for the
 //                     pose increments and retracts T <- Exp(dxi) T.
@@ -214,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__
 struct LinSmem {
     int W, G, Gs, ES, EC;  // window cap, chunk cap, odd slot stride, E-column stride, edge capacity
     size_t off_pose, off_rjj, off_rtg, off_rwt, off_rpx, off_rpy, off_rdep, off_rseg, off_idx, off_sc4, off_sc1,
-        off_ec, off_mp, off_relo, off_reln, off_adj, off_mc, off_aj, off_bp, off_bii, off_pd, off_zk, off_ps, off_dx;
+        off_ec, off_mp, off_reln, off_adj, off_mc, off_aj, off_bp, off_bii, off_pd, off_ps, off_dx;
     size_t bytes;
 };
 
@@ -231,8 +234,12 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     s.ES = es;
     s.EC = W * G;
     const size_t slots = (size_t)W * s.Gs;
+    // the per-slot sums share their buffer with the staged Schur rows of the
+    // next chunk (read before the slots are written)
+    const size_t rows = (size_t)G * erow_smem_stride(nf_max) * 4;
+    const size_t sc4 = slots * 16 > rows ? slots * 16 : rows;
     size_t o = 0;
-    s.off_pose = o; o = align16(o + 2 * (size_t)n_max * 7 * 4);
+    s.off_pose = o; o = align16(o + (size_t)n_max * 7 * 4);
     s.off_rjj = o;  o = align16(o + (size_t)s.EC * 4);
     s.off_rtg = o;  o = align16(o + (size_t)s.EC * 8);
     s.off_rwt = o;  o = align16(o + (size_t)s.EC * 8);
@@ -241,11 +248,10 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     s.off_rdep = o; o = align16(o + (size_t)G * 4);
     s.off_rseg = o; o = align16(o + (size_t)(G + 1) * 4);
     s.off_idx = o;  o = align16(o + slots * 2);
-    s.off_sc4 = o;  o = align16(o + slots * 16);
+    s.off_sc4 = o;  o = align16(o + sc4);
     s.off_sc1 = o;  o = align16(o + slots * 4);
     s.off_ec = o;   o = align16(o + (size_t)G * es * 4);
     s.off_mp = o;   o = align16(o + (size_t)kThreads * 27 * 4);
-    s.off_relo = o; o = align16(o + (size_t)W * 12 * 4);
     s.off_reln = o; o = align16(o + (size_t)W * 12 * 4);
     s.off_adj = o;  o = align16(o + (size_t)W * 36 * 4);
     s.off_mc = o;   o = align16(o + (size_t)W * 27 * 4);
@@ -253,9 +259,8 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     s.off_bp = o;   o = align16(o + (size_t)W * 42 * 4);
     s.off_bii = o;  o = align16(o + 42 * 4);
     s.off_pd = o;   o = align16(o + (size_t)G * 16);
-    s.off_zk = o;   o = align16(o + (size_t)G * 16);
     s.off_ps = o;   o = align16(o + (size_t)G * 8 * 4);
-    s.off_dx = o;   o = align16(o + kMaxFree * 6 * 4);
+    s.off_dx = o;   o = align16(o + (size_t)erow_len(kMaxFree) * 4);
     s.bytes = o;
     return s;
 }
@@ -276,6 +281,10 @@ __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -305,6 +314,22 @@ __device__ __forceinline__ void prefetch_chunk(const Prob &pr, const Chunk &ch, 
     }
     for (int q = threadIdx.x; q <= ch.count; q += kThreads) cp_async4(rseg + q, pr.seg + ch.k0 + q);
     cp_async_commit();
+}
+
+// Start copying one chunk's stored Schur rows (erow_len floats each) into
+// shared memory at row stride rss.
+__device__ __forceinline__ void prefetch_rows(const Prob &pr, const Chunk &ch, int rs, int rss, float *dst) {
+    const int n4 = rs / 4, total = ch.count * n4;
+    const float4 *src = reinterpret_cast<const float4 *>(pr.erow + (size_t)ch.k0 * rs);
+    for (int q = threadIdx.x; q < total; q += kThreads) {
+        const int p = q / n4, c = q - p * n4;
+        cp_async16(dst + p * rss + 4 * c, src + q);
+    }
+    cp_async_commit();
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
 }
 
 // Relative poses of the window frames w.r.t. the anchor (and their adjoints).
@@ -347,7 +372,6 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     // E C^-1 dbar (dbar = gradient w.r.t. the inverse depths) into the
     // right-hand-side strips, for the adjoint solve of iteration t
     const bool do_bs = t > 0 && !adjoint_rhs;
-    const bool do_lin = t < pr.iters;
     const bool final_pass = t == pr.iters && !adjoint_rhs;
     {
         const int st = *pr.status;
@@ -356,8 +380,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     }
 
     const LinSmem L = lin_smem_layout(W_cap, G_cap, nf_max, n_max);
-    float *spo = reinterpret_cast<float *>(smem + L.off_pose);        // old-state poses
-    float *spn = spo + n_max * 7;                                       // new-state poses
+    float *spn = reinterpret_cast<float *>(smem + L.off_pose);        // poses of iterate t
     int *rjj = reinterpret_cast<int *>(smem + L.off_rjj);
     float2 *rtg = reinterpret_cast<float2 *>(smem + L.off_rtg);
     float2 *rwt = reinterpret_cast<float2 *>(smem + L.off_rwt);
@@ -367,10 +390,10 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     int *rseg = reinterpret_cast<int *>(smem + L.off_rseg);
     short *sidx = reinterpret_cast<short *>(smem + L.off_idx);
     float4 *sc4 = reinterpret_cast<float4 *>(smem + L.off_sc4);
+    float *srow = reinterpret_cast<float *>(smem + L.off_sc4);        // staged Schur rows (aliases sc4)
     float *sc1 = reinterpret_cast<float *>(smem + L.off_sc1);
     float *Ec = reinterpret_cast<float *>(smem + L.off_ec);
     float *Mp = reinterpret_cast<float *>(smem + L.off_mp);
-    float *relo = reinterpret_cast<float *>(smem + L.off_relo);
     float *reln = reinterpret_cast<float *>(smem + L.off_reln);
     float *adj = reinterpret_cast<float *>(smem + L.off_adj);
     float *Mc = reinterpret_cast<float *>(smem + L.off_mc);
@@ -378,15 +401,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     float *Bp = reinterpret_cast<float *>(smem + L.off_bp);
     float *Bii = reinterpret_cast<float *>(smem + L.off_bii);
     float4 *pd = reinterpret_cast<float4 *>(smem + L.off_pd);
-    float4 *zk = reinterpret_cast<float4 *>(smem + L.off_zk);
     float *ps = reinterpret_cast<float *>(smem + L.off_ps);
     float *dxs = reinterpret_cast<float *>(smem + L.off_dx);
     const int Gs = L.Gs, ES = L.ES;
 
     const int N = pr.N, t0 = pr.t0, nf = pr.nf;
+    const int RS = erow_len(nf), RSS = erow_smem_stride(nf);
     const float fx = pr.fx, fy = pr.fy, cx = pr.cx, cy = pr.cy, z_min = pr.z_min, lam = pr.damping;
     const float ifx = 1.0f / fx, ify = 1.0f / fy;
-    const float *pose_old = pr.pose_it + (size_t)(t > 0 ? t - 1 : 0) * N * 7;
     const float *pose_new = pr.pose_it + (size_t)t * N * 7;
     const float *depth_old = pr.depth_it + (size_t)(t > 0 ? t - 1 : 0) * pr.P;
     float *depth_new = pr.depth_it + (size_t)t * pr.P;
@@ -396,6 +418,38 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     const int c_begin = (int)(((long long)itm.item * nch) / pr.n_items);
     const int c_end = (int)(((long long)(itm.item + 1) * nch) / pr.n_items);
 
+    if (do_bs) {   // the previous iteration's pose increments, zero-padded to the row length
+        const double *dx = pr.dxi + (size_t)(t - 1) * nf * 6;
+        for (int q = tid; q < RS; q += kThreads) dxs[q] = q < 6 * nf ? (float)dx[q] : 0.f;
+    }
+    if (final_pass) {
+        // last back-substitution: dd_k = C_k^-1/2 (C_k^-1/2 w_k - (C_k^-1/2 e_k) . dxi)
+        // for every patch of this item's chunks, four lanes per patch
+        __syncthreads();
+        if (c_begin < c_end) {
+            const Chunk ca = pr.chunks[c_begin], cz = pr.chunks[c_end - 1];
+            const int k_lo = ca.k0, k_hi = cz.k0 + cz.count;
+            const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
+            const int sub = tid & 3;
+            for (int kb = k_lo; kb < k_hi; kb += kThreads / 4) {
+                const int k = kb + (tid >> 2);
+                float s = 0.f;
+                const float *row = pr.erow + (size_t)k * RS;
+                if (k < k_hi)
+                    for (int q = sub; q < RS / 4; q += 4) s = dot4(reinterpret_cast<const float4 *>(row)[q], dz4[q], s);
+                s = quad_sum(s);
+                if (k < k_hi && sub == 0) {
+                    const float dnew = depth_old[k] + row[6 * nf + 1] * (row[6 * nf] - s);
+                    depth_new[k] = dnew;
+                    if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
+                }
+            }
+        }
+        if (itm.item == 0 && !pr.no_writeback)
+            for (int q = tid; q < N * 7; q += kThreads) pr.poses[q] = pose_new[q];
+        return;
+    }
+
     // strip ownership of the Schur accumulation
     const int nbp = n_block_pairs(nf);
     const int nbs = 2 * nbp;
@@ -404,7 +458,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     const int my_strip = nst > 0 ? tid % nst : 0;
     const int my_ks = nst > 0 ? tid / nst : KS;
     const bool is_vstrip = my_strip >= nbs;
-    const bool owns = do_lin && nst > 0 && my_ks < KS && (is_vstrip || !adjoint_rhs);
+    const bool owns = nst > 0 && my_ks < KS && (is_vstrip || !adjoint_rhs);
     int sa = 0, sb = 0, sh = 0;
     if (owns) {
         if (!is_vstrip) {
@@ -418,14 +472,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 #pragma unroll
     for (int q = 0; q < 18; ++q) { acc_s[q] = 0.f; acc_c[q] = 0.f; blk[q] = 0.f; }
 
-    for (int q = tid; q < N * 7; q += kThreads) {
-        spo[q] = pose_old[q];
-        spn[q] = pose_new[q];
-    }
-    if (do_bs) {
-        const double *dx = pr.dxi + (size_t)(t - 1) * nf * 6;
-        for (int q = tid; q < nf * 6; q += kThreads) dxs[q] = (float)dx[q];
-    }
+    for (int q = tid; q < N * 7; q += kThreads) spn[q] = pose_new[q];
 
     __shared__ __align__(16) Chunk s_ch[2];
     if (c_begin < c_end) {
@@ -433,6 +480,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         __syncthreads();
         prefetch_chunk(pr, s_ch[0], depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
                        c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1]);
+        if (do_bs) prefetch_rows(pr, s_ch[0], RS, RSS, srow);
     }
     int cur = 0;
     bool group_open = false;   // the previous chunk continues into this one
@@ -484,100 +532,38 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                     sidx[jl * Gs + p] = (short)idx;
                 }
-                if (do_lin)   // E columns of free frames outside the window are zero
-                    for (int f = tid >> 6; f < nf; f += kThreads / 64) {
-                        const int fr = t0 + f;
-                        if (fr < jlo || fr > ch.jhi) {
-                            float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * f);
-                            e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            e4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-                    }
-                if (tid < 64) {
-                    const float px = (rpx[p] - cx) * ifx, py = (rpy[p] - cy) * ify, d = rdep[p];
-                    pd[p] = make_float4(px, py, d, 0.f);
-                    if (do_bs && anc_free) {
-                        // z_k = d dxi_i,v + dxi_i,w x pbar, for the anchor term of the back-substitution
-                        const float *di = dxs + 6 * (anc - t0);
-                        zk[p] = make_float4(fmaf(d, di[0], di[4] - di[5] * py), fmaf(d, di[1], di[5] * px - di[3]),
-                                            fmaf(d, di[2], di[3] * py - di[4] * px), 0.f);
+                for (int f = tid >> 6; f < nf; f += kThreads / 64) {   // E columns of free frames outside the window are zero
+                    const int fr = t0 + f;
+                    if (fr < jlo || fr > ch.jhi) {
+                        float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * f);
+                        e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        e4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                 }
             }
         }
-        if (!group_open) {
-            if (do_bs) window_poses(spo, anc, jlo, W, relo, nullptr);
-            if (do_lin) window_poses(spn, anc, jlo, W, reln, adj);
+        {   // patch data, after the back-substitution of the previous iteration
+            // from the staged rows (four lanes per patch)
+            const int p = tid >> 2, sub = tid & 3;
+            float s = 0.f;
+            if (do_bs && p < cnt) {
+                const float4 *row = reinterpret_cast<const float4 *>(srow + p * RSS);
+                const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
+                for (int q = sub; q < RS / 4; q += 4) s = dot4(row[q], dz4[q], s);
+            }
+            s = quad_sum(s);
+            if (sub == 0 && p < cnt) {
+                float d = rdep[p];
+                if (do_bs) {
+                    const float *row = srow + p * RSS;
+                    d += row[6 * nf + 1] * (row[6 * nf] - s);
+                    depth_new[k0 + p] = d;
+                }
+                pd[p] = make_float4((rpx[p] - cx) * ifx, (rpy[p] - cy) * ify, d, 0.f);
+            }
         }
+        if (!group_open) window_poses(spn, anc, jlo, W, reln, adj);
         __syncthreads();
-
-        // -- (a) back-substitution of the previous iteration at the old state
-        if (do_bs) {
-            if (edge_thread) {
-                float Rr[12];
-#pragma unroll
-                for (int q = 0; q < 12; ++q) Rr[q] = relo[my_jl * 12 + q];
-                const bool jfree = my_j >= t0 && my_j != anc;
-                const float *dj = dxs + 6 * (jfree ? my_j - t0 : 0);
-                for (int p = my_g; p < cnt; p += NG) {
-                    const int slot = my_jl * Gs + p;
-                    const int ei = sidx[slot];
-                    float Ce = 0.f, we = 0.f, se = 0.f;
-                    if (ei >= 0 && my_j != anc) {
-                        const float2 tv = rtg[ei], wv = rwt[ei];
-                        const float4 q = pd[p];
-                        EdgeLin E;
-                        if ((wv.x != 0.f || wv.y != 0.f) &&
-                            edge_linearize(Rr, Rr + 9, q.x, q.y, q.z, tv.x, tv.y, fx, fy, cx, cy, z_min, E)) {
-                            float wjd0, wjd1;
-                            depth_terms(E, wv.x, wv.y, wjd0, wjd1, Ce, we);
-                            if (jfree) {
-#pragma unroll
-                                for (int m = 0; m < 6; ++m) se = fmaf(fmaf(E.j1[m], wjd1, E.j0[m] * wjd0), dj[m], se);
-                            }
-                            if (anc_free) {
-                                float Y0, Y1, Y2;
-                                anchor_terms(E, Rr, wjd0, wjd1, Y0, Y1, Y2);
-                                const float4 z = zk[p];
-                                se -= fmaf(Y2, z.z, fmaf(Y1, z.y, Y0 * z.x));
-                            }
-                        }
-                    }
-                    sc4[slot] = make_float4(Ce, we, se, 0.f);
-                }
-            }
-            __syncthreads();
-            {   // per-patch sums over the window by four lanes, then dd_k = (w_k - e_k . dxi) / C_k
-                const int p = tid >> 2, sub = tid & 3;
-                float C = sub == 0 ? lam : 0.f, w = 0.f, s = 0.f;
-                if (p < cnt)
-                    for (int jl = sub; jl < W; jl += 4) {
-                        const float4 v = sc4[jl * Gs + p];
-                        C += v.x;
-                        w += v.y;
-                        s += v.z;
-                    }
-                C = quad_sum(C);
-                w = quad_sum(w);
-                s = quad_sum(s);
-                if (sub == 0 && p < cnt) {
-                    const float dnew = pd[p].z + (w - s) / C;
-                    pd[p].z = dnew;
-                    depth_new[k0 + p] = dnew;
-                    if (final_pass && !pr.no_writeback) pr.patches[3 * (k0 + p) + 2] = dnew;
-                }
-            }
-            if (!do_lin) {
-                // the staging buffers are free: start the next chunk's copies
-                if (have_next)
-                    prefetch_chunk(pr, nx, depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
-                                   c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur]);
-                group_open = group_next;
-                cur ^= 1;
-                continue;
-            }
-            __syncthreads();
-        }
 
         // -- (b) linearise at the new state.  Each edge thread keeps its frame
         // sums (M_j, v_j) in its own Mp slot between the chunks of a group.
@@ -689,6 +675,8 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
         }
         __syncthreads();
+        // the per-slot sums are consumed: start copying the next chunk's stored rows
+        if (do_bs && have_next) prefetch_rows(pr, nx, RS, RSS, srow);
         if (!group_next && !adjoint_rhs) {
             // combine the per-thread frame sums (M_j, v_j) over patch groups, compensated
             for (int q = tid; q < W * 27; q += kThreads) {
@@ -711,6 +699,32 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
         }
         __syncthreads();
+        if (!adjoint_rhs) {
+            // store each patch's row C_k^-1/2 (e_k, w_k, 1), pose columns compacted
+            // to 6 floats per free frame, for the next back-substitution
+            const int n4 = RS / 4, n6 = 6 * nf;
+            float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)k0 * RS);
+            for (int q = tid; q < cnt * n4; q += kThreads) {
+                const int p = q / n4, c = q - p * n4;
+                const float *e = Ec + p * ES;
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int o = 4 * c + u;
+                    float x = 0.f;
+                    if (o < n6) {
+                        const int f = o / 6, m = o - 6 * f;
+                        x = e[8 * f + m + (m >= 3 ? 1 : 0)];
+                    } else if (o == n6) {
+                        x = e[8 * nf];
+                    } else if (o == n6 + 1) {
+                        x = ps[p * 8];
+                    }
+                    v[u] = x;
+                }
+                dst[q] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
         if (!group_next && anc_free && !adjoint_rhs) {
             // pose-pair blocks involving the anchor, per window frame j:
             //   B_ij = -Ad_ij^T M_j,  B_ii += Ad_ij^T M_j Ad_ij,  v_i += -Ad_ij^T v_j
@@ -861,9 +875,6 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 #pragma unroll
             for (int q = 0; q < 6; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
         }
-    }
-    if (final_pass && itm.item == 0 && !pr.no_writeback) {
-        for (int q = tid; q < N * 7; q += kThreads) pr.poses[q] = pose_new[q];
     }
 }
 
