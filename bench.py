@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--parity-samples", type=int, default=2)
     ap.add_argument("--serving", type=int, default=1, help="run the serving measurement (Poisson sessions)")
+    ap.add_argument("--tf32", type=int, default=1, help="also time the opt-in tensor-core Schur mode")
     return ap.parse_args()
 
 
@@ -323,17 +324,20 @@ def main():
     statuses = batch.status.cpu().numpy()
     parity = None
     cpu_baseline = None
+    refs = {}
     if rank == 0 and args.parity_samples > 0:
         from oracle import dense_gn as dg
         idx = sorted(set([0, B - 1] + list(range(1, B - 1, max(1, B // max(1, args.parity_samples))))))[
             :args.parity_samples]
         errs_p, errs_d = [], []
         t_or = 0.0
+        refs = {}
         for b in idx:
             sc = scenes[b]
             t = time.perf_counter()
             ref = dg.solve_scene(sc)
             t_or += time.perf_counter() - t
+            refs[b] = ref
             poses = batch.view("poses", b).view(-1, 7).cpu().numpy().astype(np.float64)
             poses[:, 3:] *= np.sign((poses[:, 3:] * ref["poses"][:, 3:]).sum(1))[:, None]
             p0 = sc.poses.astype(np.float64).copy()
@@ -460,6 +464,41 @@ def main():
         e2e_s = float(tt.item())
     e2e_value = world * B * args.e2e_steps / e2e_s
 
+    # ---- opt-in tensor-core Schur mode on the same batch: throughput, parity
+    tf32 = None
+    if args.tf32:
+        tsolver = ba.Solver(schur_tf32=True)
+        tsolver.reserve(22, 2112, 39552, 2, B)
+        for _ in range(3):
+            tsolver.solve_arrays(batch.dims, batch.probs, B, stream)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            tsolver.solve_arrays(batch.dims, batch.probs, B, stream)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        tf32 = {"solves_per_s": world * B * args.steps / (a0.elapsed_time(a1) / 1e3),
+                "note": "sum_k E_k C_k^-1 E_k^T as three TF32 products on the tensor cores (tcgen05, TMEM)"}
+        if refs:
+            sub = ba.PackedBatch([scenes[b] for b in refs], "cuda")
+            tsolver.solve_arrays(sub.dims, sub.probs, len(refs), stream)
+            torch.cuda.synchronize()
+            ep, ed = [], []
+            for i, (b, ref) in enumerate(refs.items()):
+                sc = scenes[b]
+                poses = sub.view("poses", i).view(-1, 7).cpu().numpy().astype(np.float64)
+                poses[:, 3:] *= np.sign((poses[:, 3:] * ref["poses"][:, 3:]).sum(1))[:, None]
+                p0 = sc.poses.astype(np.float64).copy()
+                p0[:, 3:] *= np.sign((p0[:, 3:] * ref["poses"][:, 3:]).sum(1))[:, None]
+                ep.append(float(np.linalg.norm(poses[sc.t0:] - ref["poses"][sc.t0:]) /
+                                np.linalg.norm(ref["poses"][sc.t0:] - p0[sc.t0:])))
+                d = sub.view("patches", i).view(-1, 3)[:, 2].cpu().numpy().astype(np.float64)
+                ed.append(float(np.linalg.norm(d - ref["depths"]) / np.linalg.norm(ref["depths"] - sc.patches[:, 2])))
+            tf32["pose_update_rel_err_max"] = max(ep)
+            tf32["depth_update_rel_err_max"] = max(ed)
+        tsolver.close()
+
     serving = serving_bench() if (rank == 0 and args.serving) else None
 
     if rank == 0:
@@ -483,6 +522,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": args.e2e_steps, "api": "dpvo_ba_solve_host (pinned host buffers)"},
             "serving": serving,
+            "tf32_schur": tf32,
             "gpu_launches": world * n_launch_per_solve * args.steps,
             "clocks": clocks.summary(),
         }

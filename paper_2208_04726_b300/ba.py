@@ -27,7 +27,7 @@ class Dims(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("damping", ctypes.c_float), ("z_min", ctypes.c_float), ("mem_budget_bytes", ctypes.c_size_t),
-                ("max_sessions", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_sessions", ctypes.c_int32), ("schur_tf32", ctypes.c_int32)]
 
 
 class Grads(ctypes.Structure):
@@ -42,7 +42,7 @@ class Problem(ctypes.Structure):
 
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
-STATUS_OK, STATUS_NOT_SPD, STATUS_BAD_INPUT, STATUS_NONFINITE = 0, 1, 2, 4
+STATUS_OK, STATUS_NOT_SPD, STATUS_BAD_INPUT, STATUS_NONFINITE, STATUS_TIMEOUT = 0, 1, 2, 4, 8
 MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 15, 16
 
 # Every symbol the header declares (checked by the CPU tests).
@@ -168,9 +168,10 @@ class Solver:
     """A library handle (workspace + staging) on the current CUDA device."""
 
     def __init__(self, damping: float = 1e-4, z_min: float = 0.1, mem_budget_bytes: int = 0,
-                 max_sessions: int = 0):
+                 max_sessions: int = 0, schur_tf32: bool = False):
         self.lib = load()
-        cfg = Config(damping, z_min, mem_budget_bytes, max_sessions, 0)
+        self.schur_tf32 = bool(schur_tf32)
+        cfg = Config(damping, z_min, mem_budget_bytes, max_sessions, 1 if schur_tf32 else 0)
         h = ctypes.c_void_p()
         _check(self.lib.dpvo_ba_create(ctypes.byref(cfg), ctypes.byref(h)), "dpvo_ba_create")
         self.h = h

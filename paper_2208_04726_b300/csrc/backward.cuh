@@ -344,8 +344,6 @@ __global__ void __launch_bounds__(kThreads, 2) bw_edge_kernel(const Prob *__rest
     const float *pose_t = pr.pose_it + (size_t)t * N * 7;
     const float *depth_t = pr.depth_it + (size_t)t * pr.P;
     const float *depth_t1 = pr.depth_it + (size_t)(t + 1) * pr.P;
-    const float2 *tg_g = reinterpret_cast<const float2 *>(pr.target);
-    (void)tg_g;
 
     const int nch = *pr.n_chunks;
     const int c_begin = (int)(((long long)itm.item * nch) / pr.n_items);

@@ -25,8 +25,27 @@ struct Layout {
     std::vector<Item> items;
     size_t bytes = 0, off_probs = 0, off_items = 0;
     int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0, n_max = 1;
+    bool tc = false;               // Schur accumulation on the tensor cores
     size_t lin_smem = 0, solve_smem = 0;
 };
+
+// Stored Schur rows: one row per patch, or in the tensor-core variant one
+// block of kTcRows x Kmax floats per chunk.
+static size_t erow_bytes(bool tc, const Prob &p, int G_cap) {
+    if (tc) return (size_t)p.max_chunks * kTcRows * tc_kmax(G_cap) * 4 + 16;
+    return (size_t)p.P * erow_len(p.nf) * 4 + 16;
+}
+
+// One linearise launch, in the batch's variant.
+static void launch_linearize(bool tc, int grid, size_t smem, cudaStream_t stream, const Prob *probs,
+                             const Item *items, int t, int W_cap, int G_cap, int nf_max, int n_max, int adjoint_rhs) {
+    if (tc)
+        linearize_kernel<true><<<grid, kThreads, smem, stream>>>(probs, items, t, W_cap, G_cap, nf_max, n_max,
+                                                                 adjoint_rhs);
+    else
+        linearize_kernel<false><<<grid, kThreads, smem, stream>>>(probs, items, t, W_cap, G_cap, nf_max, n_max,
+                                                                  adjoint_rhs);
+}
 
 int check_dims(const dpvo_ba_dims &d) {
     if (d.n_frames < 1 || d.n_frames > DPVO_BA_MAX_FRAMES) return DPVO_BA_EINVAL;
@@ -55,10 +74,12 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         L.iters_max = std::max(L.iters_max, dims[b].n_iters);
     }
     L.n_max = n_max;
+    L.tc = cfg.schur_tf32 && use_tensor_cores(L.nf_max);
     L.W_cap = std::min(n_max, kMaxWindow);
     L.G_cap = 64;
-    while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max).bytes > kLinSmemBudget) L.G_cap -= 8;
-    L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max).bytes;
+    while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes > kLinSmemBudget)
+        L.G_cap -= 8;
+    L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
     const int n6 = 6 * L.nf_max;
     L.solve_smem = (size_t)n6 * (n6 + 1) * 8 + (size_t)n6 * 8 + 16;
 
@@ -76,7 +97,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.chunk_cap = L.G_cap;
         p.win_cap = L.W_cap;
         p.max_chunks = (d.n_patches + L.G_cap - 1) / L.G_cap + d.n_frames;
-        p.ks = k_split(p.nf);
+        p.ks = L.tc ? 1 : k_split(p.nf);
         p.L = partial_len(p.nf);
         int est_chunks = std::max(1, (d.n_patches + L.G_cap - 1) / L.G_cap);
         int items = n >= target_ctas ? 1 : (target_ctas + n - 1) / n;
@@ -92,7 +113,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.depth_it = (float *)(uintptr_t)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
         p.dxi = (double *)(uintptr_t)take((size_t)d.n_iters * p.nf * 6 * 8 + 8);
         p.partial = (double *)(uintptr_t)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
-        p.erow = (float *)(uintptr_t)take((size_t)d.n_patches * erow_len(p.nf) * 4 + 16);
+        p.erow = (float *)(uintptr_t)take(erow_bytes(L.tc, p, L.G_cap));
         if (adjoint) {
             const size_t n6 = 6 * (size_t)p.nf;
             p.store_factor = 1;
@@ -187,7 +208,10 @@ static bool g_attr_set[64] = {false};
 
 static int set_kernel_attrs(int device) {
     if (device >= 0 && device < 64 && g_attr_set[device]) return DPVO_BA_OK;
-    if (cudaFuncSetAttribute(linearize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+    if (cudaFuncSetAttribute(linearize_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(linearize_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
@@ -247,16 +271,16 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         }
         return DPVO_BA_OK;
     };
-    if ((rc = timed(0, [&] { plan_kernel<<<n, kThreads, 0, stream>>>(d_probs); }))) return rc;
+    if ((rc = timed(0, [&] { plan_kernel<<<n, kPlanThreads, 0, stream>>>(d_probs); }))) return rc;
     if (S_out) {
-        linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, 0, L.W_cap, L.G_cap,
-                                                                     L.nf_max, L.n_max, 0);
+        launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, 0, L.W_cap, L.G_cap, L.nf_max,
+                         L.n_max, 0);
         solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, 0, S_out, v_out);
     } else {
         for (int t = 0; t <= L.iters_max; ++t) {
             rc = timed(1, [&] {
-                linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap,
-                                                                             L.G_cap, L.nf_max, L.n_max, 0);
+                launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, t, L.W_cap, L.G_cap,
+                                 L.nf_max, L.n_max, 0);
             });
             if (rc) return rc;
             if (t < L.iters_max) {
@@ -319,17 +343,17 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
     const int n_items = (int)L.items.size();
     const size_t bw_smem = bw_smem_layout(L.W_cap, L.G_cap, L.n_max).bytes;
-    plan_kernel<<<n, kThreads, 0, stream>>>(d_probs);
+    plan_kernel<<<n, kPlanThreads, 0, stream>>>(d_probs);
     for (int t = 0; t <= L.iters_max; ++t) {
-        linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap,
-                                                                     L.nf_max, L.n_max, 0);
+        launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, t, L.W_cap, L.G_cap, L.nf_max,
+                         L.n_max, 0);
         if (t < L.iters_max) solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
     }
     bw_init_kernel<<<n, kThreads, 0, stream>>>(d_probs);
     for (int t = L.iters_max - 1; t >= 0; --t) {
         bw_retract_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
-        linearize_kernel<<<n_items, kThreads, L.lin_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap,
-                                                                     L.nf_max, L.n_max, 1);
+        launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, t, L.W_cap, L.G_cap, L.nf_max,
+                         L.n_max, 1);
         bw_solve_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
         bw_edge_kernel<<<n_items, kThreads, bw_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap, L.n_max);
     }
@@ -361,7 +385,7 @@ int dpvo_ba_create(const dpvo_ba_config *cfg, dpvo_ba_handle **out) {
     h->cfg.z_min = 0.1f;
     h->cfg.mem_budget_bytes = (size_t)8 << 30;
     h->cfg.max_sessions = 256;
-    h->cfg.reserved = 0;
+    h->cfg.schur_tf32 = 0;
     if (cfg) {
         h->cfg = *cfg;
         if (h->cfg.mem_budget_bytes == 0) h->cfg.mem_budget_bytes = (size_t)8 << 30;
@@ -974,9 +998,10 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     const dpvo_ba_dims &d = *dims;
     const int nf = d.n_frames - d.t0;
     const int W_cap = std::min(d.n_frames, kMaxWindow);
+    const bool tc = cfg && cfg->schur_tf32 && use_tensor_cores(nf);
     int G_cap = 64;
-    while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf, d.n_frames).bytes > kLinSmemBudget) G_cap -= 8;
-    const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf, d.n_frames).bytes;
+    while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes > kLinSmemBudget) G_cap -= 8;
+    const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes;
     const size_t solve_smem = (size_t)(6 * nf) * (6 * nf + 1) * 8 + (size_t)(6 * nf) * 8 + 16;
     Prob p;
     std::memset(&p, 0, sizeof(Prob));
@@ -988,7 +1013,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.chunk_cap = G_cap;
     p.win_cap = W_cap;
     p.max_chunks = (d.n_patches + G_cap - 1) / G_cap + d.n_frames;
-    p.ks = k_split(nf);
+    p.ks = tc ? 1 : k_split(nf);
     p.L = partial_len(nf);
     const int est_chunks = std::max(1, (d.n_patches + G_cap - 1) / G_cap);
     p.n_items = std::max(1, std::min(2 * g_noalloc_sms[dev], est_chunks));
@@ -1004,16 +1029,15 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.depth_it = (float *)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
     p.dxi = (double *)take((size_t)d.n_iters * nf * 6 * 8 + 8);
     p.partial = (double *)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
-    p.erow = (float *)take((size_t)d.n_patches * erow_len(nf) * 4 + 16);
+    p.erow = (float *)take(erow_bytes(tc, p, G_cap));
     Prob *d_prob = (Prob *)take(sizeof(Prob));
     Item *d_items = (Item *)take(sizeof(Item) * p.n_items);
     if (off > kNoAllocScratchBytes) return DPVO_BA_EINVAL;   // problem too large for the fixed scratch
 
     noalloc_descriptors_kernel<<<1, kThreads, 0, stream>>>(p, p.n_items, d_prob, d_items);
-    plan_kernel<<<1, kThreads, 0, stream>>>(d_prob);
+    plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_prob);
     for (int t = 0; t <= d.n_iters; ++t) {
-        linearize_kernel<<<p.n_items, kThreads, lin_smem, stream>>>(d_prob, d_items, t, W_cap, G_cap, nf,
-                                                                     d.n_frames, 0);
+        launch_linearize(tc, p.n_items, lin_smem, stream, d_prob, d_items, t, W_cap, G_cap, nf, d.n_frames, 0);
         if (t < d.n_iters) solve_kernel<<<1, kSolveThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
     }
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;

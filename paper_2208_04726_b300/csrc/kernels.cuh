@@ -1,7 +1,8 @@
 // Bundle-adjustment kernels (Deep Patch Visual Odometry, Sec. 3.1 Eq. 6).
 //
 //   plan_kernel       once per solve: validates indices and ordering, builds the
-//                     patch -> edge offsets and the chunk table, copies the
+//                     patch -> edge offsets and the chunk table in one pass
+//                     over the anchors and one over the edges, copies the
 //                     initial state into iterate 0.
 //   linearize_kernel  once per iteration (and once more at the end): for each
 //                     chunk of patches that share a source frame,
@@ -28,6 +29,7 @@
 
 #include "ba_common.cuh"
 #include "se3.cuh"
+#include "tc.cuh"
 
 namespace dpvo {
 
@@ -94,19 +96,16 @@ __device__ __forceinline__ void anchor_terms(const EdgeLin &L, const float *Rij,
     Y2 = fmaf(Rij[8], g2, fmaf(Rij[5], g1, Rij[2] * g0));
 }
 
-__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int key) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (a[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
+// ----------------------------------------------------------------------------
+// plan_kernel: one CTA of kPlanThreads per problem.  One coalesced pass over
+// the anchors and one over the edges check the ordering and, at every change
+// of anchor (patch), record where each frame's patches (each patch's edges)
+// begin; no searches.
+// ----------------------------------------------------------------------------
+constexpr int kPlanThreads = 1024;
+constexpr int kPlanUnroll = 4;
 
-// ----------------------------------------------------------------------------
-// plan_kernel: one CTA per problem.
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__ probs) {
+__global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__restrict__ probs) {
     const Prob &pr = probs[blockIdx.x];
     const int tid = threadIdx.x;
     const int N = pr.N, P = pr.P, E = pr.E;
@@ -114,37 +113,62 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__
     __shared__ int s_fstart[DPVO_BA_MAX_FRAMES + 1];
     __shared__ int s_choff[DPVO_BA_MAX_FRAMES + 1];
     if (tid == 0) s_bad = 0;
+    if (P == 0)
+        for (int i = tid; i <= N; i += kPlanThreads) s_fstart[i] = 0;
+    if (E == 0)
+        for (int k = tid; k <= P; k += kPlanThreads) pr.seg[k] = 0;
     __syncthreads();
 
-    for (int i = tid; i < N * 7; i += kThreads) pr.pose_it[i] = pr.poses[i];
-    for (int k = tid; k < P; k += kThreads) pr.depth_it[k] = pr.patches[3 * k + 2];
-
     int bad = 0;
-    for (int k = tid; k < P; k += kThreads) {
-        const int a = pr.anchor[k];
-        if (a < 0 || a >= N) bad = 1;
-        else if (k > 0 && pr.anchor[k - 1] > a) bad = 1;
+    for (int i = tid; i < N * 7; i += kPlanThreads) {
+        const float v = pr.poses[i];
+        pr.pose_it[i] = v;
+        if (!isfinite(v)) bad = 1;
     }
-    for (int e = tid; e < E; e += kThreads) {
-        const int k = pr.kk[e], j = pr.jj[e];
-        if (k < 0 || k >= P || j < 0 || j >= N) { bad = 1; continue; }
-        if (e > 0) {
-            const int kp = pr.kk[e - 1];
-            if (kp > k) bad = 1;
-            else if (kp == k && pr.jj[e - 1] >= j) bad = 1;
+    for (int k = tid; k < P; k += kPlanThreads) {
+        pr.depth_it[k] = pr.patches[3 * k + 2];
+        const int a = pr.anchor[k];
+        const int ap = k > 0 ? pr.anchor[k - 1] : -1;
+        if (a < 0 || a >= N || ap > a) {
+            bad = 1;
+        } else {
+            for (int i = max(ap + 1, 0); i <= a; ++i) s_fstart[i] = k;     // frames (ap, a] start at k
+            if (k == P - 1)
+                for (int i = a + 1; i <= N; ++i) s_fstart[i] = P;
         }
     }
-    for (int i = tid; i < N * 7; i += kThreads)
-        if (!isfinite(pr.poses[i])) bad = 1;
+    for (int base = 0; base < E; base += kPlanUnroll * kPlanThreads) {
+        int kv[kPlanUnroll], jv[kPlanUnroll], kp[kPlanUnroll], jp[kPlanUnroll];
+#pragma unroll
+        for (int u = 0; u < kPlanUnroll; ++u) {   // loads of all unrolled edges first
+            const int e = base + u * kPlanThreads + tid;
+            kv[u] = 0; jv[u] = 0; kp[u] = -1; jp[u] = -1;
+            if (e < E) {
+                kv[u] = pr.kk[e];
+                jv[u] = pr.jj[e];
+                if (e > 0) { kp[u] = pr.kk[e - 1]; jp[u] = pr.jj[e - 1]; }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPlanUnroll; ++u) {
+            const int e = base + u * kPlanThreads + tid;
+            if (e >= E) continue;
+            const int k = kv[u], j = jv[u];
+            if (k < 0 || k >= P || j < 0 || j >= N || kp[u] > k || (kp[u] == k && jp[u] >= j)) {
+                bad = 1;
+                continue;
+            }
+            for (int q = max(kp[u] + 1, 0); q <= k; ++q) pr.seg[q] = e;   // patches (kp, k] start at e
+            if (e == E - 1)
+                for (int q = k + 1; q <= P; ++q) pr.seg[q] = E;
+        }
+    }
     if (bad) atomicOr(&s_bad, 1);
     __syncthreads();
     if (s_bad) {
         if (tid == 0) { *pr.status = DPVO_BA_STATUS_BAD_INPUT; *pr.n_chunks = 0; }
         return;
     }
-    for (int k = tid; k <= P; k += kThreads) pr.seg[k] = lower_bound_i32(pr.kk, E, k);
-    for (int i = tid; i <= N; i += kThreads) s_fstart[i] = lower_bound_i32(pr.anchor, P, i);
-    __syncthreads();
     if (tid == 0) {
         int off = 0;
         for (int i = 0; i < N; ++i) {
@@ -156,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__
         if (off > pr.max_chunks) s_bad = 1;
     }
     __syncthreads();
-    for (int i = tid; i < N && !s_bad; i += kThreads) {
+    for (int i = tid; i < N && !s_bad; i += kPlanThreads) {
         const int cnt = s_fstart[i + 1] - s_fstart[i];
         const int nch = s_choff[i + 1] - s_choff[i];
         if (nch == 0) continue;
@@ -182,8 +206,8 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__
     // frame, so its first and last edges bound it
     const int lane = tid & 31, warp = tid >> 5;
     const int n_built = s_bad ? 0 : s_choff[N];    // 0 if the chunk table overflowed
-    for (int c = warp; c < n_built; c += kThreads / 32) {
-        Chunk ch = pr.chunks[c];
+    for (int c = warp; c < n_built; c += kPlanThreads / 32) {
+        const Chunk ch = pr.chunks[c];
         int jlo = ch.anchor, jhi = ch.anchor;
         for (int q = ch.k0 + lane; q < ch.k0 + ch.count; q += 32) {
             const int s0 = pr.seg[q], s1 = pr.seg[q + 1];
@@ -216,14 +240,26 @@ __global__ void __launch_bounds__(kThreads) plan_kernel(const Prob *__restrict__
 // ----------------------------------------------------------------------------
 struct LinSmem {
     int W, G, Gs, ES, EC;  // window cap, chunk cap, odd slot stride, E-column stride, edge capacity
+    uint32_t sbo;          // tensor-core operand: bytes between 8-row groups
     size_t off_pose, off_rjj, off_rtg, off_rwt, off_rpx, off_rpy, off_rdep, off_rseg, off_idx, off_sc4, off_sc1,
-        off_ec, off_mp, off_reln, off_adj, off_mc, off_aj, off_bp, off_bii, off_pd, off_ps, off_dx;
+        off_ec, off_op, off_mp, off_reln, off_adj, off_mc, off_aj, off_bp, off_bii, off_pd, off_ps, off_dx;
     size_t bytes;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int n_max) {
+// Free poses up to which the Schur accumulation runs on the tensor cores:
+// 6 nf + 2 rows (pose columns, then C^-1/2 w split in two) fit one 64-row operand.
+constexpr int kTcMaxFree = 10;
+constexpr int kTcRows = 64;                    // rows of each half (lo, hi) of the operand
+constexpr int kTcXStride = 65;                 // row stride (floats) of the accumulator read-back
+__host__ __device__ inline bool use_tensor_cores(int nf_max) { return nf_max <= kTcMaxFree; }
+
+// tc: tensor-core variant.  It keeps no E_k rows (Ec); instead a K-major TF32
+// operand of 2 x 64 rows (lo half, hi half) by G patches, and reads the TMEM
+// accumulator back through a 128 x 65 float buffer that overlays the staging
+// buffers, dead by then.
+__host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int n_max, bool tc) {
     LinSmem s;
     s.W = W;
     s.G = G;
@@ -233,10 +269,12 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     const int es = 8 * nf_max + 4;
     s.ES = es;
     s.EC = W * G;
+    const int kmax = (G + 7) & ~7;
+    s.sbo = (uint32_t)(kmax / 4) * 144u;
     const size_t slots = (size_t)W * s.Gs;
     // the per-slot sums share their buffer with the staged Schur rows of the
     // next chunk (read before the slots are written)
-    const size_t rows = (size_t)G * erow_smem_stride(nf_max) * 4;
+    const size_t rows = tc ? (size_t)kTcRows * kmax * 4 : (size_t)G * erow_smem_stride(nf_max) * 4;
     const size_t sc4 = slots * 16 > rows ? slots * 16 : rows;
     size_t o = 0;
     s.off_pose = o; o = align16(o + (size_t)n_max * 7 * 4);
@@ -250,19 +288,62 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     s.off_idx = o;  o = align16(o + slots * 2);
     s.off_sc4 = o;  o = align16(o + sc4);
     s.off_sc1 = o;  o = align16(o + slots * 4);
-    s.off_ec = o;   o = align16(o + (size_t)G * es * 4);
+    if (tc) {
+        s.off_ec = 0;
+        s.off_op = o; o = align16(o + (size_t)2 * (kTcRows / 8) * s.sbo);
+        const size_t xend = s.off_rjj + (size_t)2 * kTcRows * kTcXStride * 4;
+        if (o < xend) o = align16(xend);
+    } else {
+        s.off_op = 0;
+        s.off_ec = o; o = align16(o + (size_t)G * es * 4);
+    }
+    // the anchor-pair products (A_j, B_j) overlay the per-thread frame sums,
+    // which are consumed before them
     s.off_mp = o;   o = align16(o + (size_t)kThreads * 27 * 4);
+    s.off_aj = s.off_mp;
+    s.off_bp = s.off_mp + align16((size_t)W * 42 * 4);
     s.off_reln = o; o = align16(o + (size_t)W * 12 * 4);
     s.off_adj = o;  o = align16(o + (size_t)W * 36 * 4);
     s.off_mc = o;   o = align16(o + (size_t)W * 27 * 4);
-    s.off_aj = o;   o = align16(o + (size_t)W * 42 * 4);
-    s.off_bp = o;   o = align16(o + (size_t)W * 42 * 4);
     s.off_bii = o;  o = align16(o + 42 * 4);
     s.off_pd = o;   o = align16(o + (size_t)G * 16);
-    s.off_ps = o;   o = align16(o + (size_t)G * 8 * 4);
+    s.off_ps = o;   o = align16(o + (size_t)2 * G * 4);
     s.off_dx = o;   o = align16(o + (size_t)erow_len(kMaxFree) * 4);
     s.bytes = o;
     return s;
+}
+
+// Tensor-core variant: the stored Schur rows of chunk c form one block of
+// kTcRows x Kmax floats (Kmax = chunk cap rounded up to 8) at c * kTcRows *
+// Kmax, element (row r, patch p of the chunk) at (p / 4) * 256 + 4 r + p % 4:
+// rows 0..6nf-1 hold C_k^-1/2 e_k, row 62 C_k^-1/2 w_k, row 63 C_k^-1/2, the
+// rest zero.  The 8 x 4 (row, patch) tiles of the MMA operand map to 128
+// contiguous bytes of it.
+__host__ __device__ inline int tc_kmax(int G) { return (G + 7) & ~7; }
+__host__ __device__ inline int tc_blk(int r, int p) { return (p >> 2) * (4 * kTcRows) + 4 * r + (p & 3); }
+
+// Back-substitution dot products of one 4-patch group of a stored block
+// (tensor-core variant): the 8 lanes rs = 0..7 of an aligned octet take rows
+// rs, rs + 8, ... (< n6), each row one float4 of the 4 patches; the octet sum
+// lands in every lane.  Returns the 4 dot products with dx (zero beyond n6).
+__device__ __forceinline__ float4 group_dots(const float *grp, const float *dx, int n6, int rs) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = rs; r < n6; r += 8) {
+        const float4 v = *reinterpret_cast<const float4 *>(grp + 4 * r);
+        const float x = dx[r];
+        acc.x = fmaf(v.x, x, acc.x);
+        acc.y = fmaf(v.y, x, acc.y);
+        acc.z = fmaf(v.z, x, acc.z);
+        acc.w = fmaf(v.w, x, acc.w);
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+    }
+    return acc;
 }
 
 // Compensated (Kahan) update of a running sum (s, c) with the block sum blk.
@@ -328,6 +409,14 @@ __device__ __forceinline__ void prefetch_rows(const Prob &pr, const Chunk &ch, i
     cp_async_commit();
 }
 
+// Start copying chunk c's block of stored rows (its first ceil8(count) patches) to dst.
+__device__ __forceinline__ void prefetch_block(const Prob &pr, int c, const Chunk &ch, int kmax, float *dst) {
+    const int n16 = ((ch.count + 7) & ~7) * kTcRows / 4;
+    const float4 *src = reinterpret_cast<const float4 *>(pr.erow + (size_t)c * kTcRows * kmax);
+    for (int q = threadIdx.x; q < n16; q += kThreads) cp_async16(dst + 4 * q, src + q);
+    cp_async_commit();
+}
+
 __device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
     return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
 }
@@ -358,7 +447,18 @@ __device__ __forceinline__ float quad_sum(float v) {
 // previous chunk is still being reduced.  Consecutive chunks with the same
 // anchor and frame window form a group that shares its window poses and its
 // pose-pair blocks.
+//
+// TC (tensor-core variant, at most kTcMaxFree free poses): instead of FP32
+// strips, sum_k E_k C_k^-1 E_k^T and sum_k E_k C_k^-1 w_k accumulate in TMEM
+// through kind::tf32 MMAs with each operand value x split as hi = tf32(x),
+// lo = tf32(x - hi) and the product taken as hi.hi + lo.hi + (lo.hi)^T (three
+// TF32 terms, near-FP32 accuracy).  Per chunk, the operand holds lo (rows
+// 0-63) and hi (rows 64-127) of C_k^-1/2 E_k^T by patch (K-major); rows 62 and
+// 63 of the hi half carry hi and lo of C_k^-1/2 w_k.  One MMA per 8 patches
+// with A = all 128 rows and B = the hi half gives D = [lo; hi] hi^T; the CTA
+// reads D back once, after its last chunk.
 // ----------------------------------------------------------------------------
+template <bool TC>
 __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__restrict__ probs,
                                                              const Item *__restrict__ items, int t,
                                                              int W_cap, int G_cap, int nf_max, int n_max,
@@ -366,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     extern __shared__ __align__(16) unsigned char smem[];
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (t > pr.iters) return;
     // adjoint_rhs: linearise at iterate t only and accumulate the pose part of
     // E C^-1 dbar (dbar = gradient w.r.t. the inverse depths) into the
@@ -379,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         if (st != 0) return;
     }
 
-    const LinSmem L = lin_smem_layout(W_cap, G_cap, nf_max, n_max);
+    const LinSmem L = lin_smem_layout(W_cap, G_cap, nf_max, n_max, TC);
     float *spn = reinterpret_cast<float *>(smem + L.off_pose);        // poses of iterate t
     int *rjj = reinterpret_cast<int *>(smem + L.off_rjj);
     float2 *rtg = reinterpret_cast<float2 *>(smem + L.off_rtg);
@@ -393,6 +493,8 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     float *srow = reinterpret_cast<float *>(smem + L.off_sc4);        // staged Schur rows (aliases sc4)
     float *sc1 = reinterpret_cast<float *>(smem + L.off_sc1);
     float *Ec = reinterpret_cast<float *>(smem + L.off_ec);
+    unsigned char *op = smem + L.off_op;                                // tensor-core operand
+    const uint32_t sbo = L.sbo;
     float *Mp = reinterpret_cast<float *>(smem + L.off_mp);
     float *reln = reinterpret_cast<float *>(smem + L.off_reln);
     float *adj = reinterpret_cast<float *>(smem + L.off_adj);
@@ -407,6 +509,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
     const int N = pr.N, t0 = pr.t0, nf = pr.nf;
     const int RS = erow_len(nf), RSS = erow_smem_stride(nf);
+    const int kmax = tc_kmax(G_cap);
     const float fx = pr.fx, fy = pr.fy, cx = pr.cx, cy = pr.cy, z_min = pr.z_min, lam = pr.damping;
     const float ifx = 1.0f / fx, ify = 1.0f / fy;
     const float *pose_new = pr.pose_it + (size_t)t * N * 7;
@@ -420,13 +523,37 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
     if (do_bs) {   // the previous iteration's pose increments, zero-padded to the row length
         const double *dx = pr.dxi + (size_t)(t - 1) * nf * 6;
-        for (int q = tid; q < RS; q += kThreads) dxs[q] = q < 6 * nf ? (float)dx[q] : 0.f;
+        const int len = TC ? kTcRows : RS;
+        for (int q = tid; q < len; q += kThreads) dxs[q] = q < 6 * nf ? (float)dx[q] : 0.f;
     }
     if (final_pass) {
         // last back-substitution: dd_k = C_k^-1/2 (C_k^-1/2 w_k - (C_k^-1/2 e_k) . dxi)
         // for every patch of this item's chunks, four lanes per patch
         __syncthreads();
-        if (c_begin < c_end) {
+        if constexpr (TC) {
+            // one warp per chunk, one lane octet per 4-patch group
+            const int n6 = 6 * nf, rs = lane & 7, gw = lane >> 3;
+            for (int c = c_begin + warp; c < c_end; c += kThreads / 32) {
+                const Chunk ch = pr.chunks[c];
+                const float *eb = pr.erow + (size_t)c * kTcRows * kmax;
+                const int ng = (ch.count + 3) >> 2;
+                for (int gb = 0; gb < ng; gb += 4) {      // warp-uniform trip count
+                    const int g = gb + gw;
+                    const float *grp = eb + (size_t)(g < ng ? g : 0) * (4 * kTcRows);
+                    const float4 dots = group_dots(grp, dxs, g < ng ? n6 : 0, rs);
+                    if (g < ng && rs < 4) {
+                        const int p = 4 * g + rs;
+                        if (p < ch.count) {
+                            const float dot = rs == 0 ? dots.x : rs == 1 ? dots.y : rs == 2 ? dots.z : dots.w;
+                            const int k = ch.k0 + p;
+                            const float dnew = depth_old[k] + grp[4 * (kTcRows - 1) + rs] * (grp[4 * (kTcRows - 2) + rs] - dot);
+                            depth_new[k] = dnew;
+                            if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
+                        }
+                    }
+                }
+            }
+        } else if (c_begin < c_end) {
             const Chunk ca = pr.chunks[c_begin], cz = pr.chunks[c_end - 1];
             const int k_lo = ca.k0, k_hi = cz.k0 + cz.count;
             const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
@@ -474,13 +601,34 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
     for (int q = tid; q < N * 7; q += kThreads) spn[q] = pose_new[q];
 
+    // tensor-core state: TMEM accumulator (64 columns), MMA-completion barrier
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_tc_bad;
+    uint32_t tmem = 0;
+    int n_commit = 0;          // MMA batches committed so far (the same in every thread)
+    if constexpr (TC) {
+        if (warp == 0) tmem_alloc(&s_tmem, 64);
+        if (tid == 0) {
+            mbar_init(smem_u32(&s_mbar), 1);
+            s_tc_bad = 0;
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        tmem = s_tmem;
+    }
+
     __shared__ __align__(16) Chunk s_ch[2];
     if (c_begin < c_end) {
         if (tid == 0) s_ch[0] = pr.chunks[c_begin];
         __syncthreads();
         prefetch_chunk(pr, s_ch[0], depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
                        c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1]);
-        if (do_bs) prefetch_rows(pr, s_ch[0], RS, RSS, srow);
+        if (do_bs) {
+            if constexpr (TC) prefetch_block(pr, c_begin, s_ch[0], kmax, srow);
+            else prefetch_rows(pr, s_ch[0], RS, RSS, srow);
+        }
     }
     int cur = 0;
     bool group_open = false;   // the previous chunk continues into this one
@@ -504,6 +652,10 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
         // -- (0) slot -> edge table, patch data, window poses, cleared E columns.
         // Thread (p = tid mod 64, jl = tid / 64 + 4 i) for the slots.
+        if constexpr (TC) {
+            // the previous chunk's MMAs read the operand: wait before rewriting it
+            if (n_commit > 0 && !mbar_wait(smem_u32(&s_mbar), (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_tc_bad, 1);
+        }
         {
             const int p = tid & 63;
             if (p < cnt) {
@@ -535,31 +687,57 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 for (int f = tid >> 6; f < nf; f += kThreads / 64) {   // E columns of free frames outside the window are zero
                     const int fr = t0 + f;
                     if (fr < jlo || fr > ch.jhi) {
-                        float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * f);
-                        e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        e4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if constexpr (TC) {
+#pragma unroll
+                            for (int m = 0; m < 6; ++m)
+                                *reinterpret_cast<float *>(op + op_offset(kTcRows + 6 * f + m, p, sbo)) = 0.f;
+                        } else {
+                            float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * f);
+                            e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            e4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
                     }
                 }
             }
         }
         {   // patch data, after the back-substitution of the previous iteration
             // from the staged rows (four lanes per patch)
-            const int p = tid >> 2, sub = tid & 3;
-            float s = 0.f;
-            if (do_bs && p < cnt) {
-                const float4 *row = reinterpret_cast<const float4 *>(srow + p * RSS);
-                const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
-                for (int q = sub; q < RS / 4; q += 4) s = dot4(row[q], dz4[q], s);
-            }
-            s = quad_sum(s);
-            if (sub == 0 && p < cnt) {
-                float d = rdep[p];
-                if (do_bs) {
-                    const float *row = srow + p * RSS;
-                    d += row[6 * nf + 1] * (row[6 * nf] - s);
-                    depth_new[k0 + p] = d;
+            if constexpr (TC) {
+                // thread (group g = tid / 8, row slice tid % 8): 4 patches per group
+                const int g = tid >> 3, rs = tid & 7, ng = (cnt + 3) >> 2;
+                float4 dots = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float *grp = srow + (size_t)(g < ng ? g : 0) * (4 * kTcRows);
+                if (do_bs) dots = group_dots(grp, dxs, g < ng ? 6 * nf : 0, rs);
+                if (g < ng && rs < 4) {
+                    const int p = 4 * g + rs;
+                    if (p < cnt) {
+                        float d = rdep[p];
+                        if (do_bs) {
+                            const float dot = rs == 0 ? dots.x : rs == 1 ? dots.y : rs == 2 ? dots.z : dots.w;
+                            d += grp[4 * (kTcRows - 1) + rs] * (grp[4 * (kTcRows - 2) + rs] - dot);
+                            depth_new[k0 + p] = d;
+                        }
+                        pd[p] = make_float4((rpx[p] - cx) * ifx, (rpy[p] - cy) * ify, d, 0.f);
+                    }
                 }
-                pd[p] = make_float4((rpx[p] - cx) * ifx, (rpy[p] - cy) * ify, d, 0.f);
+            } else {
+                const int p = tid >> 2, sub = tid & 3;
+                float s = 0.f;
+                if (do_bs && p < cnt) {
+                    const float4 *row = reinterpret_cast<const float4 *>(srow + p * RSS);
+                    const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
+                    for (int q = sub; q < RS / 4; q += 4) s = dot4(row[q], dz4[q], s);
+                }
+                s = quad_sum(s);
+                if (sub == 0 && p < cnt) {
+                    float d = rdep[p];
+                    if (do_bs) {
+                        const float *row = srow + p * RSS;
+                        d += row[6 * nf + 1] * (row[6 * nf] - s);
+                        depth_new[k0 + p] = d;
+                    }
+                    pd[p] = make_float4((rpx[p] - cx) * ifx, (rpy[p] - cy) * ify, d, 0.f);
+                }
             }
         }
         if (!group_open) window_poses(spn, anc, jlo, W, reln, adj);
@@ -622,9 +800,16 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                 }
                 if (jfree) {   // e_jk = J_j^T W J_d (zero for a missing or inactive edge)
-                    float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * fj);
-                    e4[0] = elo;
-                    e4[1] = ehi;
+                    if constexpr (TC) {   // unscaled, FP32, in the hi half
+                        const float ev[6] = {elo.x, elo.y, elo.z, ehi.x, ehi.y, ehi.z};
+#pragma unroll
+                        for (int m = 0; m < 6; ++m)
+                            *reinterpret_cast<float *>(op + op_offset(kTcRows + 6 * fj + m, p, sbo)) = ev[m];
+                    } else {
+                        float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * fj);
+                        e4[0] = elo;
+                        e4[1] = ehi;
+                    }
                 }
                 sc4[slot] = make_float4(Ce, we, Y0, Y1);
                 sc1[slot] = Y2;
@@ -662,21 +847,35 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 float *e = Ec + p * ES;
                 if (sub == 0) {
                     const float sq = sqrtf(1.0f / C);
-                    ps[p * 8] = sq;
-                    e[8 * nf] = sq * (adjoint_rhs ? pr.dbar[k0 + p] : w);
+                    const float sw = sq * (adjoint_rhs ? pr.dbar[k0 + p] : w);
+                    ps[p] = sq;
+                    if constexpr (TC) ps[G_cap + p] = sw;
+                    else e[8 * nf] = sw;
                 } else if (anc_free && sub < 3) {
                     const float4 qd = pd[p];
                     const float d = qd.z, px = qd.x, py = qd.y;
-                    float4 *ei = reinterpret_cast<float4 *>(e + 8 * (anc - t0));
-                    if (sub == 1) ei[0] = make_float4(-d * Y0, -d * Y1, -d * Y2, 0.f);
-                    else                                   // -(pbar x Y), pbar = (px, py, 1)
-                        ei[1] = make_float4(-(py * Y2 - Y1), -(Y0 - px * Y2), -(px * Y1 - py * Y0), 0.f);
+                    float3 v;
+                    if (sub == 1) v = make_float3(-d * Y0, -d * Y1, -d * Y2);
+                    else          // -(pbar x Y), pbar = (px, py, 1)
+                        v = make_float3(-(py * Y2 - Y1), -(Y0 - px * Y2), -(px * Y1 - py * Y0));
+                    if constexpr (TC) {
+                        const int r0 = kTcRows + 6 * (anc - t0) + 3 * (sub - 1);
+                        *reinterpret_cast<float *>(op + op_offset(r0, p, sbo)) = v.x;
+                        *reinterpret_cast<float *>(op + op_offset(r0 + 1, p, sbo)) = v.y;
+                        *reinterpret_cast<float *>(op + op_offset(r0 + 2, p, sbo)) = v.z;
+                    } else {
+                        float4 *ei = reinterpret_cast<float4 *>(e + 8 * (anc - t0));
+                        ei[sub - 1] = make_float4(v.x, v.y, v.z, 0.f);
+                    }
                 }
             }
         }
         __syncthreads();
         // the per-slot sums are consumed: start copying the next chunk's stored rows
-        if (do_bs && have_next) prefetch_rows(pr, nx, RS, RSS, srow);
+        if (do_bs && have_next) {
+            if constexpr (TC) prefetch_block(pr, c + 1, nx, kmax, srow);
+            else prefetch_rows(pr, nx, RS, RSS, srow);
+        }
         if (!group_next && !adjoint_rhs) {
             // combine the per-thread frame sums (M_j, v_j) over patch groups, compensated
             for (int q = tid; q < W * 27; q += kThreads) {
@@ -686,43 +885,96 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 Mc[jl * 27 + m] = s - cc;
             }
         }
-        {   // E_k (pose columns) scaled by C_k^-1/2
-            const int n4 = 2 * nf;
-            for (int p = tid >> 6; p < cnt; p += kThreads / 64) {
-                const float sq = ps[p * 8];
-                float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES);
-                for (int m = tid & 63; m < n4; m += 64) {
-                    float4 v = e4[m];
-                    v.x *= sq; v.y *= sq; v.z *= sq;
-                    e4[m] = v;
+        if constexpr (TC) {
+            // Scale each pose column by C_k^-1/2, store the rows for the next
+            // back-substitution and split the operand into TF32 hi and lo
+            // halves.  A warp takes one 8 x 4 (row, patch) tile at a time,
+            // lane = 4 (row % 8) + patch % 4: 128 contiguous bytes of the
+            // operand and of the stored block.  Patches cnt..Kc-1 and unused
+            // rows are zero.
+            const int Kc = (cnt + 7) & ~7, n6 = 6 * nf;
+            const int r8 = lane >> 2, k4 = lane & 3;
+            float *eb = pr.erow + (size_t)c * kTcRows * kmax;
+            for (int idx = warp; idx < 2 * Kc; idx += kThreads / 32) {   // 8 row groups x Kc / 4 patch groups
+                const int rg = idx & 7, kg = idx >> 3;
+                const int r = 8 * rg + r8, k = 4 * kg + k4;
+                const uint32_t off = (uint32_t)rg * sbo + (uint32_t)kg * kLbo + (uint32_t)(16 * r8 + 4 * k4);
+                uint32_t *lp = reinterpret_cast<uint32_t *>(op + off);
+                uint32_t *hp = reinterpret_cast<uint32_t *>(op + off + (kTcRows / 8) * sbo);
+                const bool in = k < cnt;
+                float x = 0.f, e = 0.f;      // operand value, stored-row value
+                if (in) {
+                    if (r < n6) e = x = __uint_as_float(*hp) * ps[k];
+                    else if (r == kTcRows - 2) e = x = ps[G_cap + k];
+                    else if (r == kTcRows - 1) e = ps[k];
+                }
+                if (!adjoint_rhs) eb[kg * (4 * kTcRows) + 4 * r + k4] = e;
+                if (r == kTcRows - 1) continue;  // its operand entries come with row 62
+                const uint32_t h = to_tf32(x);
+                const uint32_t lo = to_tf32(x - __uint_as_float(h));
+                if (r == kTcRows - 2) {          // B rows 62, 63: hi and lo of C^-1/2 w
+                    hp[0] = h;
+                    hp[4] = lo;
+                    lp[0] = 0u;
+                    lp[4] = 0u;
+                } else {
+                    *hp = h;
+                    *lp = r < n6 ? lo : 0u;
                 }
             }
-        }
-        __syncthreads();
-        if (!adjoint_rhs) {
-            // store each patch's row C_k^-1/2 (e_k, w_k, 1), pose columns compacted
-            // to 6 floats per free frame, for the next back-substitution
-            const int n4 = RS / 4, n6 = 6 * nf;
-            float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)k0 * RS);
-            for (int q = tid; q < cnt * n4; q += kThreads) {
-                const int p = q / n4, c = q - p * n4;
-                const float *e = Ec + p * ES;
-                float v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int o = 4 * c + u;
-                    float x = 0.f;
-                    if (o < n6) {
-                        const int f = o / 6, m = o - 6 * f;
-                        x = e[8 * f + m + (m >= 3 ? 1 : 0)];
-                    } else if (o == n6) {
-                        x = e[8 * nf];
-                    } else if (o == n6 + 1) {
-                        x = ps[p * 8];
-                    }
-                    v[u] = x;
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t base = smem_u32(op);
+                constexpr uint32_t idesc = idesc_tf32(2 * kTcRows, kTcRows);
+                for (int st = 0; st < (Kc >> 3); ++st) {
+                    const uint64_t ad = smem_desc(base + st * 2 * kLbo, kLbo, sbo);
+                    const uint64_t bd = smem_desc(base + (kTcRows / 8) * sbo + st * 2 * kLbo, kLbo, sbo);
+                    mma_tf32(tmem, ad, bd, idesc, (n_commit > 0 || st > 0) ? 1 : 0);
                 }
-                dst[q] = make_float4(v[0], v[1], v[2], v[3]);
+                mma_commit(smem_u32(&s_mbar));
+            }
+            ++n_commit;
+        } else {
+            {   // E_k (pose columns) scaled by C_k^-1/2
+                const int n4 = 2 * nf;
+                for (int p = tid >> 6; p < cnt; p += kThreads / 64) {
+                    const float sq = ps[p];
+                    float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES);
+                    for (int m = tid & 63; m < n4; m += 64) {
+                        float4 v = e4[m];
+                        v.x *= sq; v.y *= sq; v.z *= sq;
+                        e4[m] = v;
+                    }
+                }
+            }
+            __syncthreads();
+            if (!adjoint_rhs) {
+                // store each patch's row C_k^-1/2 (e_k, w_k, 1), pose columns compacted
+                // to 6 floats per free frame, for the next back-substitution
+                const int n4 = RS / 4, n6 = 6 * nf;
+                float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)k0 * RS);
+                for (int q = tid; q < cnt * n4; q += kThreads) {
+                    const int p = q / n4, c = q - p * n4;
+                    const float *e = Ec + p * ES;
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int o = 4 * c + u;
+                        float x = 0.f;
+                        if (o < n6) {
+                            const int f = o / 6, m = o - 6 * f;
+                            x = e[8 * f + m + (m >= 3 ? 1 : 0)];
+                        } else if (o == n6) {
+                            x = e[8 * nf];
+                        } else if (o == n6 + 1) {
+                            x = ps[p];
+                        }
+                        v[u] = x;
+                    }
+                    dst[q] = make_float4(v[0], v[1], v[2], v[3]);
+                }
             }
         }
         if (!group_next && anc_free && !adjoint_rhs) {
@@ -769,7 +1021,9 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         // -- (c) Schur accumulation over the chunk's patches, then the group's B blocks
         if (owns) {
             int since = 0;
-            if (!is_vstrip) {
+            if (TC) {
+                // patch products accumulate on the tensor cores
+            } else if (!is_vstrip) {
                 for (int p = my_ks; p < cnt; p += KS) {
                     const float *e = Ec + p * ES;
                     const float4 a4 = *reinterpret_cast<const float4 *>(e + 8 * sa + 4 * sh);
@@ -863,6 +1117,61 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     }
     cp_async_wait_all();
 
+    if constexpr (TC) {
+        // read the accumulator back (warps 0-3, one TMEM lane = one row each)
+        // into a buffer over the dead staging area, then each strip owner
+        // subtracts its entries: S -= hi.hi + lo.hi + (lo.hi)^T, v' -= the
+        // w columns (rows 62, 63 of B)
+        float *X = reinterpret_cast<float *>(smem + L.off_rjj);
+        if (n_commit > 0 && !mbar_wait(smem_u32(&s_mbar), (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_tc_bad, 1);
+        __syncthreads();
+        const bool have = n_commit > 0 && s_tc_bad == 0;
+        tc_fence_after();
+        if (have && warp < 4) {
+#pragma unroll 1
+            for (int c4 = 0; c4 < kTcRows / 16; ++c4) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + 16 * c4, v);
+                float *xr = X + (32 * warp + lane) * kTcXStride + 16 * c4;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) xr[q] = v[q];
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (have && owns) {
+            const float *XL = X, *XH = X + kTcRows * kTcXStride;
+            if (!is_vstrip) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 6; ++cc) {
+                        const int m = 6 * sa + 3 * sh + r, n = 6 * sb + cc;
+                        const float d = XH[m * kTcXStride + n] + XL[m * kTcXStride + n] + XL[n * kTcXStride + m];
+                        kahan_add(acc_s[6 * r + cc], acc_c[6 * r + cc], -d);
+                    }
+            } else {
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) {
+                    const int m = 6 * sa + cc;
+                    const float d = XH[m * kTcXStride + kTcRows - 2] + XH[m * kTcXStride + kTcRows - 1] +
+                                    XL[m * kTcXStride + kTcRows - 2];
+                    kahan_add(acc_s[cc], acc_c[cc], -d);
+                }
+            }
+        }
+        if (s_tc_bad) {
+            // an MMA batch did not complete in time: report it, give the
+            // tensor core one more bounded wait, then release TMEM
+            if (tid == 0) atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
+            if (n_commit > 0) mbar_wait(smem_u32(&s_mbar), (uint32_t)(n_commit - 1) & 1u);
+        }
+        if (warp == 0) {
+            tc_fence_after();
+            tmem_dealloc(tmem, 64);
+        }
+    }
+
     // write this CTA's partial of (S, v')
     if (owns) {
         double *out = pr.partial + ((size_t)itm.item * KS + my_ks) * pr.L;
@@ -888,6 +1197,8 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 // nothing else.
 // ----------------------------------------------------------------------------
 constexpr int kSolveThreads = 256;
+// elements of the largest trailing triangle, (6 kMaxFree - 1) 6 kMaxFree / 2, per thread
+constexpr int kSolveOwn = ((6 * kMaxFree - 1) * 6 * kMaxFree / 2 + kSolveThreads - 1) / kSolveThreads;
 
 __device__ __forceinline__ double shfl_double(double x, int src) {
     int lo = __double2loint(x), hi = __double2hiint(x);
@@ -919,6 +1230,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
     const int ld = n + 1;
     double *S = reinterpret_cast<double *>(smem);
     double *v = S + (size_t)n * ld;
+    __shared__ double s_rp[6 * kMaxFree];    // pivot reciprocals, reused by the back substitution
 
     // FP64 sum of the partials in a fixed order (deterministic)
     const int Lp = pr.L, nparts = pr.n_items * pr.ks, nbs = 2 * n_block_pairs(nf);
@@ -951,25 +1263,56 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         for (int q = tid; q < n; q += kSolveThreads) v_out[q] = v[q];
         return;
     }
-    // right-looking elimination of the lower triangle: thread (ty, tx) of a
-    // 16 x 16 grid updates rows i = ty mod 16, columns k = tx mod 16
-    const int ty = tid >> 4, tx = tid & 15;
+    // right-looking elimination of the lower triangle.  The trailing triangle
+    // of step j (rows i > j, columns j < k <= i) is enumerated in reversed
+    // coordinates r = n-1-i <= c = n-1-k, column-major in c, so that the
+    // elements of step j are exactly the first m (m + 1) / 2 of one fixed
+    // sequence (m = n-1-j): thread tid owns elements tid + kSolveThreads u of
+    // it for every step, and the warps stay full as the triangle shrinks.
+    int own[kSolveOwn];
+#pragma unroll
+    for (int u = 0; u < kSolveOwn; ++u) {
+        const int q = tid + kSolveThreads * u;
+        int c = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+        while (c * (c + 1) / 2 > q) --c;                    // exact integer correction
+        while ((c + 1) * (c + 2) / 2 <= q) ++c;
+        const int r = q - c * (c + 1) / 2;
+        own[u] = ((n - 1 - r) << 16) | (n - 1 - c);          // (i, k)
+    }
+    // The reciprocal of each pivot is formed by the thread that updates the
+    // pivot in the step before (it owns the last element of that step's
+    // triangle), first in its list, so the division overlaps the step's
+    // other updates; a pivot <= 0 or NaN is recorded as -1.
+    if (tid == 0) {
+        const double p0 = S[0];
+        s_rp[0] = p0 > 0.0 ? 1.0 / p0 : -1.0;
+    }
+    __syncthreads();
     for (int j = 0; j < n; ++j) {
-        const double piv = S[j * ld + j];
-        if (!(piv > 0.0)) {
+        const double ip = s_rp[j];
+        if (!(ip > 0.0)) {
             if (tid == 0) s_flag = DPVO_BA_STATUS_NOT_SPD;
             break;
         }
-        double ip = 0.0;
-        if (lane == 0) ip = 1.0 / piv;
-        ip = shfl_double(ip, 0);
-        const double vj = v[j];
-        for (int i = j + 1 + ty; i < n; i += 16) {
-            const double lij = S[i * ld + j] * ip;
-            double *row = S + i * ld;
-#pragma unroll 4
-            for (int k = j + 1 + tx; k <= i; k += 16) row[k] -= lij * S[k * ld + j];
-            if (tx == 0) v[i] -= lij * vj;
+        const int m = n - 1 - j, count = m * (m + 1) / 2;
+        const double *colj = S + j;
+        const int last = count - 1;                          // element (j+1, j+1)
+        if (count > 0 && tid == last % kSolveThreads) {
+            const int jn = j + 1;
+            const double pn = S[jn * ld + jn] - (colj[jn * ld] * ip) * colj[jn * ld];
+            S[jn * ld + jn] = pn;
+            s_rp[jn] = pn > 0.0 ? 1.0 / pn : -1.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kSolveOwn; ++u) {
+            const int q = tid + kSolveThreads * u;
+            if (q >= last) break;
+            const int i = own[u] >> 16, k = own[u] & 0xffff;
+            S[i * ld + k] -= (colj[i * ld] * ip) * colj[k * ld];
+        }
+        if (tid < m) {
+            const int i = j + 1 + tid;
+            v[i] -= (colj[i * ld] * ip) * v[j];
         }
         __syncthreads();
     }
@@ -982,11 +1325,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         }
     }
     if (!s_flag && tid < 32) {
-        // U^T x = v' (back substitution, one warp): x_j = v_j / U_jj, v_i -= U_ji x_j
+        // U^T x = v' (back substitution, one warp): x_j = v_j / U_jj, v_i -= U_ji x_j,
+        // with the reciprocals of the pivots kept from the factorisation
         for (int j = n - 1; j >= 0; --j) {
-            double xj = 0.0;
-            if (lane == 0) xj = v[j] / S[j * ld + j];
-            xj = shfl_double(xj, 0);
+            const double xj = v[j] * s_rp[j];
             for (int i = lane; i < j; i += 32) v[i] -= S[j * ld + i] * xj;
             __syncwarp();
             if (lane == 0) v[j] = xj;

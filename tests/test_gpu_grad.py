@@ -143,3 +143,17 @@ def test_autograd_function_gives_the_same_gradient(solver):
     ref_t, ref_w, _ = ug.gradient(sc)
     assert rel(g_t.cpu().numpy(), ref_t) < TOL_GRAD
     assert rel(g_w.cpu().numpy(), ref_w) < TOL_GRAD
+
+
+def test_tf32_schur_mode_gradient_matches_autograd_twin():
+    """The same adjoint with the opt-in tensor-core Schur accumulation."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    s = ba.Solver(schur_tf32=True)
+    try:
+        sc = S.make_scene(S.WINDOW_N22, 8)
+        gts, gws = gpu_gradients(s, [sc])
+        ref_t, ref_w, _ = ug.gradient(sc)
+        assert rel(gts[0], ref_t) < TOL_GRAD and rel(gws[0], ref_w) < TOL_GRAD
+    finally:
+        s.close()

