@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__res
 // cap W, chunk cap G and largest free-pose count.
 // ----------------------------------------------------------------------------
 struct LinSmem {
-    int W, G, Gs, ES, EC;  // window cap, chunk cap, odd slot stride, E-column stride, edge capacity
+    int W, G, Gs, Gs1, ES, EC;  // window cap, chunk cap, slot strides (float4 / float arrays), E-row stride, edge capacity
     uint32_t sbo;          // tensor-core operand: bytes between 8-row groups
     size_t off_pose, off_rjj, off_rtg, off_rwt, off_rpx, off_rpy, off_rdep, off_rseg, off_idx, off_sc4, off_sc1,
         off_ec, off_op, off_mp, off_reln, off_adj, off_mc, off_aj, off_bp, off_bii, off_pd, off_ps, off_dx;
@@ -263,7 +263,12 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     LinSmem s;
     s.W = W;
     s.G = G;
-    s.Gs = G | 1;
+    // slot (frame jl, patch p) at jl * Gs + p.  The per-patch sums read
+    // frames sub, sub + 4, ... of 8 consecutive patches by 4 lanes each: with
+    // Gs = 2 (mod 8) the 16-byte reads of a quarter warp, and with Gs1 = 8
+    // (mod 32) the 4-byte reads of a warp, fall in distinct banks.
+    s.Gs = G + ((2 - G) % 8 + 8) % 8;
+    s.Gs1 = G + ((8 - G) % 32 + 32) % 32;
     // E_k row: frame f at floats 8f..8f+7 laid out [v0 v1 v2 _ v3 v4 v5 _],
     // then C_k^-1/2 w_k; the stride is an odd multiple of 4 floats
     const int es = 8 * nf_max + 4;
@@ -271,7 +276,7 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     s.EC = W * G;
     const int kmax = (G + 7) & ~7;
     s.sbo = (uint32_t)(kmax / 4) * 144u;
-    const size_t slots = (size_t)W * s.Gs;
+    const size_t slots = (size_t)W * s.Gs, slots1 = (size_t)W * s.Gs1;
     // the per-slot sums share their buffer with the staged Schur rows of the
     // next chunk (read before the slots are written)
     const size_t rows = tc ? (size_t)kTcRows * kmax * 4 : (size_t)G * erow_smem_stride(nf_max) * 4;
@@ -287,7 +292,7 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     s.off_rseg = o; o = align16(o + (size_t)(G + 1) * 4);
     s.off_idx = o;  o = align16(o + slots * 2);
     s.off_sc4 = o;  o = align16(o + sc4);
-    s.off_sc1 = o;  o = align16(o + slots * 4);
+    s.off_sc1 = o;  o = align16(o + slots1 * 4);
     if (tc) {
         s.off_ec = 0;
         s.off_op = o; o = align16(o + (size_t)2 * (kTcRows / 8) * s.sbo);
@@ -505,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     float4 *pd = reinterpret_cast<float4 *>(smem + L.off_pd);
     float *ps = reinterpret_cast<float *>(smem + L.off_ps);
     float *dxs = reinterpret_cast<float *>(smem + L.off_dx);
-    const int Gs = L.Gs, ES = L.ES;
+    const int Gs = L.Gs, Gs1 = L.Gs1, ES = L.ES;
 
     const int N = pr.N, t0 = pr.t0, nf = pr.nf;
     const int RS = erow_len(nf), RSS = erow_smem_stride(nf);
@@ -812,7 +817,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                 }
                 sc4[slot] = make_float4(Ce, we, Y0, Y1);
-                sc1[slot] = Y2;
+                sc1[my_jl * Gs1 + p] = Y2;
             }
             float *mp = Mp + (size_t)tid * 27;
 #pragma unroll
@@ -836,45 +841,83 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     w += v.y;
                     Y0 += v.z;
                     Y1 += v.w;
-                    Y2 += sc1[jl * Gs + p];
+                    Y2 += sc1[jl * Gs1 + p];
                 }
             C = quad_sum(C);
             w = quad_sum(w);
             Y0 = quad_sum(Y0);
             Y1 = quad_sum(Y1);
             Y2 = quad_sum(Y2);
-            if (p < cnt) {
-                float *e = Ec + p * ES;
-                if (sub == 0) {
-                    const float sq = sqrtf(1.0f / C);
-                    const float sw = sq * (adjoint_rhs ? pr.dbar[k0 + p] : w);
-                    ps[p] = sq;
-                    if constexpr (TC) ps[G_cap + p] = sw;
-                    else e[8 * nf] = sw;
-                } else if (anc_free && sub < 3) {
-                    const float4 qd = pd[p];
-                    const float d = qd.z, px = qd.x, py = qd.y;
-                    float3 v;
-                    if (sub == 1) v = make_float3(-d * Y0, -d * Y1, -d * Y2);
-                    else          // -(pbar x Y), pbar = (px, py, 1)
-                        v = make_float3(-(py * Y2 - Y1), -(Y0 - px * Y2), -(px * Y1 - py * Y0));
-                    if constexpr (TC) {
+            if constexpr (TC) {
+                if (p < cnt) {
+                    if (sub == 0) {
+                        const float sq = sqrtf(1.0f / C);
+                        ps[p] = sq;
+                        ps[G_cap + p] = sq * (adjoint_rhs ? pr.dbar[k0 + p] : w);
+                    } else if (anc_free && sub < 3) {
+                        const float4 qd = pd[p];
+                        const float d = qd.z, px = qd.x, py = qd.y;
+                        float3 v;
+                        if (sub == 1) v = make_float3(-d * Y0, -d * Y1, -d * Y2);
+                        else          // -(pbar x Y), pbar = (px, py, 1)
+                            v = make_float3(-(py * Y2 - Y1), -(Y0 - px * Y2), -(px * Y1 - py * Y0));
                         const int r0 = kTcRows + 6 * (anc - t0) + 3 * (sub - 1);
                         *reinterpret_cast<float *>(op + op_offset(r0, p, sbo)) = v.x;
                         *reinterpret_cast<float *>(op + op_offset(r0 + 1, p, sbo)) = v.y;
                         *reinterpret_cast<float *>(op + op_offset(r0 + 2, p, sbo)) = v.z;
-                    } else {
+                    }
+                }
+            } else {
+                // the same four lanes then scale the patch's row of E by
+                // C_k^-1/2 and store it, compacted, for the next back-substitution
+                const float sq = sqrtf(1.0f / C);
+                float *e = Ec + p * ES;
+                if (p < cnt) {
+                    if (sub == 0) {
+                        ps[p] = sq;
+                        e[8 * nf] = sq * (adjoint_rhs ? pr.dbar[k0 + p] : w);
+                    } else if (anc_free && sub < 3) {
+                        const float4 qd = pd[p];
+                        const float d = qd.z, px = qd.x, py = qd.y;
                         float4 *ei = reinterpret_cast<float4 *>(e + 8 * (anc - t0));
-                        ei[sub - 1] = make_float4(v.x, v.y, v.z, 0.f);
+                        if (sub == 1) ei[0] = make_float4(-d * Y0, -d * Y1, -d * Y2, 0.f);
+                        else          // -(pbar x Y), pbar = (px, py, 1)
+                            ei[1] = make_float4(-(py * Y2 - Y1), -(Y0 - px * Y2), -(px * Y1 - py * Y0), 0.f);
+                    }
+                }
+                __syncwarp();
+                if (p < cnt) {
+                    float4 *e4 = reinterpret_cast<float4 *>(e);
+                    for (int m = sub; m < 2 * nf; m += 4) {
+                        float4 v = e4[m];
+                        v.x *= sq; v.y *= sq; v.z *= sq;
+                        e4[m] = v;
+                    }
+                }
+                __syncwarp();
+                if (p < cnt && !adjoint_rhs) {
+                    const int n4 = RS / 4, n6 = 6 * nf;
+                    float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)(k0 + p) * RS);
+                    for (int c4 = sub; c4 < n4; c4 += 4) {
+                        float v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int o = 4 * c4 + u;
+                            float x = 0.f;
+                            if (o < n6) {
+                                const int f = o / 6, m = o - 6 * f;
+                                x = e[8 * f + m + (m >= 3 ? 1 : 0)];
+                            } else if (o == n6) {
+                                x = e[8 * nf];
+                            } else if (o == n6 + 1) {
+                                x = sq;
+                            }
+                            v[u] = x;
+                        }
+                        dst[c4] = make_float4(v[0], v[1], v[2], v[3]);
                     }
                 }
             }
-        }
-        __syncthreads();
-        // the per-slot sums are consumed: start copying the next chunk's stored rows
-        if (do_bs && have_next) {
-            if constexpr (TC) prefetch_block(pr, c + 1, nx, kmax, srow);
-            else prefetch_rows(pr, nx, RS, RSS, srow);
         }
         if (!group_next && !adjoint_rhs) {
             // combine the per-thread frame sums (M_j, v_j) over patch groups, compensated
@@ -884,6 +927,12 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 for (int g = 0; g < NG; ++g) kahan_add(s, cc, Mp[(size_t)(jl * NG + g) * 27 + m]);
                 Mc[jl * 27 + m] = s - cc;
             }
+        }
+        __syncthreads();
+        // the per-slot sums are consumed: start copying the next chunk's stored rows
+        if (do_bs && have_next) {
+            if constexpr (TC) prefetch_block(pr, c + 1, nx, kmax, srow);
+            else prefetch_rows(pr, nx, RS, RSS, srow);
         }
         if constexpr (TC) {
             // Scale each pose column by C_k^-1/2, store the rows for the next
@@ -936,46 +985,6 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 mma_commit(smem_u32(&s_mbar));
             }
             ++n_commit;
-        } else {
-            {   // E_k (pose columns) scaled by C_k^-1/2
-                const int n4 = 2 * nf;
-                for (int p = tid >> 6; p < cnt; p += kThreads / 64) {
-                    const float sq = ps[p];
-                    float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES);
-                    for (int m = tid & 63; m < n4; m += 64) {
-                        float4 v = e4[m];
-                        v.x *= sq; v.y *= sq; v.z *= sq;
-                        e4[m] = v;
-                    }
-                }
-            }
-            __syncthreads();
-            if (!adjoint_rhs) {
-                // store each patch's row C_k^-1/2 (e_k, w_k, 1), pose columns compacted
-                // to 6 floats per free frame, for the next back-substitution
-                const int n4 = RS / 4, n6 = 6 * nf;
-                float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)k0 * RS);
-                for (int q = tid; q < cnt * n4; q += kThreads) {
-                    const int p = q / n4, c = q - p * n4;
-                    const float *e = Ec + p * ES;
-                    float v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int o = 4 * c + u;
-                        float x = 0.f;
-                        if (o < n6) {
-                            const int f = o / 6, m = o - 6 * f;
-                            x = e[8 * f + m + (m >= 3 ? 1 : 0)];
-                        } else if (o == n6) {
-                            x = e[8 * nf];
-                        } else if (o == n6 + 1) {
-                            x = ps[p];
-                        }
-                        v[u] = x;
-                    }
-                    dst[q] = make_float4(v[0], v[1], v[2], v[3]);
-                }
-            }
         }
         if (!group_next && anc_free && !adjoint_rhs) {
             // pose-pair blocks involving the anchor, per window frame j:
@@ -1024,22 +1033,43 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             if (TC) {
                 // patch products accumulate on the tensor cores
             } else if (!is_vstrip) {
-                for (int p = my_ks; p < cnt; p += KS) {
+                // two patches per step: six 16-byte loads in flight before the FMAs
+                const int oa = 8 * sa + 4 * sh, ob = 8 * sb;
+                int p = my_ks;
+                for (; p + KS < cnt; p += 2 * KS) {
+                    const float *e = Ec + p * ES, *f = Ec + (p + KS) * ES;
+                    const float4 a4 = *reinterpret_cast<const float4 *>(e + oa);
+                    const float4 b0 = *reinterpret_cast<const float4 *>(e + ob);
+                    const float4 b1 = *reinterpret_cast<const float4 *>(e + ob + 4);
+                    const float4 c4 = *reinterpret_cast<const float4 *>(f + oa);
+                    const float4 d0 = *reinterpret_cast<const float4 *>(f + ob);
+                    const float4 d1 = *reinterpret_cast<const float4 *>(f + ob + 4);
+                    const float ea[3] = {a4.x, a4.y, a4.z}, fa[3] = {c4.x, c4.y, c4.z};
+                    const float eb[6] = {b0.x, b0.y, b0.z, b1.x, b1.y, b1.z};
+                    const float fb[6] = {d0.x, d0.y, d0.z, d1.x, d1.y, d1.z};
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int cc = 0; cc < 6; ++cc)
+                            blk[6 * r + cc] = fmaf(-fa[r], fb[cc], fmaf(-ea[r], eb[cc], blk[6 * r + cc]));
+                    since += 2;
+                    if (since >= kFlushEvery) {
+#pragma unroll
+                        for (int q = 0; q < 18; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
+                        since = 0;
+                    }
+                }
+                if (p < cnt) {
                     const float *e = Ec + p * ES;
-                    const float4 a4 = *reinterpret_cast<const float4 *>(e + 8 * sa + 4 * sh);
-                    const float4 b0 = *reinterpret_cast<const float4 *>(e + 8 * sb);
-                    const float4 b1 = *reinterpret_cast<const float4 *>(e + 8 * sb + 4);
+                    const float4 a4 = *reinterpret_cast<const float4 *>(e + oa);
+                    const float4 b0 = *reinterpret_cast<const float4 *>(e + ob);
+                    const float4 b1 = *reinterpret_cast<const float4 *>(e + ob + 4);
                     const float ea[3] = {a4.x, a4.y, a4.z};
                     const float eb[6] = {b0.x, b0.y, b0.z, b1.x, b1.y, b1.z};
 #pragma unroll
                     for (int r = 0; r < 3; ++r)
 #pragma unroll
                         for (int cc = 0; cc < 6; ++cc) blk[6 * r + cc] = fmaf(-ea[r], eb[cc], blk[6 * r + cc]);
-                    if (++since == kFlushEvery) {
-#pragma unroll
-                        for (int q = 0; q < 18; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
-                        since = 0;
-                    }
                 }
             } else {
                 for (int p = my_ks; p < cnt; p += KS) {
