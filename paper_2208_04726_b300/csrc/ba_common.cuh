@@ -70,16 +70,12 @@ struct Prob {
 };
 
 // Stored Schur row of a patch, written when it is linearised and read by the
-// back-substitution of that iteration: the pose columns C_k^-1/2 e_k (6 nf
-// floats, frame-major), then C_k^-1/2 w_k and C_k^-1/2, zero-padded to a
-// multiple of 4 floats so that every row starts on a 16-byte boundary.
-__host__ __device__ inline int erow_len(int nf) { return (6 * nf + 2 + 3) & ~3; }
-// Row stride of the rows staged in shared memory: congruent to 16 mod 32
-// floats, so the 16-byte loads of two rows by 4 lanes each fall in disjoint banks.
-__host__ __device__ inline int erow_smem_stride(int nf) {
-    const int rs = erow_len(nf);
-    return rs + ((16 - rs % 32) + 32) % 32;
-}
+// back-substitution of that iteration: the pose columns C_k^-1/2 e_k, free
+// frame f at floats 8f..8f+7 as [v0 v1 v2 0 v3 v4 v5 0] (the layout the
+// linearisation keeps them in), then C_k^-1/2 w_k, C_k^-1/2, 0, 0.  Every row
+// starts on a 16-byte boundary.
+__host__ __device__ inline int erow_len(int nf) { return 8 * nf + 4; }
+__host__ __device__ inline int erow_smem_stride(int nf) { return erow_len(nf); }
 
 // One CTA of the linearise kernel: problem index and work-item index within it.
 struct Item {

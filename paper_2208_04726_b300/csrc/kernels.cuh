@@ -528,8 +528,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
     if (do_bs) {   // the previous iteration's pose increments, zero-padded to the row length
         const double *dx = pr.dxi + (size_t)(t - 1) * nf * 6;
-        const int len = TC ? kTcRows : RS;
-        for (int q = tid; q < len; q += kThreads) dxs[q] = q < 6 * nf ? (float)dx[q] : 0.f;
+        if constexpr (TC) {
+            for (int q = tid; q < kTcRows; q += kThreads) dxs[q] = q < 6 * nf ? (float)dx[q] : 0.f;
+        } else {   // in the stored rows' layout: frame f at 8f..8f+7 as [v 0 w 0]
+            for (int q = tid; q < RS; q += kThreads) {
+                const int f = q >> 3, m = q & 7;
+                dxs[q] = (f < nf && (m & 3) != 3) ? (float)dx[6 * f + m - (m >> 2)] : 0.f;
+            }
+        }
     }
     if (final_pass) {
         // last back-substitution: dd_k = C_k^-1/2 (C_k^-1/2 w_k - (C_k^-1/2 e_k) . dxi)
@@ -571,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     for (int q = sub; q < RS / 4; q += 4) s = dot4(reinterpret_cast<const float4 *>(row)[q], dz4[q], s);
                 s = quad_sum(s);
                 if (k < k_hi && sub == 0) {
-                    const float dnew = depth_old[k] + row[6 * nf + 1] * (row[6 * nf] - s);
+                    const float dnew = depth_old[k] + row[8 * nf + 1] * (row[8 * nf] - s);
                     depth_new[k] = dnew;
                     if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
                 }
@@ -738,7 +744,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     float d = rdep[p];
                     if (do_bs) {
                         const float *row = srow + p * RSS;
-                        d += row[6 * nf + 1] * (row[6 * nf] - s);
+                        d += row[8 * nf + 1] * (row[8 * nf] - s);
                         depth_new[k0 + p] = d;
                     }
                     pd[p] = make_float4((rpx[p] - cx) * ifx, (rpy[p] - cy) * ify, d, 0.f);
@@ -888,34 +894,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 __syncwarp();
                 if (p < cnt) {
                     float4 *e4 = reinterpret_cast<float4 *>(e);
+                    float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)(k0 + p) * RS);
                     for (int m = sub; m < 2 * nf; m += 4) {
                         float4 v = e4[m];
                         v.x *= sq; v.y *= sq; v.z *= sq;
                         e4[m] = v;
+                        if (!adjoint_rhs) dst[m] = v;
                     }
-                }
-                __syncwarp();
-                if (p < cnt && !adjoint_rhs) {
-                    const int n4 = RS / 4, n6 = 6 * nf;
-                    float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)(k0 + p) * RS);
-                    for (int c4 = sub; c4 < n4; c4 += 4) {
-                        float v[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int o = 4 * c4 + u;
-                            float x = 0.f;
-                            if (o < n6) {
-                                const int f = o / 6, m = o - 6 * f;
-                                x = e[8 * f + m + (m >= 3 ? 1 : 0)];
-                            } else if (o == n6) {
-                                x = e[8 * nf];
-                            } else if (o == n6 + 1) {
-                                x = sq;
-                            }
-                            v[u] = x;
-                        }
-                        dst[c4] = make_float4(v[0], v[1], v[2], v[3]);
-                    }
+                    if (sub == 0 && !adjoint_rhs) dst[2 * nf] = make_float4(e[8 * nf], sq, 0.f, 0.f);
                 }
             }
         }
