@@ -29,6 +29,12 @@ struct Layout {
     size_t lin_smem = 0, solve_smem = 0;
 };
 
+// solve_kernel shared memory: S and its FP32 copy (n x (n+1)), v, x, the FP32 right-hand side.
+static size_t solve_smem_bytes(int nf) {
+    const size_t n = 6 * (size_t)nf;
+    return n * (n + 1) * 8 + 2 * n * 8 + n * (n + 1) * 4 + n * 4 + 64;
+}
+
 // Stored Schur rows: one row per patch, or in the tensor-core variant one
 // block of kTcRows x Kmax floats per chunk.
 static size_t erow_bytes(bool tc, const Prob &p, int G_cap) {
@@ -80,8 +86,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes > kLinSmemBudget)
         L.G_cap -= 8;
     L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
-    const int n6 = 6 * L.nf_max;
-    L.solve_smem = (size_t)n6 * (n6 + 1) * 8 + (size_t)n6 * 8 + 16;
+    L.solve_smem = solve_smem_bytes(L.nf_max);
 
     const int target_ctas = 2 * num_sms;
     size_t off = 0;
@@ -1002,7 +1007,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     int G_cap = 64;
     while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes > kLinSmemBudget) G_cap -= 8;
     const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes;
-    const size_t solve_smem = (size_t)(6 * nf) * (6 * nf + 1) * 8 + (size_t)(6 * nf) * 8 + 16;
+    const size_t solve_smem = solve_smem_bytes(nf);
     Prob p;
     std::memset(&p, 0, sizeof(Prob));
     p.poses = prob->poses; p.patches = prob->patches; p.anchor = prob->anchor; p.kk = prob->kk;

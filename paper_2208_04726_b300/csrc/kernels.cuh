@@ -1223,6 +1223,56 @@ __device__ __forceinline__ double shfl_double(double x, int src) {
     return __hiloint2double(hi, lo);
 }
 
+// One warp: solve S x = b in place in b (n <= 96), with S = U D^-1 U^T
+// factored into the lower triangle of Sf (U, diagonal D) and the pivot
+// reciprocals rp: forward L y = b with L = U D^-1 (unit diagonal), then back
+// U^T x = y.  Lane l keeps b[l], b[l + 32], b[l + 64] in registers; each step
+// broadcasts one entry by shuffle, and the next step's coefficients are loaded
+// before the current step's update (zero where a row takes no update).
+__device__ __forceinline__ float lane_pick(float b0, float b1, float b2, int j) {
+    const float v = (j >> 5) == 0 ? b0 : (j >> 5) == 1 ? b1 : b2;
+    return __shfl_sync(0xffffffffu, v, j & 31);
+}
+__device__ __forceinline__ void solve_factored_f32(const float *Sf, int ld, const float *rp, float *b, int n,
+                                                   int lane) {
+    const int i0 = lane, i1 = lane + 32, i2 = lane + 64;
+    float b0 = i0 < n ? b[i0] : 0.f, b1 = i1 < n ? b[i1] : 0.f, b2 = i2 < n ? b[i2] : 0.f;
+    // forward: b_i -= (U_ij / D_j) y_j for i > j
+    auto lcoef = [&](int i, int j) { return (i > j && i < n) ? Sf[i * ld + j] * rp[j] : 0.f; };
+    float l0 = lcoef(i0, 0), l1 = lcoef(i1, 0), l2 = lcoef(i2, 0);
+    for (int j = 0; j < n; ++j) {
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
+        if (j + 1 < n) { m0 = lcoef(i0, j + 1); m1 = lcoef(i1, j + 1); m2 = lcoef(i2, j + 1); }
+        const float yj = lane_pick(b0, b1, b2, j);
+        b0 = fmaf(-l0, yj, b0);
+        b1 = fmaf(-l1, yj, b1);
+        b2 = fmaf(-l2, yj, b2);
+        l0 = m0; l1 = m1; l2 = m2;
+    }
+    // back: x_j = y_j / D_j, b_i -= U_ji x_j for i < j
+    auto ucoef = [&](int i, int j) { return i < j ? Sf[j * ld + i] : 0.f; };
+    float u0 = ucoef(i0, n - 1), u1 = ucoef(i1, n - 1), u2 = ucoef(i2, n - 1);
+    float r = rp[n - 1];
+    for (int j = n - 1; j >= 0; --j) {
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f, rn = 0.f;
+        if (j > 0) { w0 = ucoef(i0, j - 1); w1 = ucoef(i1, j - 1); w2 = ucoef(i2, j - 1); rn = rp[j - 1]; }
+        const float xj = lane_pick(b0, b1, b2, j) * r;
+        if ((j & 31) == lane) {
+            if ((j >> 5) == 0) b0 = xj; else if ((j >> 5) == 1) b1 = xj; else b2 = xj;
+        }
+        b0 = fmaf(-u0, xj, b0);
+        b1 = fmaf(-u1, xj, b1);
+        b2 = fmaf(-u2, xj, b2);
+        u0 = w0; u1 = w1; u2 = w2; r = rn;
+    }
+    if (i0 < n) b[i0] = b0;
+    if (i1 < n) b[i1] = b1;
+    if (i2 < n) b[i2] = b2;
+}
+
+constexpr int kMaxRefine = 4;          // FP64 refinement steps of the FP32 solution at most
+constexpr double kRefineTol = 1e-6;    // accept once the last correction is below this x max|x|
+
 __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__restrict__ probs, int t,
                                                               double *S_out, double *v_out) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1250,27 +1300,36 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
 
     // FP64 sum of the partials in a fixed order (deterministic)
     const int Lp = pr.L, nparts = pr.n_items * pr.ks, nbs = 2 * n_block_pairs(nf);
-    for (int q = tid; q < Lp; q += kSolveThreads) {
-        double acc = 0.0;
-        const double *src = pr.partial + q;
-        int part = 0;
-        for (; part + 8 <= nparts; part += 8) {     // eight loads in flight, summed in order
-            double x[8];
+    constexpr int kQ = 8;                       // entries per thread with loads in flight together
+    for (int q0 = tid; q0 < Lp; q0 += kQ * kSolveThreads) {
+        double accs[kQ];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = src[(size_t)(part + u) * Lp];
+        for (int u = 0; u < kQ; ++u) accs[u] = 0.0;
+        for (int part = 0; part < nparts; ++part) {   // parts summed in order
+            const double *src = pr.partial + (size_t)part * Lp;
+            double x[kQ];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) acc += x[u];
+            for (int u = 0; u < kQ; ++u) {
+                const int q = q0 + u * kSolveThreads;
+                x[u] = q < Lp ? src[q] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) accs[u] += x[u];
         }
-        for (; part < nparts; ++part) acc += src[(size_t)part * Lp];
-        if (q < 18 * nbs) {
-            const int st = q / 18, e = q - 18 * st;
-            int a, b;
-            decode_pair(st >> 1, nf, a, b);
-            const int row = 6 * a + 3 * (st & 1) + e / 6, col = 6 * b + e % 6;
-            S[row * ld + col] = acc;
-            if (a != b) S[col * ld + row] = acc;
-        } else {
-            v[q - 18 * nbs] = acc;
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int q = q0 + u * kSolveThreads;
+            if (q >= Lp) break;
+            if (q < 18 * nbs) {
+                const int st = q / 18, e = q - 18 * st;
+                int a, b;
+                decode_pair(st >> 1, nf, a, b);
+                const int row = 6 * a + 3 * (st & 1) + e / 6, col = 6 * b + e % 6;
+                S[row * ld + col] = accs[u];
+                if (a != b) S[col * ld + row] = accs[u];
+            } else {
+                v[q - 18 * nbs] = accs[u];
+            }
         }
     }
     __syncthreads();
@@ -1295,6 +1354,124 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         const int r = q - c * (c + 1) / 2;
         own[u] = ((n - 1 - r) << 16) | (n - 1 - c);          // (i, k)
     }
+
+    // Forward solves factor an FP32 copy of S (the same elimination, on the
+    // FP32 pipes) and refine its solution against S in FP64: x += S32^-1 (v -
+    // S x) until the correction is below kRefineTol of the solution.  A pivot
+    // that fails in FP32, or corrections that do not shrink, hand the system
+    // to the FP64 elimination below, which also serves the adjoint (it keeps
+    // the FP64 factor).
+    __shared__ int s_use64;
+    __shared__ float s_rpf[6 * kMaxFree];
+    __shared__ double s_red[kSolveThreads / 32][2];
+    if (tid == 0) s_use64 = pr.store_factor ? 1 : 0;
+    __syncthreads();
+    if (!s_use64) {
+        double *x = v + n;
+        float *Sf = reinterpret_cast<float *>(x + n);
+        float *bf = Sf + (size_t)n * ld;
+        for (int q = tid; q < n * n; q += kSolveThreads) {
+            const int i = q / n, k = q - i * n;
+            if (k <= i) Sf[i * ld + k] = (float)S[i * ld + k];
+        }
+        for (int q = tid; q < n; q += kSolveThreads) {
+            x[q] = 0.0;
+            bf[q] = (float)v[q];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const float p0 = Sf[0];
+            s_rpf[0] = p0 > 0.f ? 1.0f / p0 : -1.f;
+        }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const float ip = s_rpf[j];
+            if (!(ip > 0.f) || !isfinite(ip)) {
+                if (tid == 0) s_use64 = 1;
+                break;
+            }
+            const int m = n - 1 - j, count = m * (m + 1) / 2, last = count - 1;
+            const float *colj = Sf + j;
+            if (count > 0 && tid == last % kSolveThreads) {
+                const int jn = j + 1;
+                const float pn = Sf[jn * ld + jn] - (colj[jn * ld] * ip) * colj[jn * ld];
+                Sf[jn * ld + jn] = pn;
+                s_rpf[jn] = pn > 0.f ? 1.0f / pn : -1.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kSolveOwn; ++u) {
+                const int q = tid + kSolveThreads * u;
+                if (q >= last) break;
+                const int i = own[u] >> 16, k = own[u] & 0xffff;
+                Sf[i * ld + k] -= (colj[i * ld] * ip) * colj[k * ld];
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        double prev = 0.0;
+        for (int it = 0; it <= kMaxRefine && !s_use64; ++it) {
+            if (it > 0) {   // residual v - S x in FP64, four threads per row
+                const int qk = tid & 3;
+                for (int base = 0; base < n; base += kSolveThreads / 4) {
+                    const int i = base + (tid >> 2);
+                    double acc = 0.0;
+                    if (i < n)
+                        for (int k = qk; k < n; k += 4) acc = fma(S[i * ld + k], x[k], acc);
+                    acc += shfl_double(acc, lane ^ 1);
+                    acc += shfl_double(acc, lane ^ 2);
+                    if (i < n && qk == 0) bf[i] = (float)(v[i] - acc);
+                }
+                __syncthreads();
+            }
+            if (tid < 32) solve_factored_f32(Sf, ld, s_rpf, bf, n, lane);
+            __syncthreads();
+            double dmax = 0.0, xmax = 0.0;
+            for (int q = tid; q < n; q += kSolveThreads) {
+                const double d = (double)bf[q];
+                const double xn = x[q] + d;
+                x[q] = xn;
+                dmax = fmax(dmax, fabs(d));
+                xmax = fmax(xmax, fabs(xn));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dmax = fmax(dmax, shfl_double(dmax, lane ^ o));
+                xmax = fmax(xmax, shfl_double(xmax, lane ^ o));
+            }
+            if (lane == 0) { s_red[tid >> 5][0] = dmax; s_red[tid >> 5][1] = xmax; }
+            __syncthreads();
+            dmax = 0.0; xmax = 0.0;
+#pragma unroll
+            for (int w = 0; w < kSolveThreads / 32; ++w) {
+                dmax = fmax(dmax, s_red[w][0]);
+                xmax = fmax(xmax, s_red[w][1]);
+            }
+            if (!(dmax <= 1e300)) {                                 // non-finite: hand to FP64
+                if (tid == 0) s_use64 = 1;
+                __syncthreads();
+                break;
+            }
+            if (it > 0 && dmax <= kRefineTol * xmax) break;         // converged (same in every thread)
+            if (it > 1 && !(dmax <= 0.5 * prev)) {                  // not contracting
+                if (tid == 0) s_use64 = 1;
+                __syncthreads();
+                break;
+            }
+            if (it == kMaxRefine) {
+                if (tid == 0) s_use64 = 1;
+                __syncthreads();
+                break;
+            }
+            prev = dmax;
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!s_use64)
+            for (int q = tid; q < n; q += kSolveThreads) v[q] = x[q];
+        __syncthreads();
+    }
+
+    if (s_use64) {
     // The reciprocal of each pivot is formed by the thread that updates the
     // pivot in the step before (it owns the last element of that step's
     // triangle), first in its list, so the division overlaps the step's
@@ -1350,6 +1527,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
             if (lane == 0) v[j] = xj;
             __syncwarp();
         }
+    }
+    }   // FP64 elimination
+    __syncthreads();
+    if (!s_flag && tid < 32) {
         bool bad = false;
         for (int q = lane; q < n; q += 32) bad |= !isfinite(v[q]);
         if (__any_sync(0xffffffffu, bad) && lane == 0) s_flag = DPVO_BA_STATUS_NONFINITE;

@@ -50,28 +50,35 @@ __device__ inline void adjoint6(const float *R, const float *t, float *Ad) {
 // T <- Exp(xi) T in FP64 for xi = (v, w):
 //   Exp(xi) = [[R(w), V(w) v], [0, 1]],  R(w) = exp([w]x),
 //   V(w) = I + (1 - cos th)/th^2 [w]x + (th - sin th)/th^3 [w]x^2,  th = |w|;
-// quaternion of R(w) = (sin(th/2) w/th, cos(th/2)).  Series for small th.
+// quaternion of R(w) = (sin(th/2) w/th, cos(th/2)).
+// The scalar coefficients come from FP32 (sincosf, or Taylor series below
+// th = 0.1; (1 - cos th)/th^2 as 2 (sin(th/2)/th)^2, free of cancellation):
+// their rounding enters the pose only multiplied by th or th^2, and the
+// increment's quaternion is renormalised in FP64.  The composition is FP64.
 __device__ inline void se3_left_update(const double *xi, const float *pose_in, float *pose_out) {
     const double v0 = xi[0], v1 = xi[1], v2 = xi[2];
     const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
     const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    const double th = sqrt(th2);
-    double A, B, half_s, half_c;   // A = (1-cos)/th^2, B = (th-sin)/th^3, half_s = sin(th/2)/th
-    if (th < 1e-4) {
-        A = 0.5 - th2 / 24.0 + th2 * th2 / 720.0;
-        B = 1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0;
-        half_s = 0.5 - th2 / 48.0 + th2 * th2 / 3840.0;
-        half_c = 1.0 - th2 / 8.0 + th2 * th2 / 384.0;
+    const float th2f = (float)th2, tf = sqrtf(th2f);
+    float hs, hc, bf;   // sin(th/2)/th, cos(th/2), (th - sin th)/th^3
+    if (tf < 0.1f) {
+        hs = 0.5f + th2f * (-1.f / 48.f + th2f * (1.f / 3840.f - th2f * (1.f / 645120.f)));
+        hc = 1.f + th2f * (-1.f / 8.f + th2f * (1.f / 384.f - th2f * (1.f / 46080.f)));
+        bf = 1.f / 6.f + th2f * (-1.f / 120.f + th2f * (1.f / 5040.f - th2f * (1.f / 362880.f)));
     } else {
-        double s, c;
-        sincos(th, &s, &c);
-        A = (1.0 - c) / th2;
-        B = (th - s) / (th2 * th);
-        double hs, hc;
-        sincos(0.5 * th, &hs, &hc);
-        half_s = hs / th;
-        half_c = hc;
+        float s2, c2;
+        sincosf(0.5f * tf, &s2, &c2);
+        hs = s2 / tf;
+        hc = c2;
+        bf = (tf - 2.f * s2 * c2) / (th2f * tf);
     }
+    const double half_s0 = hs, half_c0 = hc, B = bf;
+    // renormalise (half_s0 w, half_c0): its squared norm is 1 to within FP32
+    // rounding, where 1.5 - s/2 approximates s^-1/2 to (3/8)(s - 1)^2
+    const double sn = half_s0 * half_s0 * th2 + half_c0 * half_c0;
+    const double nrm = 1.5 - 0.5 * sn;
+    const double half_s = half_s0 * nrm, half_c = half_c0 * nrm;
+    const double A = 2.0 * half_s * half_s;   // (1 - cos th)/th^2
     // quaternion of the increment
     const double qx = half_s * w0, qy = half_s * w1, qz = half_s * w2, qw = half_c;
     // rotation matrix of the increment from its quaternion
@@ -93,7 +100,16 @@ __device__ inline void se3_left_update(const double *xi, const float *pose_in, f
     double ny = qw * by + bw * qy + (qz * bx - qx * bz);
     double nz = qw * bz + bw * qz + (qx * by - qy * bx);
     double nw = qw * bw - (qx * bx + qy * by + qz * bz);
-    const double inv = 1.0 / sqrt(nx * nx + ny * ny + nz * nz + nw * nw);
+    // the stored quaternion is unit to within FP32 rounding: one Newton step
+    // from 1.5 - s/2; other norms take the exact root
+    const double qs = nx * nx + ny * ny + nz * nz + nw * nw;
+    double inv;
+    if (fabs(qs - 1.0) < 1e-4) {
+        const double y = 1.5 - 0.5 * qs;
+        inv = y * (1.5 - 0.5 * qs * y * y);
+    } else {
+        inv = 1.0 / sqrt(qs);
+    }
     pose_out[0] = (float)nt0; pose_out[1] = (float)nt1; pose_out[2] = (float)nt2;
     pose_out[3] = (float)(nx * inv); pose_out[4] = (float)(ny * inv);
     pose_out[5] = (float)(nz * inv); pose_out[6] = (float)(nw * inv);
