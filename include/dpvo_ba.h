@@ -61,7 +61,7 @@ extern "C" {
 
 /* ---- capacities of this build ------------------------------------------- */
 #define DPVO_BA_MAX_FRAMES       128  /* N per problem                                   */
-#define DPVO_BA_MAX_FREE          15  /* N - t0 per problem (reduced system <= 90 x 90)  */
+#define DPVO_BA_MAX_FREE          32  /* N - t0 per problem (reduced system <= 192 x 192) */
 #define DPVO_BA_MAX_ITERS         16  /* Gauss-Newton iterations per solve               */
 
 /* Sizes of one problem. */

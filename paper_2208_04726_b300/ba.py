@@ -43,7 +43,7 @@ class Problem(ctypes.Structure):
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6
 STATUS_OK, STATUS_NOT_SPD, STATUS_BAD_INPUT, STATUS_NONFINITE, STATUS_TIMEOUT = 0, 1, 2, 4, 8
-MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 15, 16
+MAX_FRAMES, MAX_FREE, MAX_ITERS = 128, 32, 16
 
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solve", "dpvo_ba_solve_host",

@@ -11,6 +11,12 @@ namespace dpvo {
 constexpr int kThreads = 256;          // block size of the linearise and solve kernels
 constexpr int kMaxWindow = 64;         // frames the edges of one patch chunk may span
 constexpr int kMaxFree = DPVO_BA_MAX_FREE;
+// Free poses up to which the Schur complement accumulates inside the linearise
+// kernel (each strip owner keeps its sums in registers) and the reduced system
+// is factored from a full n x (n + 1) array in shared memory.  Beyond it a
+// separate assembly kernel reads the stored Schur rows, and the solve keeps S
+// packed (FP32 copy in shared memory, FP64 in the workspace).
+constexpr int kFusedMaxFree = 15;
 constexpr int kFlushEvery = 16;        // patches summed in FP32 before a compensated add
 constexpr int kMaxKSplit = 8;          // patch-parity split of the Schur accumulation
 
@@ -45,7 +51,8 @@ struct Prob {
     float *pose_it;          // [iters + 1][N][7] iterates
     float *depth_it;         // [iters + 1][P]
     double *dxi;             // [iters][nf][6] pose increments
-    double *partial;         // [n_items][ks][L] Schur partial sums
+    double *partial;         // [n_parts][L] Schur partial sums (linearise CTAs, then assembly CTAs)
+    double *sglob;           // [6nf (6nf + 1) / 2] FP64 reduced system, packed lower (more than kFusedMaxFree free poses)
     float *erow;             // [P][erow_len(nf)] scaled Schur row of each patch, last linearisation
     // backward (adjoint) state; null / zero for a plain solve
     int store_factor;        // keep the factored reduced system of every iteration
@@ -63,6 +70,8 @@ struct Prob {
 
     int max_chunks;
     int n_items;             // linearise work items (CTAs) of this problem
+    int n_asm;               // Schur-assembly work items (0: accumulated inside the linearise kernel)
+    int n_parts;             // partials summed by the solve
     int ks;                  // patch-parity split of the Schur accumulation
     int L;                   // doubles per partial
     int chunk_cap;           // patches per chunk at most

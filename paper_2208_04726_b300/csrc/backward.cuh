@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kSolveThreads) bw_solve_kernel(const Prob *__r
     const int nf = pr.nf, n = 6 * nf;
     if (n == 0) return;
     __shared__ double b[6 * kMaxFree];
-    const int Lp = pr.L, nparts = pr.n_items * pr.ks, off = 18 * 2 * n_block_pairs(nf);
+    const int Lp = pr.L, nparts = pr.n_parts, off = 18 * 2 * n_block_pairs(nf);
     for (int q = tid; q < n; q += kSolveThreads) {
         double acc = pr.dxibar[q];
         for (int part = 0; part < nparts; ++part) acc += pr.partial[(size_t)part * Lp + off + q];

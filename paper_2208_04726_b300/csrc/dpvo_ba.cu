@@ -9,6 +9,7 @@
 #include "dpvo_ba.h"
 #include "ba_common.cuh"
 #include "kernels.cuh"
+#include "assemble.cuh"
 #include "backward.cuh"
 #include "serve.cuh"
 
@@ -16,17 +17,19 @@ using namespace dpvo;
 
 namespace {
 
-constexpr size_t kLinSmemBudget = 110 * 1024;   // leaves room for two CTAs per SM
+constexpr size_t kLinSmemBudget = 112 * 1024;   // two CTAs per SM (228 KB, 1 KB reserved per CTA)
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     std::vector<Prob> probs;       // workspace pointers hold offsets until rebased
-    std::vector<Item> items;
+    std::vector<Item> items;       // linearise work items, then assembly work items
     size_t bytes = 0, off_probs = 0, off_items = 0;
     int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0, n_max = 1;
     bool tc = false;               // Schur accumulation on the tensor cores
-    size_t lin_smem = 0, solve_smem = 0;
+    bool ext = false;              // more than kFusedMaxFree free poses: assembly kernel, packed solve
+    int n_lin_items = 0, n_asm_items = 0;
+    size_t lin_smem = 0, solve_smem = 0, asm_smem = 0;
 };
 
 // solve_kernel shared memory: S and its FP32 copy (n x (n+1)), v, x, the FP32 right-hand side.
@@ -42,15 +45,32 @@ static size_t erow_bytes(bool tc, const Prob &p, int G_cap) {
     return (size_t)p.P * erow_len(p.nf) * 4 + 16;
 }
 
+// Assembly launch (ext batches): grid x = assembly items, y = strip slices.
+static void launch_assembly(const Layout &L, cudaStream_t stream, const Prob *probs, const Item *asm_items, int t) {
+    const dim3 grid(L.n_asm_items, asm_slices(L.nf_max));
+    schur_assembly_kernel<<<grid, asm_threads(L.nf_max), L.asm_smem, stream>>>(probs, asm_items, t, L.G_cap,
+                                                                               erow_len(L.nf_max));
+}
+
+// Reduced solve launch, in the batch's variant.
+static void launch_solve(const Layout &L, int n, cudaStream_t stream, const Prob *probs, int t, double *S_out,
+                         double *v_out) {
+    if (L.ext) solve_large_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
+    else solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
+}
+
 // One linearise launch, in the batch's variant.
-static void launch_linearize(bool tc, int grid, size_t smem, cudaStream_t stream, const Prob *probs,
-                             const Item *items, int t, int W_cap, int G_cap, int nf_max, int n_max, int adjoint_rhs) {
-    if (tc)
-        linearize_kernel<true><<<grid, kThreads, smem, stream>>>(probs, items, t, W_cap, G_cap, nf_max, n_max,
-                                                                 adjoint_rhs);
+static void launch_linearize(const Layout &L, int grid, cudaStream_t stream, const Prob *probs, const Item *items,
+                             int t, int adjoint_rhs) {
+    if (L.tc)
+        linearize_kernel<true, false><<<grid, kThreads, L.lin_smem, stream>>>(probs, items, t, L.W_cap, L.G_cap,
+                                                                          L.nf_max, L.n_max, adjoint_rhs);
+    else if (L.ext)
+        linearize_kernel<false, true><<<grid, kThreads, L.lin_smem, stream>>>(probs, items, t, L.W_cap, L.G_cap,
+                                                                          L.nf_max, L.n_max, adjoint_rhs);
     else
-        linearize_kernel<false><<<grid, kThreads, smem, stream>>>(probs, items, t, W_cap, G_cap, nf_max, n_max,
-                                                                  adjoint_rhs);
+        linearize_kernel<false, false><<<grid, kThreads, L.lin_smem, stream>>>(probs, items, t, L.W_cap, L.G_cap,
+                                                                           L.nf_max, L.n_max, adjoint_rhs);
 }
 
 int check_dims(const dpvo_ba_dims &d) {
@@ -86,7 +106,10 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes > kLinSmemBudget)
         L.G_cap -= 8;
     L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
-    L.solve_smem = solve_smem_bytes(L.nf_max);
+    L.ext = L.nf_max > kFusedMaxFree;
+    L.solve_smem = L.ext ? solve_large_smem_bytes(L.nf_max) : solve_smem_bytes(L.nf_max);
+    L.asm_smem = L.ext ? (size_t)2 * L.G_cap * erow_len(L.nf_max) * 4 : 0;
+    const int asm_slices_max = L.ext ? asm_slices(L.nf_max) : 1;
 
     const int target_ctas = 2 * num_sms;
     size_t off = 0;
@@ -102,11 +125,18 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.chunk_cap = L.G_cap;
         p.win_cap = L.W_cap;
         p.max_chunks = (d.n_patches + L.G_cap - 1) / L.G_cap + d.n_frames;
-        p.ks = L.tc ? 1 : k_split(p.nf);
+        p.ks = (L.tc || L.ext) ? 1 : k_split(p.nf);
         p.L = partial_len(p.nf);
+        // work items: as many as fill one wave of the SMs (two linearise CTAs
+        // per SM; one assembly CTA per SM), at least one per problem
         int est_chunks = std::max(1, (d.n_patches + L.G_cap - 1) / L.G_cap);
-        int items = n >= target_ctas ? 1 : (target_ctas + n - 1) / n;
+        int items = std::max(1, target_ctas / n);
         p.n_items = std::max(1, std::min(items, est_chunks));
+        if (L.ext) {
+            const int per = std::max(1, num_sms / (n * asm_slices_max));
+            p.n_asm = std::max(1, std::min(per, est_chunks));
+        }
+        p.n_parts = L.ext ? p.n_items + p.n_asm : p.n_items * p.ks;
         // workspace offsets (rebased to device pointers later)
         auto take = [&](size_t bytes) { size_t o = off; off = al256(off + bytes); return o; };
         p.seg = (int32_t *)(uintptr_t)take((size_t)(d.n_patches + 1) * 4);
@@ -117,7 +147,11 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.pose_it = (float *)(uintptr_t)take((size_t)(d.n_iters + 1) * d.n_frames * 7 * 4);
         p.depth_it = (float *)(uintptr_t)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
         p.dxi = (double *)(uintptr_t)take((size_t)d.n_iters * p.nf * 6 * 8 + 8);
-        p.partial = (double *)(uintptr_t)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
+        p.partial = (double *)(uintptr_t)take((size_t)p.n_parts * p.L * 8 + 8);
+        if (L.ext) {
+            const size_t n6 = 6 * (size_t)p.nf;
+            p.sglob = (double *)(uintptr_t)take(n6 * (n6 + 1) / 2 * 8 + 8);
+        }
         p.erow = (float *)(uintptr_t)take(erow_bytes(L.tc, p, L.G_cap));
         if (adjoint) {
             const size_t n6 = 6 * (size_t)p.nf;
@@ -132,6 +166,10 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         }
         for (int w = 0; w < p.n_items; ++w) L.items.push_back(Item{b, w});
     }
+    L.n_lin_items = (int)L.items.size();
+    for (int b = 0; b < n; ++b)
+        for (int w = 0; w < L.probs[b].n_asm; ++w) L.items.push_back(Item{b, w});
+    L.n_asm_items = (int)L.items.size() - L.n_lin_items;
     L.off_probs = off;
     off = al256(off + sizeof(Prob) * n);
     L.off_items = off;
@@ -213,13 +251,20 @@ static bool g_attr_set[64] = {false};
 
 static int set_kernel_attrs(int device) {
     if (device >= 0 && device < 64 && g_attr_set[device]) return DPVO_BA_OK;
-    if (cudaFuncSetAttribute(linearize_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
-        cudaSuccess)
-        return DPVO_BA_ECUDA;
-    if (cudaFuncSetAttribute(linearize_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(linearize_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(linearize_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess ||
+        cudaFuncSetAttribute(linearize_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess)
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(solve_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(schur_assembly_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(bw_edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
@@ -252,6 +297,7 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         p.dxi = rebase(p.dxi, h->ws);
         p.partial = rebase(p.partial, h->ws);
         p.erow = rebase(p.erow, h->ws);
+        if (p.sglob) p.sglob = rebase(p.sglob, h->ws);
     }
     h->last = L.probs;
     std::memcpy(h->stage, L.probs.data(), sizeof(Prob) * n);
@@ -263,7 +309,7 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
 
     const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
-    const int n_items = (int)L.items.size();
+    const int n_items = L.n_lin_items;
     // with timing on, bracket each launch with a pair of events on `stream`
     auto timed = [&](int kind, auto &&launch) -> int {
         if (h->timing) {
@@ -277,21 +323,23 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         return DPVO_BA_OK;
     };
     if ((rc = timed(0, [&] { plan_kernel<<<n, kPlanThreads, 0, stream>>>(d_probs); }))) return rc;
+    const Item *d_asm_items = d_items + L.n_lin_items;
     if (S_out) {
-        launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, 0, L.W_cap, L.G_cap, L.nf_max,
-                         L.n_max, 0);
-        solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, 0, S_out, v_out);
+        launch_linearize(L, n_items, stream, d_probs, d_items, 0, 0);
+        if (L.ext) launch_assembly(L, stream, d_probs, d_asm_items, 0);
+        launch_solve(L, n, stream, d_probs, 0, S_out, v_out);
     } else {
         for (int t = 0; t <= L.iters_max; ++t) {
             rc = timed(1, [&] {
-                launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, t, L.W_cap, L.G_cap,
-                                 L.nf_max, L.n_max, 0);
+                launch_linearize(L, n_items, stream, d_probs, d_items, t, 0);
             });
             if (rc) return rc;
             if (t < L.iters_max) {
-                rc = timed(2, [&] {
-                    solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
-                });
+                if (L.ext) {
+                    rc = timed(3, [&] { launch_assembly(L, stream, d_probs, d_asm_items, t); });
+                    if (rc) return rc;
+                }
+                rc = timed(2, [&] { launch_solve(L, n, stream, d_probs, t, nullptr, nullptr); });
                 if (rc) return rc;
             }
         }
@@ -330,6 +378,7 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
         p.dxi = rebase(p.dxi, h->ws);
         p.partial = rebase(p.partial, h->ws);
         p.erow = rebase(p.erow, h->ws);
+        if (p.sglob) p.sglob = rebase(p.sglob, h->ws);
         p.ufac = rebase(p.ufac, h->ws);
         p.eps = rebase(p.eps, h->ws);
         p.dxibar = rebase(p.dxibar, h->ws);
@@ -346,19 +395,17 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
     h->stage_pending = true;
     const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
-    const int n_items = (int)L.items.size();
+    const int n_items = L.n_lin_items;
     const size_t bw_smem = bw_smem_layout(L.W_cap, L.G_cap, L.n_max).bytes;
     plan_kernel<<<n, kPlanThreads, 0, stream>>>(d_probs);
     for (int t = 0; t <= L.iters_max; ++t) {
-        launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, t, L.W_cap, L.G_cap, L.nf_max,
-                         L.n_max, 0);
+        launch_linearize(L, n_items, stream, d_probs, d_items, t, 0);
         if (t < L.iters_max) solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
     }
     bw_init_kernel<<<n, kThreads, 0, stream>>>(d_probs);
     for (int t = L.iters_max - 1; t >= 0; --t) {
         bw_retract_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
-        launch_linearize(L.tc, n_items, L.lin_smem, stream, d_probs, d_items, t, L.W_cap, L.G_cap, L.nf_max,
-                         L.n_max, 1);
+        launch_linearize(L, n_items, stream, d_probs, d_items, t, 1);
         bw_solve_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
         bw_edge_kernel<<<n_items, kThreads, bw_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap, L.n_max);
     }
@@ -374,6 +421,7 @@ int dpvo_ba_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     for (int b = 0; b < n_problems; ++b) {
         if (int rc = check_dims(dims[b])) return rc;
         if (int rc = check_problem(dims[b], probs[b])) return rc;
+        if (dims[b].n_frames - dims[b].t0 > kFusedMaxFree) return DPVO_BA_EINVAL;
         const dpvo_ba_grads &g = grads[b];
         if (!g.dL_dposes || (dims[b].n_patches > 0 && !g.dL_ddepth) ||
             (dims[b].n_edges > 0 && (!g.dL_dtarget || !g.dL_dweight)))
@@ -976,6 +1024,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     if (!dims || !prob) return DPVO_BA_EINVAL;
     if (int rc = check_dims(*dims)) return rc;
     if (int rc = check_problem(*dims, *prob)) return rc;
+    if (dims->n_frames - dims->t0 > kFusedMaxFree) return DPVO_BA_EINVAL;   // no assembly kernel on this path
     cudaStream_t stream = (cudaStream_t)stream_;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DPVO_BA_ECUDA; }
@@ -1022,6 +1071,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.L = partial_len(nf);
     const int est_chunks = std::max(1, (d.n_patches + G_cap - 1) / G_cap);
     p.n_items = std::max(1, std::min(2 * g_noalloc_sms[dev], est_chunks));
+    p.n_parts = p.n_items * p.ks;
     char *base = g_noalloc_base[dev];
     size_t off = 0;
     auto take = [&](size_t bytes) { char *q = base + off; off = al256(off + bytes); return q; };
@@ -1039,10 +1089,17 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     Item *d_items = (Item *)take(sizeof(Item) * p.n_items);
     if (off > kNoAllocScratchBytes) return DPVO_BA_EINVAL;   // problem too large for the fixed scratch
 
+    Layout lay;   // launch shapes only (no workspace from it)
+    lay.tc = tc;
+    lay.W_cap = W_cap;
+    lay.G_cap = G_cap;
+    lay.nf_max = nf;
+    lay.n_max = d.n_frames;
+    lay.lin_smem = lin_smem;
     noalloc_descriptors_kernel<<<1, kThreads, 0, stream>>>(p, p.n_items, d_prob, d_items);
     plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_prob);
     for (int t = 0; t <= d.n_iters; ++t) {
-        launch_linearize(tc, p.n_items, lin_smem, stream, d_prob, d_items, t, W_cap, G_cap, nf, d.n_frames, 0);
+        launch_linearize(lay, p.n_items, stream, d_prob, d_items, t, 0);
         if (t < d.n_iters) solve_kernel<<<1, kSolveThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
     }
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;

@@ -266,9 +266,9 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     // slot (frame jl, patch p) at jl * Gs + p.  The per-patch sums read
     // frames sub, sub + 4, ... of 8 consecutive patches by 4 lanes each: with
     // Gs = 2 (mod 8) the 16-byte reads of a quarter warp, and with Gs1 = 8
-    // (mod 32) the 4-byte reads of a warp, fall in distinct banks.
+    // (mod 16) the 4-byte reads of a warp, fall in distinct banks.
     s.Gs = G + ((2 - G) % 8 + 8) % 8;
-    s.Gs1 = G + ((8 - G) % 32 + 32) % 32;
+    s.Gs1 = G + ((8 - G) % 16 + 16) % 16;
     // E_k row: frame f at floats 8f..8f+7 laid out [v0 v1 v2 _ v3 v4 v5 _],
     // then C_k^-1/2 w_k; the stride is an odd multiple of 4 floats
     const int es = 8 * nf_max + 4;
@@ -443,6 +443,62 @@ __device__ __forceinline__ float quad_sum(float v) {
     return v;
 }
 
+// The pose-pair block entries a group of chunks adds to one strip of (S, v')
+// (the same selection the fused path makes inline for its register strips):
+// half-strip (a, b, sh) = rows 6a + 3sh .. +2, columns 6b .. 6b + 5 of the
+// (free-pose) block (a, b), or the right-hand side of free pose a (vstrip).
+// Blocks: B_jj = M_j for window frames, B_ii for the anchor, B_ij = -Ad^T M_j
+// between anchor and frame.  Returns false if the group adds nothing there.
+__device__ __forceinline__ bool strip_block_add(int sa, int sb, int sh, bool vstrip, int t0, int anc, int jlo, int W,
+                                                const float *Mc, const float *Aj, const float *Bii, float *add) {
+    const int fa = t0 + sa, fb = t0 + sb;
+    const int ja = fa - jlo, jb = fb - jlo;
+    const bool a_in = ja >= 0 && ja < W, b_in = jb >= 0 && jb < W;
+    if (vstrip) {
+        if (fa == anc) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) add[q] = Bii[36 + q];
+        } else if (a_in) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) add[q] = Mc[ja * 27 + 21 + q];
+        } else {
+            return false;
+        }
+        return true;
+    }
+    if (sa == sb) {
+        if (fa == anc) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) add[6 * r + cc] = Bii[6 * (3 * sh + r) + cc];
+        } else if (a_in) {
+            const float *Mj = Mc + ja * 27;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) add[6 * r + cc] = Mj[sym6(3 * sh + r, cc)];
+        } else {
+            return false;
+        }
+    } else if (fa == anc && b_in) {
+        const float *A = Aj + jb * 42;          // block (i, j) = -Ad^T M_j
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) add[6 * r + cc] = -A[6 * (3 * sh + r) + cc];
+    } else if (fb == anc && a_in) {
+        const float *A = Aj + ja * 42;          // block (j, i) = -(Ad^T M_j)^T
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) add[6 * r + cc] = -A[6 * cc + 3 * sh + r];
+    } else {
+        return false;
+    }
+    return true;
+}
+
 // ----------------------------------------------------------------------------
 // linearize_kernel: one CTA per work item (a range of chunks of one problem).
 // t = iteration.  For t < iters: back-substitute iteration t-1 (if t > 0), then
@@ -463,7 +519,7 @@ __device__ __forceinline__ float quad_sum(float v) {
 // with A = all 128 rows and B = the hi half gives D = [lo; hi] hi^T; the CTA
 // reads D back once, after its last chunk.
 // ----------------------------------------------------------------------------
-template <bool TC>
+template <bool TC, bool EXT>
 __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__restrict__ probs,
                                                              const Item *__restrict__ items, int t,
                                                              int W_cap, int G_cap, int nf_max, int n_max,
@@ -593,10 +649,13 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     const int nbs = 2 * nbp;
     const int nst = nbs + nf;
     const int KS = pr.ks;
+    // ext: more free poses than strips fit in registers; the patch products are
+    // summed by the assembly kernel and the pose-pair blocks go to global memory
+    constexpr bool ext = EXT;   // the host launches EXT exactly for batches with n_asm > 0
     const int my_strip = nst > 0 ? tid % nst : 0;
     const int my_ks = nst > 0 ? tid / nst : KS;
     const bool is_vstrip = my_strip >= nbs;
-    const bool owns = nst > 0 && my_ks < KS && (is_vstrip || !adjoint_rhs);
+    const bool owns = !ext && nst > 0 && my_ks < KS && (is_vstrip || !adjoint_rhs);
     int sa = 0, sb = 0, sh = 0;
     if (owns) {
         if (!is_vstrip) {
@@ -611,6 +670,10 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     for (int q = 0; q < 18; ++q) { acc_s[q] = 0.f; acc_c[q] = 0.f; blk[q] = 0.f; }
 
     for (int q = tid; q < N * 7; q += kThreads) spn[q] = pose_new[q];
+    if constexpr (EXT) {
+        double *part = pr.partial + (size_t)itm.item * pr.L;
+        for (int q = tid; q < pr.L; q += kThreads) part[q] = 0.0;
+    }
 
     // tensor-core state: TMEM accumulator (64 columns), MMA-completion barrier
     __shared__ __align__(8) uint64_t s_mbar;
@@ -1127,6 +1190,30 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 }
             }
         }
+        if constexpr (EXT) if (!group_next && !adjoint_rhs) {
+            // more strips than threads: each pose-pair block goes straight into
+            // this CTA's FP64 partial (it owns the partial; groups are sequential)
+            double *part = pr.partial + (size_t)itm.item * pr.L;
+            for (int st = tid; st < nst; st += kThreads) {
+                const bool vs = st >= nbs;
+                int a2 = st - nbs, b2 = a2, h2 = 0;
+                if (!vs) {
+                    decode_pair(st >> 1, nf, a2, b2);
+                    h2 = st & 1;
+                }
+                float add[18];
+                if (!strip_block_add(a2, b2, h2, vs, t0, anc, jlo, W, Mc, Aj, Bii, add)) continue;
+                if (vs) {
+                    double *o = part + 18 * nbs + 6 * a2;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) o[q] += (double)add[q];
+                } else {
+                    double *o = part + 18 * st;
+#pragma unroll
+                    for (int q = 0; q < 18; ++q) o[q] += (double)add[q];
+                }
+            }
+        }
         __syncthreads();
         group_open = group_next;
         cur ^= 1;
@@ -1190,7 +1277,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
     // write this CTA's partial of (S, v')
     if (owns) {
-        double *out = pr.partial + ((size_t)itm.item * KS + my_ks) * pr.L;
+        double *out = pr.partial + ((size_t)itm.item * KS + my_ks) * pr.L;   // ks parts per item
         if (!is_vstrip) {
             double *o = out + 18 * my_strip;
 #pragma unroll
@@ -1213,8 +1300,9 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 // nothing else.
 // ----------------------------------------------------------------------------
 constexpr int kSolveThreads = 256;
-// elements of the largest trailing triangle, (6 kMaxFree - 1) 6 kMaxFree / 2, per thread
-constexpr int kSolveOwn = ((6 * kMaxFree - 1) * 6 * kMaxFree / 2 + kSolveThreads - 1) / kSolveThreads;
+// elements of the largest trailing triangle of solve_kernel (at most kFusedMaxFree
+// free poses), (6 nf - 1) 6 nf / 2, per thread
+constexpr int kSolveOwn = ((6 * kFusedMaxFree - 1) * 6 * kFusedMaxFree / 2 + kSolveThreads - 1) / kSolveThreads;
 
 __device__ __forceinline__ double shfl_double(double x, int src) {
     int lo = __double2loint(x), hi = __double2hiint(x);
@@ -1299,7 +1387,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
     __shared__ double s_rp[6 * kMaxFree];    // pivot reciprocals, reused by the back substitution
 
     // FP64 sum of the partials in a fixed order (deterministic)
-    const int Lp = pr.L, nparts = pr.n_items * pr.ks, nbs = 2 * n_block_pairs(nf);
+    const int Lp = pr.L, nparts = pr.n_parts, nbs = 2 * n_block_pairs(nf);
     constexpr int kQ = 8;                       // entries per thread with loads in flight together
     for (int q0 = tid; q0 < Lp; q0 += kQ * kSolveThreads) {
         double accs[kQ];
@@ -1529,6 +1617,308 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         }
     }
     }   // FP64 elimination
+    __syncthreads();
+    if (!s_flag && tid < 32) {
+        bool bad = false;
+        for (int q = lane; q < n; q += 32) bad |= !isfinite(v[q]);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) s_flag = DPVO_BA_STATUS_NONFINITE;
+    }
+    __syncthreads();
+    if (s_flag) {
+        if (tid == 0) *pr.status = s_flag;
+        for (int q = tid; q < N * 7; q += kSolveThreads) pose_next[q] = pose_cur[q];
+        for (int q = tid; q < nf * 6; q += kSolveThreads) dxi[q] = 0.0;
+        return;
+    }
+    for (int q = tid; q < n; q += kSolveThreads) dxi[q] = v[q];
+    for (int a = tid; a < N; a += kSolveThreads) {
+        if (a >= t0) se3_left_update(v + 6 * (a - t0), pose_cur + 7 * a, pose_next + 7 * a);
+        else
+            for (int q = 0; q < 7; ++q) pose_next[7 * a + q] = pose_cur[7 * a + q];
+    }
+}
+
+
+// ----------------------------------------------------------------------------
+// solve_large_kernel: the reduced solve for more than kFusedMaxFree free poses
+// (n = 6 nf up to 192).  S is packed, lower triangle by rows: (i, k), k <= i,
+// at i (i + 1) / 2 + k.  The FP64 sum of the partials goes to the workspace
+// (pr.sglob, read again by the FP64 residuals) and, rounded, to an FP32 copy
+// in shared memory that is factored in place (S = U D^-1 U^T, a 16 x 16 thread
+// grid over the trailing triangle, the next pivot's reciprocal formed first by
+// the thread that owns it); the solution is refined in FP64 as in
+// solve_kernel.  The FP32 copy is equilibrated, Dg S Dg with Dg = diag(S)^-1/2,
+// which keeps the refinement contracting on the worse-conditioned large
+// windows: each correction solves (Dg S Dg) y = Dg r and adds Dg y.  Fallback (an FP32 pivot fails or the corrections stall): FP64
+// elimination of S loaded packed into shared memory.
+// ----------------------------------------------------------------------------
+__host__ __device__ inline int packed_index(int i, int k) { return i * (i + 1) / 2 + k; }
+
+// One warp: solve with the packed FP32 factor, b in place (n <= 32 R).
+template <int R>
+__device__ __forceinline__ void solve_packed_f32(const float *Sp, const float *rp, float *b, int n, int lane) {
+    float x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = lane + 32 * r < n ? b[lane + 32 * r] : 0.f;
+    auto pick = [&](int j) {
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r == (j >> 5)) v = x[r];
+        return __shfl_sync(0xffffffffu, v, j & 31);
+    };
+    for (int j = 0; j < n; ++j) {                 // L y = b
+        const float t = pick(j) * rp[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = lane + 32 * r;
+            if (i > j && i < n) x[r] = fmaf(-Sp[packed_index(i, j)], t, x[r]);
+        }
+    }
+    for (int j = n - 1; j >= 0; --j) {            // U^T x = y
+        const float xj = pick(j) * rp[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = lane + 32 * r;
+            if (i == j) x[r] = xj;
+            else if (i < j) x[r] = fmaf(-Sp[packed_index(j, i)], xj, x[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (lane + 32 * r < n) b[lane + 32 * r] = x[r];
+}
+
+constexpr int kMaxRefineLarge = 10;
+
+__host__ __device__ inline size_t solve_large_smem_bytes(int nf) {
+    const size_t n = 6 * (size_t)nf, np = n * (n + 1) / 2;
+    const size_t f32 = np * 4 + n * 4, f64 = np * 8;
+    return (f32 > f64 ? f32 : f64) + 2 * n * 8 + 64;
+}
+
+__global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *__restrict__ probs, int t,
+                                                                    double *S_out, double *v_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Prob &pr = probs[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (t >= pr.iters) return;
+    const int N = pr.N, t0 = pr.t0, nf = pr.nf, n = 6 * nf, np = n * (n + 1) / 2;
+    const float *pose_cur = pr.pose_it + (size_t)t * N * 7;
+    float *pose_next = pr.pose_it + (size_t)(t + 1) * N * 7;
+    double *dxi = pr.dxi + (size_t)t * nf * 6;
+    __shared__ int s_flag, s_use64;
+    __shared__ float s_rpf[6 * kMaxFree];
+    __shared__ double s_rp[6 * kMaxFree];
+    __shared__ double s_red[kSolveThreads / 32][2];
+    __shared__ double s_dsc[6 * kMaxFree];              // equilibration diag(S)^-1/2
+    if (tid == 0) s_flag = *pr.status;
+    __syncthreads();
+    if (s_flag != 0 || nf == 0) {
+        if (S_out == nullptr) {
+            for (int q = tid; q < N * 7; q += kSolveThreads) pose_next[q] = pose_cur[q];
+            for (int q = tid; q < nf * 6; q += kSolveThreads) dxi[q] = 0.0;
+        }
+        return;
+    }
+    double *v = reinterpret_cast<double *>(smem);
+    double *x = v + n;
+    float *Sp = reinterpret_cast<float *>(x + n);      // FP32 packed copy
+    float *bf = Sp + np;
+    double *Sd = reinterpret_cast<double *>(x + n);    // FP64 packed (fallback), over the FP32 copy
+    double *Sg = pr.sglob;
+
+    // FP64 sum of the partials in a fixed order: S (lower triangle) and v'
+    const int Lp = pr.L, nparts = pr.n_parts, nbs = 2 * n_block_pairs(nf);
+    constexpr int kQ = 8;                                  // entries per thread with loads in flight together
+    for (int q0 = tid; q0 < Lp; q0 += kQ * kSolveThreads) {
+        double accs[kQ];
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) accs[u] = 0.0;
+        for (int part = 0; part < nparts; ++part) {       // parts summed in order
+            const double *src = pr.partial + (size_t)part * Lp;
+            double xv[kQ];
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+                const int q = q0 + u * kSolveThreads;
+                xv[u] = q < Lp ? src[q] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) accs[u] += xv[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+            const int q = q0 + u * kSolveThreads;
+            if (q >= Lp) break;
+            if (q < 18 * nbs) {
+                const int st = q / 18, e = q - 18 * st;
+                int a, b;
+                decode_pair(st >> 1, nf, a, b);
+                const int row = 6 * a + 3 * (st & 1) + e / 6, col = 6 * b + e % 6;
+                if (a == b && col > row) continue;         // the diagonal block's mirror half
+                const int idx = col <= row ? packed_index(row, col) : packed_index(col, row);
+                Sg[idx] = accs[u];
+            } else {
+                v[q - 18 * nbs] = accs[u];
+            }
+        }
+    }
+    __syncthreads();
+    if (S_out != nullptr) {
+        for (int q = tid; q < n * n; q += kSolveThreads) {
+            const int i = q / n, k = q - i * n;
+            S_out[q] = Sg[k <= i ? packed_index(i, k) : packed_index(k, i)];
+        }
+        for (int q = tid; q < n; q += kSolveThreads) v_out[q] = v[q];
+        return;
+    }
+    for (int i = tid; i < n; i += kSolveThreads) {
+        const double sii = Sg[packed_index(i, i)];
+        s_dsc[i] = sii > 0.0 ? 1.0 / sqrt(sii) : 1.0;
+    }
+    __syncthreads();
+    for (int i = tid >> 5; i < n; i += kSolveThreads / 32) {   // FP32 copy of Dg S Dg, a warp per row
+        const int ri = packed_index(i, 0);
+        const double di = s_dsc[i];
+        for (int k = lane; k <= i; k += 32) Sp[ri + k] = (float)(Sg[ri + k] * di * s_dsc[k]);
+    }
+    __syncthreads();
+
+    const int ty = tid >> 4, tx = tid & 15;
+    if (tid == 0) {
+        s_use64 = 0;
+        const float p0 = Sp[0];
+        s_rpf[0] = p0 > 0.f ? 1.0f / p0 : -1.f;
+    }
+    for (int q = tid; q < n; q += kSolveThreads) {
+        x[q] = 0.0;
+        bf[q] = (float)(s_dsc[q] * v[q]);
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {                          // FP32 factorisation
+        const float ip = s_rpf[j];
+        if (!(ip > 0.f) || !isfinite(ip)) {
+            if (tid == 0) s_use64 = 1;
+            break;
+        }
+        const int jn = j + 1;
+        if (tid == 0 && jn < n) {                           // next pivot first
+            const float c = Sp[packed_index(jn, j)];
+            const float pn = Sp[packed_index(jn, jn)] - (c * ip) * c;
+            Sp[packed_index(jn, jn)] = pn;
+            s_rpf[jn] = pn > 0.f ? 1.0f / pn : -1.f;
+        }
+        for (int i = jn + ty; i < n; i += 16) {
+            const int ri = packed_index(i, 0);
+            const float lij = Sp[ri + j] * ip;
+            for (int k = jn + tx; k <= i; k += 16) {
+                if (k == jn && i == jn) continue;          // the pivot, done above
+                Sp[ri + k] -= lij * Sp[packed_index(k, j)];
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    double prev = 0.0;
+    for (int it = 0; it <= kMaxRefineLarge && !s_use64; ++it) {
+        if (it > 0) {   // residual v - S x in FP64 from the packed workspace copy
+            const int qk = tid & 3;
+            for (int base = 0; base < n; base += kSolveThreads / 4) {
+                const int i = base + (tid >> 2);
+                double acc = 0.0;
+                if (i < n) {
+#pragma unroll 4
+                    for (int k = qk; k < n; k += 4)
+                        acc = fma(Sg[k <= i ? packed_index(i, k) : packed_index(k, i)], x[k], acc);
+                }
+                acc += shfl_double(acc, lane ^ 1);
+                acc += shfl_double(acc, lane ^ 2);
+                if (i < n && qk == 0) bf[i] = (float)(s_dsc[i] * (v[i] - acc));
+            }
+            __syncthreads();
+        }
+        if (tid < 32) {
+            if (n <= 96) solve_packed_f32<3>(Sp, s_rpf, bf, n, lane);
+            else solve_packed_f32<6>(Sp, s_rpf, bf, n, lane);
+        }
+        __syncthreads();
+        double dmax = 0.0, xmax = 0.0;
+        for (int q = tid; q < n; q += kSolveThreads) {
+            const double d = s_dsc[q] * (double)bf[q];
+            const double xn = x[q] + d;
+            x[q] = xn;
+            dmax = fmax(dmax, fabs(d));
+            xmax = fmax(xmax, fabs(xn));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dmax = fmax(dmax, shfl_double(dmax, lane ^ o));
+            xmax = fmax(xmax, shfl_double(xmax, lane ^ o));
+        }
+        if (lane == 0) { s_red[tid >> 5][0] = dmax; s_red[tid >> 5][1] = xmax; }
+        __syncthreads();
+        dmax = 0.0; xmax = 0.0;
+#pragma unroll
+        for (int w = 0; w < kSolveThreads / 32; ++w) {
+            dmax = fmax(dmax, s_red[w][0]);
+            xmax = fmax(xmax, s_red[w][1]);
+        }
+        const bool done = it > 0 && dmax <= kRefineTol * xmax;
+        const bool fail = !(dmax <= 1e300) || (!done && (it == kMaxRefineLarge || (it > 1 && !(dmax <= 0.5 * prev))));
+        if (fail && tid == 0) s_use64 = 1;
+        __syncthreads();
+        if (done || fail) break;
+        prev = dmax;
+    }
+    __syncthreads();
+    if (!s_use64) {
+        for (int q = tid; q < n; q += kSolveThreads) v[q] = x[q];
+    } else {
+        // FP64 elimination with the right-hand side eliminated alongside
+        for (int q = tid; q < np; q += kSolveThreads) Sd[q] = Sg[q];
+        if (tid == 0) {
+            const double p0 = Sg[0];
+            s_rp[0] = p0 > 0.0 ? 1.0 / p0 : -1.0;
+        }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const double ip = s_rp[j];
+            if (!(ip > 0.0)) {
+                if (tid == 0) s_flag = DPVO_BA_STATUS_NOT_SPD;
+                break;
+            }
+            const int jn = j + 1;
+            if (tid == 0 && jn < n) {
+                const double c = Sd[packed_index(jn, j)];
+                const double pn = Sd[packed_index(jn, jn)] - (c * ip) * c;
+                Sd[packed_index(jn, jn)] = pn;
+                s_rp[jn] = pn > 0.0 ? 1.0 / pn : -1.0;
+            }
+            for (int i = jn + ty; i < n; i += 16) {
+                const int ri = packed_index(i, 0);
+                const double lij = Sd[ri + j] * ip;
+                for (int k = jn + tx; k <= i; k += 16) {
+                    if (k == jn && i == jn) continue;
+                    Sd[ri + k] -= lij * Sd[packed_index(k, j)];
+                }
+            }
+            if (tid < n - jn) {
+                const int i = jn + tid;
+                v[i] -= (Sd[packed_index(i, j)] * ip) * v[j];
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!s_flag && tid < 32) {                          // U^T x = v'
+            for (int j = n - 1; j >= 0; --j) {
+                const double xj = v[j] * s_rp[j];
+                for (int i = lane; i < j; i += 32) v[i] -= Sd[packed_index(j, i)] * xj;
+                __syncwarp();
+                if (lane == 0) v[j] = xj;
+                __syncwarp();
+            }
+        }
+    }
     __syncthreads();
     if (!s_flag && tid < 32) {
         bool bad = false;

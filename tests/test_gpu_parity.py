@@ -218,4 +218,4 @@ def test_invalid_arguments_return_einval(solver):
         solver.solve([dataclasses.replace(p, t0=-1)])
     assert e.value.code == ba.EINVAL
     with pytest.raises(ba.BAError):
-        solver.solve([dataclasses.replace(p, t0=0, poses=torch.zeros(17, 7, device="cuda"))])   # 17 free > 15
+        solver.solve([dataclasses.replace(p, t0=0, poses=torch.zeros(33, 7, device="cuda"))])   # 33 free > 32
