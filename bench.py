@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--parity-samples", type=int, default=2)
     ap.add_argument("--serving", type=int, default=1, help="run the serving measurement (Poisson sessions)")
     ap.add_argument("--tf32", type=int, default=1, help="also time the opt-in tensor-core Schur mode")
+    ap.add_argument("--stress", type=int, default=64,
+                    help="large-window sessions timed (64 frames, 256 patches each, radius 24, 32 free poses, 4 "
+                         "iterations); 0 skips")
     return ap.parse_args()
 
 
@@ -160,6 +163,54 @@ def algorithmic_work(scene):
     flops = 200.0 * E + float(np.sum(36 * f * (f + 1) + 12 * f))
     bytes_ = 24.0 * scene.n_edges + 20.0 * scene.n_patches
     return flops, bytes_
+
+
+def stress_bench(n_sessions, steps, stream, hbm_peak):
+    """Large-window workload: n_sessions problems of 64 frames x 256 patches
+    (16,384), radius 24 (649,216 edges), the last 32 poses free (192 x 192), 4
+    Gauss-Newton iterations, 20 % outliers; 8 distinct seeded scenes tiled.
+    Per-kernel times from the library's launch events."""
+    import torch
+    from paper_2208_04726_b300 import ba
+    from paper_2208_04726_b300 import scenes as S
+    distinct = [S.make_scene(S.STRESS_N64, 500 + s) for s in range(min(8, n_sessions))]
+    batch = ba.PackedBatch([distinct[b % len(distinct)] for b in range(n_sessions)], "cuda")
+    solver = ba.Solver()
+    for _ in range(2):
+        solver.solve_arrays(batch.dims, batch.probs, n_sessions, stream)
+    torch.cuda.synchronize()
+    statuses = batch.status.cpu().numpy()
+    solver.set_timing(True)
+    solver.timing()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        solver.solve_arrays(batch.dims, batch.probs, n_sessions, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = solver.timing(cap=64 * steps + 64)
+    solver.set_timing(False)
+    solver.close()
+    kinds = {}
+    for k, v in launches:
+        kinds.setdefault(int(k), []).append(v)
+    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly"}
+    kern = {names[k] + "_ms": float(np.mean(v)) for k, v in kinds.items() if k in names}
+    kern.update({names[k] + "_launches_per_step": len(v) // steps for k, v in kinds.items() if k in names})
+    sc = distinct[0]
+    bytes_lin = n_sessions * (24.0 * sc.n_edges + 20.0 * sc.n_patches)
+    lin = np.array(kinds.get(1, [0.0] * 5 * steps)).reshape(steps, -1)
+    t_lin = float(lin[:, :-1].mean())          # the launches that linearise (the last only back-substitutes)
+    kern["linearize_linearising_ms"] = t_lin
+    gbs = bytes_lin / (t_lin / 1e3) / 1e9 if t_lin > 0 else None
+    return {"workload": "64 frames x 256 patches (16,384), radius 24 (649,216 edges), last 32 poses free "
+                        "(192 x 192 reduced system), 4 GN iterations, 20 % outliers, weights U[0,1]",
+            "sessions": n_sessions, "solves_per_s": n_sessions / (ms / 1e3), "ms_per_step": ms,
+            "statuses_nonzero": int((statuses != 0).sum()), "kernels": kern,
+            "linearize_hbm": {"algorithmic_bytes_per_launch": bytes_lin, "achieved_gbs": gbs,
+                              "peak_gbs": hbm_peak, "frac": (gbs / hbm_peak) if gbs else None},
+            "parity": "tests/test_gpu_large.py: one instance against the dense FP64 oracle"}
 
 
 def traffic_from_profiles(kernel_source_sha):
@@ -500,6 +551,7 @@ def main():
         tsolver.close()
 
     serving = serving_bench() if (rank == 0 and args.serving) else None
+    stress = stress_bench(args.stress, 5, stream, load_peaks()[0]) if (rank == 0 and args.stress > 0) else None
 
     if rank == 0:
         line = {
@@ -523,6 +575,7 @@ def main():
                     "steps": args.e2e_steps, "api": "dpvo_ba_solve_host (pinned host buffers)"},
             "serving": serving,
             "tf32_schur": tf32,
+            "stress": stress,
             "gpu_launches": world * n_launch_per_solve * args.steps,
             "clocks": clocks.summary(),
         }
