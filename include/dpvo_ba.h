@@ -164,7 +164,9 @@ typedef struct {
  * per-edge residual and Jacobian terms including the Jacobian's own
  * derivative.  Inactive edges and self edges get zero gradient; a problem
  * whose status is not OK gets zero gradients.  Asynchronous on stream.
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * Errors: EINVAL (as dpvo_ba_solve, a NULL gradient buffer, or more than 15
+ * free poses: the adjoint keeps the fused Schur path's FP64 factor), ENOMEM,
+ * ECUDA. */
 int dpvo_ba_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
                      const dpvo_ba_grads *grads, int n_problems, void *stream);
 
@@ -263,12 +265,14 @@ int dpvo_ba_timing(dpvo_ba_handle *h, float *ms_out, int *kind_out, int cap);
  *     overlaps on the GPU -- on different streams, or from several host
  *     threads -- race on it and corrupt each other: serialise them.
  *   - Returns DPVO_BA_EINVAL, launching nothing, when the problem's workspace
- *     exceeds the array.  The workspace grows with the patch count (one
- *     64-patch work item per CTA, up to two CTAs per SM, each with its own
- *     partial reduced system) and with the square of the free-pose count: an
- *     8-frame problem of 512 patches needs 0.25 MiB, a 22-frame window of 2112
- *     patches with 10 free poses 1.07 MiB, a 32-frame window of 3072 patches
- *     with 10 free poses 1.55 MiB.
+ *     exceeds the array, or when it has more than 15 free poses (this entry
+ *     point has no separate Schur-assembly pass).  The workspace grows with
+ *     the patch count (one chunk of up to 64 patches per work item, up to two
+ *     CTAs per SM, each with its own partial reduced system; one stored Schur
+ *     row per patch) and with the square of the free-pose count: an 8-frame
+ *     problem of 512 patches needs about 0.4 MiB, a 22-frame window of 2112
+ *     patches with 10 free poses about 1.9 MiB, a 32-frame window of 3072
+ *     patches with 10 free poses about 3.4 MiB.
  * Errors: EINVAL, ECUDA. */
 int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_dims *dims, const dpvo_ba_problem *prob,
                           void *stream);
