@@ -25,16 +25,12 @@ namespace dpvo {
 
 constexpr int kAsmMaxThreads = 576;            // 2 slices of 544 strips at 32 free poses
 
-// One thread: bulk-copy `bytes` (a multiple of 16, both addresses 16-byte
-// aligned) from global to shared memory; the mbarrier's current phase
-// completes when they have landed.
+// One thread: expect `bytes` on the mbarrier's current phase and bulk-copy
+// them (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory; the phase completes when they have landed.
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint32_t mbar) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(mbar)
-        : "memory");
+    bulk_copy_g2s(dst, src, bytes, mbar);
 }
 
 // Strips: 2 per block pair (a <= b), then one per free pose.

@@ -72,6 +72,7 @@ struct Prob {
     int n_items;             // linearise work items (CTAs) of this problem
     int n_asm;               // Schur-assembly work items (0: accumulated inside the linearise kernel)
     int n_parts;             // partials summed by the solve
+    int bulk_edges;          // jj, target, weight 16-byte aligned: chunks staged by bulk copies
     int ks;                  // patch-parity split of the Schur accumulation
     int L;                   // doubles per partial
     int chunk_cap;           // patches per chunk at most

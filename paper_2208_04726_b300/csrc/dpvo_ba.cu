@@ -21,6 +21,11 @@ constexpr size_t kLinSmemBudget = 112 * 1024;   // two CTAs per SM (228 KB, 1 KB
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The edge arrays can be staged by bulk copies (16-byte aligned starts).
+bool aligned16(const void *a, const void *b, const void *c) {
+    return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 15) == 0;
+}
+
 struct Layout {
     std::vector<Prob> probs;       // workspace pointers hold offsets until rebased
     std::vector<Item> items;       // linearise work items, then assembly work items
@@ -288,6 +293,7 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         const dpvo_ba_problem &q = probs[b];
         p.poses = q.poses; p.patches = q.patches; p.anchor = q.anchor; p.kk = q.kk; p.jj = q.jj;
         p.target = q.target; p.weight = q.weight; p.status_user = q.status;
+        p.bulk_edges = aligned16(q.jj, q.target, q.weight);
         p.seg = rebase(p.seg, h->ws);
         p.chunks = rebase(p.chunks, h->ws);
         p.n_chunks = rebase(p.n_chunks, h->ws);
@@ -365,6 +371,7 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
         const dpvo_ba_problem &q = probs[b];
         p.poses = q.poses; p.patches = q.patches; p.anchor = q.anchor; p.kk = q.kk; p.jj = q.jj;
         p.target = q.target; p.weight = q.weight; p.status_user = q.status;
+        p.bulk_edges = aligned16(q.jj, q.target, q.weight);
         p.dL_dposes = grads[b].dL_dposes;
         p.dL_ddepth = grads[b].dL_ddepth;
         p.dL_dtarget = grads[b].dL_dtarget;
@@ -1061,6 +1068,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     std::memset(&p, 0, sizeof(Prob));
     p.poses = prob->poses; p.patches = prob->patches; p.anchor = prob->anchor; p.kk = prob->kk;
     p.jj = prob->jj; p.target = prob->target; p.weight = prob->weight; p.status_user = prob->status;
+    p.bulk_edges = aligned16(prob->jj, prob->target, prob->weight);
     p.N = d.n_frames; p.P = d.n_patches; p.E = d.n_edges; p.t0 = d.t0; p.iters = d.n_iters; p.nf = nf;
     p.fx = d.fx; p.fy = d.fy; p.cx = d.cx; p.cy = d.cy;
     p.damping = damping; p.z_min = z_min;

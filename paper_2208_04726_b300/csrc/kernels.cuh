@@ -283,9 +283,10 @@ __host__ __device__ inline LinSmem lin_smem_layout(int W, int G, int nf_max, int
     const size_t sc4 = slots * 16 > rows ? slots * 16 : rows;
     size_t o = 0;
     s.off_pose = o; o = align16(o + (size_t)n_max * 7 * 4);
-    s.off_rjj = o;  o = align16(o + (size_t)s.EC * 4);
-    s.off_rtg = o;  o = align16(o + (size_t)s.EC * 8);
-    s.off_rwt = o;  o = align16(o + (size_t)s.EC * 8);
+    // edge staging, with room for the alignment slack of bulk copies
+    s.off_rjj = o;  o = align16(o + (size_t)(s.EC + 8) * 4);
+    s.off_rtg = o;  o = align16(o + (size_t)(s.EC + 2) * 8);
+    s.off_rwt = o;  o = align16(o + (size_t)(s.EC + 2) * 8);
     s.off_rpx = o;  o = align16(o + (size_t)G * 4);
     s.off_rpy = o;  o = align16(o + (size_t)G * 4);
     s.off_rdep = o; o = align16(o + (size_t)G * 4);
@@ -377,20 +378,58 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Start copying one chunk's inputs -- frames, targets and weights of its
 // edges, its patches' centres and inverse depths, its patch -> edge offsets --
-// into the staging buffers.
+// into the staging buffers.  With an mbarrier (bar != 0) and 16-byte aligned
+// edge arrays, the three edge ranges go by bulk asynchronous copies from one
+// thread, each widened to 16-byte boundaries (but not past the array's last
+// whole 16 bytes; the elements beyond go by per-thread copies) and completing
+// on bar; the staged range then starts staged_offset() elements before e0.
+// Otherwise every element goes by a per-thread copy at offset 0 (and bar, if
+// given, gets a plain arrival so that it completes one phase per chunk).
+__device__ __forceinline__ void staged_offsets(const Prob &pr, const Chunk &ch, bool bulk_path, int &o_jj,
+                                               int &o_tw) {
+    const bool bulk = bulk_path && pr.bulk_edges && ch.e1 > ch.e0;
+    o_jj = bulk ? (ch.e0 & 3) : 0;
+    o_tw = bulk ? (ch.e0 & 1) : 0;
+}
+
 __device__ __forceinline__ void prefetch_chunk(const Prob &pr, const Chunk &ch, const float *depth_src, int *rjj,
                                                float2 *rtg, float2 *rwt, float *rpx, float *rpy, float *rdep,
-                                               int *rseg, const Chunk *desc_src, Chunk *desc_dst) {
+                                               int *rseg, const Chunk *desc_src, Chunk *desc_dst,
+                                               uint32_t bar = 0) {
     if (desc_src && threadIdx.x < 8)   // the descriptor of the chunk after this one
         cp_async4(reinterpret_cast<int *>(desc_dst) + threadIdx.x, reinterpret_cast<const int *>(desc_src) + threadIdx.x);
     const float2 *tg = reinterpret_cast<const float2 *>(pr.target);
     const float2 *wt = reinterpret_cast<const float2 *>(pr.weight);
-    const int ne = ch.e1 - ch.e0;
-    for (int q = threadIdx.x; q < ne; q += kThreads) {
-        const int e = ch.e0 + q;
-        cp_async4(rjj + q, pr.jj + e);
-        cp_async8(rtg + q, tg + e);
-        cp_async8(rwt + q, wt + e);
+    const int e0 = ch.e0, e1 = ch.e1;
+    if (bar != 0 && pr.bulk_edges && e1 > e0) {
+        const int a0 = e0 & ~3, a1 = min((e1 + 3) & ~3, pr.E & ~3);   // jj: 4 per 16 bytes
+        const int b0 = e0 & ~1, b1 = min((e1 + 1) & ~1, pr.E & ~1);   // target, weight: 2 per 16 bytes
+        if (threadIdx.x == 0) {
+            const uint32_t bj = a1 > a0 ? (uint32_t)(a1 - a0) * 4u : 0u;
+            const uint32_t bt = b1 > b0 ? (uint32_t)(b1 - b0) * 8u : 0u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bj + 2u * bt)
+                         : "memory");
+            if (bj) bulk_copy_g2s(rjj, pr.jj + a0, bj, bar);
+            if (bt) {
+                bulk_copy_g2s(rtg, tg + b0, bt, bar);
+                bulk_copy_g2s(rwt, wt + b0, bt, bar);
+            }
+        }
+        for (int e = max(e0, a1 > a0 ? a1 : e0) + (int)threadIdx.x; e < e1; e += kThreads)
+            cp_async4(rjj + (e - a0), pr.jj + e);
+        for (int e = max(e0, b1 > b0 ? b1 : e0) + (int)threadIdx.x; e < e1; e += kThreads) {
+            cp_async8(rtg + (e - b0), tg + e);
+            cp_async8(rwt + (e - b0), wt + e);
+        }
+    } else {
+        if (bar != 0 && threadIdx.x == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+        for (int q = threadIdx.x; q < e1 - e0; q += kThreads) {
+            const int e = e0 + q;
+            cp_async4(rjj + q, pr.jj + e);
+            cp_async8(rtg + q, tg + e);
+            cp_async8(rwt + q, wt + e);
+        }
     }
     for (int q = threadIdx.x; q < ch.count; q += kThreads) {
         const int k = ch.k0 + q;
@@ -434,6 +473,26 @@ __device__ __forceinline__ void window_poses(const float *poses, int anchor, int
         relative_pose(poses + 7 * anchor, poses + 7 * (jlo + jl), R, R + 9);
         if (adj) adjoint6(R, R + 9, adj + jl * 36);
     }
+}
+
+// Sum over aligned groups of lp consecutive lanes (lp a power of two <= 32,
+// the same in the whole warp; fixed order), broadcast to the group.
+__device__ __forceinline__ float lane_group_sum(float v, int lp) {
+    for (int o = 1; o < lp; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Lanes per patch for the per-patch phases of a chunk of cnt patches: 256 /
+// (cnt rounded up to a power of two), at least 4, at most 32; log2 in *sh.
+__device__ __forceinline__ int lanes_per_patch(int cnt, int *sh) {
+    int p2 = 1;
+    while (p2 < cnt) p2 <<= 1;
+    int lp = kThreads / p2;
+    lp = lp < 4 ? 4 : (lp > 32 ? 32 : lp);
+    int l = 0;
+    while ((1 << l) < lp) ++l;
+    *sh = l;
+    return lp;
 }
 
 // Sum of 4 consecutive lanes' values (fixed order), broadcast to all four.
@@ -542,9 +601,9 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
     const LinSmem L = lin_smem_layout(W_cap, G_cap, nf_max, n_max, TC);
     float *spn = reinterpret_cast<float *>(smem + L.off_pose);        // poses of iterate t
-    int *rjj = reinterpret_cast<int *>(smem + L.off_rjj);
-    float2 *rtg = reinterpret_cast<float2 *>(smem + L.off_rtg);
-    float2 *rwt = reinterpret_cast<float2 *>(smem + L.off_rwt);
+    int *rjj_s = reinterpret_cast<int *>(smem + L.off_rjj);              // edge staging bases
+    float2 *rtg_s = reinterpret_cast<float2 *>(smem + L.off_rtg);
+    float2 *rwt_s = reinterpret_cast<float2 *>(smem + L.off_rwt);
     float *rpx = reinterpret_cast<float *>(smem + L.off_rpx);
     float *rpy = reinterpret_cast<float *>(smem + L.off_rpy);
     float *rdep = reinterpret_cast<float *>(smem + L.off_rdep);
@@ -694,11 +753,18 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     }
 
     __shared__ __align__(16) Chunk s_ch[2];
+    __shared__ __align__(8) uint64_t s_ldbar;    // edge staging: one phase per chunk
+    __shared__ int s_ld_bad;
+    const uint32_t ldbar = smem_u32(&s_ldbar);
     if (c_begin < c_end) {
-        if (tid == 0) s_ch[0] = pr.chunks[c_begin];
+        if (tid == 0) {
+            s_ch[0] = pr.chunks[c_begin];
+            mbar_init(ldbar, 1);
+            s_ld_bad = 0;
+        }
         __syncthreads();
-        prefetch_chunk(pr, s_ch[0], depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
-                       c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1]);
+        prefetch_chunk(pr, s_ch[0], depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg,
+                       c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1], ldbar);
         if (do_bs) {
             if constexpr (TC) prefetch_block(pr, c_begin, s_ch[0], kmax, srow);
             else prefetch_rows(pr, s_ch[0], RS, RSS, srow);
@@ -711,7 +777,11 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         const Chunk ch = s_ch[cur];
         const bool have_next = c + 1 < c_end;
         cp_async_wait_all();
+        if (!mbar_wait(ldbar, (uint32_t)(c - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
         __syncthreads();                                   // this chunk's inputs are in shared memory
+        if (s_ld_bad) break;                               // a bulk copy never landed: reported below
+        int o_jj, o_tw;                                    // alignment slack of the staged edge ranges
+        staged_offsets(pr, ch, true, o_jj, o_tw);
         Chunk nx = ch;
         if (have_next) nx = s_ch[cur ^ 1];
         const bool group_next = have_next && nx.anchor == ch.anchor && nx.jlo == ch.jlo && nx.jhi == ch.jhi;
@@ -725,23 +795,28 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         const bool edge_thread = my_jl < W;
 
         // -- (0) slot -> edge table, patch data, window poses, cleared E columns.
-        // Thread (p = tid mod 64, jl = tid / 64 + 4 i) for the slots.
+        // Thread (p = tid mod PS, jl = tid / PS + (256 / PS) i) for the slots,
+        // PS = cnt rounded up to a power of two (at least 8); LP lanes per
+        // patch for the per-patch phases.
+        int lp_sh = 2;                                     // 4 lanes per patch in the fused variants
+        const int LP = EXT ? lanes_per_patch(cnt, &lp_sh) : 4;
+        const int ps_sh = 8 - lp_sh, PSm = (1 << ps_sh) - 1;
         if constexpr (TC) {
             // the previous chunk's MMAs read the operand: wait before rewriting it
             if (n_commit > 0 && !mbar_wait(smem_u32(&s_mbar), (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_tc_bad, 1);
         }
         {
-            const int p = tid & 63;
+            const int p = tid & PSm;
             if (p < cnt) {
                 const int a = rseg[p] - e0, b = rseg[p + 1] - e0;
                 int jf = 0, jz = -1;
                 bool contig = true;
                 if (b > a) {
-                    jf = rjj[a];
-                    jz = rjj[b - 1];
+                    jf = rjj_s[o_jj + a];
+                    jz = rjj_s[o_jj + b - 1];
                     contig = jz - jf + 1 == b - a;         // frames of this patch are contiguous
                 }
-                for (int jl = tid >> 6; jl < W; jl += kThreads / 64) {
+                for (int jl = tid >> ps_sh; jl < W; jl += kThreads >> ps_sh) {
                     const int j = jlo + jl;
                     int idx = -1;
                     if (j >= jf && j <= jz) {
@@ -751,14 +826,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                             int lo = a, hi = b - 1;
                             while (lo < hi) {
                                 const int mid = (lo + hi) >> 1;
-                                if (rjj[mid] < j) lo = mid + 1; else hi = mid;
+                                if (rjj_s[o_jj + mid] < j) lo = mid + 1; else hi = mid;
                             }
-                            if (rjj[lo] == j) idx = lo;
+                            if (rjj_s[o_jj + lo] == j) idx = lo;
                         }
                     }
-                    sidx[jl * Gs + p] = (short)idx;
+                    sidx[jl * Gs + p] = (short)(idx >= 0 ? idx + o_tw : -1);   // position in the staged target/weight
                 }
-                for (int f = tid >> 6; f < nf; f += kThreads / 64) {   // E columns of free frames outside the window are zero
+                for (int f = tid >> ps_sh; f < nf; f += kThreads >> ps_sh) {   // E columns of free frames outside the window are zero
                     const int fr = t0 + f;
                     if (fr < jlo || fr > ch.jhi) {
                         if constexpr (TC) {
@@ -795,14 +870,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                 }
             } else {
-                const int p = tid >> 2, sub = tid & 3;
+                const int p = tid >> lp_sh, sub = tid & (LP - 1);
                 float s = 0.f;
                 if (do_bs && p < cnt) {
                     const float4 *row = reinterpret_cast<const float4 *>(srow + p * RSS);
                     const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
-                    for (int q = sub; q < RS / 4; q += 4) s = dot4(row[q], dz4[q], s);
+                    for (int q = sub; q < RS / 4; q += LP) s = dot4(row[q], dz4[q], s);
                 }
-                s = quad_sum(s);
+                s = lane_group_sum(s, LP);
                 if (sub == 0 && p < cnt) {
                     float d = rdep[p];
                     if (do_bs) {
@@ -839,7 +914,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 float Ce = 0.f, we = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
                 float4 elo = make_float4(0.f, 0.f, 0.f, 0.f), ehi = elo;
                 if (ei >= 0 && my_j != anc) {
-                    const float2 tv = rtg[ei], wv = rwt[ei];
+                    const float2 tv = rtg_s[ei], wv = rwt_s[ei];
                     const float4 q = pd[p];
                     EdgeLin E;
                     if ((wv.x != 0.f || wv.y != 0.f) &&
@@ -897,14 +972,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         __syncthreads();
         // the staging buffers are free: start the next chunk's copies
         if (have_next)
-            prefetch_chunk(pr, nx, depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg,
-                           c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur]);
-        {   // per-patch sums over the window by four lanes: C_k, w_k, Y; then
+            prefetch_chunk(pr, nx, depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg,
+                           c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur], ldbar);
+        {   // per-patch sums over the window by LP lanes: C_k, w_k, Y; then
             // C_k^-1/2, C_k^-1/2 w_k and the anchor column e_ik = -[d Y; pbar x Y]
-            const int p = tid >> 2, sub = tid & 3;
+            const int p = tid >> lp_sh, sub = tid & (LP - 1);
             float C = sub == 0 ? lam : 0.f, w = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
             if (p < cnt)
-                for (int jl = sub; jl < W; jl += 4) {
+                for (int jl = sub; jl < W; jl += LP) {
                     const float4 v = sc4[jl * Gs + p];
                     C += v.x;
                     w += v.y;
@@ -912,11 +987,11 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     Y1 += v.w;
                     Y2 += sc1[jl * Gs1 + p];
                 }
-            C = quad_sum(C);
-            w = quad_sum(w);
-            Y0 = quad_sum(Y0);
-            Y1 = quad_sum(Y1);
-            Y2 = quad_sum(Y2);
+            C = lane_group_sum(C, LP);
+            w = lane_group_sum(w, LP);
+            Y0 = lane_group_sum(Y0, LP);
+            Y1 = lane_group_sum(Y1, LP);
+            Y2 = lane_group_sum(Y2, LP);
             if constexpr (TC) {
                 if (p < cnt) {
                     if (sub == 0) {
@@ -937,7 +1012,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                 }
             } else {
-                // the same four lanes then scale the patch's row of E by
+                // the same lanes then scale the patch's row of E by
                 // C_k^-1/2 and store it, compacted, for the next back-substitution
                 const float sq = sqrtf(1.0f / C);
                 float *e = Ec + p * ES;
@@ -958,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 if (p < cnt) {
                     float4 *e4 = reinterpret_cast<float4 *>(e);
                     float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)(k0 + p) * RS);
-                    for (int m = sub; m < 2 * nf; m += 4) {
+                    for (int m = sub; m < 2 * nf; m += LP) {
                         float4 v = e4[m];
                         v.x *= sq; v.y *= sq; v.z *= sq;
                         e4[m] = v;
@@ -1219,6 +1294,15 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         cur ^= 1;
     }
     cp_async_wait_all();
+    if (c_begin < c_end && s_ld_bad) {
+        // report, and give the copy that did not land one more bounded wait
+        if (tid == 0) {
+            atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
+            mbar_wait(ldbar, 0u);
+            mbar_wait(ldbar, 1u);
+        }
+        __syncthreads();
+    }
 
     if constexpr (TC) {
         // read the accumulator back (warps 0-3, one TMEM lane = one row each)

@@ -98,6 +98,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// One thread: bulk asynchronous copy of `bytes` (a multiple of 16; both
+// addresses 16-byte aligned) from global to shared memory, counted against the
+// mbarrier's expected transaction bytes.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane (the
 // warp reads lanes 32 (warp % 4) .. +31).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
