@@ -1738,46 +1738,77 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
 // ----------------------------------------------------------------------------
 __host__ __device__ inline int packed_index(int i, int k) { return i * (i + 1) / 2 + k; }
 
-// One warp: solve with the packed FP32 factor, b in place (n <= 32 R).
-template <int R>
-__device__ __forceinline__ void solve_packed_f32(const float *Sp, const float *rp, float *b, int n, int lane) {
-    float x[R];
+constexpr int kPanel = 32;             // panel width of the blocked factorisation and solves
+constexpr int kDiagLd = 36;            // row stride (floats) of a staged diagonal block (16-byte rows)
+
+// FP32 path of solve_large_kernel, in floats from the start of the packed
+// copy: the copy (np) and the right-hand side (n), then the two panel buffers
+// (kPanel rows of panel_ld(n) each, 16-byte aligned).
+__host__ __device__ inline int panel_ld(int n) { return (n + 7) & ~3; }
+__host__ __device__ inline int panel_off(int n) { return (n * (n + 1) / 2 + n + 3) & ~3; }
+
+// All threads: solve S x = b in place in b (shared memory), S = U D^-1 U^T
+// packed in Sp (the eliminated values a_ij, j <= i) with pivot reciprocals
+// rp, by panels of kPanel: each panel's diagonal block by one warp (lane =
+// row, values by shuffle), the rows outside it by one thread each.
+__device__ void solve_blocked_f32(const float *Sp, const float *rp, float *b, int n, int tid) {
+    __shared__ float s_t[kPanel];                          // y_j / p_j of the current panel
+    const int lane = tid & 31;
+    for (int J = 0; J < n; J += kPanel) {                  // forward: y_i = b_i - sum_j<i a_ij y_j / p_j
+        const int nb = min(kPanel, n - J);
+        if (tid < 32) {
+            const int ri = packed_index(J + min(lane, nb - 1), J);
+            float y = lane < nb ? b[J + lane] : 0.f;
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = lane + 32 * r < n ? b[lane + 32 * r] : 0.f;
-    auto pick = [&](int j) {
-        float v = 0.f;
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (r == (j >> 5)) v = x[r];
-        return __shfl_sync(0xffffffffu, v, j & 31);
-    };
-    for (int j = 0; j < n; ++j) {                 // L y = b
-        const float t = pick(j) * rp[j];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = lane + 32 * r;
-            if (i > j && i < n) x[r] = fmaf(-Sp[packed_index(i, j)], t, x[r]);
+            for (int j = 0; j < kPanel; ++j) {
+                if (j < nb) {
+                    const float t = __shfl_sync(0xffffffffu, y, j) * rp[J + j];
+                    const float c = lane > j && lane < nb ? Sp[ri + j] : 0.f;
+                    y = fmaf(-c, t, y);
+                    if (lane == j) s_t[j] = t;
+                }
+            }
+            if (lane < nb) b[J + lane] = y;
         }
-    }
-    for (int j = n - 1; j >= 0; --j) {            // U^T x = y
-        const float xj = pick(j) * rp[j];
+        __syncthreads();
+        for (int i = J + nb + tid; i < n; i += kSolveThreads) {   // nb == kPanel here
+            const int ri = packed_index(i, J);
+            float acc = 0.f;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int i = lane + 32 * r;
-            if (i == j) x[r] = xj;
-            else if (i < j) x[r] = fmaf(-Sp[packed_index(j, i)], xj, x[r]);
+            for (int j = 0; j < kPanel; ++j) acc = fmaf(Sp[ri + j], s_t[j], acc);
+            b[i] -= acc;
         }
+        __syncthreads();
     }
+    for (int J = ((n - 1) / kPanel) * kPanel; J >= 0; J -= kPanel) {   // backward: x_i = (y_i - sum_j>i a_ji x_j) / p_i
+        const int nb = min(kPanel, n - J);
+        if (tid < 32) {
+            float y = lane < nb ? b[J + lane] : 0.f;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-        if (lane + 32 * r < n) b[lane + 32 * r] = x[r];
+            for (int j = kPanel - 1; j >= 0; --j) {
+                if (j < nb) {
+                    const float xj = __shfl_sync(0xffffffffu, y, j) * rp[J + j];
+                    const float c = lane < j ? Sp[packed_index(J + j, J) + lane] : 0.f;
+                    y = lane == j ? xj : fmaf(-c, xj, y);
+                }
+            }
+            if (lane < nb) b[J + lane] = y;
+        }
+        __syncthreads();
+        for (int i = tid; i < J; i += kSolveThreads) {
+            float acc = 0.f;
+            for (int j = 0; j < nb; ++j) acc = fmaf(Sp[packed_index(J + j, i)], b[J + j], acc);
+            b[i] -= acc;
+        }
+        __syncthreads();
+    }
 }
 
 constexpr int kMaxRefineLarge = 10;
 
 __host__ __device__ inline size_t solve_large_smem_bytes(int nf) {
     const size_t n = 6 * (size_t)nf, np = n * (n + 1) / 2;
-    const size_t f32 = np * 4 + n * 4, f64 = np * 8;
+    const size_t f32 = ((size_t)panel_off((int)n) + 2 * kPanel * (size_t)panel_ld((int)n)) * 4, f64 = np * 8;
     return (f32 > f64 ? f32 : f64) + 2 * n * 8 + 64;
 }
 
@@ -1812,38 +1843,85 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
     double *Sd = reinterpret_cast<double *>(x + n);    // FP64 packed (fallback), over the FP32 copy
     double *Sg = pr.sglob;
 
-    // FP64 sum of the partials in a fixed order: S (lower triangle) and v'
+    // Block pair (a, b), a <= b, of each pair index, as a << 8 | b.
+    __shared__ unsigned short s_pair[kMaxFree * (kMaxFree + 1) / 2];
+    __shared__ __align__(16) float s_dR[kPanel * kDiagLd];   // factored diagonal block, by rows
+    for (int a = tid; a < nf; a += kSolveThreads) {
+        const int base = a * nf - a * (a - 1) / 2;
+        for (int b = a; b < nf; ++b) s_pair[base + b - a] = (unsigned short)(a << 8 | b);
+    }
+    // FP64 sums of the partials, parts added in order.  First the diagonal,
+    // for the equilibration Dg = diag(S)^-1/2.
     const int Lp = pr.L, nparts = pr.n_parts, nbs = 2 * n_block_pairs(nf);
-    constexpr int kQ = 8;                                  // entries per thread with loads in flight together
-    for (int q0 = tid; q0 < Lp; q0 += kQ * kSolveThreads) {
-        double accs[kQ];
+    constexpr int kU = 4;                                  // parts with loads in flight together
+    for (int i = tid; i < n; i += kSolveThreads) {
+        const int a = i / 6, r = i - 6 * a, h = r / 3;
+        const int q = 18 * (2 * (a * nf - a * (a - 1) / 2) + h) + 6 * (r - 3 * h) + r;
+        double sii = 0.0;
+        for (int p0 = 0; p0 < nparts; p0 += kU) {
+            double xv[kU];
 #pragma unroll
-        for (int u = 0; u < kQ; ++u) accs[u] = 0.0;
-        for (int part = 0; part < nparts; ++part) {       // parts summed in order
-            const double *src = pr.partial + (size_t)part * Lp;
-            double xv[kQ];
+            for (int u = 0; u < kU; ++u) xv[u] = p0 + u < nparts ? pr.partial[(size_t)(p0 + u) * Lp + q] : 0.0;
 #pragma unroll
-            for (int u = 0; u < kQ; ++u) {
-                const int q = q0 + u * kSolveThreads;
-                xv[u] = q < Lp ? src[q] : 0.0;
+            for (int u = 0; u < kU; ++u)
+                if (p0 + u < nparts) sii += xv[u];
+        }
+        s_dsc[i] = sii > 0.0 ? 1.0 / sqrt(sii) : 1.0;
+    }
+    __syncthreads();
+    // Then every entry, two at a time (a strip's entries (row, col), (row,
+    // col + 1)): to the FP64 workspace copy and, equilibrated and rounded, to
+    // the FP32 copy.
+    {
+        const double2 *P2 = reinterpret_cast<const double2 *>(pr.partial);
+        const int L2 = Lp >> 1, nsp = 9 * nbs;
+        constexpr int kQ = 4;
+        auto put = [&](int i, int k, double val) {
+            const int idx = packed_index(i, k);
+            Sg[idx] = val;
+            Sp[idx] = (float)(val * s_dsc[i] * s_dsc[k]);
+        };
+        for (int q0 = tid; q0 < L2; q0 += kQ * kSolveThreads) {
+            double2 acc[kQ];
+#pragma unroll
+            for (int w = 0; w < kQ; ++w) acc[w] = make_double2(0.0, 0.0);
+            for (int p0 = 0; p0 < nparts; p0 += kU) {
+                double2 xv[kU][kQ];
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+#pragma unroll
+                    for (int w = 0; w < kQ; ++w) {
+                        const int q = q0 + w * kSolveThreads;
+                        xv[u][w] = p0 + u < nparts && q < L2 ? P2[(size_t)(p0 + u) * L2 + q] : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (p0 + u < nparts)
+#pragma unroll
+                        for (int w = 0; w < kQ; ++w) {
+                            acc[w].x += xv[u][w].x;
+                            acc[w].y += xv[u][w].y;
+                        }
             }
 #pragma unroll
-            for (int u = 0; u < kQ; ++u) accs[u] += xv[u];
-        }
-#pragma unroll
-        for (int u = 0; u < kQ; ++u) {
-            const int q = q0 + u * kSolveThreads;
-            if (q >= Lp) break;
-            if (q < 18 * nbs) {
-                const int st = q / 18, e = q - 18 * st;
-                int a, b;
-                decode_pair(st >> 1, nf, a, b);
-                const int row = 6 * a + 3 * (st & 1) + e / 6, col = 6 * b + e % 6;
-                if (a == b && col > row) continue;         // the diagonal block's mirror half
-                const int idx = col <= row ? packed_index(row, col) : packed_index(col, row);
-                Sg[idx] = accs[u];
-            } else {
-                v[q - 18 * nbs] = accs[u];
+            for (int w = 0; w < kQ; ++w) {
+                const int q = q0 + w * kSolveThreads;
+                if (q >= L2) break;
+                if (q < nsp) {
+                    const int st = q / 9, e = 2 * (q - 9 * st);
+                    const int pc = s_pair[st >> 1], a = pc >> 8, b = pc & 255;
+                    const int row = 6 * a + 3 * (st & 1) + e / 6, col = 6 * b + e % 6;
+                    if (a == b) {                          // diagonal block: its lower half only
+                        if (col <= row) put(row, col, acc[w].x);
+                        if (col + 1 <= row) put(row, col + 1, acc[w].y);
+                    } else {                               // a < b: the mirror entries (col, row)
+                        put(col, row, acc[w].x);
+                        put(col + 1, row, acc[w].y);
+                    }
+                } else {
+                    v[2 * (q - nsp)] = acc[w].x;
+                    v[2 * (q - nsp) + 1] = acc[w].y;
+                }
             }
         }
     }
@@ -1856,48 +1934,118 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
         for (int q = tid; q < n; q += kSolveThreads) v_out[q] = v[q];
         return;
     }
-    for (int i = tid; i < n; i += kSolveThreads) {
-        const double sii = Sg[packed_index(i, i)];
-        s_dsc[i] = sii > 0.0 ? 1.0 / sqrt(sii) : 1.0;
-    }
-    __syncthreads();
-    for (int i = tid >> 5; i < n; i += kSolveThreads / 32) {   // FP32 copy of Dg S Dg, a warp per row
-        const int ri = packed_index(i, 0);
-        const double di = s_dsc[i];
-        for (int k = lane; k <= i; k += 32) Sp[ri + k] = (float)(Sg[ri + k] * di * s_dsc[k]);
-    }
-    __syncthreads();
 
+    // FP32 factorisation Dg S Dg = U D^-1 U^T by panels of kPanel columns.
+    // Per panel: (1) one warp factors the diagonal block (lane = row, the
+    // eliminated column values by shuffle); (2) a thread per row below it
+    // eliminates the panel's columns from its row, and records the eliminated
+    // values a_ij and the multipliers a_ij / p_j; (3) the trailing triangle
+    // takes the panel's rank-kPanel update, A_ik -= sum_j (a_ij / p_j) a_kj,
+    // in 4 x 4 register tiles.
+    const int ld = panel_ld(n);
+    float *PuT = Sp + panel_off(n);                        // a_ij at [j * ld + i]
+    float *PwT = PuT + kPanel * ld;                        // a_ij / p_j at [j * ld + i]
     const int ty = tid >> 4, tx = tid & 15;
-    if (tid == 0) {
-        s_use64 = 0;
-        const float p0 = Sp[0];
-        s_rpf[0] = p0 > 0.f ? 1.0f / p0 : -1.f;
-    }
+    if (tid == 0) s_use64 = 0;
     for (int q = tid; q < n; q += kSolveThreads) {
         x[q] = 0.0;
         bf[q] = (float)(s_dsc[q] * v[q]);
     }
+    for (int q = tid; q < kPanel * (ld - n); q += kSolveThreads) {   // tile columns past n read zeros
+        const int j = q / (ld - n), c = n + q - j * (ld - n);
+        PuT[j * ld + c] = 0.f;
+        PwT[j * ld + c] = 0.f;
+    }
     __syncthreads();
-    for (int j = 0; j < n; ++j) {                          // FP32 factorisation
-        const float ip = s_rpf[j];
-        if (!(ip > 0.f) || !isfinite(ip)) {
-            if (tid == 0) s_use64 = 1;
-            break;
+    for (int J = 0; J < n; J += kPanel) {
+        const int nb = min(kPanel, n - J), Rb = J + nb, m = n - Rb;
+        if (tid < 32) {                                    // (1)
+            const int ri = packed_index(J + lane, J);
+            float xr[kPanel];
+#pragma unroll
+            for (int c = 0; c < kPanel; ++c) xr[c] = lane < nb && c <= lane ? Sp[ri + c] : 0.f;
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < kPanel; ++j) {
+                if (j < nb) {
+                    const float pj = __shfl_sync(0xffffffffu, xr[j], j);
+                    const float ip = pj > 0.f ? 1.0f / pj : -1.f;
+                    bad |= !(ip > 0.f) || !isfinite(ip);
+                    if (lane == 0) s_rpf[J + j] = ip;
+                    const float l = xr[j] * ip;
+#pragma unroll
+                    for (int c = j + 1; c < kPanel; ++c) {
+                        const float acj = __shfl_sync(0xffffffffu, xr[j], c);
+                        if (lane > j && c <= lane) xr[c] = fmaf(-l, acj, xr[c]);
+                    }
+                }
+            }
+            if (lane < nb) {
+#pragma unroll
+                for (int c = 0; c < kPanel; ++c)
+                    if (c <= lane) {
+                        Sp[ri + c] = xr[c];
+                        s_dR[lane * kDiagLd + c] = xr[c];
+                    }
+            }
+            if (bad && lane == 0) s_use64 = 1;
         }
-        const int jn = j + 1;
-        if (tid == 0 && jn < n) {                           // next pivot first
-            const float c = Sp[packed_index(jn, j)];
-            const float pn = Sp[packed_index(jn, jn)] - (c * ip) * c;
-            Sp[packed_index(jn, jn)] = pn;
-            s_rpf[jn] = pn > 0.f ? 1.0f / pn : -1.f;
+        __syncthreads();
+        if (s_use64) break;
+        if (m == 0) break;                                 // the last panel
+        for (int i = Rb + tid; i < n; i += kSolveThreads) {   // (2); nb == kPanel here
+            const int ri = packed_index(i, J);
+            float l[kPanel];
+#pragma unroll
+            for (int c = 0; c < kPanel; ++c) {             // a_ic = A_ic - sum_j<c l_j a_cj, l_c = a_ic / p_c
+                float a0 = Sp[ri + c], a1 = 0.f;
+#pragma unroll
+                for (int g = 0; g < (c + 3) / 4; ++g) {
+                    const float4 d = *reinterpret_cast<const float4 *>(s_dR + c * kDiagLd + 4 * g);
+                    if (4 * g + 0 < c) a0 = fmaf(-l[4 * g + 0], d.x, a0);
+                    if (4 * g + 1 < c) a1 = fmaf(-l[4 * g + 1], d.y, a1);
+                    if (4 * g + 2 < c) a0 = fmaf(-l[4 * g + 2], d.z, a0);
+                    if (4 * g + 3 < c) a1 = fmaf(-l[4 * g + 3], d.w, a1);
+                }
+                const float a = a0 + a1;
+                l[c] = a * s_rpf[J + c];
+                Sp[ri + c] = a;
+                PuT[c * ld + i] = a;
+                PwT[c * ld + i] = l[c];
+                asm volatile("" ::: "memory");             // keeps the s_dR loads per column (no spills)
+            }
         }
-        for (int i = jn + ty; i < n; i += 16) {
-            const int ri = packed_index(i, 0);
-            const float lij = Sp[ri + j] * ip;
-            for (int k = jn + tx; k <= i; k += 16) {
-                if (k == jn && i == jn) continue;          // the pivot, done above
-                Sp[ri + k] -= lij * Sp[packed_index(k, j)];
+        __syncthreads();
+        const int mt = (m + 3) >> 2, ntile = mt * (mt + 1) / 2;
+        for (int q = tid; q < ntile; q += kSolveThreads) {  // (3)
+            int ti = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+            while (ti * (ti + 1) / 2 > q) --ti;
+            while ((ti + 1) * (ti + 2) / 2 <= q) ++ti;
+            const int tk = q - ti * (ti + 1) / 2;
+            const int i0 = Rb + 4 * ti, k0 = Rb + 4 * tk;
+            float acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 8
+            for (int j = 0; j < kPanel; ++j) {
+                const float4 w = *reinterpret_cast<const float4 *>(PwT + j * ld + i0);
+                const float4 u = *reinterpret_cast<const float4 *>(PuT + j * ld + k0);
+                const float wv[4] = {w.x, w.y, w.z, w.w}, uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wv[a], uv[b], acc[a][b]);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int i = i0 + a;
+                if (i >= n) break;
+                const int ri = packed_index(i, 0);
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (k0 + b <= i) Sp[ri + k0 + b] -= acc[a][b];
             }
         }
         __syncthreads();
@@ -1921,11 +2069,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
             }
             __syncthreads();
         }
-        if (tid < 32) {
-            if (n <= 96) solve_packed_f32<3>(Sp, s_rpf, bf, n, lane);
-            else solve_packed_f32<6>(Sp, s_rpf, bf, n, lane);
-        }
-        __syncthreads();
+        solve_blocked_f32(Sp, s_rpf, bf, n, tid);
         double dmax = 0.0, xmax = 0.0;
         for (int q = tid; q < n; q += kSolveThreads) {
             const double d = s_dsc[q] * (double)bf[q];
