@@ -5,14 +5,28 @@
 // read from the rows C_k^-1/2 (e_k, w_k, 1) the linearise kernel stores for the
 // back-substitution, into FP64 partials in the strip layout of (S, v').
 //
-// One CTA per (problem, work item, strip slice): it takes a range of chunks
-// and one thread per strip (a 3 x 6 half of a pose-pair block, or a pose's
-// right-hand side).  A chunk's rows arrive in shared memory by one bulk
-// asynchronous copy that completes on an mbarrier, double-buffered so the
-// next chunk streams in while this one is summed.  A strip whose frames lie
-// outside a chunk's frame window has zero rows there and skips the chunk.
-// Sums: FP32 over blocks of kFlushEvery patches (across chunk boundaries),
-// compensated across blocks, written once as FP64.
+// One CTA per (problem, work item, slice): it takes a range of chunks, and
+// each compute thread one 6 x 6 pose-pair block (a, b), a <= b, in
+// registers; a warp holds a 4 x 8 block of frame pairs (rows a, columns b),
+// so that its operand loads from shared memory mostly coincide, and whole
+// warps skip a chunk whose frame window misses their frames.  The right-hand
+// side v' has warps of its own (a lane per free pose).
+//
+// Rows stream through kAsmStages shared-memory stages of up to
+// kAsmStageRows patches (a chunk takes one or more stages).  One producer
+// warp issues a bulk asynchronous copy per stage once every compute warp has
+// released the stage (its "empty" mbarrier); a compute warp waits for the
+// stage's copy (its "full" mbarrier), sums it or skips it, and releases it.
+// No block-wide barrier inside the loop: each warp moves at the pace of its
+// own work, up to kAsmStages stages ahead of the slowest.  Every wait is
+// bounded; on a timeout the CTA reports DPVO_BA_STATUS_TIMEOUT, waits (again
+// bounded) for its copies in flight and leaves.
+//
+// Sums: FP32 over blocks of kFlushEvery patches (a stage's last block may be
+// shorter), compensated across blocks (the running sums in registers, their
+// compensation terms in shared memory, thread-private), written once as FP64
+// in the strip layout (the 6 x 6 block of pair (a, b) row-major at 36 x its
+// pair index, then v').
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,7 +37,10 @@
 
 namespace dpvo {
 
-constexpr int kAsmMaxThreads = 576;            // 2 slices of 544 strips at 32 free poses
+constexpr int kAsmMaxWarps = 11;               // compute warps per CTA at most (6 x 6 register blocks)
+constexpr int kAsmMaxThreads = 32 * (kAsmMaxWarps + 1);   // + the producer warp
+constexpr int kAsmStages = 4;
+constexpr int kAsmStageRows = 32;
 
 // One thread: expect `bytes` on the mbarrier's current phase and bulk-copy
 // them (a multiple of 16, both addresses 16-byte aligned) from global to
@@ -33,141 +50,243 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
     bulk_copy_g2s(dst, src, bytes, mbar);
 }
 
-// Strips: 2 per block pair (a <= b), then one per free pose.
-__host__ __device__ inline int asm_slices(int nf) {
-    const int nst = n_strips(nf);
-    return nst <= 0 ? 1 : (nst + kAsmMaxThreads - 1) / kAsmMaxThreads;
+// Warp blocks: for each column block B (frames 8B .. 8B+7), the row blocks
+// of 4 frames that hold a pair a <= b; then ceil(nf / 32) warps for v'.
+__host__ __device__ inline int asm_col_warps(int nf, int B) {
+    const int last = 8 * B + 7 < nf - 1 ? 8 * B + 7 : nf - 1;
+    return last / 4 + 1;
 }
+__host__ __device__ inline int asm_pair_warps(int nf) {
+    int w = 0;
+    for (int B = 0; 8 * B < nf; ++B) w += asm_col_warps(nf, B);
+    return w;
+}
+__host__ __device__ inline int asm_warps(int nf) { return asm_pair_warps(nf) + (nf + 31) / 32; }
+__host__ __device__ inline int asm_slices(int nf) {
+    const int w = asm_warps(nf);
+    return w <= 0 ? 1 : (w + kAsmMaxWarps - 1) / kAsmMaxWarps;
+}
+// Threads per CTA: the compute warps of a slice, then the producer warp.
 __host__ __device__ inline int asm_threads(int nf) {
-    const int nst = n_strips(nf), sl = asm_slices(nf);
-    const int per = (nst + sl - 1) / sl;
-    return per < 32 ? 32 : (per + 31) & ~31;
+    const int w = asm_warps(nf), sl = asm_slices(nf);
+    const int per = (w + sl - 1) / sl;
+    return 32 * ((per < 1 ? 1 : per) + 1);
 }
 
-// Grid: x = assembly work items (Item{prob, item}), y = strip slices.  G_cap
-// bounds the patches of a chunk, rs_max the row length; t = iteration.
-__global__ void __launch_bounds__(kAsmMaxThreads) schur_assembly_kernel(const Prob *__restrict__ probs,
-                                                                        const Item *__restrict__ items, int t,
-                                                                        int G_cap, int rs_max) {
+// Dynamic shared memory: the stages (kAsmStageRows x rs_max floats each),
+// then 36 compensation terms per thread.
+__host__ __device__ inline size_t asm_smem_bytes(int rs_max, int threads) {
+    return ((size_t)kAsmStages * kAsmStageRows * rs_max + (size_t)36 * threads) * 4;
+}
+
+// Shared-memory accesses by 32-bit shared addresses (bytes).
+__device__ __forceinline__ float4 lds4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ float lds1(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];\n" : "=f"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts4(uint32_t addr, float4 v) {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
+// Compensated add of a finished block: s += blk (Kahan), for NQ entries
+// (a multiple of 4) whose compensation terms sit in shared memory as float4
+// groups at c4 + g * gs (bytes); then blk = 0.  Three groups at a time: their
+// loads in flight together, the updates independent.
+template <int NQ>
+__device__ __forceinline__ void flush_block(float *acc_s, float *blk, uint32_t c4, uint32_t gs) {
+#pragma unroll
+    for (int g0 = 0; g0 < NQ / 4; g0 += 3) {
+        float4 cv[3];
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+            if (g0 + g < NQ / 4) cv[g] = lds4(c4 + (g0 + g) * gs);
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+            if (g0 + g < NQ / 4) {
+                float *b = blk + 4 * (g0 + g), *a = acc_s + 4 * (g0 + g);
+                kahan_add(a[0], cv[g].x, b[0]);
+                kahan_add(a[1], cv[g].y, b[1]);
+                kahan_add(a[2], cv[g].z, b[2]);
+                kahan_add(a[3], cv[g].w, b[3]);
+                b[0] = b[1] = b[2] = b[3] = 0.f;
+            }
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+            if (g0 + g < NQ / 4) sts4(c4 + (g0 + g) * gs, cv[g]);
+    }
+}
+
+// One patch's product into a pair block: blk -= e_a e_b^T (6 x 6; ra, rb
+// the shared addresses of the padded frame entries a and b of the row).
+__device__ __forceinline__ void pair_patch(uint32_t ra, uint32_t rb, float *blk) {
+    const float4 a0 = lds4(ra);
+    const float4 a1 = lds4(ra + 16);
+    const float4 b0 = lds4(rb);
+    const float4 b1 = lds4(rb + 16);
+    const float ea[6] = {a0.x, a0.y, a0.z, a1.x, a1.y, a1.z};
+    const float eb[6] = {b0.x, b0.y, b0.z, b1.x, b1.y, b1.z};
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) blk[6 * r + cc] = fmaf(-ea[r], eb[cc], blk[6 * r + cc]);
+}
+
+// Grid: x = assembly work items (Item{prob, item}), y = slices (warp blocks
+// dealt round robin).  rs_max bounds the row length; t = iteration.
+__global__ void __launch_bounds__(kAsmMaxThreads, 1) schur_assembly_kernel(const Prob *__restrict__ probs,
+                                                                           const Item *__restrict__ items, int t,
+                                                                           int rs_max) {
     extern __shared__ __align__(16) unsigned char smem[];
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (t >= pr.iters || *pr.status != 0) return;
-    __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ int s_bad;
+    __shared__ __align__(8) uint64_t s_full[kAsmStages], s_empty[kAsmStages];
+    __shared__ int s_bad, s_issued;
+    const int n_comp = (int)(blockDim.x >> 5) - 1;         // compute warps; warp n_comp produces
 
     const int nf = pr.nf, t0 = pr.t0, RS = erow_len(nf);
-    const int nbs = 2 * n_block_pairs(nf), nst = nbs + nf;
-    const int st = blockIdx.y * blockDim.x + tid;
-    const bool active = st < nst, vs = st >= nbs;
-    int sa = 0, sb = 0, sh = 0;
-    if (active) {
+    const int nbs = 2 * n_block_pairs(nf), npw = asm_pair_warps(nf);
+    const int gw = warp * gridDim.y + blockIdx.y;
+    int a = -1, b = -1;
+    const bool vs = gw >= npw;                             // a right-hand-side warp
+    if (warp < n_comp) {
         if (!vs) {
-            decode_pair(st >> 1, nf, sa, sb);
-            sh = st & 1;
-        } else {
-            sa = sb = st - nbs;
+            int rem = gw, B = 0;
+            while (rem >= asm_col_warps(nf, B)) rem -= asm_col_warps(nf, B++);
+            a = 4 * rem + (lane >> 3);
+            b = 8 * B + (lane & 7);
+            if (a > b || b >= nf) a = b = -1;
+        } else if (gw < npw + (nf + 31) / 32) {
+            a = b = 32 * (gw - npw) + lane;
+            if (a >= nf) a = b = -1;
         }
     }
-    const int fa = t0 + sa, fb = t0 + sb;
-    const int oa = vs ? 8 * sa : 8 * sa + 4 * sh, ob = 8 * sb;
+    const bool active = a >= 0;
+    const int fa = t0 + a, fb = t0 + b;
+    const int oa = 8 * a, ob = vs ? 8 * nf : 8 * b;
 
     const int nch = *pr.n_chunks;
     const int c_begin = (int)(((long long)itm.item * nch) / pr.n_asm);
     const int c_end = (int)(((long long)(itm.item + 1) * nch) / pr.n_asm);
-    float *buf[2] = {reinterpret_cast<float *>(smem), reinterpret_cast<float *>(smem) + (size_t)G_cap * rs_max};
-    const uint32_t bar[2] = {smem_u32(&s_bar[0]), smem_u32(&s_bar[1])};
+    float *stage0 = reinterpret_cast<float *>(smem);
+    const size_t stage_len = (size_t)kAsmStageRows * rs_max;
     if (tid == 0) {
-        mbar_init(bar[0], 1);
-        mbar_init(bar[1], 1);
-        s_bad = 0;
-    }
-    __syncthreads();
-    if (tid == 0)
-        for (int c = c_begin; c < c_end && c < c_begin + 2; ++c) {
-            const Chunk ch = pr.chunks[c];
-            bulk_load(buf[c - c_begin], pr.erow + (size_t)ch.k0 * RS, (uint32_t)(ch.count * RS * 4), bar[c - c_begin]);
+        for (int s = 0; s < kAsmStages; ++s) {
+            mbar_init(smem_u32(&s_full[s]), 1);
+            mbar_init(smem_u32(&s_empty[s]), n_comp);
         }
+        s_bad = 0;
+        s_issued = 0;
+    }
+    // compensation terms, float4 groups: the g-th (entries 4g .. 4g+3) of
+    // this thread at acc_c + g * gs (bytes)
+    const uint32_t acc_c = smem_u32(stage0 + kAsmStages * stage_len + 4 * tid), gs = 16 * blockDim.x;
+#pragma unroll
+    for (int g = 0; g < 9; ++g) sts4(acc_c + g * gs, make_float4(0.f, 0.f, 0.f, 0.f));
+    __syncthreads();
 
-    float acc_s[18], acc_c[18], blk[18];
-#pragma unroll
-    for (int q = 0; q < 18; ++q) { acc_s[q] = 0.f; acc_c[q] = 0.f; blk[q] = 0.f; }
-    int issued = c_end - c_begin < 2 ? c_end - c_begin : 2;   // copies started (thread 0's count)
-    int waited = 0, since = 0;
-    for (int c = c_begin; c < c_end; ++c) {
-        const int u = c - c_begin, bi = u & 1;
-        if (!mbar_wait(bar[bi], (uint32_t)(u >> 1) & 1u)) atomicOr(&s_bad, 1);
-        ++waited;
-        __syncthreads();
-        if (s_bad) break;                          // a copy never landed: stop, report below
-        const Chunk ch = pr.chunks[c];
-        const bool win_a = fa >= ch.jlo && fa <= ch.jhi, win_b = fb >= ch.jlo && fb <= ch.jhi;
-        if (active && win_a && win_b) {
-            const float *rows = buf[bi];
-            if (!vs) {
-                for (int p = 0; p < ch.count; ++p) {
-                    const float *e = rows + (size_t)p * RS;
-                    const float4 a4 = *reinterpret_cast<const float4 *>(e + oa);
-                    const float4 b0 = *reinterpret_cast<const float4 *>(e + ob);
-                    const float4 b1 = *reinterpret_cast<const float4 *>(e + ob + 4);
-                    const float ea[3] = {a4.x, a4.y, a4.z};
-                    const float eb[6] = {b0.x, b0.y, b0.z, b1.x, b1.y, b1.z};
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int cc = 0; cc < 6; ++cc) blk[6 * r + cc] = fmaf(-ea[r], eb[cc], blk[6 * r + cc]);
-                    if (++since == kFlushEvery) {
-#pragma unroll
-                        for (int q = 0; q < 18; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
-                        since = 0;
+    volatile int *bad = &s_bad;
+    if (warp == n_comp) {
+        // producer: one lane issues the stages in order
+        if (lane == 0) {
+            int u = 0;
+            for (int c = c_begin; c < c_end && !*bad; ++c) {
+                const Chunk ch = pr.chunks[c];
+                for (int r0 = 0; r0 < ch.count; r0 += kAsmStageRows, ++u) {
+                    const int s = u % kAsmStages;
+                    if (u >= kAsmStages && !mbar_wait(smem_u32(&s_empty[s]), (uint32_t)(u / kAsmStages - 1) & 1u)) {
+                        *bad = 1;
+                        break;
                     }
-                }
-            } else {
-                for (int p = 0; p < ch.count; ++p) {
-                    const float *e = rows + (size_t)p * RS;
-                    const float sw = e[8 * nf];
-                    const float4 a0 = *reinterpret_cast<const float4 *>(e + oa);
-                    const float4 a1 = *reinterpret_cast<const float4 *>(e + oa + 4);
-                    const float ea[6] = {a0.x, a0.y, a0.z, a1.x, a1.y, a1.z};
-#pragma unroll
-                    for (int cc = 0; cc < 6; ++cc) blk[cc] = fmaf(-ea[cc], sw, blk[cc]);
-                    if (++since == kFlushEvery) {
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
-                        since = 0;
-                    }
+                    const int rows = min(kAsmStageRows, ch.count - r0);
+                    bulk_load(stage0 + s * stage_len, pr.erow + (size_t)(ch.k0 + r0) * RS, (uint32_t)(rows * RS * 4),
+                              smem_u32(&s_full[s]));
+                    s_issued = u + 1;
                 }
             }
         }
-        __syncthreads();                           // buffer bi is free again
-        if (tid == 0 && c + 2 < c_end) {
-            const Chunk cn = pr.chunks[c + 2];
-            bulk_load(buf[bi], pr.erow + (size_t)cn.k0 * RS, (uint32_t)(cn.count * RS * 4), bar[bi]);
-            ++issued;
+    } else {
+        float acc_s[36], blk[36];
+#pragma unroll
+        for (int q = 0; q < 36; ++q) { acc_s[q] = 0.f; blk[q] = 0.f; }
+        int u = 0;
+        for (int c = c_begin; c < c_end; ++c) {
+            const Chunk ch = pr.chunks[c];
+            const bool on = active && fa >= ch.jlo && fa <= ch.jhi && fb >= ch.jlo && fb <= ch.jhi;
+            bool stop = false;
+            for (int r0 = 0; r0 < ch.count; r0 += kAsmStageRows, ++u) {
+                const int s = u % kAsmStages;
+                if (*bad || !mbar_wait(smem_u32(&s_full[s]), (uint32_t)(u / kAsmStages) & 1u)) {
+                    *bad = 1;
+                    stop = true;
+                    break;
+                }
+                const float *rows = stage0 + s * stage_len;
+                const int nrow = min(kAsmStageRows, ch.count - r0);
+                if (on) {
+                    // blocks of kFlushEvery patches (the stage's last one may be shorter)
+                    const uint32_t rs4 = 4 * RS;
+                    for (int p0 = 0; p0 < nrow; p0 += kFlushEvery) {
+                        const uint32_t rb0 = smem_u32(rows) + p0 * rs4;
+                        const int m = min(kFlushEvery, nrow - p0);
+                        if (!vs) {
+                            const uint32_t ra = rb0 + 4 * oa, rb = rb0 + 4 * ob;
+                            if (m == kFlushEvery) {
+#pragma unroll
+                                for (int k = 0; k < kFlushEvery; ++k) pair_patch(ra + k * rs4, rb + k * rs4, blk);
+                            } else {
+                                for (int k = 0; k < m; ++k) pair_patch(ra + k * rs4, rb + k * rs4, blk);
+                            }
+                            flush_block<36>(acc_s, blk, acc_c, gs);
+                        } else {
+                            for (int k = 0; k < m; ++k) {
+                                const uint32_t re = rb0 + k * rs4;
+                                const float sw = lds1(re + 4 * ob);
+                                const float4 a0 = lds4(re + 4 * oa);
+                                const float4 a1 = lds4(re + 4 * oa + 16);
+                                const float ea[6] = {a0.x, a0.y, a0.z, a1.x, a1.y, a1.z};
+#pragma unroll
+                                for (int cc = 0; cc < 6; ++cc) blk[cc] = fmaf(-ea[cc], sw, blk[cc]);
+                            }
+                            flush_block<8>(acc_s, blk, acc_c, gs);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&s_empty[s]));
+            }
+            if (stop) break;
+        }
+        if (active && !*bad) {
+            double *out = pr.partial + (size_t)(pr.n_items + itm.item) * pr.L;
+            if (!vs) {
+                double *o = out + 36 * (a * nf - a * (a - 1) / 2 + (b - a));
+#pragma unroll
+                for (int q = 0; q < 36; ++q) o[q] = (double)acc_s[q] - (double)lds1(acc_c + (q >> 2) * gs + 4 * (q & 3));
+            } else {
+                double *o = out + 18 * nbs + 6 * a;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) o[q] = (double)acc_s[q] - (double)lds1(acc_c + (q >> 2) * gs + 4 * (q & 3));
+            }
         }
     }
-    if (s_bad) {
-        // report, and give every copy this CTA started a bounded wait before it exits
-        if (tid == 0) {
-            atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
-            for (int u = waited - 1; u < issued; ++u) mbar_wait(bar[u & 1], (uint32_t)(u >> 1) & 1u);
-        }
-        return;
-    }
-#pragma unroll
-    for (int q = 0; q < 18; ++q) kahan_add(acc_s[q], acc_c[q], blk[q]);
-    if (active) {
-        double *out = pr.partial + (size_t)(pr.n_items + itm.item) * pr.L;
-        if (!vs) {
-            double *o = out + 18 * st;
-#pragma unroll
-            for (int q = 0; q < 18; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
-        } else {
-            double *o = out + 18 * nbs + 6 * sa;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
-        }
+    __syncthreads();
+    if (s_bad && tid == 0) {
+        // report, and give every copy still in flight a bounded wait before the CTA exits
+        atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
+        const int iss = s_issued;
+        for (int u = iss > kAsmStages ? iss - kAsmStages : 0; u < iss; ++u)
+            mbar_wait(smem_u32(&s_full[u % kAsmStages]), (uint32_t)(u / kAsmStages) & 1u);
     }
 }
 

@@ -53,7 +53,7 @@ static size_t erow_bytes(bool tc, const Prob &p, int G_cap) {
 // Assembly launch (ext batches): grid x = assembly items, y = strip slices.
 static void launch_assembly(const Layout &L, cudaStream_t stream, const Prob *probs, const Item *asm_items, int t) {
     const dim3 grid(L.n_asm_items, asm_slices(L.nf_max));
-    schur_assembly_kernel<<<grid, asm_threads(L.nf_max), L.asm_smem, stream>>>(probs, asm_items, t, L.G_cap,
+    schur_assembly_kernel<<<grid, asm_threads(L.nf_max), L.asm_smem, stream>>>(probs, asm_items, t,
                                                                                erow_len(L.nf_max));
 }
 
@@ -113,7 +113,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
     L.ext = L.nf_max > kFusedMaxFree;
     L.solve_smem = L.ext ? solve_large_smem_bytes(L.nf_max) : solve_smem_bytes(L.nf_max);
-    L.asm_smem = L.ext ? (size_t)2 * L.G_cap * erow_len(L.nf_max) * 4 : 0;
+    L.asm_smem = L.ext ? asm_smem_bytes(erow_len(L.nf_max), asm_threads(L.nf_max)) : 0;
     const int asm_slices_max = L.ext ? asm_slices(L.nf_max) : 1;
 
     const int target_ctas = 2 * num_sms;

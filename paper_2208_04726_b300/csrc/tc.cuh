@@ -98,6 +98,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
+// One arrival on the mbarrier's current phase.
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
 // One thread: bulk asynchronous copy of `bytes` (a multiple of 16; both
 // addresses 16-byte aligned) from global to shared memory, counted against the
 // mbarrier's expected transaction bytes.
