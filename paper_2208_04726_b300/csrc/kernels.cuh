@@ -773,9 +773,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     int cur = 0;
     bool group_open = false;   // the previous chunk continues into this one
 
+    bool rows_pending = false;   // warp 0: a bulk row store may still read Ec
     for (int c = c_begin; c < c_end; ++c) {
         const Chunk ch = s_ch[cur];
         const bool have_next = c + 1 < c_end;
+        if (rows_pending) {                                // Ec is rewritten after the next barrier
+            bulk_wait_read_all();
+            rows_pending = false;
+        }
         cp_async_wait_all();
         if (!mbar_wait(ldbar, (uint32_t)(c - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
         __syncthreads();                                   // this chunk's inputs are in shared memory
@@ -1012,14 +1017,16 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                 }
             } else {
-                // the same lanes then scale the patch's row of E by
-                // C_k^-1/2 and store it, compacted, for the next back-substitution
+                // the same lanes then scale the patch's row of E by C_k^-1/2 in
+                // place; the chunk's rows go to global memory by one bulk copy
+                // (below), for the next back-substitution
                 const float sq = sqrtf(1.0f / C);
                 float *e = Ec + p * ES;
                 if (p < cnt) {
                     if (sub == 0) {
                         ps[p] = sq;
-                        e[8 * nf] = sq * (adjoint_rhs ? pr.dbar[k0 + p] : w);
+                        *reinterpret_cast<float4 *>(e + 8 * nf) =
+                            make_float4(sq * (adjoint_rhs ? pr.dbar[k0 + p] : w), sq, 0.f, 0.f);
                     } else if (anc_free && sub < 3) {
                         const float4 qd = pd[p];
                         const float d = qd.z, px = qd.x, py = qd.y;
@@ -1032,15 +1039,13 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 __syncwarp();
                 if (p < cnt) {
                     float4 *e4 = reinterpret_cast<float4 *>(e);
-                    float4 *dst = reinterpret_cast<float4 *>(pr.erow + (size_t)(k0 + p) * RS);
                     for (int m = sub; m < 2 * nf; m += LP) {
                         float4 v = e4[m];
                         v.x *= sq; v.y *= sq; v.z *= sq;
                         e4[m] = v;
-                        if (!adjoint_rhs) dst[m] = v;
                     }
-                    if (sub == 0 && !adjoint_rhs) dst[2 * nf] = make_float4(e[8 * nf], sq, 0.f, 0.f);
                 }
+                fence_async_smem();                        // the rows are read by the bulk copy
             }
         }
         if (!group_next && !adjoint_rhs) {
@@ -1053,6 +1058,20 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
         }
         __syncthreads();
+        if constexpr (!TC) {
+            // this chunk's scaled rows to global memory: one bulk copy when the
+            // shared row stride is the problem's, else one per row (warp 0)
+            if (warp == 0 && !adjoint_rhs) {
+                if (ES == RS) {
+                    if (lane == 0) bulk_copy_s2g(pr.erow + (size_t)k0 * RS, Ec, (uint32_t)(cnt * RS * 4));
+                } else {
+                    for (int p = lane; p < cnt; p += 32)
+                        bulk_copy_s2g(pr.erow + (size_t)(k0 + p) * RS, Ec + p * ES, (uint32_t)(RS * 4));
+                }
+                bulk_commit();
+                rows_pending = true;
+            }
+        }
         // the per-slot sums are consumed: start copying the next chunk's stored rows
         if (do_bs && have_next) {
             if constexpr (TC) prefetch_block(pr, c + 1, nx, kmax, srow);
@@ -1267,15 +1286,28 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         }
         if constexpr (EXT) if (!group_next && !adjoint_rhs) {
             // more strips than threads: each pose-pair block goes straight into
-            // this CTA's FP64 partial (it owns the partial; groups are sequential)
+            // this CTA's FP64 partial (it owns the partial; groups are
+            // sequential).  Only strips of a window frame or the anchor change:
+            // per free pose f, its diagonal block (two strips), its v'-strip and
+            // the block pairing it with the anchor (two strips).
             double *part = pr.partial + (size_t)itm.item * pr.L;
-            for (int st = tid; st < nst; st += kThreads) {
-                const bool vs = st >= nbs;
-                int a2 = st - nbs, b2 = a2, h2 = 0;
-                if (!vs) {
-                    decode_pair(st >> 1, nf, a2, b2);
-                    h2 = st & 1;
+            const int fanc = anc - t0;
+            for (int it5 = tid; it5 < 5 * nf; it5 += kThreads) {
+                const int f = it5 / 5, kind = it5 - 5 * f, fr = t0 + f;
+                const bool in_w = fr >= jlo && fr < jlo + W;
+                int a2 = f, b2 = f, h2 = kind & 1;
+                bool vs = false;
+                if (kind < 3) {
+                    if (!in_w && fr != anc) continue;
+                    vs = kind == 2;
+                    h2 = kind & 1;
+                } else {
+                    if (!anc_free || fr == anc || !in_w) continue;
+                    a2 = min(f, fanc);
+                    b2 = max(f, fanc);
+                    h2 = kind - 3;
                 }
+                const int st = vs ? nbs + f : 2 * (a2 * nf - a2 * (a2 - 1) / 2 + (b2 - a2)) + h2;
                 float add[18];
                 if (!strip_block_add(a2, b2, h2, vs, t0, anc, jlo, W, Mc, Aj, Bii, add)) continue;
                 if (vs) {
@@ -1294,6 +1326,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         cur ^= 1;
     }
     cp_async_wait_all();
+    if (rows_pending) bulk_wait_all();                     // the stored rows are written
     if (c_begin < c_end && s_ld_bad) {
         // report, and give the copy that did not land one more bounded wait
         if (tid == 0) {

@@ -114,6 +114,22 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
         : "memory");
 }
 
+// One thread: bulk asynchronous copy of `bytes` (a multiple of 16; both
+// addresses 16-byte aligned) from shared to global memory, in this thread's
+// bulk async-group (committed by bulk_commit).
+__device__ __forceinline__ void bulk_copy_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+// Wait until the shared-memory sources of this thread's bulk groups have been read.
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+// Wait until this thread's bulk groups have completed (writes performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+
 // 16 consecutive FP32 accumulator columns of this thread's TMEM lane (the
 // warp reads lanes 32 (warp % 4) .. +31).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
