@@ -441,16 +441,13 @@ __device__ __forceinline__ void prefetch_chunk(const Prob &pr, const Chunk &ch, 
     cp_async_commit();
 }
 
-// Start copying one chunk's stored Schur rows (erow_len floats each) into
-// shared memory at row stride rss.
-__device__ __forceinline__ void prefetch_rows(const Prob &pr, const Chunk &ch, int rs, int rss, float *dst) {
-    const int n4 = rs / 4, total = ch.count * n4;
-    const float4 *src = reinterpret_cast<const float4 *>(pr.erow + (size_t)ch.k0 * rs);
-    for (int q = threadIdx.x; q < total; q += kThreads) {
-        const int p = q / n4, c = q - p * n4;
-        cp_async16(dst + p * rss + 4 * c, src + q);
-    }
-    cp_async_commit();
+// One thread: start one bulk copy of a chunk's stored Schur rows (rs floats
+// each, contiguous) into shared memory, completing on the mbarrier.
+__device__ __forceinline__ void prefetch_rows_bulk(const Prob &pr, const Chunk &ch, int rs, float *dst, uint32_t bar) {
+    const uint32_t bytes = (uint32_t)(ch.count * rs * 4);
+    fence_async_smem();                            // the buffer's earlier shared-memory reads come first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+    if (bytes) bulk_copy_g2s(dst, pr.erow + (size_t)ch.k0 * rs, bytes, bar);
 }
 
 // Start copying chunk c's block of stored rows (its first ceil8(count) patches) to dst.
@@ -754,12 +751,14 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
 
     __shared__ __align__(16) Chunk s_ch[2];
     __shared__ __align__(8) uint64_t s_ldbar;    // edge staging: one phase per chunk
+    __shared__ __align__(8) uint64_t s_rowbar;   // stored-row staging (back-substitution): one phase per chunk
     __shared__ int s_ld_bad;
-    const uint32_t ldbar = smem_u32(&s_ldbar);
+    const uint32_t ldbar = smem_u32(&s_ldbar), rowbar = smem_u32(&s_rowbar);
     if (c_begin < c_end) {
         if (tid == 0) {
             s_ch[0] = pr.chunks[c_begin];
             mbar_init(ldbar, 1);
+            mbar_init(rowbar, 1);
             s_ld_bad = 0;
         }
         __syncthreads();
@@ -767,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                        c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1], ldbar);
         if (do_bs) {
             if constexpr (TC) prefetch_block(pr, c_begin, s_ch[0], kmax, srow);
-            else prefetch_rows(pr, s_ch[0], RS, RSS, srow);
+            else if (tid == 0) prefetch_rows_bulk(pr, s_ch[0], RS, srow, rowbar);
         }
     }
     int cur = 0;
@@ -783,6 +782,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         }
         cp_async_wait_all();
         if (!mbar_wait(ldbar, (uint32_t)(c - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
+        if (!TC && do_bs && !mbar_wait(rowbar, (uint32_t)(c - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
         __syncthreads();                                   // this chunk's inputs are in shared memory
         if (s_ld_bad) break;                               // a bulk copy never landed: reported below
         int o_jj, o_tw;                                    // alignment slack of the staged edge ranges
@@ -1075,7 +1075,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         // the per-slot sums are consumed: start copying the next chunk's stored rows
         if (do_bs && have_next) {
             if constexpr (TC) prefetch_block(pr, c + 1, nx, kmax, srow);
-            else prefetch_rows(pr, nx, RS, RSS, srow);
+            else if (tid == 0) prefetch_rows_bulk(pr, nx, RS, srow, rowbar);
         }
         if constexpr (TC) {
             // Scale each pose column by C_k^-1/2, store the rows for the next
@@ -1333,6 +1333,10 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
             mbar_wait(ldbar, 0u);
             mbar_wait(ldbar, 1u);
+            if (!TC && do_bs) {
+                mbar_wait(rowbar, 0u);
+                mbar_wait(rowbar, 1u);
+            }
         }
         __syncthreads();
     }
