@@ -228,10 +228,14 @@ def traffic_from_profiles(kernel_source_sha):
     return val if (sha == kernel_source_sha and val is not None) else None
 
 
+# the sources the linearise kernel and its launch are built from
+KERNEL_SOURCES = ("ba_common.cuh", "dpvo_ba.cu", "kernels.cuh", "se3.cuh", "tc.cuh")
+
+
 def kernel_sha():
     import hashlib
     h = hashlib.sha1()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2208_04726_b300", "csrc"))):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2208_04726_b300", "csrc", f), "rb").read())
     return h.hexdigest()
 

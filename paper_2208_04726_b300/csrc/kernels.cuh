@@ -1784,28 +1784,60 @@ constexpr int kDiagLd = 36;            // row stride (floats) of a staged diagon
 __host__ __device__ inline int panel_ld(int n) { return (n + 7) & ~3; }
 __host__ __device__ inline int panel_off(int n) { return (n * (n + 1) / 2 + n + 3) & ~3; }
 
+constexpr int kLinvLd = kPanel + 1;     // row stride of an inverted diagonal block (conflict-free rows and columns)
+
+// Warp w of the CTA, for panel J = kPanel w: the inverse of the panel's unit
+// lower diagonal block, L_rj = a_rj / p_j (r > j), into Linv + w kPanel kLinvLd
+// at [r kLinvLd + c].  Lane c computes column c by forward substitution.
+__device__ void invert_diag_blocks(const float *Sp, const float *rp, float *Linv, int n, int tid) {
+    const int warp = tid >> 5, lane = tid & 31, J = kPanel * warp;
+    if (J >= n) return;
+    const int nb = min(kPanel, n - J);
+    float z[kPanel];
+#pragma unroll
+    for (int r = 0; r < kPanel; ++r) {
+        float acc = 0.f;
+        if (r < nb) {
+            const int rr = packed_index(J + r, J);
+#pragma unroll
+            for (int j = 0; j < r; ++j) acc = fmaf(Sp[rr + j] * rp[J + j], z[j], acc);
+        }
+        z[r] = r == lane ? 1.f : -acc;             // zero above the diagonal (z_j = 0 for j < lane)
+    }
+    float *L = Linv + warp * kPanel * kLinvLd;
+    if (lane < nb) {
+#pragma unroll
+        for (int r = 0; r < kPanel; ++r)
+            if (r < nb) L[r * kLinvLd + lane] = z[r];
+    }
+}
+
 // All threads: solve S x = b in place in b (shared memory), S = U D^-1 U^T
 // packed in Sp (the eliminated values a_ij, j <= i) with pivot reciprocals
-// rp, by panels of kPanel: each panel's diagonal block by one warp (lane =
-// row, values by shuffle), the rows outside it by one thread each.
-__device__ void solve_blocked_f32(const float *Sp, const float *rp, float *b, int n, int tid) {
+// rp, by panels of kPanel: each panel's diagonal block by one warp as a
+// product with its inverse (invert_diag_blocks), the rows outside it by one
+// thread each.
+__device__ void solve_blocked_f32(const float *Sp, const float *rp, const float *Linv, float *b, int n, int tid) {
     __shared__ float s_t[kPanel];                          // y_j / p_j of the current panel
     const int lane = tid & 31;
-    for (int J = 0; J < n; J += kPanel) {                  // forward: y_i = b_i - sum_j<i a_ij y_j / p_j
+    for (int J = 0; J < n; J += kPanel) {                  // forward: y_J = L_JJ^-1 b_J, then the rows below
         const int nb = min(kPanel, n - J);
         if (tid < 32) {
-            const int ri = packed_index(J + min(lane, nb - 1), J);
-            float y = lane < nb ? b[J + lane] : 0.f;
+            const float *L = Linv + (J / kPanel) * kPanel * kLinvLd + lane * kLinvLd;
+            float y0 = 0.f, y1 = 0.f;
+            if (lane < nb) {
 #pragma unroll
-            for (int j = 0; j < kPanel; ++j) {
-                if (j < nb) {
-                    const float t = __shfl_sync(0xffffffffu, y, j) * rp[J + j];
-                    const float c = lane > j && lane < nb ? Sp[ri + j] : 0.f;
-                    y = fmaf(-c, t, y);
-                    if (lane == j) s_t[j] = t;
+                for (int c = 0; c < kPanel; c += 2) {
+                    if (c <= lane && c < nb) y0 = fmaf(L[c], b[J + c], y0);
+                    if (c + 1 <= lane && c + 1 < nb) y1 = fmaf(L[c + 1], b[J + c + 1], y1);
                 }
             }
-            if (lane < nb) b[J + lane] = y;
+            __syncwarp();
+            if (lane < nb) {
+                const float y = y0 + y1;
+                b[J + lane] = y;
+                s_t[lane] = y * rp[J + lane];
+            }
         }
         __syncthreads();
         for (int i = J + nb + tid; i < n; i += kSolveThreads) {   // nb == kPanel here
@@ -1817,19 +1849,20 @@ __device__ void solve_blocked_f32(const float *Sp, const float *rp, float *b, in
         }
         __syncthreads();
     }
-    for (int J = ((n - 1) / kPanel) * kPanel; J >= 0; J -= kPanel) {   // backward: x_i = (y_i - sum_j>i a_ji x_j) / p_i
+    for (int J = ((n - 1) / kPanel) * kPanel; J >= 0; J -= kPanel) {   // backward: x_J = L_JJ^-T D_J^-1 w_J
         const int nb = min(kPanel, n - J);
         if (tid < 32) {
-            float y = lane < nb ? b[J + lane] : 0.f;
+            const float *L = Linv + (J / kPanel) * kPanel * kLinvLd + lane;
+            float x0 = 0.f, x1 = 0.f;
+            if (lane < nb) {
 #pragma unroll
-            for (int j = kPanel - 1; j >= 0; --j) {
-                if (j < nb) {
-                    const float xj = __shfl_sync(0xffffffffu, y, j) * rp[J + j];
-                    const float c = lane < j ? Sp[packed_index(J + j, J) + lane] : 0.f;
-                    y = lane == j ? xj : fmaf(-c, xj, y);
+                for (int c = 0; c < kPanel; c += 2) {
+                    if (c >= lane && c < nb) x0 = fmaf(L[c * kLinvLd], rp[J + c] * b[J + c], x0);
+                    if (c + 1 >= lane && c + 1 < nb) x1 = fmaf(L[(c + 1) * kLinvLd], rp[J + c + 1] * b[J + c + 1], x1);
                 }
             }
-            if (lane < nb) b[J + lane] = y;
+            __syncwarp();
+            if (lane < nb) b[J + lane] = x0 + x1;
         }
         __syncthreads();
         for (int i = tid; i < J; i += kSolveThreads) {
@@ -2009,12 +2042,11 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
                     const float ip = pj > 0.f ? 1.0f / pj : -1.f;
                     bad |= !(ip > 0.f) || !isfinite(ip);
                     if (lane == 0) s_rpf[J + j] = ip;
-                    const float l = xr[j] * ip;
+                    // rows below the pivot only; the entries right of a row's
+                    // diagonal (c > lane) take harmless updates and are never read
+                    const float l = lane > j ? xr[j] * ip : 0.f;
 #pragma unroll
-                    for (int c = j + 1; c < kPanel; ++c) {
-                        const float acj = __shfl_sync(0xffffffffu, xr[j], c);
-                        if (lane > j && c <= lane) xr[c] = fmaf(-l, acj, xr[c]);
-                    }
+                    for (int c = j + 1; c < kPanel; ++c) xr[c] = fmaf(-l, __shfl_sync(0xffffffffu, xr[j], c), xr[c]);
                 }
             }
             if (lane < nb) {
@@ -2088,6 +2120,11 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
         __syncthreads();
     }
     __syncthreads();
+    // inverted diagonal blocks over the panel buffers (free now): ceil(n / kPanel)
+    // x kPanel x kLinvLd floats, within 2 kPanel panel_ld(n) for n >= 26 and, for
+    // smaller n, within the FP32 region the launch sizes for more than 15 free poses
+    if (!s_use64) invert_diag_blocks(Sp, s_rpf, PuT, n, tid);
+    __syncthreads();
     double prev = 0.0;
     for (int it = 0; it <= kMaxRefineLarge && !s_use64; ++it) {
         if (it > 0) {   // residual v - S x in FP64 from the packed workspace copy
@@ -2106,7 +2143,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
             }
             __syncthreads();
         }
-        solve_blocked_f32(Sp, s_rpf, bf, n, tid);
+        solve_blocked_f32(Sp, s_rpf, PuT, bf, n, tid);
         double dmax = 0.0, xmax = 0.0;
         for (int q = tid; q < n; q += kSolveThreads) {
             const double d = s_dsc[q] * (double)bf[q];
