@@ -9,6 +9,7 @@
 #include "dpvo_ba.h"
 #include "ba_common.cuh"
 #include "kernels.cuh"
+#include "solve_large.cuh"
 #include "assemble.cuh"
 #include "backward.cuh"
 #include "serve.cuh"
