@@ -19,6 +19,9 @@ Also measured and reported on the same JSON line:
   serving   256 VO sessions (uneven shapes) with device-resident state, Poisson
             requests at 2000/s: p50/p99 latency and solves/s, continuous
             batching vs one launch per solve, plus a saturated closed loop
+  stress    64 large-window sessions (64 frames, 32 free poses, 4 iterations)
+  grad      16 eight-frame problems: forward, the pose supervision loss of
+            Sec. 3.4 on the device, and the backward to targets and weights
 
 ``--impl reference`` times the FP64 oracle (the reference arm) instead.
 Launch: ``python bench.py --gpus N --steps K --warmup W`` (torchrun for N > 1,
@@ -58,6 +61,7 @@ def parse():
     ap.add_argument("--parity-samples", type=int, default=2)
     ap.add_argument("--serving", type=int, default=1, help="run the serving measurement (Poisson sessions)")
     ap.add_argument("--tf32", type=int, default=1, help="also time the opt-in tensor-core Schur mode")
+    ap.add_argument("--grad", type=int, default=16, help="problems of the differentiation workload; 0 skips")
     ap.add_argument("--stress", type=int, default=64,
                     help="large-window sessions timed (64 frames, 256 patches each, radius 24, 32 free poses, 4 "
                          "iterations); 0 skips")
@@ -211,6 +215,64 @@ def stress_bench(n_sessions, steps, stream, hbm_peak):
             "linearize_hbm": {"algorithmic_bytes_per_launch": bytes_lin, "achieved_gbs": gbs,
                               "peak_gbs": hbm_peak, "frac": (gbs / hbm_peak) if gbs else None},
             "parity": "tests/test_gpu_large.py: one instance against the dense FP64 oracle"}
+
+
+def grad_bench(n_problems=16, steps=20, warmup=3, parity=True):
+    """The differentiation workload: n_problems eight-frame problems (64
+    patches per frame, every frame connected, 2 fixed poses, 2 iterations).
+    A step = forward solve from the initial state, the pose supervision loss
+    of Sec. 3.4 (Eq. 7) and its pose gradient on the device, and the backward
+    to the targets and weights -- all through the C ABI, CUDA events around
+    each part.  Parity: problem 0's target/weight gradients vs autograd of the
+    FP64 twin with the same loss."""
+    import torch
+    from paper_2208_04726_b300 import ba
+    from paper_2208_04726_b300 import scenes as S
+    scenes = [S.make_scene(S.PLAIN_N8, 300 + b) for b in range(n_problems)]
+    start = [ba.problem_from_scene(sc) for sc in scenes]
+    work = [ba.problem_from_scene(sc) for sc in scenes]
+    gt = [torch.tensor(sc.poses_gt, dtype=torch.float32, device="cuda") for sc in scenes]
+    zero_d = [torch.zeros_like(p.patches[:, 2]) for p in start]
+    solver = ba.Solver()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_fwd, t_loss, t_bwd = [], [], []
+    out = None
+    for it in range(warmup + steps):
+        for w, s0 in zip(work, start):
+            w.poses.copy_(s0.poses)
+            w.patches.copy_(s0.patches)
+        ev[0].record()
+        solver.solve(work)
+        ev[1].record()
+        loss, gp = ba.pose_loss([w.poses for w in work], gt)
+        ev[2].record()
+        gts, gws = solver.backward(start, gp, zero_d)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if it >= warmup:
+            t_fwd.append(ev[0].elapsed_time(ev[1]))
+            t_loss.append(ev[1].elapsed_time(ev[2]))
+            t_bwd.append(ev[2].elapsed_time(ev[3]))
+        out = (gts[0].cpu().numpy(), gws[0].cpu().numpy())
+    solver.close()
+    step = float(np.median(np.array(t_fwd) + np.array(t_loss) + np.array(t_bwd)))
+    res = {"workload": f"{n_problems} problems of 8 frames x 64 patches (512), all frames connected (4096 edges), "
+                       "t0 = 2, 2 GN iterations; loss = pose supervision of Eq. 7 (ordered frame pairs)",
+           "ms_per_step": step, "problems_per_s": n_problems / step * 1e3,
+           "forward_ms": float(np.median(t_fwd)), "pose_loss_ms": float(np.median(t_loss)),
+           "backward_ms": float(np.median(t_bwd)), "steps": steps}
+    if parity:
+        from oracle import pose_loss as PL
+        from oracle import unrolled_grad as ug
+        sc = scenes[0]
+        target = torch.tensor(np.asarray(sc.target, np.float64), requires_grad=True)
+        weight = torch.tensor(np.asarray(sc.weight, np.float64), requires_grad=True)
+        R, t, _ = ug.unrolled(sc, target, weight)
+        rt, rw = torch.autograd.grad(PL.loss_torch(R, t, sc.poses_gt), [target, weight])
+        res["parity"] = {"problem": 0, "tolerance": 1e-3,
+                         "dL_dtarget_rel_err": float(np.linalg.norm(out[0] - rt.numpy()) / np.linalg.norm(rt.numpy())),
+                         "dL_dweight_rel_err": float(np.linalg.norm(out[1] - rw.numpy()) / np.linalg.norm(rw.numpy()))}
+    return res
 
 
 def traffic_from_profiles(kernel_source_sha):
@@ -556,6 +618,7 @@ def main():
 
     serving = serving_bench() if (rank == 0 and args.serving) else None
     stress = stress_bench(args.stress, 5, stream, load_peaks()[0]) if (rank == 0 and args.stress > 0) else None
+    grad = grad_bench(args.grad, parity=args.parity_samples > 0) if (rank == 0 and args.grad > 0) else None
 
     if rank == 0:
         line = {
@@ -580,6 +643,7 @@ def main():
             "serving": serving,
             "tf32_schur": tf32,
             "stress": stress,
+            "grad": grad,
             "gpu_launches": world * n_launch_per_solve * args.steps,
             "clocks": clocks.summary(),
         }

@@ -277,6 +277,39 @@ int dpvo_ba_timing(dpvo_ba_handle *h, float *ms_out, int *kind_out, int cap);
 int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_dims *dims, const dpvo_ba_problem *prob,
                           void *stream);
 
+/* ---- pose supervision (Sec. 3.4, Eq. 7) -----------------------------------
+ * The training loss on the poses, L = sum over ordered frame pairs (i, j),
+ * i != j, of || Log_SE(3)[ (G_i^-1 G_j)^-1 (T_i^-1 T_j) ] || (the Euclidean norm
+ * of the twist (rho, phi), translation first), with T the predicted and G the
+ * ground-truth poses, and its gradient dL/dT in the layout dpvo_ba_grads takes,
+ * so that dpvo_ba_backward carries it to the targets and weights.  The
+ * predicted translations are first multiplied by `scale` (the Umeyama scale
+ * alignment of the paper, computed by the caller and held constant).  One
+ * problem per descriptor; all pointers DEVICE, caller-owned:
+ *   poses      [N][7]  predicted poses (t, q xyzw), world -> camera   (read)
+ *   gt_poses   [N][7]  ground-truth poses, same layout                (read)
+ *   loss       [1]     L                                              (written)
+ *   dL_dposes  [N][7]  dL/d(t, q): the translation gradient, and the
+ *                      quaternion gradient of L(t, q / |q|) (orthogonal to q)
+ *                      (written)
+ * A pair whose twist is shorter than 1e-5 adds its length to L but nothing to
+ * the gradient (the norm is not differentiable at zero, and below that length
+ * the twist's direction is FP32 rounding of the relative poses).  FP32 arithmetic; J_l^-1 of the twist by its
+ * Bernoulli series in ad (converges for rotation angles up to pi, which Log
+ * returns).  Asynchronous on stream; no workspace.
+ * Errors: EINVAL (NULL pointers, n_frames outside [1, DPVO_BA_MAX_FRAMES],
+ * n_problems < 0), ECUDA. */
+typedef struct {
+    const float *poses;
+    const float *gt_poses;
+    float *loss;
+    float *dL_dposes;
+    int32_t n_frames;
+    float scale;
+} dpvo_ba_pose_loss_problem;
+
+int dpvo_ba_pose_loss(const dpvo_ba_pose_loss_problem *probs, int n_problems, void *stream);
+
 /* Human-readable name of a return code. */
 const char *dpvo_ba_strerror(int code);
 

@@ -15,6 +15,9 @@ Contents
 ``unrolled_grad`` FP64 torch-autograd twin of the unrolled iterations, written
                   independently of ``dense_gn``, giving the reference gradient of a
                   loss on the final state w.r.t. targets and weights.
+``pose_loss``     FP64 pose supervision loss of Sec. 3.4 (Eq. 7): a matrix-logarithm
+                  form with central-difference gradients, and a differentiable torch
+                  form for the gradient through the unrolled twin.
 
 Parity unpinned: nothing here is checked against the authors' implementation,
 which is not available; every pin is mathematical (finite differences, exact

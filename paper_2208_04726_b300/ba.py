@@ -35,6 +35,11 @@ class Grads(ctypes.Structure):
                 ("dL_dweight", ctypes.c_void_p)]
 
 
+class PoseLossProblem(ctypes.Structure):
+    _fields_ = [("poses", ctypes.c_void_p), ("gt_poses", ctypes.c_void_p), ("loss", ctypes.c_void_p),
+                ("dL_dposes", ctypes.c_void_p), ("n_frames", ctypes.c_int32), ("scale", ctypes.c_float)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("poses", ctypes.c_void_p), ("patches", ctypes.c_void_p), ("anchor", ctypes.c_void_p),
                 ("kk", ctypes.c_void_p), ("jj", ctypes.c_void_p), ("target", ctypes.c_void_p),
@@ -50,7 +55,7 @@ EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solv
            "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_set_timing", "dpvo_ba_timing",
            "dpvo_ba_solve_noalloc", "dpvo_ba_backward", "dpvo_ba_serve_start",
            "dpvo_ba_serve_stop", "dpvo_ba_session_open", "dpvo_ba_session_close", "dpvo_ba_session_read",
-           "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror"]
+           "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror", "dpvo_ba_pose_loss"]
 
 _lib = None
 
@@ -91,6 +96,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
     lib.dpvo_ba_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(ctypes.c_int32),
                                  ctypes.POINTER(ctypes.c_double)]
+    lib.dpvo_ba_pose_loss.argtypes = [ctypes.POINTER(PoseLossProblem), i32, vp]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -391,6 +397,35 @@ class PackedBatch:
         return int(sum(self.flat[n].numel() * self.flat[n].element_size() for n in names))
 
 _default_solver = None
+
+
+def pose_loss(poses, gt_poses, scale=1.0, stream=None):
+    """Pose supervision loss (Sec. 3.4, Eq. 7) of each problem and its gradient
+    w.r.t. the predicted poses, on the device (dpvo_ba_pose_loss).
+
+    poses, gt_poses: lists of [N, 7] float32 CUDA tensors (t, q xyzw);
+    scale: a float or one per problem (applied to the predicted translations,
+    held constant).  Returns (loss [B] tensor, [dL/dposes [N, 7]] list)."""
+    lib = load()
+    B = len(poses)
+    scales = [float(scale)] * B if not isinstance(scale, (list, tuple)) else [float(x) for x in scale]
+    if len(gt_poses) != B or len(scales) != B:
+        raise ValueError("poses, gt_poses and scale must have one entry per problem")
+    dev = poses[0].device if B else torch.device("cuda")
+    loss = torch.zeros(B, dtype=torch.float32, device=dev)
+    grads, keep, descs = [], [], (PoseLossProblem * max(B, 1))()
+    for b in range(B):
+        T = poses[b].detach().to(torch.float32).contiguous()
+        G = gt_poses[b].detach().to(torch.float32).contiguous()
+        if T.shape != G.shape or T.dim() != 2 or T.shape[1] != 7:
+            raise ValueError("poses and gt_poses must be matching [N, 7] tensors")
+        g = torch.empty_like(T)
+        keep += [T, G]
+        grads.append(g)
+        descs[b] = PoseLossProblem(T.data_ptr(), G.data_ptr(), loss.data_ptr() + 4 * b, g.data_ptr(),
+                                   T.shape[0], scales[b])
+    _check(lib.dpvo_ba_pose_loss(descs, B, ctypes.c_void_p(_stream_ptr(stream))), "dpvo_ba_pose_loss")
+    return loss, grads
 
 
 def default_solver() -> Solver:
