@@ -22,6 +22,8 @@ Also measured and reported on the same JSON line:
   stress    64 large-window sessions (64 frames, 32 free poses, 4 iterations)
   grad      16 eight-frame problems: forward, the pose supervision loss of
             Sec. 3.4 on the device, and the backward to targets and weights
+  window    256 sliding windows kept on the device: append a frame to each,
+            then one batched solve
 
 ``--impl reference`` times the FP64 oracle (the reference arm) instead.
 Launch: ``python bench.py --gpus N --steps K --warmup W`` (torchrun for N > 1,
@@ -62,6 +64,7 @@ def parse():
     ap.add_argument("--serving", type=int, default=1, help="run the serving measurement (Poisson sessions)")
     ap.add_argument("--tf32", type=int, default=1, help="also time the opt-in tensor-core Schur mode")
     ap.add_argument("--grad", type=int, default=16, help="problems of the differentiation workload; 0 skips")
+    ap.add_argument("--window", type=int, default=256, help="sliding windows maintained on the device; 0 skips")
     ap.add_argument("--stress", type=int, default=64,
                     help="large-window sessions timed (64 frames, 256 patches each, radius 24, 32 free poses, 4 "
                          "iterations); 0 skips")
@@ -273,6 +276,55 @@ def grad_bench(n_problems=16, steps=20, warmup=3, parity=True):
                          "dL_dtarget_rel_err": float(np.linalg.norm(out[0] - rt.numpy()) / np.linalg.norm(rt.numpy())),
                          "dL_dweight_rel_err": float(np.linalg.norm(out[1] - rw.numpy()) / np.linalg.norm(rw.numpy()))}
     return res
+
+
+def window_bench(n_windows=256, steps=10, warmup=3, seed=0):
+    """Sliding windows kept on the device (Sec. 3.3): n_windows windows of 22
+    frames (96 patches per new frame, radius 13, the last 10 poses free).  A
+    step appends one frame to every window (constant-velocity pose, median
+    depth, the oldest frame dropped, the edges regenerated; one batched call,
+    two launches per 128 windows) and then runs one batched 2-iteration solve over all windows with
+    the regenerated targets revised by N(0, 0.5 px^2) noise."""
+    import torch
+    from paper_2208_04726_b300 import ba
+    rng = np.random.default_rng(seed)
+    intr = (320.0, 320.0, 320.0, 240.0)
+    wins = [ba.Window(22, 96, 13, 10, intr) for _ in range(n_windows)]
+    xy = [torch.tensor(rng.uniform([16, 16], [624, 464], (96, 2)).astype(np.float32), device="cuda")
+          for _ in range(8)]
+    for f in range(22):                               # fill the windows
+        ba.append_windows(wins, [xy[f % 8]] * n_windows)
+    solver = ba.Solver()
+    solver.reserve(22, 2112, 39552, 2, n_windows)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_app, t_solve = [], []
+    statuses = 0
+    for it in range(warmup + steps):
+        ev[0].record()
+        ba.append_windows(wins, [xy[it % 8]] * n_windows)
+        ev[1].record()
+        probs = [w.problem() for w in wins]           # views of the windows' arrays
+        for p in probs:                               # the update operator's revision, simulated
+            p.target.add_(torch.randn_like(p.target), alpha=0.7071)
+        n, dims, cp = solver._arrays(probs)
+        ev[2].record()
+        solver.solve_arrays(dims, cp, n)
+        ev[3].record()
+        torch.cuda.synchronize()
+        if it >= warmup:
+            t_app.append(ev[0].elapsed_time(ev[1]))
+            t_solve.append(ev[2].elapsed_time(ev[3]))
+            statuses += sum(int(p.status.item()) != 0 for p in probs)
+    solver.close()
+    for w in wins:
+        w.close()
+    a, sv = float(np.median(t_app)), float(np.median(t_solve))
+    return {"workload": f"{n_windows} windows of 22 frames x 96 patches per frame, radius 13, last 10 poses free; "
+                        "per step one appended frame per window, then one batched 2-iteration solve",
+            "append_all_ms": a, "append_us_per_window": a * 1e3 / n_windows,
+            "solve_ms": sv, "frames_per_s": n_windows / (a + sv) * 1e3, "statuses_nonzero": statuses,
+            "note": "device time of the batched append call and of the batched solve (CUDA events); the target "
+                    "revision and the host marshalling between them are not counted"}
 
 
 def traffic_from_profiles(kernel_source_sha):
@@ -619,6 +671,7 @@ def main():
     serving = serving_bench() if (rank == 0 and args.serving) else None
     stress = stress_bench(args.stress, 5, stream, load_peaks()[0]) if (rank == 0 and args.stress > 0) else None
     grad = grad_bench(args.grad, parity=args.parity_samples > 0) if (rank == 0 and args.grad > 0) else None
+    window = window_bench(args.window) if (rank == 0 and args.window > 0) else None
 
     if rank == 0:
         line = {
@@ -644,6 +697,7 @@ def main():
             "tf32_schur": tf32,
             "stress": stress,
             "grad": grad,
+            "window": window,
             "gpu_launches": world * n_launch_per_solve * args.steps,
             "clocks": clocks.summary(),
         }

@@ -310,6 +310,62 @@ typedef struct {
 
 int dpvo_ba_pose_loss(const dpvo_ba_pose_loss_problem *probs, int n_problems, void *stream);
 
+/* ---- window maintenance (Sec. 3.3 "Expansion" and "Optimization") -------
+ * A sliding optimisation window kept on the device: frames are appended one at
+ * a time and, once the window holds max_frames frames, the oldest frame leaves
+ * with every patch extracted from it.  Appending a frame (one kernel launch):
+ *   - its pose from the constant-velocity model T_n = T_{n-1} T_{n-2}^-1 T_{n-1}
+ *     (T_n = T_{n-1} for the second frame, identity for the first; FP64
+ *     composition, stored FP32);
+ *   - its patches at the caller's pixel centres, all with the median inverse
+ *     depth of the patches extracted from the previous 3 frames (the lower
+ *     median: rank floor((K - 1) / 2) of the K values; 1 when K = 0);
+ *   - the edges regenerated from the patch graph rule: patch k connects to
+ *     every frame j of the window with |j - anchor_k| <= radius, edges grouped
+ *     by patch, frames increasing (the layout dpvo_ba_solve requires);
+ *   - targets set to the reprojection at the current state (Eq. 2; the patch
+ *     centre for self edges and for points behind the camera), weights to 1:
+ *     the caller overwrites both (the update operator's output) before a solve;
+ *   - t0 = max(0, n_frames - free_poses): the last free_poses poses are free.
+ * The host keeps the per-frame patch counts, so the new sizes are known without
+ * reading the device.  The window's arrays are library-owned device memory;
+ * dpvo_ba_window_problem returns them, valid until the next append or destroy
+ * (poses, inverse depths, targets and weights may be written through them). */
+typedef struct dpvo_ba_window dpvo_ba_window;
+
+typedef struct {
+    int32_t max_frames;       /* frames kept, 1 .. DPVO_BA_MAX_FRAMES                     */
+    int32_t max_new_patches;  /* patches per appended frame, at most (>= 0)               */
+    int32_t radius;           /* graph radius in frames (>= 0)                            */
+    int32_t free_poses;       /* the last free_poses poses are free (>= 0)                */
+    int32_t n_iters;          /* Gauss-Newton iterations recorded in the window's dims    */
+    float fx, fy, cx, cy;     /* pinhole intrinsics (Eq. 3)                               */
+} dpvo_ba_window_params;
+
+/* Create an empty window (device memory for its maximum sizes).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int dpvo_ba_window_create(const dpvo_ba_window_params *params, dpvo_ba_window **out);
+
+/* Free the window's memory (after the work queued on its arrays). */
+int dpvo_ba_window_destroy(dpvo_ba_window *w);
+
+/* Append a frame with n_new patches at DEVICE pixel centres new_xy [n_new][2]
+ * (read).  Asynchronous on stream; the window's earlier work must be ordered
+ * before it (same stream).  Errors: EINVAL (NULL, n_new outside
+ * [0, max_new_patches]), ECUDA. */
+int dpvo_ba_window_append(dpvo_ba_window *w, const float *new_xy, int n_new, void *stream);
+
+/* Append one frame to each of n distinct windows (ws[b] with n_new[b] patches
+ * at DEVICE new_xy[b]); host arrays of length n.  Two launches per 128
+ * windows.  Errors: EINVAL (as dpvo_ba_window_append, or a window listed
+ * twice), ECUDA. */
+int dpvo_ba_window_append_batch(dpvo_ba_window *const *ws, const float *const *new_xy, const int *n_new, int n,
+                                void *stream);
+
+/* The window's current problem: sizes (with t0, n_iters, intrinsics) and its
+ * device arrays (status included).  Errors: EINVAL (NULL, empty window). */
+int dpvo_ba_window_problem(const dpvo_ba_window *w, dpvo_ba_dims *dims, dpvo_ba_problem *prob);
+
 /* Human-readable name of a return code. */
 const char *dpvo_ba_strerror(int code);
 

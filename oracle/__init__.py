@@ -18,6 +18,9 @@ Contents
 ``pose_loss``     FP64 pose supervision loss of Sec. 3.4 (Eq. 7): a matrix-logarithm
                   form with central-difference gradients, and a differentiable torch
                   form for the gradient through the unrolled twin.
+``window``        the sliding optimisation window of Sec. 3.3 (constant-velocity pose,
+                  median-depth patches, dropping the oldest frame, the patch-graph
+                  edges and their reprojection targets), in numpy.
 
 Parity unpinned: nothing here is checked against the authors' implementation,
 which is not available; every pin is mathematical (finite differences, exact

@@ -40,6 +40,12 @@ class PoseLossProblem(ctypes.Structure):
                 ("dL_dposes", ctypes.c_void_p), ("n_frames", ctypes.c_int32), ("scale", ctypes.c_float)]
 
 
+class WindowParams(ctypes.Structure):
+    _fields_ = [("max_frames", ctypes.c_int32), ("max_new_patches", ctypes.c_int32), ("radius", ctypes.c_int32),
+                ("free_poses", ctypes.c_int32), ("n_iters", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("poses", ctypes.c_void_p), ("patches", ctypes.c_void_p), ("anchor", ctypes.c_void_p),
                 ("kk", ctypes.c_void_p), ("jj", ctypes.c_void_p), ("target", ctypes.c_void_p),
@@ -55,7 +61,9 @@ EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solv
            "dpvo_ba_reduced_system", "dpvo_ba_iterate", "dpvo_ba_set_timing", "dpvo_ba_timing",
            "dpvo_ba_solve_noalloc", "dpvo_ba_backward", "dpvo_ba_serve_start",
            "dpvo_ba_serve_stop", "dpvo_ba_session_open", "dpvo_ba_session_close", "dpvo_ba_session_read",
-           "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror", "dpvo_ba_pose_loss"]
+           "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror", "dpvo_ba_pose_loss",
+           "dpvo_ba_window_create", "dpvo_ba_window_destroy", "dpvo_ba_window_append", "dpvo_ba_window_problem",
+           "dpvo_ba_window_append_batch"]
 
 _lib = None
 
@@ -97,6 +105,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_wait.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(ctypes.c_int32),
                                  ctypes.POINTER(ctypes.c_double)]
     lib.dpvo_ba_pose_loss.argtypes = [ctypes.POINTER(PoseLossProblem), i32, vp]
+    lib.dpvo_ba_window_create.argtypes = [ctypes.POINTER(WindowParams), ctypes.POINTER(vp)]
+    lib.dpvo_ba_window_destroy.argtypes = [vp]
+    lib.dpvo_ba_window_append.argtypes = [vp, vp, i32, vp]
+    lib.dpvo_ba_window_problem.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem)]
+    lib.dpvo_ba_window_append_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32), i32, vp]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -426,6 +439,78 @@ def pose_loss(poses, gt_poses, scale=1.0, stream=None):
                                    T.shape[0], scales[b])
     _check(lib.dpvo_ba_pose_loss(descs, B, ctypes.c_void_p(_stream_ptr(stream))), "dpvo_ba_pose_loss")
     return loss, grads
+
+
+class _DeviceArray:
+    """A view of library-owned device memory for torch.as_tensor (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class Window:
+    """Sliding optimisation window kept on the device (Sec. 3.3; dpvo_ba_window_*).
+
+    append(new_xy) adds a frame with patches at the given pixel centres (a
+    [n, 2] float32 CUDA tensor): constant-velocity pose, median inverse depth
+    of the previous 3 frames' patches, the oldest frame dropped when full, the
+    edges regenerated.  problem() returns the current BAProblem whose tensors
+    view the library's arrays (valid until the next append)."""
+
+    def __init__(self, max_frames, max_new_patches, radius, free_poses, intrinsics, n_iters=2):
+        self.lib = load()
+        fx, fy, cx, cy = (float(v) for v in intrinsics)
+        self.params = WindowParams(max_frames, max_new_patches, radius, free_poses, n_iters, fx, fy, cx, cy)
+        h = ctypes.c_void_p()
+        _check(self.lib.dpvo_ba_window_create(ctypes.byref(self.params), ctypes.byref(h)), "dpvo_ba_window_create")
+        self.h = h
+
+    def append(self, new_xy, stream=None):
+        xy = new_xy.detach().to(torch.float32).contiguous() if new_xy is not None else None
+        n = 0 if xy is None else int(xy.shape[0])
+        ptr = ctypes.c_void_p(xy.data_ptr() if n > 0 else 0)
+        self._keep = xy
+        _check(self.lib.dpvo_ba_window_append(self.h, ptr, n, ctypes.c_void_p(_stream_ptr(stream))),
+               "dpvo_ba_window_append")
+
+    def problem(self) -> BAProblem:
+        d, p = Dims(), Problem()
+        _check(self.lib.dpvo_ba_window_problem(self.h, ctypes.byref(d), ctypes.byref(p)), "dpvo_ba_window_problem")
+        N, P, E = d.n_frames, d.n_patches, d.n_edges
+
+        def view(ptr, shape, ts):
+            return torch.as_tensor(_DeviceArray(ptr, shape, ts), device="cuda")
+        return BAProblem(view(p.poses, (N, 7), "<f4"), view(p.patches, (P, 3), "<f4"), view(p.anchor, (P,), "<i4"),
+                         view(p.kk, (E,), "<i4"), view(p.jj, (E,), "<i4"), view(p.target, (E, 2), "<f4"),
+                         view(p.weight, (E, 2), "<f4"), (d.fx, d.fy, d.cx, d.cy), d.t0, d.n_iters,
+                         status=view(p.status, (1,), "<i4"))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dpvo_ba_window_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def append_windows(windows, new_xy, stream=None):
+    """Append one frame to each window in one batched call
+    (dpvo_ba_window_append_batch); new_xy: one [n_b, 2] CUDA tensor per window."""
+    lib = load()
+    n = len(windows)
+    xs = [x.detach().to(torch.float32).contiguous() for x in new_xy]
+    hs = (ctypes.c_void_p * max(n, 1))(*[w.h for w in windows])
+    ps = (ctypes.c_void_p * max(n, 1))(*[x.data_ptr() if x.shape[0] else 0 for x in xs])
+    ns = (ctypes.c_int32 * max(n, 1))(*[int(x.shape[0]) for x in xs])
+    for w, x in zip(windows, xs):
+        w._keep = x
+    _check(lib.dpvo_ba_window_append_batch(hs, ps, ns, n, ctypes.c_void_p(_stream_ptr(stream))),
+           "dpvo_ba_window_append_batch")
 
 
 def default_solver() -> Solver:
