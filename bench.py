@@ -24,6 +24,9 @@ Also measured and reported on the same JSON line:
             Sec. 3.4 on the device, and the backward to targets and weights
   window    256 sliding windows kept on the device: append a frame to each,
             then one batched solve
+  vo_mix    the paper's Default and Fast configurations as one mix of 256
+            sliding-window sessions: initialisation (8 frames, 12 solves),
+            then frames
 
 ``--impl reference`` times the FP64 oracle (the reference arm) instead.
 Launch: ``python bench.py --gpus N --steps K --warmup W`` (torchrun for N > 1,
@@ -65,6 +68,7 @@ def parse():
     ap.add_argument("--tf32", type=int, default=1, help="also time the opt-in tensor-core Schur mode")
     ap.add_argument("--grad", type=int, default=16, help="problems of the differentiation workload; 0 skips")
     ap.add_argument("--window", type=int, default=256, help="sliding windows maintained on the device; 0 skips")
+    ap.add_argument("--vo-mix", type=int, default=1, help="the Default/Fast serving mix with initialisation; 0 skips")
     ap.add_argument("--stress", type=int, default=64,
                     help="large-window sessions timed (64 frames, 256 patches each, radius 24, 32 free poses, 4 "
                          "iterations); 0 skips")
@@ -325,6 +329,72 @@ def window_bench(n_windows=256, steps=10, warmup=3, seed=0):
             "solve_ms": sv, "frames_per_s": n_windows / (a + sv) * 1e3, "statuses_nonzero": statuses,
             "note": "device time of the batched append call and of the batched solve (CUDA events); the target "
                     "revision and the host marshalling between them are not counted"}
+
+
+def vo_mix_bench(n_default=128, n_fast=128, steps=10, warmup=3, seed=1):
+    """The paper's two configurations as one serving mix on device-maintained
+    windows (Sec. 4: Default 96 patches/frame and 10 free poses, Fast 48 and 7;
+    radius 13, 22-frame buffers).  Initialisation (Sec. 3.3): every session
+    accumulates 8 frames and runs 12 update iterations, each a 2-iteration
+    solve on revised targets, batched over all sessions.  Steady state: per
+    step one appended frame per session and one mixed batched solve.  Device
+    time by CUDA events (target revision and host marshalling not counted)."""
+    import torch
+    from paper_2208_04726_b300 import ba
+    rng = np.random.default_rng(seed)
+    intr = (320.0, 320.0, 320.0, 240.0)
+    kinds = [(96, 10)] * n_default + [(48, 7)] * n_fast
+    wins = [ba.Window(22, m, 13, f, intr) for m, f in kinds]
+    xy = {m: [torch.tensor(rng.uniform([16, 16], [624, 464], (m, 2)).astype(np.float32), device="cuda")
+              for _ in range(8)] for m in (96, 48)}
+    solver = ba.Solver()
+    solver.reserve(22, 2112, 39552, 2, len(wins))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def solve_all():
+        probs = [w.problem() for w in wins]
+        for p in probs:
+            p.target.add_(torch.randn_like(p.target), alpha=0.7071)
+        n, dims, cp = solver._arrays(probs)
+        ev[2].record()
+        solver.solve_arrays(dims, cp, n)
+        ev[3].record()
+        torch.cuda.synchronize()
+        return ev[2].elapsed_time(ev[3]), sum(int(p.status.item()) != 0 for p in probs)
+
+    # initialisation: 8 frames, then 12 update iterations
+    t_init, bad = 0.0, 0
+    for f in range(8):
+        ev[0].record()
+        ba.append_windows(wins, [xy[m][f] for m, _ in kinds])
+        ev[1].record()
+        torch.cuda.synchronize()
+        t_init += ev[0].elapsed_time(ev[1])
+    for _ in range(12):
+        t, b = solve_all()
+        t_init += t
+        bad += b
+    # steady state
+    t_app, t_solve = [], []
+    for it in range(warmup + steps):
+        ev[0].record()
+        ba.append_windows(wins, [xy[m][it % 8] for m, _ in kinds])
+        ev[1].record()
+        torch.cuda.synchronize()
+        t, b = solve_all()
+        if it >= warmup:
+            t_app.append(ev[0].elapsed_time(ev[1]))
+            t_solve.append(t)
+            bad += b
+    solver.close()
+    for w in wins:
+        w.close()
+    a, sv = float(np.median(t_app)), float(np.median(t_solve))
+    return {"workload": f"{n_default} Default (96 patches/frame, 10 free poses) + {n_fast} Fast (48, 7) sessions, "
+                       "radius 13, 22-frame windows, 2 GN iterations per solve",
+            "init_ms": t_init, "init_note": "8 appended frames, then 12 batched 2-iteration solves, all sessions",
+            "append_all_ms": a, "solve_ms": sv, "frames_per_s": len(wins) / (a + sv) * 1e3,
+            "statuses_nonzero": bad}
 
 
 def traffic_from_profiles(kernel_source_sha):
@@ -672,6 +742,7 @@ def main():
     stress = stress_bench(args.stress, 5, stream, load_peaks()[0]) if (rank == 0 and args.stress > 0) else None
     grad = grad_bench(args.grad, parity=args.parity_samples > 0) if (rank == 0 and args.grad > 0) else None
     window = window_bench(args.window) if (rank == 0 and args.window > 0) else None
+    vo_mix = vo_mix_bench() if (rank == 0 and args.vo_mix) else None
 
     if rank == 0:
         line = {
@@ -698,6 +769,7 @@ def main():
             "stress": stress,
             "grad": grad,
             "window": window,
+            "vo_mix": vo_mix,
             "gpu_launches": world * n_launch_per_solve * args.steps,
             "clocks": clocks.summary(),
         }

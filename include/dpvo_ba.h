@@ -326,7 +326,9 @@ int dpvo_ba_pose_loss(const dpvo_ba_pose_loss_problem *probs, int n_problems, vo
  *   - targets set to the reprojection at the current state (Eq. 2; the patch
  *     centre for self edges and for points behind the camera), weights to 1:
  *     the caller overwrites both (the update operator's output) before a solve;
- *   - t0 = max(0, n_frames - free_poses): the last free_poses poses are free.
+ *   - t0 = min(n_frames, max(2, n_frames - free_poses)): the last free_poses
+ *     poses are free, but the first two always stay fixed (gauge and
+ *     monocular scale; with fewer fixed poses S is singular).
  * The host keeps the per-frame patch counts, so the new sizes are known without
  * reading the device.  The window's arrays are library-owned device memory;
  * dpvo_ba_window_problem returns them, valid until the next append or destroy

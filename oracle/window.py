@@ -16,7 +16,8 @@ Appending a frame to a window of at most ``max_frames`` frames:
    |j - anchor_k| <= radius, grouped by patch, frames increasing;
 5. targets at the reprojection of Eq. 2 at the current state (the patch
    centre for self edges and for points behind the camera), weights 1;
-6. t0 = max(0, n_frames - free_poses).
+6. t0 = min(n_frames, max(2, n_frames - free_poses)): the first two poses stay
+   fixed (gauge and monocular scale).
 """
 from __future__ import annotations
 
@@ -107,4 +108,4 @@ class WindowOracle:
         return out
 
     def t0(self):
-        return max(0, len(self.poses) - self.free)
+        return min(len(self.poses), max(2, len(self.poses) - self.free))

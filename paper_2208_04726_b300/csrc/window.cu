@@ -350,9 +350,12 @@ extern "C" int dpvo_ba_window_append(dpvo_ba_window *w, const float *new_xy, int
 
 extern "C" int dpvo_ba_window_problem(const dpvo_ba_window *w, dpvo_ba_dims *dims, dpvo_ba_problem *prob) {
     if (!w || !dims || !prob || w->N == 0) return DPVO_BA_EINVAL;
-    const int t0 = w->N - w->prm.free_poses;
-    *dims = dpvo_ba_dims{w->N, w->P, w->E, t0 > 0 ? t0 : 0, w->prm.n_iters, w->prm.fx, w->prm.fy, w->prm.cx,
-                         w->prm.cy};
+    // the last free_poses poses are free, but at least the first two stay fixed (gauge and
+    // monocular scale), all of them while the window has fewer than three frames
+    int t0 = w->N - w->prm.free_poses;
+    t0 = t0 < 2 ? 2 : t0;
+    t0 = t0 > w->N ? w->N : t0;
+    *dims = dpvo_ba_dims{w->N, w->P, w->E, t0, w->prm.n_iters, w->prm.fx, w->prm.fy, w->prm.cx, w->prm.cy};
     *prob = dpvo_ba_problem{w->pose[w->cur], w->patch[w->cur], w->anchor[w->cur], w->kk, w->jj, w->target,
                             w->weight, w->status};
     return 0;
