@@ -27,6 +27,8 @@ Also measured and reported on the same JSON line:
   vo_mix    the paper's Default and Fast configurations as one mix of 256
             sliding-window sessions: initialisation (8 frames, 12 solves),
             then frames
+  corr      the correlation features (Sec. 3.2) of every edge of the window
+            graph on the tensor cores
 
 ``--impl reference`` times the FP64 oracle (the reference arm) instead.
 Launch: ``python bench.py --gpus N --steps K --warmup W`` (torchrun for N > 1,
@@ -69,6 +71,7 @@ def parse():
     ap.add_argument("--grad", type=int, default=16, help="problems of the differentiation workload; 0 skips")
     ap.add_argument("--window", type=int, default=256, help="sliding windows maintained on the device; 0 skips")
     ap.add_argument("--vo-mix", type=int, default=1, help="the Default/Fast serving mix with initialisation; 0 skips")
+    ap.add_argument("--corr", type=int, default=1, help="the correlation features of the window graph; 0 skips")
     ap.add_argument("--stress", type=int, default=64,
                     help="large-window sessions timed (64 frames, 256 patches each, radius 24, 32 free poses, 4 "
                          "iterations); 0 skips")
@@ -395,6 +398,62 @@ def vo_mix_bench(n_default=128, n_fast=128, steps=10, warmup=3, seed=1):
             "init_ms": t_init, "init_note": "8 appended frames, then 12 batched 2-iteration solves, all sessions",
             "append_all_ms": a, "solve_ms": sv, "frames_per_s": len(wins) / (a + sv) * 1e3,
             "statuses_nonzero": bad}
+
+
+def corr_bench(steps=20, warmup=3, seed=7, hbm_peak=6400.0, parity=True):
+    """Correlation features (Sec. 3.2, Eq. 4) of the sliding-window graph: 22
+    frames of 120 x 160 x 128 bfloat16 matching features (a quarter of a 640 x
+    480 image), level 1 pooled by 4, 2112 patches of 3 x 3 pixels, radius 13
+    (39,552 edges), 7 x 7 grids at both levels.  One call = every edge.  Device
+    time by CUDA events; flops as executed by the tensor cores (footprint x 16
+    patch-pixel GEMMs) and as defined (49 bilinear samples per pixel and
+    level); bytes = the inputs read once and the outputs written."""
+    import torch
+    from paper_2208_04726_b300 import ba
+    from paper_2208_04726_b300 import corr_inputs as CI
+    inp = CI.make_corr_inputs(22, 96, 13, 120, 160, 4, seed)
+    bf = lambda a: torch.from_numpy(a.view(np.int16)).view(torch.bfloat16).cuda()
+    args = (bf(inp.fmap0), bf(inp.fmap1), bf(inp.gpatch), torch.from_numpy(inp.kk).cuda(),
+            torch.from_numpy(inp.jj).cuda(), torch.from_numpy(inp.coords).cuda())
+    out = torch.empty((inp.n_edges, 2, 9, 7, 7), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(warmup):
+        ba.correlation(*args, inp.scale, out=out, status=st)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        ba.correlation(*args, inp.scale, out=out, status=st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    E = inp.n_edges
+    # footprint chunks per edge and level, from the coordinates (as the kernel forms them)
+    fl_exec = 0.0
+    for s_ in (1.0, float(inp.scale)):
+        xy = np.floor(inp.coords.astype(np.float32) / np.float32(s_))
+        w = xy[:, :, 0].max(1) - xy[:, :, 0].min(1) + 8
+        h = xy[:, :, 1].max(1) - xy[:, :, 1].min(1) + 8
+        fl_exec += float(np.sum(np.ceil(w * h / 128.0))) * 128 * 16 * 128 * 2
+    fl_def = E * 2 * 9 * 49 * (128 * 2 + 4 * 128 * 2)
+    byts = (inp.fmap0.nbytes + inp.fmap1.nbytes + inp.gpatch.nbytes + inp.kk.nbytes + inp.jj.nbytes
+            + inp.coords.nbytes + out.numel() * 4)
+    res = {"workload": "22 frames x 120 x 160 x 128 bf16 features (level 1 pooled by 4), 2112 patches of 3 x 3, "
+                       "radius 13 (39,552 edges), 7 x 7 grids at 2 levels",
+           "ms_per_call": ms, "edges_per_s": E / ms * 1e3,
+           "tensor_tflops_executed": fl_exec / ms / 1e9, "tflops_by_definition": fl_def / ms / 1e9,
+           "hbm": {"bytes_per_call": byts, "achieved_gbs": byts / ms / 1e6, "peak_gbs": hbm_peak,
+                   "frac": byts / ms / 1e6 / hbm_peak},
+           "status": int(st.item())}
+    if parity:
+        from oracle import corr as C
+        edges = np.random.default_rng(0).choice(E, 32, replace=False)
+        ref = C.correlation(inp, edges)
+        got = out.cpu().numpy()[edges].astype(np.float64)
+        res["parity"] = {"edges_checked": 32, "max_abs_err": float(np.abs(got - ref).max()),
+                         "rel_err": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                         "tolerance": "1e-3 abs, 1e-5 rel"}
+    return res
 
 
 def traffic_from_profiles(kernel_source_sha):
@@ -743,6 +802,7 @@ def main():
     grad = grad_bench(args.grad, parity=args.parity_samples > 0) if (rank == 0 and args.grad > 0) else None
     window = window_bench(args.window) if (rank == 0 and args.window > 0) else None
     vo_mix = vo_mix_bench() if (rank == 0 and args.vo_mix) else None
+    corr = corr_bench(hbm_peak=load_peaks()[0], parity=args.parity_samples > 0) if (rank == 0 and args.corr) else None
 
     if rank == 0:
         line = {
@@ -770,6 +830,7 @@ def main():
             "grad": grad,
             "window": window,
             "vo_mix": vo_mix,
+            "corr": corr,
             "gpu_launches": world * n_launch_per_solve * args.steps,
             "clocks": clocks.summary(),
         }

@@ -368,6 +368,47 @@ int dpvo_ba_window_append_batch(dpvo_ba_window *const *ws, const float *const *n
  * device arrays (status included).  Errors: EINVAL (NULL, empty window). */
 int dpvo_ba_window_problem(const dpvo_ba_window *w, dpvo_ba_dims *dims, dpvo_ba_problem *prob);
 
+/* ---- correlation features (Sec. 3.2 "Correlation", Eq. 4; Appendix
+ * "Correlation Operation") -----------------------------------------------------
+ * For every edge (k, j) and every pixel (u, v) of patch k's p x p grid, the
+ * inner products of its feature vector g_uv with frame j's features bilinearly
+ * sampled on the 7 x 7 integer grid around the pixel's reprojection, at both
+ * pyramid levels:
+ *   C[e][l][uv][a][b] = < g_uv , f_l( P'_kj(u, v) / s_l + (a - 3, b - 3) ) >
+ * with s_0 = 1, s_1 = level1_scale.  Coordinates are in level-0 feature-map
+ * pixels (x along the width), pixel centres at integers; bilinear sampling
+ * reads zero outside the map.  By linearity each 7 x 7 grid is a bilinear
+ * combination of the 8 x 8 integer-pixel inner products around it; those are
+ * computed for the bounding box of the patch's 9 windows as one small GEMM on
+ * the tensor cores (tcgen05, BF16 operands, FP32 accumulators in TMEM).
+ * All pointers DEVICE, caller-owned:
+ *   fmap0   [N][H0][W0][128] bf16  level-0 matching features            (read)
+ *   fmap1   [N][H1][W1][128] bf16  level 1, H1 = H0 / s, W1 = W0 / s     (read)
+ *   gpatch  [P][9][128] bf16       patch features, pixel uv = 3 u + v      (read)
+ *   kk, jj  [E] int32              patch and frame of each edge            (read)
+ *   coords  [E][9][2] float        P'_kj(u, v) as (x, y), level-0 pixels  (read)
+ *   corr    [E][2][9][7][7] float  the correlation features               (written)
+ *   status  [1] int32              bits OR-ed in: DPVO_BA_STATUS_BAD_INPUT for an
+ *                                  edge whose kk or jj is out of range (its
+ *                                  output is zero), DPVO_BA_STATUS_TIMEOUT if
+ *                                  a bounded wait ran out (the outputs from
+ *                                  then on are zero)                       (read, OR-ed)
+ * An edge-level whose coordinates are not finite or beyond 1e4 gets zeros;
+ * one whose 9 windows span more than 4 x 128 pixels is computed on the CUDA
+ * cores instead.  Asynchronous on stream.
+ * Errors: EINVAL (NULL, sizes out of range: maps of 1 .. 4096 pixels per side,
+ * level1_scale >= 1, at least one frame), ECUDA. */
+#define DPVO_BA_CORR_DIM 128
+typedef struct {
+    int32_t n_frames, n_patches, n_edges;
+    int32_t height, width;       /* level-0 map H0 x W0                                  */
+    int32_t level1_scale;        /* level 1 = level 0 average-pooled by this factor (4)  */
+} dpvo_ba_corr_dims;
+
+int dpvo_ba_correlation(const dpvo_ba_corr_dims *dims, const void *fmap0, const void *fmap1, const void *gpatch,
+                        const int32_t *kk, const int32_t *jj, const float *coords, float *corr, int32_t *status,
+                        void *stream);
+
 /* Human-readable name of a return code. */
 const char *dpvo_ba_strerror(int code);
 

@@ -18,6 +18,8 @@ Contents
 ``pose_loss``     FP64 pose supervision loss of Sec. 3.4 (Eq. 7): a matrix-logarithm
                   form with central-difference gradients, and a differentiable torch
                   form for the gradient through the unrolled twin.
+``corr``          the correlation features of Sec. 3.2 (Eq. 4): the definition written out,
+                  and the correlation-volume form the paper names as equivalent.
 ``window``        the sliding optimisation window of Sec. 3.3 (constant-velocity pose,
                   median-depth patches, dropping the oldest frame, the patch-graph
                   edges and their reprojection targets), in numpy.

@@ -46,6 +46,11 @@ class WindowParams(ctypes.Structure):
                 ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
 
 
+class CorrDims(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int32), ("n_patches", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("width", ctypes.c_int32), ("level1_scale", ctypes.c_int32)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("poses", ctypes.c_void_p), ("patches", ctypes.c_void_p), ("anchor", ctypes.c_void_p),
                 ("kk", ctypes.c_void_p), ("jj", ctypes.c_void_p), ("target", ctypes.c_void_p),
@@ -63,7 +68,7 @@ EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solv
            "dpvo_ba_serve_stop", "dpvo_ba_session_open", "dpvo_ba_session_close", "dpvo_ba_session_read",
            "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror", "dpvo_ba_pose_loss",
            "dpvo_ba_window_create", "dpvo_ba_window_destroy", "dpvo_ba_window_append", "dpvo_ba_window_problem",
-           "dpvo_ba_window_append_batch"]
+           "dpvo_ba_window_append_batch", "dpvo_ba_correlation"]
 
 _lib = None
 
@@ -109,6 +114,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_window_destroy.argtypes = [vp]
     lib.dpvo_ba_window_append.argtypes = [vp, vp, i32, vp]
     lib.dpvo_ba_window_problem.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem)]
+    lib.dpvo_ba_correlation.argtypes = [ctypes.POINTER(CorrDims), vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dpvo_ba_window_append_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32), i32, vp]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
@@ -511,6 +517,29 @@ def append_windows(windows, new_xy, stream=None):
         w._keep = x
     _check(lib.dpvo_ba_window_append_batch(hs, ps, ns, n, ctypes.c_void_p(_stream_ptr(stream))),
            "dpvo_ba_window_append_batch")
+
+
+def correlation(fmap0, fmap1, gpatch, kk, jj, coords, level1_scale, out=None, status=None, stream=None):
+    """Correlation features of every edge (Sec. 3.2, Eq. 4; dpvo_ba_correlation).
+
+    fmap0 [N, H0, W0, 128] and fmap1 [N, H1, W1, 128] bfloat16 CUDA tensors,
+    gpatch [P, 9, 128] bfloat16, kk/jj [E] int32, coords [E, 9, 2] float32
+    (level-0 pixels).  Returns (corr [E, 2, 9, 7, 7] float32, status [1] int32)."""
+    lib = load()
+    N, H, W, D = fmap0.shape
+    E = int(kk.shape[0])
+    if D != 128 or fmap0.dtype != torch.bfloat16 or fmap1.dtype != torch.bfloat16 or gpatch.dtype != torch.bfloat16:
+        raise ValueError("feature maps and patch features must be bfloat16 with 128 channels")
+    for t in (fmap0, fmap1, gpatch, kk, jj, coords):
+        if not t.is_contiguous():
+            raise ValueError("inputs must be contiguous")
+    out = torch.empty((E, 2, 9, 7, 7), dtype=torch.float32, device=fmap0.device) if out is None else out
+    status = torch.zeros(1, dtype=torch.int32, device=fmap0.device) if status is None else status
+    d = CorrDims(N, int(gpatch.shape[0]), E, H, W, int(level1_scale))
+    _check(lib.dpvo_ba_correlation(ctypes.byref(d), fmap0.data_ptr(), fmap1.data_ptr(), gpatch.data_ptr(),
+                                   kk.data_ptr(), jj.data_ptr(), coords.data_ptr(), out.data_ptr(),
+                                   status.data_ptr(), ctypes.c_void_p(_stream_ptr(stream))), "dpvo_ba_correlation")
+    return out, status
 
 
 def default_solver() -> Solver:

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libdpvo_ba.so")
-SOURCES = [os.path.join(CSRC, f) for f in ("dpvo_ba.cu", "pose_loss.cu", "window.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("dpvo_ba.cu", "pose_loss.cu", "window.cu", "corr.cu")]
 DEPENDS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [
     os.path.join(ROOT, "include", "dpvo_ba.h")]
 
