@@ -32,8 +32,9 @@ constexpr int kD = DPVO_BA_CORR_DIM;            // channels
 constexpr int kQ = 9;                           // patch pixels (3 x 3)
 constexpr int kChunk = 128;                     // footprint pixels per MMA (M)
 constexpr int kN = 16;                          // patch pixels padded (N)
-constexpr int kMaxChunks = 4;
-constexpr uint32_t kSbo = (kD / 8) * kLbo;      // bytes between 8-row groups (16 core matrices of K)
+constexpr int kMaxChunks = 2;                   // general path: footprints up to 256 pixels on the tensor cores
+constexpr uint32_t kSbo = (kD / 8) * kLbo + 16; // bytes between 8-row groups (16 core matrices of K, +16 so
+                                                 // that the row groups a warp writes fall in distinct banks)
 constexpr uint32_t kAbytes = (kChunk / 8) * kSbo, kBbytes = (kN / 8) * kSbo;
 constexpr int kDld = 17;                        // row stride (floats) of the accumulator copy
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
@@ -73,25 +74,129 @@ struct Args {
     float scale1;
 };
 
+// Per-edge plan, double-buffered across the pipeline: patch, frame, the two
+// levels' coordinates and footprint boxes, and the edge's mode.
+enum Mode { kZero = 0, kFast = 1, kGeneral = 2, kBadIndex = 3 };
+struct Plan {
+    float xy[2][kQ][2];
+    int box[2][4];                               // fx0, fy0, w, h per level
+    int k, j, mode;
+};
+
+// Warp 0: plan edge e (coordinates, boxes, mode).
+__device__ void plan_edge(const Args &A, int e, Plan &P, int lane) {
+    const int k = A.kk[e], j = A.jj[e];
+    const bool valid = k >= 0 && k < A.P && j >= 0 && j < A.N;
+    bool finite = true;
+    int npix[2] = {0, 0};
+    for (int l = 0; l < 2; ++l) {
+        const float s = l == 0 ? 1.f : A.scale1;
+        float xs = 0.f, ys = 0.f;
+        if (lane < kQ) {
+            xs = A.coords[((size_t)e * kQ + lane) * 2] / s;
+            ys = A.coords[((size_t)e * kQ + lane) * 2 + 1] / s;
+            P.xy[l][lane][0] = xs;
+            P.xy[l][lane][1] = ys;
+        }
+        const bool ok = lane >= kQ || (fabsf(xs) <= kCoordMax && fabsf(ys) <= kCoordMax);
+        finite = finite && __all_sync(0xffffffffu, ok);
+        const int xi = lane < kQ && ok ? (int)floorf(xs) : 0, yi = lane < kQ && ok ? (int)floorf(ys) : 0;
+        const int x0 = __reduce_min_sync(0xffffffffu, lane < kQ ? xi : 0x7fffffff);
+        const int x1 = __reduce_max_sync(0xffffffffu, lane < kQ ? xi : -0x7fffffff);
+        const int y0 = __reduce_min_sync(0xffffffffu, lane < kQ ? yi : 0x7fffffff);
+        const int y1 = __reduce_max_sync(0xffffffffu, lane < kQ ? yi : -0x7fffffff);
+        if (lane == 0) {
+            P.box[l][0] = x0 - 3;
+            P.box[l][1] = y0 - 3;
+            P.box[l][2] = x1 - x0 + 8;
+            P.box[l][3] = y1 - y0 + 8;
+        }
+        npix[l] = (x1 - x0 + 8) * (y1 - y0 + 8);
+    }
+    if (lane == 0) {
+        P.k = k;
+        P.j = j;
+        P.mode = !valid ? kBadIndex : !finite ? kZero : (npix[0] <= kChunk && npix[1] <= kChunk) ? kFast : kGeneral;
+    }
+}
+
+// All threads: stage a footprint chunk (rows t = t0 .. t0 + 127 of the box) of
+// map fm into the operand at aOp, one row (pixel: 16 copies of 8 channels) per
+// thread; rows outside the box or the map are zero.
+__device__ __forceinline__ void stage_footprint(uint32_t aOp, const uint16_t *fm, int H, int W, const int *box,
+                                                int t0, int tid) {
+    const int w = box[2], npix = w * box[3];
+    for (int r = tid; r < kChunk; r += kThreads) {
+        const int t = t0 + r;
+        const int py = box[1] + t / w, px = box[0] + t % w;
+        const bool in = t < npix && py >= 0 && py < H && px >= 0 && px < W;
+        const uint16_t *src = in ? fm + ((size_t)py * W + px) * kD : fm;
+        const uint32_t dst = aOp + (uint32_t)(r >> 3) * kSbo + (uint32_t)(r & 7) * 16u, nb = in ? 16u : 0u;
+#pragma unroll
+        for (int g = 0; g < kD / 8; ++g) cp16(dst + g * kLbo, src + (in ? 8 * g : 0), nb);
+    }
+}
+
+__device__ __forceinline__ void stage_patch(uint32_t aB, const uint16_t *gpatch, int k, int tid) {
+    for (int idx = tid; idx < kQ * (kD / 8); idx += kThreads) {
+        const int r = idx / (kD / 8), g = idx % (kD / 8);
+        cp16(aB + op_off(r, 8 * g), gpatch + ((size_t)k * kQ + r) * kD + 8 * g, 16u);
+    }
+}
+
+// The 7 outputs b = 0..6 of grid row a, patch pixel q, level l, from an
+// accumulator copy D (row t of the footprint at D[t * kDld + q]) or from
+// per-pixel 8 x 8 windows (Dw[64 q + 8 m + n]), to out[0..6].
+__device__ __forceinline__ void bilinear_row(const Plan &P, int l, int q, int a, const float *D, const float *Dw,
+                                             float *out) {
+    const float x = P.xy[l][q][0], y = P.xy[l][q][1];
+    const float xf = floorf(x), yf = floorf(y), wx = x - xf, wy = y - yf;
+    float r0[8], r1[8];                           // window rows a and a + 1, columns 0..7
+    if (D) {
+        const int w = P.box[l][2];
+        const int t = ((int)yf - 3 + a - P.box[l][1]) * w + ((int)xf - 3 - P.box[l][0]);
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            r0[n] = D[(t + n) * kDld + q];
+            r1[n] = D[(t + w + n) * kDld + q];
+        }
+    } else {
+        const float *Dq = Dw + 64 * q + 8 * a;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+            r0[n] = Dq[n];
+            r1[n] = Dq[8 + n];
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 7; ++b)
+        out[b] = (1.f - wy) * ((1.f - wx) * r0[b] + wx * r0[b + 1]) + wy * ((1.f - wx) * r1[b] + wx * r1[b + 1]);
+}
+
+// One CTA of 4 warps takes edges blockIdx.x, + gridDim.x, ...  Fast edges
+// (both levels' footprints within one 128-pixel chunk): both footprints and the
+// patch are staged together, the two GEMMs run under one commit, and the next
+// edge's copies are issued before this edge's epilogue.  Other edges: level by
+// level, chunk by chunk, or on the CUDA cores when the footprint exceeds
+// kMaxChunks chunks.
 __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *opA = smem, *opB = smem + kAbytes;
-    float *Dbuf = reinterpret_cast<float *>(smem + kAbytes + kBbytes);   // kMaxChunks * kChunk x kDld
+    unsigned char *opA0 = smem, *opA1 = smem + kAbytes, *opB = smem + 2 * kAbytes;
+    float *Dfast = reinterpret_cast<float *>(smem + 2 * kAbytes + kBbytes);   // [2][kChunk][kDld]
+    float *Dgen = reinterpret_cast<float *>(opA1);                             // general path, over A1
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
-    __shared__ float s_xy[kQ][2];
-    __shared__ int s_box[6];                     // fx0, fy0, w, h, mode (0 zeros, 1 tensor, 2 CUDA cores), nchunk
+    __shared__ Plan s_plan[2];
     __shared__ int s_bad, s_badin;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t aA = smem_u32(opA), aB = smem_u32(opB), mbar = smem_u32(&s_mbar);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t aA0 = smem_u32(opA0), aA1 = smem_u32(opA1), aB = smem_u32(opB), mbar = smem_u32(&s_mbar);
     if (warp == 0) dpvo::tmem_alloc(&s_tmem, 32);
     if (tid == 0) {
         dpvo::mbar_init(mbar, 1);
         s_bad = 0;
         s_badin = 0;
     }
-    // rows 9..15 of the B operand stay zero
-    for (int idx = tid; idx < (kN - kQ) * (kD / 8); idx += kThreads) {
+    for (int idx = tid; idx < (kN - kQ) * (kD / 8); idx += kThreads) {   // rows 9..15 of B stay zero
         const int r = kQ + idx / (kD / 8), g = idx % (kD / 8);
         *reinterpret_cast<uint4 *>(opB + op_off(r, 8 * g)) = make_uint4(0u, 0u, 0u, 0u);
     }
@@ -99,136 +204,152 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
     __syncthreads();
     dpvo::tc_fence_after();
     const uint32_t tmem = s_tmem;
-    int n_commit = 0;
+    int n_commit = 0, slot = 0;
 
-    for (int e = blockIdx.x; e < A.E; e += gridDim.x) {
-        const int k = A.kk[e], j = A.jj[e];
-        const bool valid = k >= 0 && k < A.P && j >= 0 && j < A.N;   // the same in every thread
-        if (!valid) {
-            for (int o = tid; o < 2 * kQ * 49; o += kThreads) A.corr[(size_t)e * 2 * kQ * 49 + o] = 0.f;
-            if (tid == 0) s_badin = 1;
-            continue;
-        }
-        // the patch's features: B rows 0..8
-        for (int idx = tid; idx < kQ * (kD / 8); idx += kThreads) {
-            const int r = idx / (kD / 8), g = idx % (kD / 8);
-            cp16(aB + op_off(r, 8 * g), A.gpatch + ((size_t)k * kQ + r) * kD + 8 * g, 16u);
-        }
-        for (int level = 0; level < 2; ++level) {
-            const float s = level == 0 ? 1.f : A.scale1;
-            const int H = A.H[level], W = A.W[level];
-            const uint16_t *fm = A.fmap[level] + (size_t)j * H * W * kD;
-            if (tid < kQ) {
-                s_xy[tid][0] = A.coords[((size_t)e * kQ + tid) * 2] / s;
-                s_xy[tid][1] = A.coords[((size_t)e * kQ + tid) * 2 + 1] / s;
-            }
+    auto fmap_of = [&](int l, int j) { return A.fmap[l] + (size_t)j * A.H[l] * A.W[l] * kD; };
+    auto issue_fast = [&](const Plan &P) {
+        stage_footprint(aA0, fmap_of(0, P.j), A.H[0], A.W[0], P.box[0], 0, tid);
+        stage_footprint(aA1, fmap_of(1, P.j), A.H[1], A.W[1], P.box[1], 0, tid);
+        stage_patch(aB, A.gpatch, P.k, tid);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    int e = blockIdx.x;
+    if (e < A.E) {
+        if (warp == 0) plan_edge(A, e, s_plan[0], lane);
+        __syncthreads();
+        if (s_plan[0].mode == kFast) issue_fast(s_plan[0]);
+    }
+    for (; e < A.E; e += gridDim.x) {
+        Plan &P = s_plan[slot];
+        const int mode = P.mode;
+        float *out = A.corr + (size_t)e * 2 * kQ * 49;
+        if (mode == kFast) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            dpvo::fence_async_smem();
             __syncthreads();
-            if (tid == 0) {
-                bool ok = s_bad == 0;                // after a timed-out wait: no further MMAs
-                int x0 = 1 << 30, x1 = -(1 << 30), y0 = 1 << 30, y1 = -(1 << 30);
-                for (int q = 0; q < kQ; ++q) {
-                    const float x = s_xy[q][0], y = s_xy[q][1];
-                    if (!(fabsf(x) <= kCoordMax && fabsf(y) <= kCoordMax)) ok = false;
-                    if (!ok) break;
-                    const int xi = (int)floorf(x), yi = (int)floorf(y);
-                    x0 = min(x0, xi); x1 = max(x1, xi);
-                    y0 = min(y0, yi); y1 = max(y1, yi);
-                }
-                if (!ok) {
-                    s_box[4] = 0;
-                } else {
-                    const int w = x1 - x0 + 8, h = y1 - y0 + 8;
-                    const long long np = (long long)w * h;
-                    s_box[0] = x0 - 3; s_box[1] = y0 - 3; s_box[2] = w; s_box[3] = h;
-                    s_box[5] = (int)((np + kChunk - 1) / kChunk);
-                    s_box[4] = np <= (long long)kMaxChunks * kChunk ? 1 : 2;
-                }
-            }
-            __syncthreads();
-            const int mode = s_box[4];
-            if (mode == 1) {
-                const int fx0 = s_box[0], fy0 = s_box[1], w = s_box[2], npix = w * s_box[3], nch = s_box[5];
-                for (int c = 0; c < nch; ++c) {
-                    for (int idx = tid; idx < kChunk * (kD / 8); idx += kThreads) {
-                        const int r = idx / (kD / 8), g = idx % (kD / 8), t = kChunk * c + r;
-                        const int py = fy0 + t / w, px = fx0 + t % w;
-                        const bool in = t < npix && py >= 0 && py < H && px >= 0 && px < W;
-                        const uint16_t *src = in ? fm + ((size_t)py * W + px) * kD + 8 * g : fm;
-                        cp16(aA + op_off(r, 8 * g), src, in ? 16u : 0u);
-                    }
-                    cp_wait_all();
-                    dpvo::fence_async_smem();
-                    __syncthreads();
-                    if (tid == 0) {
-                        dpvo::tc_fence_after();
-                        for (int ks = 0; ks < kD / 16; ++ks)
-                            mma_bf16(tmem, dpvo::smem_desc(aA + ks * 2 * kLbo, kLbo, kSbo),
-                                     dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
-                        dpvo::mma_commit(mbar);
-                    }
-                    ++n_commit;
-                    if (!dpvo::mbar_wait(mbar, (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_bad, 1);
-                    __syncthreads();
-                    if (s_bad) break;                    // reported below; outputs of this edge stay zero
+            if (s_bad == 0) {
+                if (tid == 0) {
                     dpvo::tc_fence_after();
-                    float v[16];
-                    dpvo::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
-                    const int t = kChunk * c + tid;
-                    if (t < npix) {
+                    for (int ks = 0; ks < kD / 16; ++ks)
+                        mma_bf16(tmem, dpvo::smem_desc(aA0 + ks * 2 * kLbo, kLbo, kSbo),
+                                 dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
+                    for (int ks = 0; ks < kD / 16; ++ks)
+                        mma_bf16(tmem + kN, dpvo::smem_desc(aA1 + ks * 2 * kLbo, kLbo, kSbo),
+                                 dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
+                    dpvo::mma_commit(mbar);
+                }
+                ++n_commit;
+                if (!dpvo::mbar_wait(mbar, (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_bad, 1);
+            }
+            __syncthreads();
+            if (s_bad == 0) {
+                dpvo::tc_fence_after();
+                float v[16];
 #pragma unroll
-                        for (int q = 0; q < kQ; ++q) Dbuf[t * kDld + q] = v[q];
-                    }
-                    dpvo::tc_fence_before();
-                    __syncthreads();                     // the operand and the accumulator are reused
+                for (int l = 0; l < 2; ++l) {
+                    dpvo::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + kN * l, v);
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) Dfast[(l * kChunk + tid) * kDld + q] = v[q];
                 }
-            } else if (mode == 2) {
-                // windows too far apart: each patch pixel's 8 x 8 inner products on the CUDA cores
-                for (int idx = tid; idx < kQ * 64; idx += kThreads) {
-                    const int q = idx >> 6, m = (idx >> 3) & 7, n = idx & 7;
-                    const int py = (int)floorf(s_xy[q][1]) - 3 + m, px = (int)floorf(s_xy[q][0]) - 3 + n;
-                    float acc = 0.f;
-                    if (py >= 0 && py < H && px >= 0 && px < W) {
-                        const uint16_t *f = fm + ((size_t)py * W + px) * kD, *g = A.gpatch + ((size_t)k * kQ + q) * kD;
-                        for (int c = 0; c < kD; ++c) acc = fmaf(bf16_to_f(g[c]), bf16_to_f(f[c]), acc);
+            }
+            dpvo::tc_fence_before();
+            __syncthreads();                             // operands free, accumulators copied
+        } else if (mode == kGeneral && s_bad == 0) {
+            for (int l = 0; l < 2; ++l) {
+                const int H = A.H[l], W = A.W[l];
+                const uint16_t *fm = fmap_of(l, P.j);
+                const int npix = P.box[l][2] * P.box[l][3];
+                const int nch = (npix + kChunk - 1) / kChunk;
+                if (l == 0) stage_patch(aB, A.gpatch, P.k, tid);
+                if (nch <= kMaxChunks) {
+                    for (int c = 0; c < nch; ++c) {
+                        stage_footprint(aA0, fm, H, W, P.box[l], kChunk * c, tid);
+                        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+                        dpvo::fence_async_smem();
+                        __syncthreads();
+                        if (tid == 0) {
+                            dpvo::tc_fence_after();
+                            for (int ks = 0; ks < kD / 16; ++ks)
+                                mma_bf16(tmem, dpvo::smem_desc(aA0 + ks * 2 * kLbo, kLbo, kSbo),
+                                         dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
+                            dpvo::mma_commit(mbar);
+                        }
+                        ++n_commit;
+                        if (!dpvo::mbar_wait(mbar, (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_bad, 1);
+                        __syncthreads();
+                        if (s_bad) break;
+                        dpvo::tc_fence_after();
+                        float v[16];
+                        dpvo::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), v);
+                        const int t = kChunk * c + tid;
+                        if (t < npix) {
+#pragma unroll
+                            for (int q = 0; q < kQ; ++q) Dgen[t * kDld + q] = v[q];
+                        }
+                        dpvo::tc_fence_before();
+                        __syncthreads();
                     }
-                    Dbuf[idx] = acc;
+                } else {
+                    // windows too far apart: each patch pixel's 8 x 8 inner products on the CUDA cores
+                    for (int idx = tid; idx < kQ * 64; idx += kThreads) {
+                        const int q = idx >> 6, m = (idx >> 3) & 7, n = idx & 7;
+                        const int py = (int)floorf(P.xy[l][q][1]) - 3 + m, px = (int)floorf(P.xy[l][q][0]) - 3 + n;
+                        float acc = 0.f;
+                        if (py >= 0 && py < H && px >= 0 && px < W) {
+                            const uint16_t *f = fm + ((size_t)py * W + px) * kD;
+                            const uint16_t *g = A.gpatch + ((size_t)P.k * kQ + q) * kD;
+                            for (int c = 0; c < kD; ++c) acc = fmaf(bf16_to_f(g[c]), bf16_to_f(f[c]), acc);
+                        }
+                        Dgen[idx] = acc;
+                    }
+                    __syncthreads();
                 }
+                for (int task = tid; task < kQ * 7; task += kThreads) {
+                    const int q = task / 7, a = task - 7 * q;
+                    float *o = out + (l * kQ + q) * 49 + 7 * a;
+                    if (s_bad) {
+                        for (int b = 0; b < 7; ++b) o[b] = 0.f;
+                    } else {
+                        bilinear_row(P, l, q, a, nch <= kMaxChunks ? Dgen : nullptr, Dgen, o);
+                    }
+                }
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
                 __syncthreads();
             }
-            // epilogue: the 9 x 49 outputs of this level
-            float *out = A.corr + ((size_t)e * 2 + level) * kQ * 49;
-            for (int o = tid; o < kQ * 49; o += kThreads) {
-                const int q = o / 49, ab = o - 49 * q, a = ab / 7, b = ab - 7 * a;
-                float r = 0.f;
-                if (mode != 0 && !s_bad) {
-                    const float x = s_xy[q][0], y = s_xy[q][1];
-                    const float xf = floorf(x), yf = floorf(y), wx = x - xf, wy = y - yf;
-                    float d00, d01, d10, d11;
-                    if (mode == 1) {
-                        const int w = s_box[2];
-                        const int t = ((int)yf - 3 + a - s_box[1]) * w + ((int)xf - 3 + b - s_box[0]);
-                        d00 = Dbuf[t * kDld + q];
-                        d01 = Dbuf[(t + 1) * kDld + q];
-                        d10 = Dbuf[(t + w) * kDld + q];
-                        d11 = Dbuf[(t + w + 1) * kDld + q];
-                    } else {
-                        const float *Dq = Dbuf + 64 * q + 8 * a + b;
-                        d00 = Dq[0]; d01 = Dq[1]; d10 = Dq[8]; d11 = Dq[9];
-                    }
-                    r = (1.f - wy) * ((1.f - wx) * d00 + wx * d01) + wy * ((1.f - wx) * d10 + wx * d11);
-                }
-                out[o] = r;
-            }
-            __syncthreads();
         }
-        cp_wait_all();                                   // this edge's copies are done before the next edge's
+        // plan the next edge and start its copies (they fly during this epilogue)
+        const int en = e + gridDim.x;
+        if (en < A.E) {
+            if (warp == 0) plan_edge(A, en, s_plan[slot ^ 1], lane);
+            __syncthreads();
+            if (s_plan[slot ^ 1].mode == kFast && s_bad == 0) issue_fast(s_plan[slot ^ 1]);
+        }
+        if (mode == kFast) {
+            for (int task = tid; task < 2 * kQ * 7; task += kThreads) {   // (level, pixel, grid row)
+                const int l = task / (kQ * 7), r = task - l * kQ * 7, q = r / 7, a = r - 7 * q;
+                float *o = out + (l * kQ + q) * 49 + 7 * a;
+                if (s_bad) {
+                    for (int b = 0; b < 7; ++b) o[b] = 0.f;
+                } else {
+                    bilinear_row(P, l, q, a, Dfast + l * kChunk * kDld, nullptr, o);
+                }
+            }
+        } else if (mode == kZero || mode == kBadIndex || s_bad) {
+            if (mode != kGeneral || s_bad)
+                for (int o = tid; o < 2 * kQ * 49; o += kThreads) out[o] = 0.f;
+            if (mode == kBadIndex && tid == 0) s_badin = 1;
+        }
+        __syncthreads();                                 // this edge's plan and accumulator copy are consumed
+        slot ^= 1;
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
         if (s_bad) {
             // report, and give the last commit one more bounded wait before the TMEM is freed
             atomicOr(A.status, DPVO_BA_STATUS_TIMEOUT);
-            dpvo::mbar_wait(mbar, (uint32_t)(n_commit - 1) & 1u);
+            if (n_commit > 0) dpvo::mbar_wait(mbar, (uint32_t)(n_commit - 1) & 1u);
         }
         if (s_badin) atomicOr(A.status, DPVO_BA_STATUS_BAD_INPUT);
     }
@@ -252,8 +373,8 @@ extern "C" int dpvo_ba_correlation(const dpvo_ba_corr_dims *d, const void *fmap0
     static int configured_device = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DPVO_BA_ECUDA;
-    const size_t smem = dpvo_corr::kAbytes + dpvo_corr::kBbytes +
-                        (size_t)dpvo_corr::kMaxChunks * dpvo_corr::kChunk * dpvo_corr::kDld * 4;
+    const size_t smem = 2 * dpvo_corr::kAbytes + dpvo_corr::kBbytes +
+                        (size_t)2 * dpvo_corr::kChunk * dpvo_corr::kDld * 4;
     if (configured_device != dev) {
         if (cudaFuncSetAttribute(dpvo_corr::corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
