@@ -38,10 +38,11 @@ struct Layout {
     size_t lin_smem = 0, solve_smem = 0, asm_smem = 0;
 };
 
-// solve_kernel shared memory: S and its FP32 copy (n x (n+1)), v, x, the FP32 right-hand side.
+// solve_kernel shared memory: S and its FP32 copy (n x (n+1)), v, x, the FP32 right-hand side,
+// the inverted diagonal blocks of the factor.
 static size_t solve_smem_bytes(int nf) {
-    const size_t n = 6 * (size_t)nf;
-    return n * (n + 1) * 8 + 2 * n * 8 + n * (n + 1) * 4 + n * 4 + 64;
+    const size_t n = 6 * (size_t)nf, panels = (n + kPanel - 1) / kPanel;
+    return n * (n + 1) * 8 + 2 * n * 8 + n * (n + 1) * 4 + n * 4 + panels * kPanel * kLinvLd * 4 + 64;
 }
 
 // Stored Schur rows: one row per patch, or in the tensor-core variant one

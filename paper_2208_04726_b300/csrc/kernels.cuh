@@ -1432,52 +1432,108 @@ __device__ __forceinline__ double shfl_double(double x, int src) {
     return __hiloint2double(hi, lo);
 }
 
-// One warp: solve S x = b in place in b (n <= 96), with S = U D^-1 U^T
-// factored into the lower triangle of Sf (U, diagonal D) and the pivot
-// reciprocals rp: forward L y = b with L = U D^-1 (unit diagonal), then back
-// U^T x = y.  Lane l keeps b[l], b[l + 32], b[l + 64] in registers; each step
-// broadcasts one entry by shuffle, and the next step's coefficients are loaded
-// before the current step's update (zero where a row takes no update).
-__device__ __forceinline__ float lane_pick(float b0, float b1, float b2, int j) {
-    const float v = (j >> 5) == 0 ? b0 : (j >> 5) == 1 ? b1 : b2;
-    return __shfl_sync(0xffffffffu, v, j & 31);
-}
-__device__ __forceinline__ void solve_factored_f32(const float *Sf, int ld, const float *rp, float *b, int n,
-                                                   int lane) {
-    const int i0 = lane, i1 = lane + 32, i2 = lane + 64;
-    float b0 = i0 < n ? b[i0] : 0.f, b1 = i1 < n ? b[i1] : 0.f, b2 = i2 < n ? b[i2] : 0.f;
-    // forward: b_i -= (U_ij / D_j) y_j for i > j
-    auto lcoef = [&](int i, int j) { return (i > j && i < n) ? Sf[i * ld + j] * rp[j] : 0.f; };
-    float l0 = lcoef(i0, 0), l1 = lcoef(i1, 0), l2 = lcoef(i2, 0);
-    for (int j = 0; j < n; ++j) {
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f;
-        if (j + 1 < n) { m0 = lcoef(i0, j + 1); m1 = lcoef(i1, j + 1); m2 = lcoef(i2, j + 1); }
-        const float yj = lane_pick(b0, b1, b2, j);
-        b0 = fmaf(-l0, yj, b0);
-        b1 = fmaf(-l1, yj, b1);
-        b2 = fmaf(-l2, yj, b2);
-        l0 = m0; l1 = m1; l2 = m2;
-    }
-    // back: x_j = y_j / D_j, b_i -= U_ji x_j for i < j
-    auto ucoef = [&](int i, int j) { return i < j ? Sf[j * ld + i] : 0.f; };
-    float u0 = ucoef(i0, n - 1), u1 = ucoef(i1, n - 1), u2 = ucoef(i2, n - 1);
-    float r = rp[n - 1];
-    for (int j = n - 1; j >= 0; --j) {
-        float w0 = 0.f, w1 = 0.f, w2 = 0.f, rn = 0.f;
-        if (j > 0) { w0 = ucoef(i0, j - 1); w1 = ucoef(i1, j - 1); w2 = ucoef(i2, j - 1); rn = rp[j - 1]; }
-        const float xj = lane_pick(b0, b1, b2, j) * r;
-        if ((j & 31) == lane) {
-            if ((j >> 5) == 0) b0 = xj; else if ((j >> 5) == 1) b1 = xj; else b2 = xj;
+// ---- blocked triangular solves with inverted diagonal blocks (both reduced solves)
+constexpr int kPanel = 32;             // panel width of the blocked factorisation and solves
+constexpr int kLinvLd = kPanel + 1;     // row stride of an inverted diagonal block (conflict-free rows and columns)
+
+// Warp w of the CTA, for panel J = kPanel w: the inverse of the panel's unit
+// lower diagonal block, L_rj = a_rj / p_j (r > j), into Linv + w kPanel kLinvLd
+// at [r kLinvLd + c].  Lane c computes column c by forward substitution.  The
+// factor's element (i, k), k <= i, is Sp[idx(i, k)], each row's entries
+// consecutive.
+template <class Idx>
+__device__ void invert_diag_blocks(const float *Sp, Idx idx, const float *rp, float *Linv, int n, int tid) {
+    const int warp = tid >> 5, lane = tid & 31, J = kPanel * warp;
+    if (J >= n) return;
+    const int nb = min(kPanel, n - J);
+    float z[kPanel];
+#pragma unroll
+    for (int r = 0; r < kPanel; ++r) {
+        float acc = 0.f;
+        if (r < nb) {
+            const int rr = idx(J + r, J);
+#pragma unroll
+            for (int j = 0; j < r; ++j) acc = fmaf(Sp[rr + j] * rp[J + j], z[j], acc);
         }
-        b0 = fmaf(-u0, xj, b0);
-        b1 = fmaf(-u1, xj, b1);
-        b2 = fmaf(-u2, xj, b2);
-        u0 = w0; u1 = w1; u2 = w2; r = rn;
+        z[r] = r == lane ? 1.f : -acc;             // zero above the diagonal (z_j = 0 for j < lane)
     }
-    if (i0 < n) b[i0] = b0;
-    if (i1 < n) b[i1] = b1;
-    if (i2 < n) b[i2] = b2;
+    float *L = Linv + warp * kPanel * kLinvLd;
+    if (lane < nb) {
+#pragma unroll
+        for (int r = 0; r < kPanel; ++r)
+            if (r < nb) L[r * kLinvLd + lane] = z[r];
+    }
 }
+
+// All threads: solve S x = b in place in b (shared memory), S = U D^-1 U^T
+// held as the eliminated values a_ij (j <= i) at Sp[idx(i, j)] with pivot
+// reciprocals rp, by panels of kPanel: each panel's diagonal block by one warp
+// as a product with its inverse (invert_diag_blocks), the rows outside it by
+// one thread each.
+template <class Idx>
+__device__ void solve_blocked_f32(const float *Sp, Idx idx, const float *rp, const float *Linv, float *b, int n,
+                                  int tid) {
+    __shared__ float s_t[kPanel];                          // y_j / p_j of the current panel
+    const int lane = tid & 31;
+    for (int J = 0; J < n; J += kPanel) {                  // forward: y_J = L_JJ^-1 b_J, then the rows below
+        const int nb = min(kPanel, n - J);
+        if (tid < 32) {
+            const float *L = Linv + (J / kPanel) * kPanel * kLinvLd + lane * kLinvLd;
+            float y0 = 0.f, y1 = 0.f;
+            if (lane < nb) {
+#pragma unroll
+                for (int c = 0; c < kPanel; c += 2) {
+                    if (c <= lane && c < nb) y0 = fmaf(L[c], b[J + c], y0);
+                    if (c + 1 <= lane && c + 1 < nb) y1 = fmaf(L[c + 1], b[J + c + 1], y1);
+                }
+            }
+            __syncwarp();
+            if (lane < nb) {
+                const float y = y0 + y1;
+                b[J + lane] = y;
+                s_t[lane] = y * rp[J + lane];
+            }
+        }
+        __syncthreads();
+        for (int i = J + nb + tid; i < n; i += kSolveThreads) {   // nb == kPanel here
+            const int ri = idx(i, J);
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < kPanel; ++j) acc = fmaf(Sp[ri + j], s_t[j], acc);
+            b[i] -= acc;
+        }
+        __syncthreads();
+    }
+    for (int J = ((n - 1) / kPanel) * kPanel; J >= 0; J -= kPanel) {   // backward: x_J = L_JJ^-T D_J^-1 w_J
+        const int nb = min(kPanel, n - J);
+        if (tid < 32) {
+            const float *L = Linv + (J / kPanel) * kPanel * kLinvLd + lane;
+            float x0 = 0.f, x1 = 0.f;
+            if (lane < nb) {
+#pragma unroll
+                for (int c = 0; c < kPanel; c += 2) {
+                    if (c >= lane && c < nb) x0 = fmaf(L[c * kLinvLd], rp[J + c] * b[J + c], x0);
+                    if (c + 1 >= lane && c + 1 < nb) x1 = fmaf(L[(c + 1) * kLinvLd], rp[J + c + 1] * b[J + c + 1], x1);
+                }
+            }
+            __syncwarp();
+            if (lane < nb) b[J + lane] = x0 + x1;
+        }
+        __syncthreads();
+        for (int i = tid; i < J; i += kSolveThreads) {
+            float acc = 0.f;
+            for (int j = 0; j < nb; ++j) acc = fmaf(Sp[idx(J + j, i)], b[J + j], acc);
+            b[i] -= acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Row-major storage with leading dimension ld.
+struct RowMajorIdx {
+    int ld;
+    __device__ __forceinline__ int operator()(int i, int k) const { return i * ld + k; }
+};
 
 constexpr int kMaxRefine = 4;          // FP64 refinement steps of the FP32 solution at most
 constexpr double kRefineTol = 1e-6;    // accept once the last correction is below this x max|x|
@@ -1579,6 +1635,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         double *x = v + n;
         float *Sf = reinterpret_cast<float *>(x + n);
         float *bf = Sf + (size_t)n * ld;
+        float *Linv = bf + n;                               // inverted diagonal blocks of the factor
         for (int q = tid; q < n * n; q += kSolveThreads) {
             const int i = q / n, k = q - i * n;
             if (k <= i) Sf[i * ld + k] = (float)S[i * ld + k];
@@ -1617,6 +1674,8 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
             __syncthreads();
         }
         __syncthreads();
+        if (!s_use64) invert_diag_blocks(Sf, RowMajorIdx{ld}, s_rpf, Linv, n, tid);
+        __syncthreads();
         double prev = 0.0;
         for (int it = 0; it <= kMaxRefine && !s_use64; ++it) {
             if (it > 0) {   // residual v - S x in FP64, four threads per row
@@ -1632,8 +1691,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
                 }
                 __syncthreads();
             }
-            if (tid < 32) solve_factored_f32(Sf, ld, s_rpf, bf, n, lane);
-            __syncthreads();
+            solve_blocked_f32(Sf, RowMajorIdx{ld}, s_rpf, Linv, bf, n, tid);
             double dmax = 0.0, xmax = 0.0;
             for (int q = tid; q < n; q += kSolveThreads) {
                 const double d = (double)bf[q];

@@ -26,8 +26,10 @@ namespace dpvo {
 // corrections stall): FP64 elimination of S loaded packed into shared memory.
 // ----------------------------------------------------------------------------
 __host__ __device__ inline int packed_index(int i, int k) { return i * (i + 1) / 2 + k; }
+struct PackedIdx {
+    __device__ __forceinline__ int operator()(int i, int k) const { return packed_index(i, k); }
+};
 
-constexpr int kPanel = 32;             // panel width of the blocked factorisation and solves
 constexpr int kDiagLd = 36;            // row stride (floats) of a staged diagonal block (16-byte rows)
 
 // FP32 path of solve_large_kernel, in floats from the start of the packed
@@ -35,96 +37,6 @@ constexpr int kDiagLd = 36;            // row stride (floats) of a staged diagon
 // (kPanel rows of panel_ld(n) each, 16-byte aligned).
 __host__ __device__ inline int panel_ld(int n) { return (n + 7) & ~3; }
 __host__ __device__ inline int panel_off(int n) { return (n * (n + 1) / 2 + n + 3) & ~3; }
-
-constexpr int kLinvLd = kPanel + 1;     // row stride of an inverted diagonal block (conflict-free rows and columns)
-
-// Warp w of the CTA, for panel J = kPanel w: the inverse of the panel's unit
-// lower diagonal block, L_rj = a_rj / p_j (r > j), into Linv + w kPanel kLinvLd
-// at [r kLinvLd + c].  Lane c computes column c by forward substitution.
-__device__ void invert_diag_blocks(const float *Sp, const float *rp, float *Linv, int n, int tid) {
-    const int warp = tid >> 5, lane = tid & 31, J = kPanel * warp;
-    if (J >= n) return;
-    const int nb = min(kPanel, n - J);
-    float z[kPanel];
-#pragma unroll
-    for (int r = 0; r < kPanel; ++r) {
-        float acc = 0.f;
-        if (r < nb) {
-            const int rr = packed_index(J + r, J);
-#pragma unroll
-            for (int j = 0; j < r; ++j) acc = fmaf(Sp[rr + j] * rp[J + j], z[j], acc);
-        }
-        z[r] = r == lane ? 1.f : -acc;             // zero above the diagonal (z_j = 0 for j < lane)
-    }
-    float *L = Linv + warp * kPanel * kLinvLd;
-    if (lane < nb) {
-#pragma unroll
-        for (int r = 0; r < kPanel; ++r)
-            if (r < nb) L[r * kLinvLd + lane] = z[r];
-    }
-}
-
-// All threads: solve S x = b in place in b (shared memory), S = U D^-1 U^T
-// packed in Sp (the eliminated values a_ij, j <= i) with pivot reciprocals
-// rp, by panels of kPanel: each panel's diagonal block by one warp as a
-// product with its inverse (invert_diag_blocks), the rows outside it by one
-// thread each.
-__device__ void solve_blocked_f32(const float *Sp, const float *rp, const float *Linv, float *b, int n, int tid) {
-    __shared__ float s_t[kPanel];                          // y_j / p_j of the current panel
-    const int lane = tid & 31;
-    for (int J = 0; J < n; J += kPanel) {                  // forward: y_J = L_JJ^-1 b_J, then the rows below
-        const int nb = min(kPanel, n - J);
-        if (tid < 32) {
-            const float *L = Linv + (J / kPanel) * kPanel * kLinvLd + lane * kLinvLd;
-            float y0 = 0.f, y1 = 0.f;
-            if (lane < nb) {
-#pragma unroll
-                for (int c = 0; c < kPanel; c += 2) {
-                    if (c <= lane && c < nb) y0 = fmaf(L[c], b[J + c], y0);
-                    if (c + 1 <= lane && c + 1 < nb) y1 = fmaf(L[c + 1], b[J + c + 1], y1);
-                }
-            }
-            __syncwarp();
-            if (lane < nb) {
-                const float y = y0 + y1;
-                b[J + lane] = y;
-                s_t[lane] = y * rp[J + lane];
-            }
-        }
-        __syncthreads();
-        for (int i = J + nb + tid; i < n; i += kSolveThreads) {   // nb == kPanel here
-            const int ri = packed_index(i, J);
-            float acc = 0.f;
-#pragma unroll
-            for (int j = 0; j < kPanel; ++j) acc = fmaf(Sp[ri + j], s_t[j], acc);
-            b[i] -= acc;
-        }
-        __syncthreads();
-    }
-    for (int J = ((n - 1) / kPanel) * kPanel; J >= 0; J -= kPanel) {   // backward: x_J = L_JJ^-T D_J^-1 w_J
-        const int nb = min(kPanel, n - J);
-        if (tid < 32) {
-            const float *L = Linv + (J / kPanel) * kPanel * kLinvLd + lane;
-            float x0 = 0.f, x1 = 0.f;
-            if (lane < nb) {
-#pragma unroll
-                for (int c = 0; c < kPanel; c += 2) {
-                    if (c >= lane && c < nb) x0 = fmaf(L[c * kLinvLd], rp[J + c] * b[J + c], x0);
-                    if (c + 1 >= lane && c + 1 < nb) x1 = fmaf(L[(c + 1) * kLinvLd], rp[J + c + 1] * b[J + c + 1], x1);
-                }
-            }
-            __syncwarp();
-            if (lane < nb) b[J + lane] = x0 + x1;
-        }
-        __syncthreads();
-        for (int i = tid; i < J; i += kSolveThreads) {
-            float acc = 0.f;
-            for (int j = 0; j < nb; ++j) acc = fmaf(Sp[packed_index(J + j, i)], b[J + j], acc);
-            b[i] -= acc;
-        }
-        __syncthreads();
-    }
-}
 
 constexpr int kMaxRefineLarge = 10;
 
@@ -375,7 +287,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
     // inverted diagonal blocks over the panel buffers (free now): ceil(n / kPanel)
     // x kPanel x kLinvLd floats, within 2 kPanel panel_ld(n) for n >= 26 and, for
     // smaller n, within the FP32 region the launch sizes for more than 15 free poses
-    if (!s_use64) invert_diag_blocks(Sp, s_rpf, PuT, n, tid);
+    if (!s_use64) invert_diag_blocks(Sp, PackedIdx{}, s_rpf, PuT, n, tid);
     __syncthreads();
     double prev = 0.0;
     for (int it = 0; it <= kMaxRefineLarge && !s_use64; ++it) {
@@ -395,7 +307,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
             }
             __syncthreads();
         }
-        solve_blocked_f32(Sp, s_rpf, PuT, bf, n, tid);
+        solve_blocked_f32(Sp, PackedIdx{}, s_rpf, PuT, bf, n, tid);
         double dmax = 0.0, xmax = 0.0;
         for (int q = tid; q < n; q += kSolveThreads) {
             const double d = s_dsc[q] * (double)bf[q];
