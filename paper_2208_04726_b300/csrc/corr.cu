@@ -35,8 +35,15 @@ constexpr int kN = 16;                          // patch pixels padded (N)
 constexpr int kMaxChunks = 2;                   // general path: footprints up to 256 pixels on the tensor cores
 constexpr uint32_t kSbo = (kD / 8) * kLbo + 16; // bytes between 8-row groups (16 core matrices of K, +16 so
                                                  // that the row groups a warp writes fall in distinct banks)
-constexpr uint32_t kAbytes = (kChunk / 8) * kSbo, kBbytes = (kN / 8) * kSbo;
-constexpr int kDld = 17;                        // row stride (floats) of the accumulator copy
+constexpr int kRows1 = 88;                      // level-1 fast footprints: at most 88 pixels (11 row groups)
+constexpr uint32_t kAbytes = (kChunk / 8) * kSbo, kA1bytes = (kRows1 / 8) * kSbo, kBbytes = (kN / 8) * kSbo;
+constexpr int kDld = kQ;                        // row stride (floats) of the accumulator copy
+// Dynamic shared memory: A0 (128 rows), A1 (88 rows), B (16 rows), the accumulator copies
+// (128 + 88 rows).  The level-1 GEMM reads 128 rows from A1: rows 88..127 fall on B and the
+// copies (inside the allocation), and their results are never read.  3 CTAs per SM.
+constexpr size_t kSmemBytes = kAbytes + kA1bytes + kBbytes + (size_t)(kChunk + kRows1) * kDld * 4;
+static_assert(kA1bytes + kBbytes + (size_t)(kChunk + kRows1) * kDld * 4 >= kAbytes,
+              "the level-1 GEMM's 128 operand rows stay inside the allocation");
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kChunk >> 4) << 24);   // FP32 D, BF16 A and B, K-major, 128 x 16
 constexpr float kCoordMax = 1e4f;
@@ -116,17 +123,17 @@ __device__ void plan_edge(const Args &A, int e, Plan &P, int lane) {
     if (lane == 0) {
         P.k = k;
         P.j = j;
-        P.mode = !valid ? kBadIndex : !finite ? kZero : (npix[0] <= kChunk && npix[1] <= kChunk) ? kFast : kGeneral;
+        P.mode = !valid ? kBadIndex : !finite ? kZero : (npix[0] <= kChunk && npix[1] <= kRows1) ? kFast : kGeneral;
     }
 }
 
-// All threads: stage a footprint chunk (rows t = t0 .. t0 + 127 of the box) of
-// map fm into the operand at aOp, one row (pixel: 16 copies of 8 channels) per
-// thread; rows outside the box or the map are zero.
+// All threads: stage rows t = t0 .. t0 + nrows - 1 of a footprint box of map
+// fm into the operand at aOp (nrows rows of capacity), one row (pixel: 16
+// copies of 8 channels) per thread; rows outside the box or the map are zero.
 __device__ __forceinline__ void stage_footprint(uint32_t aOp, const uint16_t *fm, int H, int W, const int *box,
-                                                int t0, int tid) {
+                                                int t0, int nrows, int tid) {
     const int w = box[2], npix = w * box[3];
-    for (int r = tid; r < kChunk; r += kThreads) {
+    for (int r = tid; r < nrows; r += kThreads) {
         const int t = t0 + r;
         const int py = box[1] + t / w, px = box[0] + t % w;
         const bool in = t < npix && py >= 0 && py < H && px >= 0 && px < W;
@@ -181,9 +188,9 @@ __device__ __forceinline__ void bilinear_row(const Plan &P, int l, int q, int a,
 // kMaxChunks chunks.
 __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *opA0 = smem, *opA1 = smem + kAbytes, *opB = smem + 2 * kAbytes;
-    float *Dfast = reinterpret_cast<float *>(smem + 2 * kAbytes + kBbytes);   // [2][kChunk][kDld]
-    float *Dgen = reinterpret_cast<float *>(opA1);                             // general path, over A1
+    unsigned char *opA0 = smem, *opA1 = smem + kAbytes, *opB = smem + kAbytes + kA1bytes;
+    float *Dfast = reinterpret_cast<float *>(smem + kAbytes + kA1bytes + kBbytes);   // rows 0..127 level 0, then level 1
+    float *Dgen = reinterpret_cast<float *>(opA1);   // general path (up to kMaxChunks x 128 rows), over A1 .. copies
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
     __shared__ Plan s_plan[2];
@@ -208,8 +215,8 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
 
     auto fmap_of = [&](int l, int j) { return A.fmap[l] + (size_t)j * A.H[l] * A.W[l] * kD; };
     auto issue_fast = [&](const Plan &P) {
-        stage_footprint(aA0, fmap_of(0, P.j), A.H[0], A.W[0], P.box[0], 0, tid);
-        stage_footprint(aA1, fmap_of(1, P.j), A.H[1], A.W[1], P.box[1], 0, tid);
+        stage_footprint(aA0, fmap_of(0, P.j), A.H[0], A.W[0], P.box[0], 0, kChunk, tid);
+        stage_footprint(aA1, fmap_of(1, P.j), A.H[1], A.W[1], P.box[1], 0, kRows1, tid);
         stage_patch(aB, A.gpatch, P.k, tid);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -249,8 +256,10 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
 #pragma unroll
                 for (int l = 0; l < 2; ++l) {
                     dpvo::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + kN * l, v);
+                    if (l == 0 || tid < kRows1) {
 #pragma unroll
-                    for (int q = 0; q < kQ; ++q) Dfast[(l * kChunk + tid) * kDld + q] = v[q];
+                        for (int q = 0; q < kQ; ++q) Dfast[(l * kChunk + tid) * kDld + q] = v[q];
+                    }
                 }
             }
             dpvo::tc_fence_before();
@@ -264,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
                 if (l == 0) stage_patch(aB, A.gpatch, P.k, tid);
                 if (nch <= kMaxChunks) {
                     for (int c = 0; c < nch; ++c) {
-                        stage_footprint(aA0, fm, H, W, P.box[l], kChunk * c, tid);
+                        stage_footprint(aA0, fm, H, W, P.box[l], kChunk * c, kChunk, tid);
                         asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
                         dpvo::fence_async_smem();
                         __syncthreads();
@@ -373,8 +382,7 @@ extern "C" int dpvo_ba_correlation(const dpvo_ba_corr_dims *d, const void *fmap0
     static int configured_device = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DPVO_BA_ECUDA;
-    const size_t smem = 2 * dpvo_corr::kAbytes + dpvo_corr::kBbytes +
-                        (size_t)2 * dpvo_corr::kChunk * dpvo_corr::kDld * 4;
+    const size_t smem = dpvo_corr::kSmemBytes;
     if (configured_device != dev) {
         if (cudaFuncSetAttribute(dpvo_corr::corr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -400,7 +408,7 @@ extern "C" int dpvo_ba_correlation(const dpvo_ba_corr_dims *d, const void *fmap0
     A.H[1] = H1;
     A.W[1] = W1;
     A.scale1 = (float)d->level1_scale;
-    const int grid = d->n_edges < 2 * sms ? d->n_edges : 2 * sms;
+    const int grid = d->n_edges < 3 * sms ? d->n_edges : 3 * sms;
     dpvo_corr::corr_kernel<<<grid, dpvo_corr::kThreads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(A);
     return cudaGetLastError() == cudaSuccess ? 0 : DPVO_BA_ECUDA;
 }
