@@ -209,13 +209,12 @@ def stress_bench(n_sessions, steps, stream, hbm_peak):
     kinds = {}
     for k, v in launches:
         kinds.setdefault(int(k), []).append(v)
-    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly"}
+    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub"}
     kern = {names[k] + "_ms": float(np.mean(v)) for k, v in kinds.items() if k in names}
     kern.update({names[k] + "_launches_per_step": len(v) // steps for k, v in kinds.items() if k in names})
     sc = distinct[0]
     bytes_lin = n_sessions * (24.0 * sc.n_edges + 20.0 * sc.n_patches)
-    lin = np.array(kinds.get(1, [0.0] * 5 * steps)).reshape(steps, -1)
-    t_lin = float(lin[:, :-1].mean())          # the launches that linearise (the last only back-substitutes)
+    t_lin = float(np.mean(kinds.get(1, [0.0])))   # the launches that linearise (kind 4 back-substitutes)
     kern["linearize_linearising_ms"] = t_lin
     gbs = bytes_lin / (t_lin / 1e3) / 1e9 if t_lin > 0 else None
     return {"workload": "64 frames x 256 patches (16,384), radius 24 (649,216 edges), last 32 poses free "

@@ -35,6 +35,7 @@ struct Layout {
     bool tc = false;               // Schur accumulation on the tensor cores
     bool ext = false;              // more than kFusedMaxFree free poses: assembly kernel, packed solve
     int n_lin_items = 0, n_asm_items = 0;
+    int final_slices = 1;          // y extent of the last back-substitution's grid
     size_t lin_smem = 0, solve_smem = 0, asm_smem = 0;
 };
 
@@ -64,6 +65,22 @@ static void launch_solve(const Layout &L, int n, cudaStream_t stream, const Prob
                          double *v_out) {
     if (L.ext) solve_large_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
     else solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
+}
+
+// Slices of one problem in the last back-substitution's grid: all of them, at
+// most `cap` (the CTAs then stride over the rest, which spreads each CTA's
+// start-up over several slices).
+static int final_slices_of(bool tc, int n_patches, int max_chunks, int cap) {
+    const int units = tc ? max_chunks : n_patches, per = tc ? kFinalChunks : kFinalPatches;
+    return std::min(std::min(65535, cap), std::max(1, (units + per - 1) / per));
+}
+
+// The last back-substitution (iteration t = the batch's last): n problems.
+static void launch_final(const Layout &L, int n, cudaStream_t stream, const Prob *probs, int t) {
+    const dim3 grid(n, L.final_slices);
+    const size_t smem = 4 * (size_t)std::max(kTcRows, erow_len(L.nf_max));
+    if (L.tc) final_kernel<true><<<grid, kThreads, smem, stream>>>(probs, t, L.G_cap);
+    else final_kernel<false><<<grid, kThreads, smem, stream>>>(probs, t, L.G_cap);
 }
 
 // One linearise launch, in the batch's variant.
@@ -119,6 +136,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     const int asm_slices_max = L.ext ? asm_slices(L.nf_max) : 1;
 
     const int target_ctas = 2 * num_sms;
+    const int final_cap = std::max(1, (8 * num_sms + n - 1) / n);   // one wave of final_kernel CTAs
     size_t off = 0;
     L.probs.resize(n);
     for (int b = 0; b < n; ++b) {
@@ -172,6 +190,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
             p.pgrad = (double *)(uintptr_t)take((size_t)p.n_items * d.n_frames * 6 * 8);
         }
         for (int w = 0; w < p.n_items; ++w) L.items.push_back(Item{b, w});
+        L.final_slices = std::max(L.final_slices, final_slices_of(L.tc, d.n_patches, p.max_chunks, final_cap));
     }
     L.n_lin_items = (int)L.items.size();
     for (int b = 0; b < n; ++b)
@@ -338,9 +357,8 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         launch_solve(L, n, stream, d_probs, 0, S_out, v_out);
     } else {
         for (int t = 0; t <= L.iters_max; ++t) {
-            rc = timed(1, [&] {
-                launch_linearize(L, n_items, stream, d_probs, d_items, t, 0);
-            });
+            if (t < L.iters_max) rc = timed(1, [&] { launch_linearize(L, n_items, stream, d_probs, d_items, t, 0); });
+            else rc = timed(4, [&] { launch_final(L, n, stream, d_probs, t); });
             if (rc) return rc;
             if (t < L.iters_max) {
                 if (L.ext) {
@@ -407,10 +425,11 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
     const int n_items = L.n_lin_items;
     const size_t bw_smem = bw_smem_layout(L.W_cap, L.G_cap, L.n_max).bytes;
     plan_kernel<<<n, kPlanThreads, 0, stream>>>(d_probs);
-    for (int t = 0; t <= L.iters_max; ++t) {
+    for (int t = 0; t < L.iters_max; ++t) {
         launch_linearize(L, n_items, stream, d_probs, d_items, t, 0);
-        if (t < L.iters_max) solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+        solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
     }
+    launch_final(L, n, stream, d_probs, L.iters_max);
     bw_init_kernel<<<n, kThreads, 0, stream>>>(d_probs);
     for (int t = L.iters_max - 1; t >= 0; --t) {
         bw_retract_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
@@ -1106,12 +1125,14 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     lay.nf_max = nf;
     lay.n_max = d.n_frames;
     lay.lin_smem = lin_smem;
+    lay.final_slices = final_slices_of(tc, d.n_patches, p.max_chunks, 65535);
     noalloc_descriptors_kernel<<<1, kThreads, 0, stream>>>(p, p.n_items, d_prob, d_items);
     plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_prob);
-    for (int t = 0; t <= d.n_iters; ++t) {
+    for (int t = 0; t < d.n_iters; ++t) {
         launch_linearize(lay, p.n_items, stream, d_prob, d_items, t, 0);
-        if (t < d.n_iters) solve_kernel<<<1, kSolveThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
+        solve_kernel<<<1, kSolveThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
     }
+    launch_final(lay, 1, stream, d_prob, d.n_iters);
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
     return DPVO_BA_OK;
 }

@@ -499,6 +499,76 @@ __device__ __forceinline__ float quad_sum(float v) {
     return v;
 }
 
+// Last back-substitution of the depths (Eq. 6 with the final pose increment):
+// dd_k = C_k^-1/2 (C_k^-1/2 w_k - (C_k^-1/2 e_k) . dxi), read from the stored
+// Schur rows.  Row layout: patches [k_lo, k_hi), four lanes per patch, dxs the
+// increment in the rows' padded frame layout.
+__device__ __forceinline__ void backsub_rows(const Prob &pr, const float *dxs, const float *depth_old,
+                                             float *depth_new, int k_lo, int k_hi, int tid) {
+    const int nf = pr.nf, RS = erow_len(nf);
+    const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
+    const int sub = tid & 3;
+    for (int kb = k_lo; kb < k_hi; kb += kThreads / 4) {
+        const int k = kb + (tid >> 2);
+        float s = 0.f;
+        const float *row = pr.erow + (size_t)k * RS;
+        if (k < k_hi) {
+#pragma unroll 2
+            for (int q = sub; q < RS / 4; q += 4) s = dot4(reinterpret_cast<const float4 *>(row)[q], dz4[q], s);
+        }
+        s = quad_sum(s);
+        if (k < k_hi && sub == 0) {
+            const float dnew = depth_old[k] + row[8 * nf + 1] * (row[8 * nf] - s);
+            depth_new[k] = dnew;
+            if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
+        }
+    }
+}
+
+// The same for chunk c in the tensor-core row layout (4-patch groups), one
+// warp, one lane octet per group; dxs the increment zero-padded to kTcRows.
+__device__ __forceinline__ void backsub_chunk_tc(const Prob &pr, int c, const float *dxs, const float *depth_old,
+                                                 float *depth_new, int kmax, int lane) {
+    const int n6 = 6 * pr.nf, rs = lane & 7, gw = lane >> 3;
+    const Chunk ch = pr.chunks[c];
+    const float *eb = pr.erow + (size_t)c * kTcRows * kmax;
+    const int ng = (ch.count + 3) >> 2;
+    for (int gb = 0; gb < ng; gb += 4) {      // warp-uniform trip count
+        const int g = gb + gw;
+        const float *grp = eb + (size_t)(g < ng ? g : 0) * (4 * kTcRows);
+        const float4 dots = group_dots(grp, dxs, g < ng ? n6 : 0, rs);
+        if (g < ng && rs < 4) {
+            const int p = 4 * g + rs;
+            if (p < ch.count) {
+                const float dot = rs == 0 ? dots.x : rs == 1 ? dots.y : rs == 2 ? dots.z : dots.w;
+                const int k = ch.k0 + p;
+                const float dnew = depth_old[k] + grp[4 * (kTcRows - 1) + rs] * (grp[4 * (kTcRows - 2) + rs] - dot);
+                depth_new[k] = dnew;
+                if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
+            }
+        }
+    }
+}
+
+// Pose increment of iteration t - 1 as the back-substitution reads it: the
+// tensor-core layout (zero-padded to kTcRows) or the rows' frame layout (frame
+// f at 8f..8f+7 as [v 0 w 0], zero-padded to the row length).
+template <bool TC>
+__device__ __forceinline__ void stage_dxi(const Prob &pr, int t, float *dxs, int tid, int nthreads) {
+    const int nf = pr.nf;
+    const double *dx = pr.dxi + (size_t)(t - 1) * nf * 6;
+    if constexpr (TC) {
+        for (int q = tid; q < kTcRows; q += nthreads) dxs[q] = q < 6 * nf ? (float)dx[q] : 0.f;
+    } else {
+        const int RS = erow_len(nf);
+        for (int q = tid; q < RS; q += nthreads) {
+            const int f = q >> 3, m = q & 7;
+            dxs[q] = (f < nf && (m & 3) != 3) ? (float)dx[6 * f + m - (m >> 2)] : 0.f;
+        }
+    }
+}
+
+
 // The pose-pair block entries a group of chunks adds to one strip of (S, v')
 // (the same selection the fused path makes inline for its register strips):
 // half-strip (a, b, sh) = rows 6a + 3sh .. +2, columns 6b .. 6b + 5 of the
@@ -638,62 +708,15 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     const int c_begin = (int)(((long long)itm.item * nch) / pr.n_items);
     const int c_end = (int)(((long long)(itm.item + 1) * nch) / pr.n_items);
 
-    if (do_bs) {   // the previous iteration's pose increments, zero-padded to the row length
-        const double *dx = pr.dxi + (size_t)(t - 1) * nf * 6;
-        if constexpr (TC) {
-            for (int q = tid; q < kTcRows; q += kThreads) dxs[q] = q < 6 * nf ? (float)dx[q] : 0.f;
-        } else {   // in the stored rows' layout: frame f at 8f..8f+7 as [v 0 w 0]
-            for (int q = tid; q < RS; q += kThreads) {
-                const int f = q >> 3, m = q & 7;
-                dxs[q] = (f < nf && (m & 3) != 3) ? (float)dx[6 * f + m - (m >> 2)] : 0.f;
-            }
-        }
-    }
+    if (do_bs) stage_dxi<TC>(pr, t, dxs, tid, kThreads);   // the previous iteration's pose increments
     if (final_pass) {
-        // last back-substitution: dd_k = C_k^-1/2 (C_k^-1/2 w_k - (C_k^-1/2 e_k) . dxi)
-        // for every patch of this item's chunks, four lanes per patch
         __syncthreads();
         if constexpr (TC) {
-            // one warp per chunk, one lane octet per 4-patch group
-            const int n6 = 6 * nf, rs = lane & 7, gw = lane >> 3;
-            for (int c = c_begin + warp; c < c_end; c += kThreads / 32) {
-                const Chunk ch = pr.chunks[c];
-                const float *eb = pr.erow + (size_t)c * kTcRows * kmax;
-                const int ng = (ch.count + 3) >> 2;
-                for (int gb = 0; gb < ng; gb += 4) {      // warp-uniform trip count
-                    const int g = gb + gw;
-                    const float *grp = eb + (size_t)(g < ng ? g : 0) * (4 * kTcRows);
-                    const float4 dots = group_dots(grp, dxs, g < ng ? n6 : 0, rs);
-                    if (g < ng && rs < 4) {
-                        const int p = 4 * g + rs;
-                        if (p < ch.count) {
-                            const float dot = rs == 0 ? dots.x : rs == 1 ? dots.y : rs == 2 ? dots.z : dots.w;
-                            const int k = ch.k0 + p;
-                            const float dnew = depth_old[k] + grp[4 * (kTcRows - 1) + rs] * (grp[4 * (kTcRows - 2) + rs] - dot);
-                            depth_new[k] = dnew;
-                            if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
-                        }
-                    }
-                }
-            }
+            for (int c = c_begin + warp; c < c_end; c += kThreads / 32)
+                backsub_chunk_tc(pr, c, dxs, depth_old, depth_new, kmax, lane);
         } else if (c_begin < c_end) {
             const Chunk ca = pr.chunks[c_begin], cz = pr.chunks[c_end - 1];
-            const int k_lo = ca.k0, k_hi = cz.k0 + cz.count;
-            const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
-            const int sub = tid & 3;
-            for (int kb = k_lo; kb < k_hi; kb += kThreads / 4) {
-                const int k = kb + (tid >> 2);
-                float s = 0.f;
-                const float *row = pr.erow + (size_t)k * RS;
-                if (k < k_hi)
-                    for (int q = sub; q < RS / 4; q += 4) s = dot4(reinterpret_cast<const float4 *>(row)[q], dz4[q], s);
-                s = quad_sum(s);
-                if (k < k_hi && sub == 0) {
-                    const float dnew = depth_old[k] + row[8 * nf + 1] * (row[8 * nf] - s);
-                    depth_new[k] = dnew;
-                    if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
-                }
-            }
+            backsub_rows(pr, dxs, depth_old, depth_new, ca.k0, cz.k0 + cz.count, tid);
         }
         if (itm.item == 0 && !pr.no_writeback)
             for (int q = tid; q < N * 7; q += kThreads) pr.poses[q] = pose_new[q];
@@ -1407,6 +1430,51 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             double *o = out + 18 * nbs + 6 * sa;
 #pragma unroll
             for (int q = 0; q < 6; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// final_kernel: the last back-substitution of the depths, on its own.  Only
+// reads the stored Schur rows, so it runs with a few hundred bytes of shared
+// memory, many CTAs per SM and the problem's patches cut into slices of
+// kFinalPatches (row layout) or kFinalChunks chunks (tensor-core layout):
+// grid (problems, slices), y-stride over the slices.  Slice 0 also reports the
+// status and writes the final poses back.  Problems whose last iteration is
+// not t return at once (their final pass ran inside an earlier linearise
+// launch).  Dynamic shared memory: the increment, max(kTcRows, erow_len(nf))
+// floats.
+// ----------------------------------------------------------------------------
+constexpr int kFinalPatches = kThreads / 4;
+constexpr int kFinalChunks = kThreads / 32;
+
+template <bool TC>
+__global__ void __launch_bounds__(kThreads, TC ? 5 : 8) final_kernel(const Prob *__restrict__ probs, int t, int G_cap) {
+    extern __shared__ __align__(16) float dxf[];
+    const Prob &pr = probs[blockIdx.x];
+    const int tid = threadIdx.x;
+    if (t != pr.iters) return;
+    const int st = *pr.status;
+    if (blockIdx.y == 0 && tid == 0 && pr.status_user) *pr.status_user = st;
+    if (st != 0) return;
+    const int N = pr.N;
+    if (blockIdx.y == 0 && !pr.no_writeback) {
+        const float *pose_new = pr.pose_it + (size_t)t * N * 7;
+        for (int q = tid; q < N * 7; q += kThreads) pr.poses[q] = pose_new[q];
+    }
+    const int n_units = TC ? *pr.n_chunks : pr.P;
+    const int per = TC ? kFinalChunks : kFinalPatches;
+    if ((int)blockIdx.y * per >= n_units) return;
+    stage_dxi<TC>(pr, t, dxf, tid, kThreads);
+    __syncthreads();
+    const float *depth_old = pr.depth_it + (size_t)(t - 1) * pr.P;
+    float *depth_new = pr.depth_it + (size_t)t * pr.P;
+    for (int lo = blockIdx.y * per; lo < n_units; lo += gridDim.y * per) {
+        if constexpr (TC) {
+            const int c = lo + (tid >> 5);
+            if (c < n_units) backsub_chunk_tc(pr, c, dxf, depth_old, depth_new, tc_kmax(G_cap), tid & 31);
+        } else {
+            backsub_rows(pr, dxf, depth_old, depth_new, lo, min(n_units, lo + per), tid);
         }
     }
 }
