@@ -136,7 +136,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     const int asm_slices_max = L.ext ? asm_slices(L.nf_max) : 1;
 
     const int target_ctas = 2 * num_sms;
-    const int final_cap = std::max(1, (8 * num_sms + n - 1) / n);   // one wave of final_kernel CTAs
+    const int final_cap = std::max(1, (6 * num_sms + n - 1) / n);   // one wave of final_kernel CTAs
     size_t off = 0;
     L.probs.resize(n);
     for (int b = 0; b < n; ++b) {

@@ -103,7 +103,8 @@ __device__ __forceinline__ void anchor_terms(const EdgeLin &L, const float *Rij,
 // begin; no searches.
 // ----------------------------------------------------------------------------
 constexpr int kPlanThreads = 1024;
-constexpr int kPlanUnroll = 4;
+constexpr int kPlanUnroll = 4;       // patches per thread with loads in flight together
+constexpr int kPlanQuads = 1;        // 4-edge groups per thread with loads in flight together
 
 __global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__restrict__ probs) {
     const Prob &pr = probs[blockIdx.x];
@@ -119,49 +120,102 @@ __global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__res
         for (int k = tid; k <= P; k += kPlanThreads) pr.seg[k] = 0;
     __syncthreads();
 
+    // Where kk and jj share their 16-byte phase the edges are read in groups
+    // of four by 16-byte loads.
+    const uintptr_t ka = (uintptr_t)pr.kk, ja = (uintptr_t)pr.jj;
+    const bool vec = (ka & 3) == 0 && (ka & 15) == (ja & 15);
+    const int head = vec ? min(E, (int)(((16 - (ka & 15)) & 15) >> 2)) : 0;
+    const int Q = vec ? (E - head) >> 2 : 0;
+    const int4 *kk4 = reinterpret_cast<const int4 *>(pr.kk + head);
+    const int4 *jj4 = reinterpret_cast<const int4 *>(pr.jj + head);
+
     int bad = 0;
     for (int i = tid; i < N * 7; i += kPlanThreads) {
         const float v = pr.poses[i];
         pr.pose_it[i] = v;
         if (!isfinite(v)) bad = 1;
     }
-    for (int k = tid; k < P; k += kPlanThreads) {
-        pr.depth_it[k] = pr.patches[3 * k + 2];
-        const int a = pr.anchor[k];
-        const int ap = k > 0 ? pr.anchor[k - 1] : -1;
-        if (a < 0 || a >= N || ap > a) {
-            bad = 1;
-        } else {
-            for (int i = max(ap + 1, 0); i <= a; ++i) s_fstart[i] = k;     // frames (ap, a] start at k
-            if (k == P - 1)
-                for (int i = a + 1; i <= N; ++i) s_fstart[i] = P;
-        }
-    }
-    for (int base = 0; base < E; base += kPlanUnroll * kPlanThreads) {
-        int kv[kPlanUnroll], jv[kPlanUnroll], kp[kPlanUnroll], jp[kPlanUnroll];
+    for (int base = 0; base < P; base += kPlanUnroll * kPlanThreads) {
+        int av[kPlanUnroll], ap[kPlanUnroll];
+        float dv[kPlanUnroll];
 #pragma unroll
-        for (int u = 0; u < kPlanUnroll; ++u) {   // loads of all unrolled edges first
-            const int e = base + u * kPlanThreads + tid;
-            kv[u] = 0; jv[u] = 0; kp[u] = -1; jp[u] = -1;
-            if (e < E) {
-                kv[u] = pr.kk[e];
-                jv[u] = pr.jj[e];
-                if (e > 0) { kp[u] = pr.kk[e - 1]; jp[u] = pr.jj[e - 1]; }
+        for (int u = 0; u < kPlanUnroll; ++u) {   // loads of all unrolled patches first
+            const int k = base + u * kPlanThreads + tid;
+            av[u] = 0; ap[u] = -1; dv[u] = 0.f;
+            if (k < P) {
+                av[u] = pr.anchor[k];
+                if (k > 0) ap[u] = pr.anchor[k - 1];
+                dv[u] = pr.patches[3 * k + 2];
             }
         }
 #pragma unroll
         for (int u = 0; u < kPlanUnroll; ++u) {
-            const int e = base + u * kPlanThreads + tid;
-            if (e >= E) continue;
-            const int k = kv[u], j = jv[u];
-            if (k < 0 || k >= P || j < 0 || j >= N || kp[u] > k || (kp[u] == k && jp[u] >= j)) {
+            const int k = base + u * kPlanThreads + tid;
+            if (k >= P) continue;
+            pr.depth_it[k] = dv[u];
+            const int a = av[u];
+            if (a < 0 || a >= N || ap[u] > a) {
                 bad = 1;
-                continue;
+            } else {
+                for (int i = max(ap[u] + 1, 0); i <= a; ++i) s_fstart[i] = k;     // frames (ap, a] start at k
+                if (k == P - 1)
+                    for (int i = a + 1; i <= N; ++i) s_fstart[i] = P;
             }
-            for (int q = max(kp[u] + 1, 0); q <= k; ++q) pr.seg[q] = e;   // patches (kp, k] start at e
-            if (e == E - 1)
-                for (int q = k + 1; q <= P; ++q) pr.seg[q] = E;
         }
+    }
+    // edge e = (k, j) after (kp, jp): valid and ordered, and patches (kp, k] start at e
+    auto edge = [&](int e, int k, int j, int kp, int jp) {
+        if (k < 0 || k >= P || j < 0 || j >= N || kp > k || (kp == k && jp >= j)) {
+            bad = 1;
+            return;
+        }
+        for (int q = max(kp + 1, 0); q <= k; ++q) pr.seg[q] = e;
+        if (e == E - 1)
+            for (int q = k + 1; q <= P; ++q) pr.seg[q] = E;
+    };
+    auto edge_scalar = [&](int e) {   // one edge with its own loads
+        edge(e, pr.kk[e], pr.jj[e], e > 0 ? pr.kk[e - 1] : -1, e > 0 ? pr.jj[e - 1] : -1);
+    };
+    // Grouped read: a scalar head up to the 16-byte boundary, then four edges
+    // per thread per step (the previous edge of a group is the neighbouring
+    // lane's last; a warp's first lane loads its own), then a scalar tail.
+    const int lane = tid & 31, warp = tid >> 5;
+    if (vec) {
+        const int tail0 = head + 4 * Q;
+        if (tid < head) edge_scalar(tid);
+        else if (tid >= 32 && tid - 32 < E - tail0) edge_scalar(tail0 + tid - 32);
+        for (int base = 0; base < Q; base += kPlanQuads * kPlanThreads) {
+            int4 kv[kPlanQuads], jv[kPlanQuads];
+            int kq[kPlanQuads], jq[kPlanQuads];
+#pragma unroll
+            for (int u = 0; u < kPlanQuads; ++u) {   // loads of all unrolled quads first
+                const int q = base + u * kPlanThreads + tid;
+                kv[u] = make_int4(0, 0, 0, 0); jv[u] = kv[u]; kq[u] = -1; jq[u] = -1;
+                if (q < Q) {
+                    kv[u] = kk4[q];
+                    jv[u] = jj4[q];
+                    if (lane == 0 && head + 4 * q > 0) {
+                        kq[u] = pr.kk[head + 4 * q - 1];
+                        jq[u] = pr.jj[head + 4 * q - 1];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPlanQuads; ++u) {
+                const int q = base + u * kPlanThreads + tid;
+                const int ks = __shfl_up_sync(0xffffffffu, kv[u].w, 1);
+                const int js = __shfl_up_sync(0xffffffffu, jv[u].w, 1);
+                if (lane > 0) { kq[u] = ks; jq[u] = js; }
+                if (q >= Q) continue;
+                const int e = head + 4 * q;
+                edge(e, kv[u].x, jv[u].x, kq[u], jq[u]);
+                edge(e + 1, kv[u].y, jv[u].y, kv[u].x, jv[u].x);
+                edge(e + 2, kv[u].z, jv[u].z, kv[u].y, jv[u].y);
+                edge(e + 3, kv[u].w, jv[u].w, kv[u].z, jv[u].z);
+            }
+        }
+    } else {
+        for (int e = tid; e < E; e += kPlanThreads) edge_scalar(e);
     }
     if (bad) atomicOr(&s_bad, 1);
     __syncthreads();
@@ -169,15 +223,25 @@ __global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__res
         if (tid == 0) { *pr.status = DPVO_BA_STATUS_BAD_INPUT; *pr.n_chunks = 0; }
         return;
     }
-    if (tid == 0) {
-        int off = 0;
-        for (int i = 0; i < N; ++i) {
-            s_choff[i] = off;
-            const int cnt = s_fstart[i + 1] - s_fstart[i];
-            off += (cnt + pr.chunk_cap - 1) / pr.chunk_cap;
+    if (warp == 0) {   // first chunk of each frame: exclusive scan of the frames' chunk counts
+        int carry = 0;
+        for (int i0 = 0; i0 < N; i0 += 32) {
+            const int i = i0 + lane;
+            const int cnt = i < N ? s_fstart[i + 1] - s_fstart[i] : 0;
+            const int nc = (cnt + pr.chunk_cap - 1) / pr.chunk_cap;
+            int incl = nc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (i < N) s_choff[i] = carry + incl - nc;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        s_choff[N] = off;
-        if (off > pr.max_chunks) s_bad = 1;
+        if (lane == 0) {
+            s_choff[N] = carry;
+            if (carry > pr.max_chunks) s_bad = 1;
+        }
     }
     __syncthreads();
     for (int i = tid; i < N && !s_bad; i += kPlanThreads) {
@@ -204,7 +268,6 @@ __global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__res
     __syncthreads();
     // frame window [jlo, jhi] of each chunk: edges of a patch are sorted by
     // frame, so its first and last edges bound it
-    const int lane = tid & 31, warp = tid >> 5;
     const int n_built = s_bad ? 0 : s_choff[N];    // 0 if the chunk table overflowed
     for (int c = warp; c < n_built; c += kPlanThreads / 32) {
         const Chunk ch = pr.chunks[c];
@@ -503,6 +566,8 @@ __device__ __forceinline__ float quad_sum(float v) {
 // dd_k = C_k^-1/2 (C_k^-1/2 w_k - (C_k^-1/2 e_k) . dxi), read from the stored
 // Schur rows.  Row layout: patches [k_lo, k_hi), four lanes per patch, dxs the
 // increment in the rows' padded frame layout.
+constexpr int kBsLoads = 5;   // float4 loads of a stored row per lane in flight together
+
 __device__ __forceinline__ void backsub_rows(const Prob &pr, const float *dxs, const float *depth_old,
                                              float *depth_new, int k_lo, int k_hi, int tid) {
     const int nf = pr.nf, RS = erow_len(nf);
@@ -512,9 +577,17 @@ __device__ __forceinline__ void backsub_rows(const Prob &pr, const float *dxs, c
         const int k = kb + (tid >> 2);
         float s = 0.f;
         const float *row = pr.erow + (size_t)k * RS;
-        if (k < k_hi) {
-#pragma unroll 2
-            for (int q = sub; q < RS / 4; q += 4) s = dot4(reinterpret_cast<const float4 *>(row)[q], dz4[q], s);
+        if (k < k_hi) {   // the lane's float4s q = sub + 4i, kBsLoads loads in flight at a time
+            const float4 *row4 = reinterpret_cast<const float4 *>(row);
+            for (int q0 = sub; q0 < RS / 4; q0 += 4 * kBsLoads) {
+                float4 v[kBsLoads];
+#pragma unroll
+                for (int i = 0; i < kBsLoads; ++i)
+                    v[i] = q0 + 4 * i < RS / 4 ? row4[q0 + 4 * i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < kBsLoads; ++i)
+                    if (q0 + 4 * i < RS / 4) s = dot4(v[i], dz4[q0 + 4 * i], s);
+            }
         }
         s = quad_sum(s);
         if (k < k_hi && sub == 0) {
@@ -1449,7 +1522,7 @@ constexpr int kFinalPatches = kThreads / 4;
 constexpr int kFinalChunks = kThreads / 32;
 
 template <bool TC>
-__global__ void __launch_bounds__(kThreads, TC ? 5 : 8) final_kernel(const Prob *__restrict__ probs, int t, int G_cap) {
+__global__ void __launch_bounds__(kThreads, TC ? 5 : 6) final_kernel(const Prob *__restrict__ probs, int t, int G_cap) {
     extern __shared__ __align__(16) float dxf[];
     const Prob &pr = probs[blockIdx.x];
     const int tid = threadIdx.x;

@@ -175,8 +175,13 @@ def test_empty_graph_is_not_spd_and_leaves_state(solver):
     assert torch.equal(probs[0].patches.cpu(), torch.as_tensor(sc.patches))
 
 
-@pytest.mark.parametrize("breakage", ["unsorted_kk", "frame_out_of_range", "duplicate_edge", "anchor_order"])
+@pytest.mark.parametrize("breakage", ["unsorted_kk", "frame_out_of_range", "duplicate_edge", "anchor_order",
+                                      "duplicate_at_quad_start", "unsorted_at_warp_start"])
 def test_bad_input_is_flagged_and_leaves_state(solver, breakage):
+    """Ordering and range violations anywhere in the edge list, including at
+    the first edge of a 4-edge group (its predecessor comes from the
+    neighbouring thread) and at the first edge of a warp's span (read on its
+    own); every patch of this scene has 8 edges, so edges 128..135 are patch 16."""
     sc = S.make_scene(S.PLAIN_N8, 46)
     kk, jj, anchor = sc.kk.copy(), sc.jj.copy(), sc.anchor.copy()
     if breakage == "unsorted_kk":
@@ -185,6 +190,11 @@ def test_bad_input_is_flagged_and_leaves_state(solver, breakage):
         jj[7] = sc.n_frames
     elif breakage == "duplicate_edge":
         jj[9] = jj[8]
+    elif breakage == "duplicate_at_quad_start":
+        assert kk[132] == kk[131]
+        jj[132] = jj[131]
+    elif breakage == "unsorted_at_warp_start":
+        kk[128] = kk[127] - 1
     else:
         anchor[3], anchor[400] = anchor[400], anchor[3]
     bad = dataclasses.replace(sc, kk=kk, jj=jj, anchor=anchor)
@@ -197,6 +207,34 @@ def test_bad_input_is_flagged_and_leaves_state(solver, breakage):
     assert int(probs[1].status.item()) == 0
     for e_xi, e_dd in step_errors(solver, good, 1, 2):
         assert e_xi < TOL_POSE and e_dd < TOL_DEPTH
+
+
+@pytest.mark.parametrize("kk_off,jj_off,drop", [(1, 1, 1), (2, 2, 3), (3, 3, 2), (0, 1, 0), (3, 1, 2)])
+def test_edge_arrays_at_any_offset_solve_identically(solver, kk_off, jj_off, drop):
+    """kk and jj at every 4-byte offset from a 16-byte boundary, with edge
+    counts that leave 0-3 edges over after the 4-edge groups: the plan reads
+    the edges in groups of four where kk and jj share their offset (a short
+    head and tail edge by edge) and edge by edge where they do not; every
+    placement gives bitwise the same solve."""
+    sc = S.make_scene(S.WINDOW_N22, 50)
+    if drop:
+        sc = dataclasses.replace(sc, kk=sc.kk[:-drop], jj=sc.jj[:-drop], target=sc.target[:-drop],
+                                 weight=sc.weight[:-drop], outlier=sc.outlier[:-drop], uv_true=sc.uv_true[:-drop])
+    ref = solve_gpu(solver, [sc])[0]
+    assert int(ref.status.item()) == 0
+
+    def shifted(t, off):
+        big = torch.zeros(t.numel() + 4, dtype=t.dtype, device=t.device)
+        big[off:off + t.numel()] = t
+        return big[off:off + t.numel()]
+
+    p = ba.problem_from_scene(sc)
+    p = dataclasses.replace(p, kk=shifted(p.kk, kk_off), jj=shifted(p.jj, jj_off))
+    assert (p.kk.data_ptr() - kk_off * 4) % 16 == 0 and (p.jj.data_ptr() - jj_off * 4) % 16 == 0
+    solver.solve([p])
+    torch.cuda.synchronize()
+    assert int(p.status.item()) == 0
+    assert torch.equal(p.poses, ref.poses) and torch.equal(p.patches, ref.patches)
 
 
 def test_host_buffer_entry_point_matches_device_entry_point(solver):
