@@ -179,17 +179,18 @@ def algorithmic_work(scene):
     return flops, bytes_
 
 
-def stress_bench(n_sessions, steps, stream, hbm_peak):
+def stress_bench(n_sessions, steps, stream, hbm_peak, tf32=False):
     """Large-window workload: n_sessions problems of 64 frames x 256 patches
     (16,384), radius 24 (649,216 edges), the last 32 poses free (192 x 192), 4
     Gauss-Newton iterations, 20 % outliers; 8 distinct seeded scenes tiled.
-    Per-kernel times from the library's launch events."""
+    Per-kernel times from the library's launch events.  tf32: the Schur
+    assembly as three TF32 products on the tensor cores."""
     import torch
     from paper_2208_04726_b300 import ba
     from paper_2208_04726_b300 import scenes as S
     distinct = [S.make_scene(S.STRESS_N64, 500 + s) for s in range(min(8, n_sessions))]
     batch = ba.PackedBatch([distinct[b % len(distinct)] for b in range(n_sessions)], "cuda")
-    solver = ba.Solver()
+    solver = ba.Solver(schur_tf32=tf32)
     for _ in range(2):
         solver.solve_arrays(batch.dims, batch.probs, n_sessions, stream)
     torch.cuda.synchronize()
@@ -798,6 +799,11 @@ def main():
 
     serving = serving_bench() if (rank == 0 and args.serving) else None
     stress = stress_bench(args.stress, 5, stream, load_peaks()[0]) if (rank == 0 and args.stress > 0) else None
+    if stress is not None and args.tf32:
+        st = stress_bench(args.stress, 5, stream, load_peaks()[0], tf32=True)
+        stress["tf32_schur"] = {k: st[k] for k in ("solves_per_s", "ms_per_step", "statuses_nonzero", "kernels")}
+        stress["tf32_schur"]["note"] = ("S - E C^-1 E^T assembled as three TF32 products on the tensor cores "
+                                        "(tcgen05, TMEM); parity: tests/test_gpu_large.py, both modes")
     grad = grad_bench(args.grad, parity=args.parity_samples > 0) if (rank == 0 and args.grad > 0) else None
     window = window_bench(args.window) if (rank == 0 and args.window > 0) else None
     vo_mix = vo_mix_bench() if (rank == 0 and args.vo_mix) else None

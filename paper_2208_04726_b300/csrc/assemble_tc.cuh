@@ -1,0 +1,210 @@
+// Schur assembly on the tensor cores, for reduced systems with more free poses
+// than the linearise kernel's strip owners hold (Sec. 3.1, the Schur
+// complement over the inverse depths), in the opt-in TF32 Schur mode:
+//     S  -= sum_k (C_k^-1/2 e_k)(C_k^-1/2 e_k)^T,   v' -= sum_k (C_k^-1/2 e_k)(C_k^-1/2 w_k).
+// For a wide window this sum is a dense product X^T X over the patches, X the
+// stored rows C_k^-1/2 (e_k, w_k): 16,384 patches by 192 pose columns on the
+// 64-frame window.
+//
+// Operand: the row entries 0..255 of each patch (frame f at 8f..8f+7 as
+// [v0 v1 v2 0 v3 v4 v5 0], the zero entries stay zero) as a 256-row K-major
+// TF32 operand over kAtcK patches, split into hi = tf32(x) and lo =
+// tf32(x - hi).  Three TF32 products hi hi^T + lo hi^T + hi lo^T give the
+// FP32-accurate product (the lo lo^T term is below FP32 rounding).  Per 8
+// patches: rows 0..127 against rows 0..255 (M = 128, N = 256: blocks (0,0)
+// and (0,1)) and rows 128..255 against themselves (M = N = 128: block (1,1)),
+// 384 TMEM columns.  With at most 16 free poses only block (0,0) is formed.
+// v' stays on the CUDA cores: it tends to zero as the iterations converge,
+// so its terms cancel, and a thread per row entry sums it in FP32 per stage
+// with compensated adds across stages, as the CUDA-core assembly does.
+//
+// One CTA of kAtcThreads threads per (problem, work item): a range of at most
+// kAtcMaxPatches patches (the FP32 accumulation length in TMEM).  Thread 0
+// streams the stored rows through two shared-memory stages by bulk copies and
+// issues the MMAs; all threads split a stage into one of two operand buffers
+// while the MMAs of the previous stage run.  Every wait is bounded; on a
+// timeout the CTA reports DPVO_BA_STATUS_TIMEOUT, waits (again bounded) for
+// its copies and MMAs in flight and leaves.  The result goes to the CTA's FP64
+// partial in the layout of schur_assembly_kernel (the 6 x 6 block of pair
+// (a, b), a <= b, row-major at 36 x its pair index, then v').
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "assemble.cuh"
+#include "ba_common.cuh"
+#include "tc.cuh"
+
+namespace dpvo {
+
+constexpr int kAtcThreads = 512;
+constexpr int kAtcK = 32;                                      // patches per stage
+constexpr int kAtcRows = 256;                                  // operand rows (row entries 0..255)
+constexpr uint32_t kAtcSbo = (kAtcK / 4) * kLbo;               // bytes between 8-row groups
+constexpr uint32_t kAtcOpBytes = (kAtcRows / 8) * kAtcSbo;     // one operand half (hi or lo)
+constexpr int kAtcMaxPatches = 2048;                           // patches per CTA at most
+constexpr int kAtcCols = 512;                                  // TMEM columns allocated (384 used)
+
+// Dynamic shared memory: two operand buffers (hi, lo), then two row stages.
+__host__ __device__ inline size_t atc_smem_bytes(int rs_max) {
+    return 4 * (size_t)kAtcOpBytes + 2 * (size_t)kAtcK * rs_max * 4;
+}
+
+// Component of a row entry within its frame ([v0 v1 v2 0 v3 v4 v5 0]), -1 for a pad.
+__device__ __forceinline__ int atc_comp(int s) { return (s == 3 || s == 7) ? -1 : (s < 3 ? s : s - 1); }
+
+__global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const Prob *__restrict__ probs,
+                                                                           const Item *__restrict__ items, int t,
+                                                                           int rs_max) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Item itm = items[blockIdx.x];
+    const Prob &pr = probs[itm.prob];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (t >= pr.iters || *pr.status != 0) return;
+
+    const int nf = pr.nf, RS = erow_len(nf), np = n_block_pairs(nf);
+    const int k_lo = (int)(((long long)itm.item * pr.P) / pr.n_asm);
+    const int k_hi = (int)(((long long)(itm.item + 1) * pr.P) / pr.n_asm);
+    const int n_st = (k_hi - k_lo + kAtcK - 1) / kAtcK;
+    const bool two = 8 * nf > kAtcRows / 2;                    // frames beyond 15: block (1,1) too
+    double *out = pr.partial + (size_t)(pr.n_items + itm.item) * pr.L;
+    if (n_st == 0) {
+        for (int q = tid; q < pr.L; q += kAtcThreads) out[q] = 0.0;
+        return;
+    }
+
+    unsigned char *ops = smem;                                 // buffer b: hi at 2b kAtcOpBytes, lo after it
+    float *raw0 = reinterpret_cast<float *>(smem + 4 * kAtcOpBytes);
+    const size_t raw_len = (size_t)kAtcK * rs_max;
+    __shared__ __align__(8) uint64_t s_full[2], s_done[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_bad;
+    if (warp == 0) tmem_alloc(&s_tmem, kAtcCols);
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&s_full[b]), 1);
+            mbar_init(smem_u32(&s_done[b]), 1);
+        }
+        s_bad = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    // thread 0's bookkeeping: stages whose rows were requested, the last stage committed
+    int n_issued = 0, last_commit = -1;
+    auto issue = [&](int s) {
+        const int k0 = k_lo + s * kAtcK, rows = min(kAtcK, k_hi - k0);
+        bulk_load(raw0 + (s & 1) * raw_len, pr.erow + (size_t)k0 * RS, (uint32_t)(rows * RS * 4),
+                  smem_u32(&s_full[s & 1]));
+        n_issued = s + 1;
+    };
+    if (tid == 0) {
+        issue(0);
+        if (n_st > 1) issue(1);
+    }
+
+    const int r8 = lane >> 2, k4 = lane & 3;
+    float v_s = 0.f, v_c = 0.f;                                // v' of row entry tid (compensated)
+    for (int s = 0; s < n_st; ++s) {
+        const int b = s & 1;
+        bool ok = mbar_wait(smem_u32(&s_full[b]), (uint32_t)(s >> 1) & 1u);
+        if (ok && s >= 2) ok = mbar_wait(smem_u32(&s_done[b]), (uint32_t)((s - 2) >> 1) & 1u);   // buffer b read
+        if (!ok) {
+            atomicOr(&s_bad, 1);
+        } else {
+            // split: a warp writes one 8 x 4 (row, patch) core-matrix tile of hi and of lo at a time
+            const float *raw = raw0 + b * raw_len;
+            const int rows = min(kAtcK, k_hi - (k_lo + s * kAtcK));
+            unsigned char *hi = ops + 2 * b * kAtcOpBytes, *lo = hi + kAtcOpBytes;
+#pragma unroll 2
+            for (int idx = warp; idx < (kAtcRows / 8) * (kAtcK / 4); idx += kAtcThreads / 32) {
+                const int rg = idx / (kAtcK / 4), kg = idx % (kAtcK / 4);
+                const int m = 8 * rg + r8, k = 4 * kg + k4;
+                const float x = (k < rows && m < 8 * nf) ? raw[k * RS + m] : 0.f;
+                const uint32_t h = to_tf32(x), l = to_tf32(x - __uint_as_float(h));
+                const uint32_t off = (uint32_t)rg * kAtcSbo + (uint32_t)kg * kLbo + (uint32_t)(16 * r8 + 4 * k4);
+                *reinterpret_cast<uint32_t *>(hi + off) = h;
+                *reinterpret_cast<uint32_t *>(lo + off) = l;
+            }
+            if (tid < 8 * nf) {   // v': thread m = tid, this stage's patches in FP32, then a compensated add
+                float blk = 0.f;
+                for (int k = 0; k < rows; ++k) blk = fmaf(-raw[k * RS + 8 * nf], raw[k * RS + tid], blk);
+                kahan_add(v_s, v_c, blk);
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (s_bad) break;
+        if (tid == 0) {
+            tc_fence_after();
+            if (s + 2 < n_st) issue(s + 2);                    // row stage b is consumed
+            const uint32_t hb = smem_u32(ops + 2 * b * kAtcOpBytes), lb = hb + kAtcOpBytes;
+            const uint32_t half = (kAtcRows / 16) * kAtcSbo;   // rows 128..255
+            const uint32_t id0 = idesc_tf32(128, two ? 256 : 128), id1 = idesc_tf32(128, 128);
+            for (int ks = 0; ks < kAtcK / 8; ++ks) {
+                const uint32_t o = ks * 2 * kLbo;
+                const int acc = (s > 0 || ks > 0) ? 1 : 0;
+                const uint64_t h0 = smem_desc(hb + o, kLbo, kAtcSbo), l0 = smem_desc(lb + o, kLbo, kAtcSbo);
+                mma_tf32(tmem, h0, h0, id0, acc);
+                mma_tf32(tmem, l0, h0, id0, 1);
+                mma_tf32(tmem, h0, l0, id0, 1);
+                if (two) {
+                    const uint64_t h1 = smem_desc(hb + half + o, kLbo, kAtcSbo);
+                    const uint64_t l1 = smem_desc(lb + half + o, kLbo, kAtcSbo);
+                    mma_tf32(tmem + 256, h1, h1, id1, acc);
+                    mma_tf32(tmem + 256, l1, h1, id1, 1);
+                    mma_tf32(tmem + 256, h1, l1, id1, 1);
+                }
+            }
+            mma_commit(smem_u32(&s_done[b]));
+            last_commit = s;
+        }
+    }
+    if (!s_bad && !mbar_wait(smem_u32(&s_done[(n_st - 1) & 1]), (uint32_t)((n_st - 1) >> 1) & 1u))
+        atomicOr(&s_bad, 1);
+    __syncthreads();
+    if (!s_bad) {
+        if (tid < 8 * nf && atc_comp(tid & 7) >= 0)
+            out[36 * np + 6 * (tid >> 3) + atc_comp(tid & 7)] = (double)v_s - (double)v_c;
+        // read-back: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows m), columns
+        // [96 (w / 4), 96 (w / 4) + 96)
+        tc_fence_after();
+        const int m = 32 * (warp & 3) + lane;
+        const int c_begin = 96 * (warp >> 2);
+        for (int c0 = c_begin; c0 < c_begin + 96; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int c = c0 + q;
+                int R, C;
+                if (c < 256) {
+                    if (!two && c >= 128) continue;
+                    R = m;
+                    C = c;
+                } else {
+                    if (!two) continue;
+                    R = 128 + m;
+                    C = c - 128;
+                }
+                const int fr = R >> 3, fc = C >> 3, ir = atc_comp(R & 7), ic = atc_comp(C & 7);
+                if (ir >= 0 && ic >= 0 && fr <= fc && fc < nf)
+                    out[36 * (fr * nf - fr * (fr - 1) / 2 + (fc - fr)) + 6 * ir + ic] = -(double)v[q];
+            }
+        }
+    } else if (tid == 0) {
+        // report, and give the copies and MMAs in flight a bounded wait before the TMEM is freed
+        atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
+        for (int u = n_issued > 2 ? n_issued - 2 : 0; u < n_issued; ++u)
+            mbar_wait(smem_u32(&s_full[u & 1]), (uint32_t)(u >> 1) & 1u);
+        if (last_commit >= 0) mbar_wait(smem_u32(&s_done[last_commit & 1]), (uint32_t)(last_commit >> 1) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kAtcCols);
+}
+
+}  // namespace dpvo

@@ -10,6 +10,7 @@
 #include "ba_common.cuh"
 #include "kernels.cuh"
 #include "solve_large.cuh"
+#include "assemble_tc.cuh"
 #include "assemble.cuh"
 #include "backward.cuh"
 #include "serve.cuh"
@@ -34,6 +35,7 @@ struct Layout {
     int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0, n_max = 1;
     bool tc = false;               // Schur accumulation on the tensor cores
     bool ext = false;              // more than kFusedMaxFree free poses: assembly kernel, packed solve
+    bool tc_asm = false;           // ext with the TF32 Schur mode: the assembly on the tensor cores
     int n_lin_items = 0, n_asm_items = 0;
     int final_slices = 1;          // y extent of the last back-substitution's grid
     size_t lin_smem = 0, solve_smem = 0, asm_smem = 0;
@@ -55,6 +57,11 @@ static size_t erow_bytes(bool tc, const Prob &p, int G_cap) {
 
 // Assembly launch (ext batches): grid x = assembly items, y = strip slices.
 static void launch_assembly(const Layout &L, cudaStream_t stream, const Prob *probs, const Item *asm_items, int t) {
+    if (L.tc_asm) {
+        schur_assembly_tc_kernel<<<L.n_asm_items, kAtcThreads, L.asm_smem, stream>>>(probs, asm_items, t,
+                                                                                     erow_len(L.nf_max));
+        return;
+    }
     const dim3 grid(L.n_asm_items, asm_slices(L.nf_max));
     schur_assembly_kernel<<<grid, asm_threads(L.nf_max), L.asm_smem, stream>>>(probs, asm_items, t,
                                                                                erow_len(L.nf_max));
@@ -131,9 +138,12 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         L.G_cap -= 8;
     L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
     L.ext = L.nf_max > kFusedMaxFree;
+    L.tc_asm = L.ext && cfg.schur_tf32;
     L.solve_smem = L.ext ? solve_large_smem_bytes(L.nf_max) : solve_smem_bytes(L.nf_max);
-    L.asm_smem = L.ext ? asm_smem_bytes(erow_len(L.nf_max), asm_threads(L.nf_max)) : 0;
-    const int asm_slices_max = L.ext ? asm_slices(L.nf_max) : 1;
+    L.asm_smem = !L.ext ? 0
+                 : L.tc_asm ? atc_smem_bytes(erow_len(L.nf_max))
+                            : asm_smem_bytes(erow_len(L.nf_max), asm_threads(L.nf_max));
+    const int asm_slices_max = L.ext && !L.tc_asm ? asm_slices(L.nf_max) : 1;
 
     const int target_ctas = 2 * num_sms;
     const int final_cap = std::max(1, (6 * num_sms + n - 1) / n);   // one wave of final_kernel CTAs
@@ -157,7 +167,11 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         int est_chunks = std::max(1, (d.n_patches + L.G_cap - 1) / L.G_cap);
         int items = std::max(1, target_ctas / n);
         p.n_items = std::max(1, std::min(items, est_chunks));
-        if (L.ext) {
+        if (L.tc_asm) {   // ranges of at most kAtcMaxPatches patches, at least one CTA per SM over the batch
+            const int need = (d.n_patches + kAtcMaxPatches - 1) / kAtcMaxPatches;
+            const int stages = std::max(1, (d.n_patches + kAtcK - 1) / kAtcK);
+            p.n_asm = std::max(1, std::min(stages, std::max(need, num_sms / n)));
+        } else if (L.ext) {
             const int per = std::max(1, num_sms / (n * asm_slices_max));
             p.n_asm = std::max(1, std::min(per, est_chunks));
         }
@@ -292,6 +306,9 @@ static int set_kernel_attrs(int device) {
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(schur_assembly_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(schur_assembly_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)atc_smem_bytes(erow_len(kMaxFree))) != cudaSuccess)
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(bw_edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
