@@ -6,14 +6,17 @@
 // stored rows C_k^-1/2 (e_k, w_k): 16,384 patches by 192 pose columns on the
 // 64-frame window.
 //
-// Operand: the row entries 0..255 of each patch (frame f at 8f..8f+7 as
-// [v0 v1 v2 0 v3 v4 v5 0], the zero entries stay zero) as a 256-row K-major
-// TF32 operand over kAtcK patches, split into hi = tf32(x) and lo =
-// tf32(x - hi).  Three TF32 products hi hi^T + lo hi^T + hi lo^T give the
-// FP32-accurate product (the lo lo^T term is below FP32 rounding).  Per 8
-// patches: rows 0..127 against rows 0..255 (M = 128, N = 256: blocks (0,0)
-// and (0,1)) and rows 128..255 against themselves (M = N = 128: block (1,1)),
-// 384 TMEM columns.  With at most 16 free poses only block (0,0) is formed.
+// Operand: the n6 = 6 nf pose entries of each patch's row (the stored row's
+// pads [v0 v1 v2 0 v3 v4 v5 0] dropped: operand row 6f + c is pose component c
+// of free frame f) as a K-major TF32 operand of kAtcOpRows rows (zero beyond
+// n6) over kAtcK patches, split into hi = tf32(x) and lo = tf32(x - hi).
+// Three TF32 products hi hi^T + lo hi^T + hi lo^T give the FP32-accurate
+// product (the lo lo^T term is below FP32 rounding).  Per 8 patches: rows
+// 0..127 against rows 0..n6-1 (M = 128, N = n6 rounded up to 16) into TMEM
+// columns 0.., and, beyond 128 rows, rows a0..a0+127 (a0 = n6 rounded up to
+// 8, less 128) against rows 120..n6-1 (from the first frame that reaches row
+// 128, rounded down to 8) into columns 256..; every pose-pair block a <= b
+// lies in one of the two.
 // v' stays on the CUDA cores: it tends to zero as the iterations converge,
 // so its terms cancel, and a thread per row entry sums it in FP32 per stage
 // with compensated adds across stages, as the CUDA-core assembly does.
@@ -40,9 +43,11 @@ namespace dpvo {
 
 constexpr int kAtcThreads = 512;
 constexpr int kAtcK = 32;                                      // patches per stage
-constexpr int kAtcRows = 256;                                  // operand rows (row entries 0..255)
+constexpr int kAtcOpRows = 200;                                // operand rows: 6 x 32 pose entries, and the
+                                                               // zero rows 192..199 the second product reads
+constexpr int kAtcB0 = 120;                                    // first row of the second product's B operand
 constexpr uint32_t kAtcSbo = (kAtcK / 4) * kLbo;               // bytes between 8-row groups
-constexpr uint32_t kAtcOpBytes = (kAtcRows / 8) * kAtcSbo;     // one operand half (hi or lo)
+constexpr uint32_t kAtcOpBytes = (kAtcOpRows / 8) * kAtcSbo;   // one operand half (hi or lo)
 constexpr int kAtcMaxPatches = 2048;                           // patches per CTA at most
 constexpr int kAtcCols = 512;                                  // TMEM columns allocated (384 used)
 
@@ -51,8 +56,11 @@ __host__ __device__ inline size_t atc_smem_bytes(int rs_max) {
     return 4 * (size_t)kAtcOpBytes + 2 * (size_t)kAtcK * rs_max * 4;
 }
 
-// Component of a row entry within its frame ([v0 v1 v2 0 v3 v4 v5 0]), -1 for a pad.
-__device__ __forceinline__ int atc_comp(int s) { return (s == 3 || s == 7) ? -1 : (s < 3 ? s : s - 1); }
+// Entry of the stored row that holds pose entry m = 6 f + c.
+__device__ __forceinline__ int atc_src(int m) {
+    const int f = m / 6, c = m - 6 * f;
+    return 8 * f + (c < 3 ? c : c + 1);
+}
 
 __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const Prob *__restrict__ probs,
                                                                            const Item *__restrict__ items, int t,
@@ -63,11 +71,12 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (t >= pr.iters || *pr.status != 0) return;
 
-    const int nf = pr.nf, RS = erow_len(nf), np = n_block_pairs(nf);
+    const int nf = pr.nf, RS = erow_len(nf), np = n_block_pairs(nf), n6 = 6 * nf;
     const int k_lo = (int)(((long long)itm.item * pr.P) / pr.n_asm);
     const int k_hi = (int)(((long long)(itm.item + 1) * pr.P) / pr.n_asm);
     const int n_st = (k_hi - k_lo + kAtcK - 1) / kAtcK;
-    const bool two = 8 * nf > kAtcRows / 2;                    // frames beyond 15: block (1,1) too
+    const bool two = n6 > 128;                                 // the second product
+    const int N0 = (n6 + 15) & ~15, a0 = ((n6 + 7) & ~7) - 128, N1 = two ? (n6 - kAtcB0 + 15) & ~15 : 0;
     double *out = pr.partial + (size_t)(pr.n_items + itm.item) * pr.L;
     if (n_st == 0) {
         for (int q = tid; q < pr.L; q += kAtcThreads) out[q] = 0.0;
@@ -120,18 +129,19 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
             const int rows = min(kAtcK, k_hi - (k_lo + s * kAtcK));
             unsigned char *hi = ops + 2 * b * kAtcOpBytes, *lo = hi + kAtcOpBytes;
 #pragma unroll 2
-            for (int idx = warp; idx < (kAtcRows / 8) * (kAtcK / 4); idx += kAtcThreads / 32) {
+            for (int idx = warp; idx < (kAtcOpRows / 8) * (kAtcK / 4); idx += kAtcThreads / 32) {
                 const int rg = idx / (kAtcK / 4), kg = idx % (kAtcK / 4);
                 const int m = 8 * rg + r8, k = 4 * kg + k4;
-                const float x = (k < rows && m < 8 * nf) ? raw[k * RS + m] : 0.f;
+                const float x = (k < rows && m < n6) ? raw[k * RS + atc_src(m)] : 0.f;
                 const uint32_t h = to_tf32(x), l = to_tf32(x - __uint_as_float(h));
                 const uint32_t off = (uint32_t)rg * kAtcSbo + (uint32_t)kg * kLbo + (uint32_t)(16 * r8 + 4 * k4);
                 *reinterpret_cast<uint32_t *>(hi + off) = h;
                 *reinterpret_cast<uint32_t *>(lo + off) = l;
             }
-            if (tid < 8 * nf) {   // v': thread m = tid, this stage's patches in FP32, then a compensated add
+            if (tid < n6) {   // v': thread m = tid, this stage's patches in FP32, then a compensated add
+                const int src = atc_src(tid);
                 float blk = 0.f;
-                for (int k = 0; k < rows; ++k) blk = fmaf(-raw[k * RS + 8 * nf], raw[k * RS + tid], blk);
+                for (int k = 0; k < rows; ++k) blk = fmaf(-raw[k * RS + 8 * nf], raw[k * RS + src], blk);
                 kahan_add(v_s, v_c, blk);
             }
         }
@@ -142,8 +152,8 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
             tc_fence_after();
             if (s + 2 < n_st) issue(s + 2);                    // row stage b is consumed
             const uint32_t hb = smem_u32(ops + 2 * b * kAtcOpBytes), lb = hb + kAtcOpBytes;
-            const uint32_t half = (kAtcRows / 16) * kAtcSbo;   // rows 128..255
-            const uint32_t id0 = idesc_tf32(128, two ? 256 : 128), id1 = idesc_tf32(128, 128);
+            const uint32_t oa = (uint32_t)(a0 >> 3) * kAtcSbo, ob = (uint32_t)(kAtcB0 >> 3) * kAtcSbo;
+            const uint32_t id0 = idesc_tf32(128, N0), id1 = idesc_tf32(128, two ? N1 : 16);
             for (int ks = 0; ks < kAtcK / 8; ++ks) {
                 const uint32_t o = ks * 2 * kLbo;
                 const int acc = (s > 0 || ks > 0) ? 1 : 0;
@@ -152,11 +162,11 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
                 mma_tf32(tmem, l0, h0, id0, 1);
                 mma_tf32(tmem, h0, l0, id0, 1);
                 if (two) {
-                    const uint64_t h1 = smem_desc(hb + half + o, kLbo, kAtcSbo);
-                    const uint64_t l1 = smem_desc(lb + half + o, kLbo, kAtcSbo);
-                    mma_tf32(tmem + 256, h1, h1, id1, acc);
-                    mma_tf32(tmem + 256, l1, h1, id1, 1);
-                    mma_tf32(tmem + 256, h1, l1, id1, 1);
+                    const uint64_t ha = smem_desc(hb + oa + o, kLbo, kAtcSbo), la = smem_desc(lb + oa + o, kLbo, kAtcSbo);
+                    const uint64_t hbb = smem_desc(hb + ob + o, kLbo, kAtcSbo), lbb = smem_desc(lb + ob + o, kLbo, kAtcSbo);
+                    mma_tf32(tmem + 256, ha, hbb, id1, acc);
+                    mma_tf32(tmem + 256, la, hbb, id1, 1);
+                    mma_tf32(tmem + 256, ha, lbb, id1, 1);
                 }
             }
             mma_commit(smem_u32(&s_done[b]));
@@ -167,32 +177,27 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
         atomicOr(&s_bad, 1);
     __syncthreads();
     if (!s_bad) {
-        if (tid < 8 * nf && atc_comp(tid & 7) >= 0)
-            out[36 * np + 6 * (tid >> 3) + atc_comp(tid & 7)] = (double)v_s - (double)v_c;
-        // read-back: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows m), columns
-        // [96 (w / 4), 96 (w / 4) + 96)
+        if (tid < n6) out[36 * np + tid] = (double)v_s - (double)v_c;
+        // read-back: warp w reads TMEM lanes 32 (w % 4) .. +31 (m) and every
+        // fourth 16-column chunk from chunk w / 4 of the N0 columns from 0
+        // and the N1 columns from 256
         tc_fence_after();
         const int m = 32 * (warp & 3) + lane;
-        const int c_begin = 96 * (warp >> 2);
-        for (int c0 = c_begin; c0 < c_begin + 96; c0 += 16) {
+        const int n_ch0 = N0 / 16, n_ch = n_ch0 + N1 / 16;
+        for (int j = warp >> 2; j < n_ch; j += kAtcThreads / 128) {
+            const bool r1 = j >= n_ch0;
+            const int c0 = r1 ? 256 + 16 * (j - n_ch0) : 16 * j;
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + c0, v);
+            const int R = r1 ? a0 + m : m;
+            if (R >= n6 || (r1 && R < 128)) continue;
+            const int fr = R / 6, ir = R - 6 * fr;
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const int c = c0 + q;
-                int R, C;
-                if (c < 256) {
-                    if (!two && c >= 128) continue;
-                    R = m;
-                    C = c;
-                } else {
-                    if (!two) continue;
-                    R = 128 + m;
-                    C = c - 128;
-                }
-                const int fr = R >> 3, fc = C >> 3, ir = atc_comp(R & 7), ic = atc_comp(C & 7);
-                if (ir >= 0 && ic >= 0 && fr <= fc && fc < nf)
-                    out[36 * (fr * nf - fr * (fr - 1) / 2 + (fc - fr)) + 6 * ir + ic] = -(double)v[q];
+                const int C = r1 ? kAtcB0 + (c0 - 256) + q : c0 + q;
+                const int fc = C / 6;
+                if (C < n6 && fr <= fc)
+                    out[36 * (fr * nf - fr * (fr - 1) / 2 + (fc - fr)) + 6 * ir + (C - 6 * fc)] = -(double)v[q];
             }
         }
     } else if (tid == 0) {
