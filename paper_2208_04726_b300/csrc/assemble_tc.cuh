@@ -9,7 +9,9 @@
 // Operand: the n6 = 6 nf pose entries of each patch's row (the stored row's
 // pads [v0 v1 v2 0 v3 v4 v5 0] dropped: operand row 6f + c is pose component c
 // of free frame f) as a K-major TF32 operand of kAtcOpRows rows (zero beyond
-// n6) over kAtcK patches, split into hi = tf32(x) and lo = tf32(x - hi).
+// n6) over kAtcK patches, split into hi = tf32(x) and lo = tf32(x - hi)
+// (rounded to nearest: |lo| <= 2^-11 |x|, and lo within 2^-11 |lo| of x - hi;
+// truncating hi instead doubled the error of S and of late increments).
 // Three TF32 products hi hi^T + lo hi^T + hi lo^T give the FP32-accurate
 // product (the lo lo^T term is below FP32 rounding).  Per 8 patches: rows
 // 0..127 against rows 0..n6-1 (M = 128, N = n6 rounded up to 16) into TMEM
@@ -56,6 +58,12 @@ __host__ __device__ inline size_t atc_smem_bytes(int rs_max) {
     return 4 * (size_t)kAtcOpBytes + 2 * (size_t)kAtcK * rs_max * 4;
 }
 
+// x rounded to TF32 (10 mantissa bits), to nearest with ties away from zero,
+// by integer operations on its bits: half a unit of the last kept place is
+// added to the magnitude (a carry moves into the exponent as it should) and
+// the 13 dropped bits are cleared.  For finite x.
+__device__ __forceinline__ uint32_t tf32_rna(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+
 // Entry of the stored row that holds pose entry m = 6 f + c.
 __device__ __forceinline__ int atc_src(int m) {
     const int f = m / 6, c = m - 6 * f;
@@ -65,7 +73,7 @@ __device__ __forceinline__ int atc_src(int m) {
 __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const Prob *__restrict__ probs,
                                                                            const Item *__restrict__ items, int t,
                                                                            int rs_max) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -124,19 +132,24 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
         if (!ok) {
             atomicOr(&s_bad, 1);
         } else {
-            // split: a warp writes one 8 x 4 (row, patch) core-matrix tile of hi and of lo at a time
+            // split: warp w takes the row groups w, w + 16, ...; lane (r8, k4) row
+            // m = 8 rg + r8 and the patches k4, k4 + 4, ...: each store of a warp
+            // fills one 128-byte core matrix of hi and one of lo
             const float *raw = raw0 + b * raw_len;
             const int rows = min(kAtcK, k_hi - (k_lo + s * kAtcK));
             unsigned char *hi = ops + 2 * b * kAtcOpBytes, *lo = hi + kAtcOpBytes;
-#pragma unroll 2
-            for (int idx = warp; idx < (kAtcOpRows / 8) * (kAtcK / 4); idx += kAtcThreads / 32) {
-                const int rg = idx / (kAtcK / 4), kg = idx % (kAtcK / 4);
-                const int m = 8 * rg + r8, k = 4 * kg + k4;
-                const float x = (k < rows && m < n6) ? raw[k * RS + atc_src(m)] : 0.f;
-                const uint32_t h = to_tf32(x), l = to_tf32(x - __uint_as_float(h));
-                const uint32_t off = (uint32_t)rg * kAtcSbo + (uint32_t)kg * kLbo + (uint32_t)(16 * r8 + 4 * k4);
-                *reinterpret_cast<uint32_t *>(hi + off) = h;
-                *reinterpret_cast<uint32_t *>(lo + off) = l;
+            for (int rg = warp; rg < kAtcOpRows / 8; rg += kAtcThreads / 32) {
+                const int m = 8 * rg + r8;
+                const bool mv = m < n6;
+                const float *src = raw + (mv ? atc_src(m) : 0) + k4 * RS;
+                const uint32_t off = (uint32_t)rg * kAtcSbo + (uint32_t)(16 * r8 + 4 * k4);
+#pragma unroll
+                for (int kg = 0; kg < kAtcK / 4; ++kg) {
+                    const float x = (mv && 4 * kg + k4 < rows) ? src[4 * kg * RS] : 0.f;
+                    const uint32_t h = tf32_rna(x);
+                    *reinterpret_cast<uint32_t *>(hi + off + kg * kLbo) = h;
+                    *reinterpret_cast<uint32_t *>(lo + off + kg * kLbo) = tf32_rna(x - __uint_as_float(h));
+                }
             }
             if (tid < n6) {   // v': thread m = tid, this stage's patches in FP32, then a compensated add
                 const int src = atc_src(tid);
