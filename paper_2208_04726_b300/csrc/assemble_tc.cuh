@@ -20,8 +20,9 @@
 // 128, rounded down to 8) into columns 256..; every pose-pair block a <= b
 // lies in one of the two.
 // v' stays on the CUDA cores: it tends to zero as the iterations converge,
-// so its terms cancel, and a thread per row entry sums it in FP32 per stage
-// with compensated adds across stages, as the CUDA-core assembly does.
+// so its terms cancel, and the lanes that split row m sum its products in
+// FP32 per stage, with compensated adds across stages, as the CUDA-core
+// assembly does.
 //
 // One CTA of kAtcThreads threads per (problem, work item): a range of at most
 // kAtcMaxPatches patches (the FP32 accumulation length in TMEM).  Thread 0
@@ -43,7 +44,8 @@
 
 namespace dpvo {
 
-constexpr int kAtcThreads = 512;
+constexpr int kAtcSplitWarps = 16;                            // warps that split the operands
+constexpr int kAtcThreads = 32 * (kAtcSplitWarps + 1);         // + the producer warp (copies, MMAs)
 constexpr int kAtcK = 32;                                      // patches per stage
 constexpr int kAtcOpRows = 200;                                // operand rows: 6 x 32 pose entries, and the
                                                                // zero rows 192..199 the second product reads
@@ -94,13 +96,14 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
     unsigned char *ops = smem;                                 // buffer b: hi at 2b kAtcOpBytes, lo after it
     float *raw0 = reinterpret_cast<float *>(smem + 4 * kAtcOpBytes);
     const size_t raw_len = (size_t)kAtcK * rs_max;
-    __shared__ __align__(8) uint64_t s_full[2], s_done[2];
+    __shared__ __align__(8) uint64_t s_full[2], s_op[2], s_done[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_bad;
     if (warp == 0) tmem_alloc(&s_tmem, kAtcCols);
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&s_full[b]), 1);
+            mbar_init(smem_u32(&s_op[b]), kAtcSplitWarps);
             mbar_init(smem_u32(&s_done[b]), 1);
         }
         s_bad = 0;
@@ -109,95 +112,115 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
+    volatile int *bad = &s_bad;
 
-    // thread 0's bookkeeping: stages whose rows were requested, the last stage committed
+    // the producer lane's bookkeeping: stages whose rows were requested, the last stage committed
     int n_issued = 0, last_commit = -1;
-    auto issue = [&](int s) {
-        const int k0 = k_lo + s * kAtcK, rows = min(kAtcK, k_hi - k0);
-        bulk_load(raw0 + (s & 1) * raw_len, pr.erow + (size_t)k0 * RS, (uint32_t)(rows * RS * 4),
-                  smem_u32(&s_full[s & 1]));
-        n_issued = s + 1;
-    };
-    if (tid == 0) {
-        issue(0);
-        if (n_st > 1) issue(1);
-    }
-
-    const int r8 = lane >> 2, k4 = lane & 3;
-    float v_s = 0.f, v_c = 0.f;                                // v' of row entry tid (compensated)
-    for (int s = 0; s < n_st; ++s) {
-        const int b = s & 1;
-        bool ok = mbar_wait(smem_u32(&s_full[b]), (uint32_t)(s >> 1) & 1u);
-        if (ok && s >= 2) ok = mbar_wait(smem_u32(&s_done[b]), (uint32_t)((s - 2) >> 1) & 1u);   // buffer b read
-        if (!ok) {
-            atomicOr(&s_bad, 1);
-        } else {
+    float v_s[2] = {0.f, 0.f}, v_c[2] = {0.f, 0.f};           // v' of the lane's rows (compensated)
+    if (warp == kAtcSplitWarps) {
+        // producer: stored rows into the two row stages, MMAs once a stage's operands are split
+        if (lane == 0) {
+            auto issue = [&](int s) {
+                const int k0 = k_lo + s * kAtcK, rows = min(kAtcK, k_hi - k0);
+                bulk_load(raw0 + (s & 1) * raw_len, pr.erow + (size_t)k0 * RS, (uint32_t)(rows * RS * 4),
+                          smem_u32(&s_full[s & 1]));
+                n_issued = s + 1;
+            };
+            issue(0);
+            if (n_st > 1) issue(1);
+            const uint32_t oa = (uint32_t)(a0 >> 3) * kAtcSbo, ob = (uint32_t)(kAtcB0 >> 3) * kAtcSbo;
+            const uint32_t id0 = idesc_tf32(128, N0), id1 = idesc_tf32(128, two ? N1 : 16);
+            for (int s = 0; s < n_st && !*bad; ++s) {
+                const int b = s & 1;
+                if (!mbar_wait(smem_u32(&s_op[b]), (uint32_t)(s >> 1) & 1u)) {
+                    *bad = 1;
+                    break;
+                }
+                tc_fence_after();
+                if (s + 2 < n_st) issue(s + 2);                // row stage b is consumed
+                const uint32_t hb = smem_u32(ops + 2 * b * kAtcOpBytes), lb = hb + kAtcOpBytes;
+                for (int ks = 0; ks < kAtcK / 8; ++ks) {
+                    const uint32_t o = ks * 2 * kLbo;
+                    const int acc = (s > 0 || ks > 0) ? 1 : 0;
+                    const uint64_t h0 = smem_desc(hb + o, kLbo, kAtcSbo), l0 = smem_desc(lb + o, kLbo, kAtcSbo);
+                    mma_tf32(tmem, h0, h0, id0, acc);
+                    mma_tf32(tmem, l0, h0, id0, 1);
+                    mma_tf32(tmem, h0, l0, id0, 1);
+                    if (two) {
+                        const uint64_t ha = smem_desc(hb + oa + o, kLbo, kAtcSbo);
+                        const uint64_t la = smem_desc(lb + oa + o, kLbo, kAtcSbo);
+                        const uint64_t hbb = smem_desc(hb + ob + o, kLbo, kAtcSbo);
+                        const uint64_t lbb = smem_desc(lb + ob + o, kLbo, kAtcSbo);
+                        mma_tf32(tmem + 256, ha, hbb, id1, acc);
+                        mma_tf32(tmem + 256, la, hbb, id1, 1);
+                        mma_tf32(tmem + 256, ha, lbb, id1, 1);
+                    }
+                }
+                mma_commit(smem_u32(&s_done[b]));
+                last_commit = s;
+            }
+        }
+    } else {
+        const int r8 = lane >> 2, k4 = lane & 3;
+        for (int s = 0; s < n_st; ++s) {
+            const int b = s & 1;
+            bool ok = !*bad && mbar_wait(smem_u32(&s_full[b]), (uint32_t)(s >> 1) & 1u);
+            if (ok && s >= 2) ok = mbar_wait(smem_u32(&s_done[b]), (uint32_t)((s - 2) >> 1) & 1u);   // buffer b read
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) *bad = 1;
+                break;
+            }
             // split: warp w takes the row groups w, w + 16, ...; lane (r8, k4) row
             // m = 8 rg + r8 and the patches k4, k4 + 4, ...: each store of a warp
             // fills one 128-byte core matrix of hi and one of lo
             const float *raw = raw0 + b * raw_len;
             const int rows = min(kAtcK, k_hi - (k_lo + s * kAtcK));
             unsigned char *hi = ops + 2 * b * kAtcOpBytes, *lo = hi + kAtcOpBytes;
-            for (int rg = warp; rg < kAtcOpRows / 8; rg += kAtcThreads / 32) {
+            // v' of row m: the lane's patches in FP32, the row's four lanes summed,
+            // then a compensated add across stages
+            for (int rg = warp, rd = 0; rg < kAtcOpRows / 8; rg += kAtcSplitWarps, ++rd) {
                 const int m = 8 * rg + r8;
                 const bool mv = m < n6;
                 const float *src = raw + (mv ? atc_src(m) : 0) + k4 * RS;
+                const float *sw = raw + 8 * nf + k4 * RS;
                 const uint32_t off = (uint32_t)rg * kAtcSbo + (uint32_t)(16 * r8 + 4 * k4);
+                float blk = 0.f;
 #pragma unroll
                 for (int kg = 0; kg < kAtcK / 4; ++kg) {
-                    const float x = (mv && 4 * kg + k4 < rows) ? src[4 * kg * RS] : 0.f;
+                    const bool in = mv && 4 * kg + k4 < rows;
+                    const float x = in ? src[4 * kg * RS] : 0.f;
+                    blk = fmaf(-(in ? sw[4 * kg * RS] : 0.f), x, blk);
                     const uint32_t h = tf32_rna(x);
                     *reinterpret_cast<uint32_t *>(hi + off + kg * kLbo) = h;
                     *reinterpret_cast<uint32_t *>(lo + off + kg * kLbo) = tf32_rna(x - __uint_as_float(h));
                 }
+                blk += __shfl_xor_sync(0xffffffffu, blk, 1);
+                blk += __shfl_xor_sync(0xffffffffu, blk, 2);
+                if (rd == 0) kahan_add(v_s[0], v_c[0], blk);
+                else kahan_add(v_s[1], v_c[1], blk);
             }
-            if (tid < n6) {   // v': thread m = tid, this stage's patches in FP32, then a compensated add
-                const int src = atc_src(tid);
-                float blk = 0.f;
-                for (int k = 0; k < rows; ++k) blk = fmaf(-raw[k * RS + 8 * nf], raw[k * RS + src], blk);
-                kahan_add(v_s, v_c, blk);
-            }
-        }
-        fence_async_smem();
-        __syncthreads();
-        if (s_bad) break;
-        if (tid == 0) {
-            tc_fence_after();
-            if (s + 2 < n_st) issue(s + 2);                    // row stage b is consumed
-            const uint32_t hb = smem_u32(ops + 2 * b * kAtcOpBytes), lb = hb + kAtcOpBytes;
-            const uint32_t oa = (uint32_t)(a0 >> 3) * kAtcSbo, ob = (uint32_t)(kAtcB0 >> 3) * kAtcSbo;
-            const uint32_t id0 = idesc_tf32(128, N0), id1 = idesc_tf32(128, two ? N1 : 16);
-            for (int ks = 0; ks < kAtcK / 8; ++ks) {
-                const uint32_t o = ks * 2 * kLbo;
-                const int acc = (s > 0 || ks > 0) ? 1 : 0;
-                const uint64_t h0 = smem_desc(hb + o, kLbo, kAtcSbo), l0 = smem_desc(lb + o, kLbo, kAtcSbo);
-                mma_tf32(tmem, h0, h0, id0, acc);
-                mma_tf32(tmem, l0, h0, id0, 1);
-                mma_tf32(tmem, h0, l0, id0, 1);
-                if (two) {
-                    const uint64_t ha = smem_desc(hb + oa + o, kLbo, kAtcSbo), la = smem_desc(lb + oa + o, kLbo, kAtcSbo);
-                    const uint64_t hbb = smem_desc(hb + ob + o, kLbo, kAtcSbo), lbb = smem_desc(lb + ob + o, kLbo, kAtcSbo);
-                    mma_tf32(tmem + 256, ha, hbb, id1, acc);
-                    mma_tf32(tmem + 256, la, hbb, id1, 1);
-                    mma_tf32(tmem + 256, ha, lbb, id1, 1);
-                }
-            }
-            mma_commit(smem_u32(&s_done[b]));
-            last_commit = s;
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_op[b]));
         }
     }
+    __syncthreads();
     if (!s_bad && !mbar_wait(smem_u32(&s_done[(n_st - 1) & 1]), (uint32_t)((n_st - 1) >> 1) & 1u))
         atomicOr(&s_bad, 1);
     __syncthreads();
     if (!s_bad) {
-        if (tid < n6) out[36 * np + tid] = (double)v_s - (double)v_c;
+        if (warp < kAtcSplitWarps && (lane & 3) == 0)
+            for (int rd = 0; rd < 2; ++rd) {
+                const int m = 8 * (warp + kAtcSplitWarps * rd) + (lane >> 2);
+                if (m < n6) out[36 * np + m] = (double)v_s[rd] - (double)v_c[rd];
+            }
         // read-back: warp w reads TMEM lanes 32 (w % 4) .. +31 (m) and every
         // fourth 16-column chunk from chunk w / 4 of the N0 columns from 0
         // and the N1 columns from 256
         tc_fence_after();
         const int m = 32 * (warp & 3) + lane;
         const int n_ch0 = N0 / 16, n_ch = n_ch0 + N1 / 16;
-        for (int j = warp >> 2; j < n_ch; j += kAtcThreads / 128) {
+        for (int j = warp >> 2; j < n_ch && warp < kAtcSplitWarps; j += kAtcSplitWarps / 4) {
             const bool r1 = j >= n_ch0;
             const int c0 = r1 ? 256 + 16 * (j - n_ch0) : 16 * j;
             float v[16];
@@ -213,7 +236,7 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
                     out[36 * (fr * nf - fr * (fr - 1) / 2 + (fc - fr)) + 6 * ir + (C - 6 * fc)] = -(double)v[q];
             }
         }
-    } else if (tid == 0) {
+    } else if (warp == kAtcSplitWarps && lane == 0) {
         // report, and give the copies and MMAs in flight a bounded wait before the TMEM is freed
         atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
         for (int u = n_issued > 2 ? n_issued - 2 : 0; u < n_issued; ++u)
