@@ -25,10 +25,11 @@
 // assembly does.
 //
 // One CTA of kAtcThreads threads per (problem, work item): a range of at most
-// kAtcMaxPatches patches (the FP32 accumulation length in TMEM).  Thread 0
-// streams the stored rows through two shared-memory stages by bulk copies and
-// issues the MMAs; all threads split a stage into one of two operand buffers
-// while the MMAs of the previous stage run.  Every wait is bounded; on a
+// kAtcMaxPatches patches (the FP32 accumulation length in TMEM).  A producer
+// warp streams the stored rows through kAtcRawStages shared-memory stages by
+// bulk copies and issues the MMAs of a stage once the split warps have
+// arrived on its operands' mbarrier; the split warps fill one of two operand
+// buffers while the MMAs of the previous stage run.  Every wait is bounded; on a
 // timeout the CTA reports DPVO_BA_STATUS_TIMEOUT, waits (again bounded) for
 // its copies and MMAs in flight and leaves.  The result goes to the CTA's FP64
 // partial in the layout of schur_assembly_kernel (the 6 x 6 block of pair
@@ -53,11 +54,12 @@ constexpr int kAtcB0 = 120;                                    // first row of t
 constexpr uint32_t kAtcSbo = (kAtcK / 4) * kLbo;               // bytes between 8-row groups
 constexpr uint32_t kAtcOpBytes = (kAtcOpRows / 8) * kAtcSbo;   // one operand half (hi or lo)
 constexpr int kAtcMaxPatches = 2048;                           // patches per CTA at most
-constexpr int kAtcCols = 512;                                  // TMEM columns allocated (384 used)
+constexpr int kAtcCols = 512;                                  // TMEM columns allocated (336 used at most)
+constexpr int kAtcRawStages = 3;                               // row stages: copies two stages ahead
 
-// Dynamic shared memory: two operand buffers (hi, lo), then two row stages.
+// Dynamic shared memory: two operand buffers (hi, lo), then the row stages.
 __host__ __device__ inline size_t atc_smem_bytes(int rs_max) {
-    return 4 * (size_t)kAtcOpBytes + 2 * (size_t)kAtcK * rs_max * 4;
+    return 4 * (size_t)kAtcOpBytes + kAtcRawStages * (size_t)kAtcK * rs_max * 4;
 }
 
 // x rounded to TF32 (10 mantissa bits), to nearest with ties away from zero,
@@ -96,13 +98,13 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
     unsigned char *ops = smem;                                 // buffer b: hi at 2b kAtcOpBytes, lo after it
     float *raw0 = reinterpret_cast<float *>(smem + 4 * kAtcOpBytes);
     const size_t raw_len = (size_t)kAtcK * rs_max;
-    __shared__ __align__(8) uint64_t s_full[2], s_op[2], s_done[2];
+    __shared__ __align__(8) uint64_t s_full[kAtcRawStages], s_op[2], s_done[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_bad;
     if (warp == 0) tmem_alloc(&s_tmem, kAtcCols);
     if (tid == 0) {
+        for (int r = 0; r < kAtcRawStages; ++r) mbar_init(smem_u32(&s_full[r]), 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&s_full[b]), 1);
             mbar_init(smem_u32(&s_op[b]), kAtcSplitWarps);
             mbar_init(smem_u32(&s_done[b]), 1);
         }
@@ -118,16 +120,15 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
     int n_issued = 0, last_commit = -1;
     float v_s[2] = {0.f, 0.f}, v_c[2] = {0.f, 0.f};           // v' of the lane's rows (compensated)
     if (warp == kAtcSplitWarps) {
-        // producer: stored rows into the two row stages, MMAs once a stage's operands are split
+        // producer: stored rows into the row stages, MMAs once a stage's operands are split
         if (lane == 0) {
             auto issue = [&](int s) {
                 const int k0 = k_lo + s * kAtcK, rows = min(kAtcK, k_hi - k0);
-                bulk_load(raw0 + (s & 1) * raw_len, pr.erow + (size_t)k0 * RS, (uint32_t)(rows * RS * 4),
-                          smem_u32(&s_full[s & 1]));
+                bulk_load(raw0 + (s % kAtcRawStages) * raw_len, pr.erow + (size_t)k0 * RS, (uint32_t)(rows * RS * 4),
+                          smem_u32(&s_full[s % kAtcRawStages]));
                 n_issued = s + 1;
             };
-            issue(0);
-            if (n_st > 1) issue(1);
+            for (int s = 0; s < kAtcRawStages && s < n_st; ++s) issue(s);
             const uint32_t oa = (uint32_t)(a0 >> 3) * kAtcSbo, ob = (uint32_t)(kAtcB0 >> 3) * kAtcSbo;
             const uint32_t id0 = idesc_tf32(128, N0), id1 = idesc_tf32(128, two ? N1 : 16);
             for (int s = 0; s < n_st && !*bad; ++s) {
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
                     break;
                 }
                 tc_fence_after();
-                if (s + 2 < n_st) issue(s + 2);                // row stage b is consumed
+                if (s + kAtcRawStages < n_st) issue(s + kAtcRawStages);   // row stage s is consumed
                 const uint32_t hb = smem_u32(ops + 2 * b * kAtcOpBytes), lb = hb + kAtcOpBytes;
                 for (int ks = 0; ks < kAtcK / 8; ++ks) {
                     const uint32_t o = ks * 2 * kLbo;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
         const int r8 = lane >> 2, k4 = lane & 3;
         for (int s = 0; s < n_st; ++s) {
             const int b = s & 1;
-            bool ok = !*bad && mbar_wait(smem_u32(&s_full[b]), (uint32_t)(s >> 1) & 1u);
+            bool ok = !*bad && mbar_wait(smem_u32(&s_full[s % kAtcRawStages]), (uint32_t)(s / kAtcRawStages) & 1u);
             if (ok && s >= 2) ok = mbar_wait(smem_u32(&s_done[b]), (uint32_t)((s - 2) >> 1) & 1u);   // buffer b read
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) *bad = 1;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
             // split: warp w takes the row groups w, w + 16, ...; lane (r8, k4) row
             // m = 8 rg + r8 and the patches k4, k4 + 4, ...: each store of a warp
             // fills one 128-byte core matrix of hi and one of lo
-            const float *raw = raw0 + b * raw_len;
+            const float *raw = raw0 + (s % kAtcRawStages) * raw_len;
             const int rows = min(kAtcK, k_hi - (k_lo + s * kAtcK));
             unsigned char *hi = ops + 2 * b * kAtcOpBytes, *lo = hi + kAtcOpBytes;
             // v' of row m: the lane's patches in FP32, the row's four lanes summed,
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
     } else if (warp == kAtcSplitWarps && lane == 0) {
         // report, and give the copies and MMAs in flight a bounded wait before the TMEM is freed
         atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
-        for (int u = n_issued > 2 ? n_issued - 2 : 0; u < n_issued; ++u)
-            mbar_wait(smem_u32(&s_full[u & 1]), (uint32_t)(u >> 1) & 1u);
+        for (int u = n_issued > kAtcRawStages ? n_issued - kAtcRawStages : 0; u < n_issued; ++u)
+            mbar_wait(smem_u32(&s_full[u % kAtcRawStages]), (uint32_t)(u / kAtcRawStages) & 1u);
         if (last_commit >= 0) mbar_wait(smem_u32(&s_done[last_commit & 1]), (uint32_t)(last_commit >> 1) & 1u);
     }
     tc_fence_before();
