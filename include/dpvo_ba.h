@@ -249,6 +249,17 @@ int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, fl
 int dpvo_ba_set_timing(dpvo_ba_handle *h, int enable);
 int dpvo_ba_timing(dpvo_ba_handle *h, float *ms_out, int *kind_out, int cap);
 
+/* Failure-detection self-test (the paper has no counterpart).  Every
+ * pipelined kernel (TF32 Schur, assembly, correlation) waits on mbarriers with
+ * a bounded number of polls and reports DPVO_BA_STATUS_TIMEOUT instead of
+ * hanging.  This launches one thread that initialises an mbarrier expecting
+ * one arrival, arrives on it if `arrive` != 0, and then waits for the phase
+ * with the same bounded wait, at most `polls` polls.  *status (device int32,
+ * caller-owned) receives DPVO_BA_STATUS_TIMEOUT if the wait gave up (the phase
+ * never completes when arrive == 0), else 0.  Asynchronous on `stream`; the
+ * context stays usable.  Errors: EINVAL (NULL status, polls < 1), ECUDA. */
+int dpvo_ba_selftest_bounded_wait(int32_t *status, int arrive, int polls, void *stream);
+
 /* Allocation-free solve of ONE problem (the paper has no counterpart: this is
  * a deployment entry point).  For callers that may not allocate device memory
  * while running -- fixed-budget embedded pipelines, processes whose device

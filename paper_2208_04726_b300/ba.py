@@ -68,7 +68,7 @@ EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solv
            "dpvo_ba_serve_stop", "dpvo_ba_session_open", "dpvo_ba_session_close", "dpvo_ba_session_read",
            "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror", "dpvo_ba_pose_loss",
            "dpvo_ba_window_create", "dpvo_ba_window_destroy", "dpvo_ba_window_append", "dpvo_ba_window_problem",
-           "dpvo_ba_window_append_batch", "dpvo_ba_correlation"]
+           "dpvo_ba_window_append_batch", "dpvo_ba_correlation", "dpvo_ba_selftest_bounded_wait"]
 
 _lib = None
 
@@ -116,6 +116,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_window_problem.argtypes = [vp, ctypes.POINTER(Dims), ctypes.POINTER(Problem)]
     lib.dpvo_ba_correlation.argtypes = [ctypes.POINTER(CorrDims), vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dpvo_ba_window_append_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32), i32, vp]
+    lib.dpvo_ba_selftest_bounded_wait.argtypes = [vp, i32, i32, vp]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -123,6 +124,16 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             getattr(lib, name).restype = i32
     _lib = lib
     return lib
+
+
+def selftest_bounded_wait(arrive: bool, polls: int = 1000, stream=None) -> int:
+    """The kernels' bounded mbarrier wait on a phase that completes only if
+    `arrive`; returns the status it reports (STATUS_TIMEOUT when it gave up)."""
+    import torch
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    _check(load().dpvo_ba_selftest_bounded_wait(st.data_ptr(), int(bool(arrive)), int(polls), _stream_ptr(stream)),
+           "dpvo_ba_selftest_bounded_wait")
+    return int(st.item())
 
 
 class BAError(RuntimeError):

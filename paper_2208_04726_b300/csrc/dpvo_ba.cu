@@ -74,6 +74,17 @@ static void launch_solve(const Layout &L, int n, cudaStream_t stream, const Prob
     else solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
 }
 
+// The bounded mbarrier wait of the pipelined kernels, on a phase that completes
+// only if `arrive` (one warp; lane 0 does the work).
+__global__ void selftest_wait_kernel(int32_t *status, int arrive, int polls) {
+    __shared__ __align__(8) uint64_t s_bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t bar = smem_u32(&s_bar);
+    mbar_init(bar, 1);
+    if (arrive) mbar_arrive(bar);
+    *status = mbar_wait(bar, 0u, polls) ? 0 : DPVO_BA_STATUS_TIMEOUT;
+}
+
 // Slices of one problem in the last back-substitution's grid: all of them, at
 // most `cap` (the CTAs then stride over the rest, which spreads each CTA's
 // start-up over several slices).
@@ -656,6 +667,12 @@ int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, fl
         cudaMemcpy(dxi_out, p.dxi + (size_t)iter * p.nf * 6, (size_t)p.nf * 6 * 8, cudaMemcpyDeviceToHost))
         return DPVO_BA_ECUDA;
     return DPVO_BA_OK;
+}
+
+int dpvo_ba_selftest_bounded_wait(int32_t *status, int arrive, int polls, void *stream) {
+    if (!status || polls < 1) return DPVO_BA_EINVAL;
+    selftest_wait_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(status, arrive, polls);
+    return cudaGetLastError() == cudaSuccess ? DPVO_BA_OK : DPVO_BA_ECUDA;
 }
 
 int dpvo_ba_set_timing(dpvo_ba_handle *h, int enable) {

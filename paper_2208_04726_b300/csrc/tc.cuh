@@ -83,9 +83,9 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 // Bounded wait for the completion of the mbarrier phase of the given parity;
-// false if it did not complete within kMbarSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (int it = 0; it < kMbarSpinLimit; ++it) {
+// false if it did not complete within `limit` polls (kMbarSpinLimit by default).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit = kMbarSpinLimit) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
