@@ -1266,11 +1266,15 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             __syncthreads();
         }
 
-        // -- (c) Schur accumulation over the chunk's patches, then the group's B blocks
+        // -- (c) Schur accumulation over the chunk's patches, then the group's B blocks.
+        // A strip with a frame outside the chunk's window would only add zeros
+        // (those columns of E are zero): its owner skips the chunk's products.
         if (owns) {
             int since = 0;
-            if (TC) {
-                // patch products accumulate on the tensor cores
+            const int fa_s = t0 + sa, fb_s = t0 + sb;
+            const bool s_on = fa_s >= jlo && fa_s <= ch.jhi && fb_s >= jlo && fb_s <= ch.jhi;
+            if (TC || !s_on) {
+                // patch products on the tensor cores, or none in this chunk
             } else if (!is_vstrip) {
                 // two patches per step: six 16-byte loads in flight before the FMAs
                 const int oa = 8 * sa + 4 * sh, ob = 8 * sb;
@@ -1326,8 +1330,10 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                 }
             }
+            if (s_on) {
 #pragma unroll
-            for (int q = 0; q < 18; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
+                for (int q = 0; q < 18; ++q) { kahan_add(acc_s[q], acc_c[q], blk[q]); blk[q] = 0.f; }
+            }
             if (my_ks == 0 && !group_next && !adjoint_rhs) {
                 const int fa = t0 + sa, fb = t0 + sb;
                 const int ja = fa - jlo, jb = fb - jlo;
