@@ -20,9 +20,9 @@
 // 128, rounded down to 8) into columns 256..; every pose-pair block a <= b
 // lies in one of the two.
 // v' stays on the CUDA cores: it tends to zero as the iterations converge,
-// so its terms cancel, and the lanes that split row m sum its products in
-// FP32 per stage, with compensated adds across stages, as the CUDA-core
-// assembly does.
+// so its terms cancel, and the two lanes that split row m (each half the
+// patches of a stage) sum its products in FP32 per stage, with compensated
+// adds across stages, as the CUDA-core assembly does; the halves meet in FP64.
 //
 // One CTA of kAtcThreads threads per (problem, work item): a range of at most
 // kAtcMaxPatches patches (the FP32 accumulation length in TMEM).  A producer
@@ -47,6 +47,7 @@ namespace dpvo {
 
 constexpr int kAtcSplitWarps = 16;                            // warps that split the operands
 constexpr int kAtcThreads = 32 * (kAtcSplitWarps + 1);         // + the producer warp (copies, MMAs)
+constexpr int kAtcRowWarps = 14;                              // split warps with rows (7 row chunks x 2 halves)
 constexpr int kAtcK = 32;                                      // patches per stage
 constexpr int kAtcOpRows = 200;                                // operand rows: 6 x 32 pose entries, and the
                                                                // zero rows 192..199 the second product reads
@@ -118,7 +119,8 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
 
     // the producer lane's bookkeeping: stages whose rows were requested, the last stage committed
     int n_issued = 0, last_commit = -1;
-    float v_s[2] = {0.f, 0.f}, v_c[2] = {0.f, 0.f};           // v' of the lane's rows (compensated)
+    float v_s = 0.f, v_c = 0.f;                                // v' of the lane's row, half the patches
+    __shared__ double s_vh[kAtcOpRows];                        // the other half's v' (warps 7..13)
     if (warp == kAtcSplitWarps) {
         // producer: stored rows into the row stages, MMAs once a stage's operands are split
         if (lane == 0) {
@@ -162,7 +164,14 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
             }
         }
     } else {
-        const int r8 = lane >> 2, k4 = lane & 3;
+        // warp w < 14 splits rows 32 (w % 7) .. +31, one row per lane, and the
+        // patch groups 4 (w / 7) .. +3 (4 patches each): a lane writes each of
+        // its rows' core-matrix rows (4 patches, 16 bytes) of hi and of lo with
+        // one store; warps 14 and 15 only arrive
+        const int rc = warp % 7, kh = warp / 7, m = 32 * rc + lane;
+        const bool row_ok = warp < kAtcRowWarps && m < kAtcOpRows, mv = row_ok && m < n6;
+        const int src = mv ? atc_src(m) : 0;
+        const uint32_t off_m = (uint32_t)(m >> 3) * kAtcSbo + (uint32_t)(m & 7) * 16u;
         for (int s = 0; s < n_st; ++s) {
             const int b = s & 1;
             bool ok = !*bad && mbar_wait(smem_u32(&s_full[s % kAtcRawStages]), (uint32_t)(s / kAtcRawStages) & 1u);
@@ -171,50 +180,46 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
                 if (lane == 0) *bad = 1;
                 break;
             }
-            // split: warp w takes the row groups w, w + 16, ...; lane (r8, k4) row
-            // m = 8 rg + r8 and the patches k4, k4 + 4, ...: each store of a warp
-            // fills one 128-byte core matrix of hi and one of lo
             const float *raw = raw0 + (s % kAtcRawStages) * raw_len;
             const int rows = min(kAtcK, k_hi - (k_lo + s * kAtcK));
             unsigned char *hi = ops + 2 * b * kAtcOpBytes, *lo = hi + kAtcOpBytes;
-            // v' of row m: the lane's patches in FP32, the row's four lanes summed,
-            // then a compensated add across stages
-            for (int rg = warp, rd = 0; rg < kAtcOpRows / 8; rg += kAtcSplitWarps, ++rd) {
-                const int m = 8 * rg + r8;
-                const bool mv = m < n6;
-                const float *src = raw + (mv ? atc_src(m) : 0) + k4 * RS;
-                const float *sw = raw + 8 * nf + k4 * RS;
-                const uint32_t off = (uint32_t)rg * kAtcSbo + (uint32_t)(16 * r8 + 4 * k4);
+            if (row_ok) {
+                // v' of row m: this lane's 16 patches in FP32, then a compensated add
+                // across stages (the other half of the patches is summed by warp w + 7)
                 float blk = 0.f;
 #pragma unroll
-                for (int kg = 0; kg < kAtcK / 4; ++kg) {
-                    const bool in = mv && 4 * kg + k4 < rows;
-                    const float x = in ? src[4 * kg * RS] : 0.f;
-                    blk = fmaf(-(in ? sw[4 * kg * RS] : 0.f), x, blk);
-                    const uint32_t h = tf32_rna(x);
-                    *reinterpret_cast<uint32_t *>(hi + off + kg * kLbo) = h;
-                    *reinterpret_cast<uint32_t *>(lo + off + kg * kLbo) = tf32_rna(x - __uint_as_float(h));
+                for (int kq = 0; kq < kAtcK / 8; ++kq) {
+                    const int kg = (kAtcK / 8) * kh + kq;
+                    uint32_t hv[4], lv[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int k = 4 * kg + j;
+                        const bool in = mv && k < rows;
+                        const float x = in ? raw[k * RS + src] : 0.f;
+                        blk = fmaf(-(in ? raw[k * RS + 8 * nf] : 0.f), x, blk);
+                        hv[j] = tf32_rna(x);
+                        lv[j] = tf32_rna(x - __uint_as_float(hv[j]));
+                    }
+                    const uint32_t off = off_m + (uint32_t)kg * kLbo;
+                    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
                 }
-                blk += __shfl_xor_sync(0xffffffffu, blk, 1);
-                blk += __shfl_xor_sync(0xffffffffu, blk, 2);
-                if (rd == 0) kahan_add(v_s[0], v_c[0], blk);
-                else kahan_add(v_s[1], v_c[1], blk);
+                kahan_add(v_s, v_c, blk);
             }
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&s_op[b]));
         }
     }
+    if (warp >= 7 && warp < kAtcRowWarps && 32 * (warp - 7) + lane < n6)
+        s_vh[32 * (warp - 7) + lane] = (double)v_s - (double)v_c;
     __syncthreads();
     if (!s_bad && !mbar_wait(smem_u32(&s_done[(n_st - 1) & 1]), (uint32_t)((n_st - 1) >> 1) & 1u))
         atomicOr(&s_bad, 1);
     __syncthreads();
     if (!s_bad) {
-        if (warp < kAtcSplitWarps && (lane & 3) == 0)
-            for (int rd = 0; rd < 2; ++rd) {
-                const int m = 8 * (warp + kAtcSplitWarps * rd) + (lane >> 2);
-                if (m < n6) out[36 * np + m] = (double)v_s[rd] - (double)v_c[rd];
-            }
+        if (warp < 7 && 32 * warp + lane < n6)
+            out[36 * np + 32 * warp + lane] = (double)v_s - (double)v_c + s_vh[32 * warp + lane];
         // read-back: warp w reads TMEM lanes 32 (w % 4) .. +31 (m) and every
         // fourth 16-column chunk from chunk w / 4 of the N0 columns from 0
         // and the N1 columns from 256
