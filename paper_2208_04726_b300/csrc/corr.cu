@@ -10,10 +10,11 @@
 // The 9 windows of a patch lie in one bounding box of footprint pixels; all
 // footprint x patch-pixel products are one GEMM, M = footprint pixels (chunks of
 // 128), N = 16 (9 patch pixels, zero-padded), K = 128 channels, BF16 operands
-// staged in shared memory by 16-byte asynchronous copies (zero outside the
-// map) and multiplied by tcgen05.mma.kind::f16 into an FP32 accumulator in
-// TMEM.  The epilogue reads the accumulator back, and forms the 49 outputs of
+// staged in shared memory (zero outside the map) -- by TMA box loads for edges
+// whose footprints fit the fixed boxes, else by 16-byte asynchronous copies --
+// and multiplied by tcgen05.mma.kind::f16 into an FP32 accumulator in TMEM.  The epilogue reads the accumulator back, and forms the 49 outputs of
 // each patch pixel and level from shared memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -44,6 +45,18 @@ constexpr int kDld = kQ;                        // row stride (floats) of the ac
 constexpr size_t kSmemBytes = kAbytes + kA1bytes + kBbytes + (size_t)(kChunk + kRows1) * kDld * 4;
 static_assert(kA1bytes + kBbytes + (size_t)(kChunk + kRows1) * kDld * 4 >= kAbytes,
               "the level-1 GEMM's 128 operand rows stay inside the allocation");
+// Fast edges load their footprints by TMA: one fixed box per level (level 0
+// 11 x 11 pixels, level 1 9 x 9) per 8-channel group, written as a slab of
+// box-pixel rows of 16 bytes (row t = y * width + x), the slabs of a level
+// kSlab0 / kSlab1 bytes apart: a K-major operand whose core matrices (8 rows x
+// 16 bytes) are 128 contiguous bytes, 8-row groups 128 bytes apart and
+// K-adjacent core matrices one slab apart.  Out-of-map pixels read as zero.
+constexpr int kBoxW0 = 11, kBoxH0 = 11, kBoxW1 = 9, kBoxH1 = 9;
+constexpr uint32_t kSlab0 = kChunk * 16, kSlab1 = kRows1 * 16;
+constexpr uint32_t kTmaBytes = (kD / 8) * 16 * (kBoxW0 * kBoxH0 + kBoxW1 * kBoxH1);
+static_assert(kBoxW0 * kBoxH0 <= kChunk && kBoxW1 * kBoxH1 <= kRows1, "boxes fit their operands");
+static_assert((kD / 8) * kSlab0 <= kAbytes && (kD / 8 - 1) * kSlab1 + kChunk * 16 <= kA1bytes,
+              "TMA slabs and the level-1 GEMM's 128 rows stay inside A0 and A1");
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kChunk >> 4) << 24);   // FP32 D, BF16 A and B, K-major, 128 x 16
 constexpr float kCoordMax = 1e4f;
@@ -72,6 +85,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ float bf16_to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 
 struct Args {
+    CUtensorMap tm[2];                            // the two levels' feature maps ([N][H][W][128] bf16)
     const uint16_t *fmap[2], *gpatch;
     const int32_t *kk, *jj;
     const float *coords;
@@ -79,6 +93,7 @@ struct Args {
     int32_t *status;
     int E, N, P, H[2], W[2];
     float scale1;
+    int use_tma;                                  // tensor maps encoded: fast edges load by TMA
 };
 
 // Per-edge plan, double-buffered across the pipeline: patch, frame, the two
@@ -91,7 +106,7 @@ struct Plan {
 };
 
 // Warp 0: plan edge e (coordinates, boxes, mode).
-__device__ void plan_edge(const Args &A, int e, Plan &P, int lane) {
+__device__ void plan_edge(const Args &A, int e, Plan &P, int lane, bool tma_ok) {
     const int k = A.kk[e], j = A.jj[e];
     const bool valid = k >= 0 && k < A.P && j >= 0 && j < A.N;
     bool finite = true;
@@ -123,7 +138,13 @@ __device__ void plan_edge(const Args &A, int e, Plan &P, int lane) {
     if (lane == 0) {
         P.k = k;
         P.j = j;
-        P.mode = !valid ? kBadIndex : !finite ? kZero : (npix[0] <= kChunk && npix[1] <= kRows1) ? kFast : kGeneral;
+        const bool fits = tma_ok && P.box[0][2] <= kBoxW0 && P.box[0][3] <= kBoxH0 && P.box[1][2] <= kBoxW1 &&
+                          P.box[1][3] <= kBoxH1;
+        P.mode = !valid ? kBadIndex : !finite ? kZero : fits ? kFast : kGeneral;
+        if (P.mode == kFast) {   // the fixed boxes from the same corners
+            P.box[0][2] = kBoxW0; P.box[0][3] = kBoxH0;
+            P.box[1][2] = kBoxW1; P.box[1][3] = kBoxH1;
+        }
     }
 }
 
@@ -186,20 +207,32 @@ __device__ __forceinline__ void bilinear_row(const Plan &P, int l, int q, int a,
 // edge's copies are issued before this edge's epilogue.  Other edges: level by
 // level, chunk by chunk, or on the CUDA cores when the footprint exceeds
 // kMaxChunks chunks.
-__global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
+// One thread: one box of a level's tensor map into shared memory, counted on mbar.
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *tm, int c, int x, int y, int f,
+                                        uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(c), "r"(x), "r"(y), "r"(f), "r"(mbar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ Args A) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *opA0 = smem, *opA1 = smem + kAbytes, *opB = smem + kAbytes + kA1bytes;
     float *Dfast = reinterpret_cast<float *>(smem + kAbytes + kA1bytes + kBbytes);   // rows 0..127 level 0, then level 1
     float *Dgen = reinterpret_cast<float *>(opA1);   // general path (up to kMaxChunks x 128 rows), over A1 .. copies
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_mbar, s_tma;
     __shared__ uint32_t s_tmem;
     __shared__ Plan s_plan[2];
     __shared__ int s_bad, s_badin;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t aA0 = smem_u32(opA0), aA1 = smem_u32(opA1), aB = smem_u32(opB), mbar = smem_u32(&s_mbar);
+    const uint32_t tbar = smem_u32(&s_tma);
+    const bool tma_ok = A.use_tma && (aA0 & 127u) == 0 && (aA1 & 127u) == 0;   // box destinations 128-byte aligned
     if (warp == 0) dpvo::tmem_alloc(&s_tmem, 32);
     if (tid == 0) {
         dpvo::mbar_init(mbar, 1);
+        dpvo::mbar_init(tbar, 1);
         s_bad = 0;
         s_badin = 0;
     }
@@ -211,19 +244,26 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
     __syncthreads();
     dpvo::tc_fence_after();
     const uint32_t tmem = s_tmem;
-    int n_commit = 0, slot = 0;
+    int n_commit = 0, slot = 0, n_tma = 0, n_tma_done = 0;   // the same in every thread
 
     auto fmap_of = [&](int l, int j) { return A.fmap[l] + (size_t)j * A.H[l] * A.W[l] * kD; };
-    auto issue_fast = [&](const Plan &P) {
-        stage_footprint(aA0, fmap_of(0, P.j), A.H[0], A.W[0], P.box[0], 0, kChunk, tid);
-        stage_footprint(aA1, fmap_of(1, P.j), A.H[1], A.W[1], P.box[1], 0, kRows1, tid);
+    auto issue_fast = [&](const Plan &P) {   // after a barrier that follows a proxy fence
+        if (tid == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tbar), "r"(kTmaBytes)
+                         : "memory");
+            for (int g = 0; g < kD / 8; ++g) {
+                tma_box(aA0 + g * kSlab0, &A.tm[0], 8 * g, P.box[0][0], P.box[0][1], P.j, tbar);
+                tma_box(aA1 + g * kSlab1, &A.tm[1], 8 * g, P.box[1][0], P.box[1][1], P.j, tbar);
+            }
+        }
+        ++n_tma;
         stage_patch(aB, A.gpatch, P.k, tid);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
     int e = blockIdx.x;
     if (e < A.E) {
-        if (warp == 0) plan_edge(A, e, s_plan[0], lane);
+        if (warp == 0) plan_edge(A, e, s_plan[0], lane, tma_ok);
         __syncthreads();
         if (s_plan[0].mode == kFast) issue_fast(s_plan[0]);
     }
@@ -233,16 +273,18 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
         float *out = A.corr + (size_t)e * 2 * kQ * 49;
         if (mode == kFast) {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            if (!dpvo::mbar_wait(tbar, (uint32_t)(n_tma - 1) & 1u)) atomicOr(&s_bad, 1);
+            else n_tma_done = n_tma;
             dpvo::fence_async_smem();
             __syncthreads();
             if (s_bad == 0) {
                 if (tid == 0) {
                     dpvo::tc_fence_after();
                     for (int ks = 0; ks < kD / 16; ++ks)
-                        mma_bf16(tmem, dpvo::smem_desc(aA0 + ks * 2 * kLbo, kLbo, kSbo),
+                        mma_bf16(tmem, dpvo::smem_desc(aA0 + ks * 2 * kSlab0, kSlab0, 128),
                                  dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
                     for (int ks = 0; ks < kD / 16; ++ks)
-                        mma_bf16(tmem + kN, dpvo::smem_desc(aA1 + ks * 2 * kLbo, kLbo, kSbo),
+                        mma_bf16(tmem + kN, dpvo::smem_desc(aA1 + ks * 2 * kSlab1, kSlab1, 128),
                                  dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
                     dpvo::mma_commit(mbar);
                 }
@@ -330,7 +372,8 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
         // plan the next edge and start its copies (they fly during this epilogue)
         const int en = e + gridDim.x;
         if (en < A.E) {
-            if (warp == 0) plan_edge(A, en, s_plan[slot ^ 1], lane);
+            if (warp == 0) plan_edge(A, en, s_plan[slot ^ 1], lane, tma_ok);
+            dpvo::fence_async_smem();                    // this CTA's generic writes before the next copies
             __syncthreads();
             if (s_plan[slot ^ 1].mode == kFast && s_bad == 0) issue_fast(s_plan[slot ^ 1]);
         }
@@ -355,6 +398,7 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
+        if (n_tma > n_tma_done) dpvo::mbar_wait(tbar, (uint32_t)(n_tma - 1) & 1u);   // a box load still in flight
         if (s_bad) {
             // report, and give the last commit one more bounded wait before the TMEM is freed
             atomicOr(A.status, DPVO_BA_STATUS_TIMEOUT);
@@ -365,6 +409,42 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(Args A) {
     dpvo::tc_fence_before();
     __syncthreads();
     if (warp == 0) dpvo::tmem_dealloc(tmem, 32);
+}
+
+// Host: the tensor maps of both levels ([N][H][W][128] bfloat16, 16-byte
+// aligned), boxes of 8 channels x the level's fixed box; false if the driver
+// entry point is missing or rejects them.
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static bool encode_maps(Args &A) {
+    static EncodeTiled encode = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<EncodeTiled>(fn);
+        else
+            cudaGetLastError();
+    }
+    if (!encode) return false;
+    for (int l = 0; l < 2; ++l) {
+        if (reinterpret_cast<uintptr_t>(A.fmap[l]) & 15) return false;
+        const cuuint64_t W = (cuuint64_t)A.W[l], H = (cuuint64_t)A.H[l];
+        const cuuint64_t dims[4] = {(cuuint64_t)kD, W, H, (cuuint64_t)A.N};
+        const cuuint64_t strides[3] = {(cuuint64_t)kD * 2, W * kD * 2, H * W * kD * 2};
+        const cuuint32_t box[4] = {8, (cuuint32_t)(l == 0 ? kBoxW0 : kBoxW1), (cuuint32_t)(l == 0 ? kBoxH0 : kBoxH1), 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (encode(&A.tm[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(A.fmap[l]), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
 }
 
 }  // namespace dpvo_corr
@@ -408,6 +488,7 @@ extern "C" int dpvo_ba_correlation(const dpvo_ba_corr_dims *d, const void *fmap0
     A.H[1] = H1;
     A.W[1] = W1;
     A.scale1 = (float)d->level1_scale;
+    A.use_tma = dpvo_corr::encode_maps(A) ? 1 : 0;   // else every edge takes the general path
     const int grid = d->n_edges < 3 * sms ? d->n_edges : 3 * sms;
     dpvo_corr::corr_kernel<<<grid, dpvo_corr::kThreads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(A);
     return cudaGetLastError() == cudaSuccess ? 0 : DPVO_BA_ECUDA;
