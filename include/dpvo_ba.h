@@ -407,9 +407,12 @@ int dpvo_ba_window_problem(const dpvo_ba_window *w, dpvo_ba_dims *dims, dpvo_ba_
  *                                  then on are zero)                       (read, OR-ed)
  * An edge-level whose coordinates are not finite or beyond 1e4 gets zeros;
  * one whose 9 windows span more than 4 x 128 pixels is computed on the CUDA
- * cores instead.  Asynchronous on stream.
- * Errors: EINVAL (NULL, sizes out of range: maps of 1 .. 4096 pixels per side,
- * level1_scale >= 1, at least one frame), ECUDA. */
+ * cores instead.  fmap0, fmap1 and gpatch must start on 16-byte boundaries
+ * (features are read in 16-byte pieces: tensor-map box loads, copies).
+ * Asynchronous on stream.
+ * Errors: EINVAL (NULL, a feature array not 16-byte aligned, sizes out of
+ * range: maps of 1 .. 4096 pixels per side, level1_scale >= 1, at least one
+ * frame), ECUDA. */
 #define DPVO_BA_CORR_DIM 128
 typedef struct {
     int32_t n_frames, n_patches, n_edges;

@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ 
 }
 
 // Host: the tensor maps of both levels ([N][H][W][128] bfloat16, 16-byte
-// aligned), boxes of 8 channels x the level's fixed box; false if the driver
-// entry point is missing or rejects them.
+// aligned: checked by the entry point), boxes of 8 channels x the level's
+// fixed box; false if the driver entry point is missing or rejects them.
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -456,6 +456,8 @@ extern "C" int dpvo_ba_correlation(const dpvo_ba_corr_dims *d, const void *fmap0
         d->height > 4096 || d->width > 4096 || d->level1_scale < 1 || !status)
         return DPVO_BA_EINVAL;
     if (d->n_edges > 0 && (!fmap0 || !fmap1 || !gpatch || !kk || !jj || !coords || !corr)) return DPVO_BA_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(fmap0) | reinterpret_cast<uintptr_t>(fmap1) | reinterpret_cast<uintptr_t>(gpatch)) & 15)
+        return DPVO_BA_EINVAL;   // features are read in 16-byte pieces
     const int H1 = d->height / d->level1_scale, W1 = d->width / d->level1_scale;
     if (H1 < 1 || W1 < 1) return DPVO_BA_EINVAL;
     if (d->n_edges == 0) return 0;

@@ -76,3 +76,19 @@ def test_sliding_window_sized_problem_sampled():
     assert st == 0
     edges = np.random.default_rng(0).choice(inp.n_edges, 64, replace=False)
     compare(got[edges], C.correlation(inp, edges))
+
+
+def test_unaligned_feature_maps_are_rejected():
+    """Features are read in 16-byte pieces (TMA boxes and copies): maps that
+    start 8 bytes past a 16-byte boundary return EINVAL and nothing runs."""
+    inp = CI.make_corr_inputs(3, 6, 1, 40, 48, 4, 5)
+    args = list(to_dev(inp))
+    for i in (0, 1, 2):
+        shifted = list(args)
+        t = args[i]
+        big = torch.zeros(t.numel() + 8, dtype=t.dtype, device=t.device)
+        shifted[i] = big[4:4 + t.numel()].view(t.shape)
+        assert shifted[i].data_ptr() % 16 == 8
+        with pytest.raises(ba.BAError) as e:
+            ba.correlation(*shifted, inp.scale)
+        assert e.value.code == ba.EINVAL
