@@ -27,6 +27,8 @@ pytestmark = pytest.mark.gpu
 MID32 = dataclasses.replace(S.STRESS_N64, n_frames=40, patches_per_frame=32, radius=16, t0=8, n_iters=2)
 # just past the fused path: 16 free poses (96 x 96)
 MID16 = dataclasses.replace(S.WINDOW_N22, n_frames=24, patches_per_frame=48, radius=12, t0=8)
+# 25 free poses (150 x 150): the tensor-core assembly's second product starts mid-frame
+MID25 = dataclasses.replace(S.STRESS_N64, n_frames=33, patches_per_frame=32, radius=16, t0=8, n_iters=2)
 
 
 @pytest.fixture(scope="module", params=[False, True], ids=["fp32-schur", "tf32-schur"])
@@ -45,7 +47,7 @@ def schur_tol(solver):
     return 2e-5 if solver.schur_tf32 else 2e-6
 
 
-@pytest.mark.parametrize("spec,seed", [(MID32, 0), (MID16, 1)])
+@pytest.mark.parametrize("spec,seed", [(MID32, 0), (MID16, 1), (MID25, 5)])
 def test_reduced_system_matches_oracle_schur(solver, spec, seed):
     sc = S.make_scene(spec, seed)
     prob = ba.problem_from_scene(sc)
@@ -58,7 +60,7 @@ def test_reduced_system_matches_oracle_schur(solver, spec, seed):
     assert rel(vg.cpu().numpy(), vr) < schur_tol(solver)
 
 
-@pytest.mark.parametrize("spec,seed", [(MID32, 2), (MID16, 3)])
+@pytest.mark.parametrize("spec,seed", [(MID32, 2), (MID16, 3), (MID25, 6)])
 def test_each_iteration_matches_oracle_step(solver, spec, seed):
     sc = S.make_scene(spec, seed)
     probs = solve_gpu(solver, [sc])
