@@ -269,9 +269,12 @@ int dpvo_ba_selftest_bounded_wait(int32_t *status, int arrive, int polls, void *
  * this library, held by every GPU that loads the library until the process
  * exits.  Arguments as for dpvo_ba_solve with n_problems == 1 (cfg may be NULL
  * for the defaults); results are the same as dpvo_ba_solve's.
- *   - The first call on each device does a one-time set-up there (it looks up
- *     the array's device address and sets kernel attributes); make that first
- *     call before any stream capture, with the device current.
+ *   - Every call looks up the array's device address in the current context
+ *     and sets the kernels' attributes: host-side calls that allocate nothing
+ *     once this library's module is loaded on the device.  The first call on a
+ *     device loads it, so make that first call before any stream capture, with
+ *     the device current.  An error left pending on the calling thread by
+ *     earlier, unrelated CUDA work is cleared, not reported as this call's.
  *   - All calls in the process share the one array and it keeps the previous
  *     call's contents (every call rewrites what it reads).  Calls whose work
  *     overlaps on the GPU -- on different streams, or from several host
@@ -349,7 +352,7 @@ typedef struct dpvo_ba_window dpvo_ba_window;
 
 typedef struct {
     int32_t max_frames;       /* frames kept, 1 .. DPVO_BA_MAX_FRAMES                     */
-    int32_t max_new_patches;  /* patches per appended frame, at most (>= 0)               */
+    int32_t max_new_patches;  /* patches per appended frame, at most (0 .. 8192)          */
     int32_t radius;           /* graph radius in frames (>= 0)                            */
     int32_t free_poses;       /* the last free_poses poses are free (>= 0)                */
     int32_t n_iters;          /* Gauss-Newton iterations recorded in the window's dims    */
@@ -357,7 +360,7 @@ typedef struct {
 } dpvo_ba_window_params;
 
 /* Create an empty window (device memory for its maximum sizes).
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * Errors: EINVAL (a parameter out of range), ENOMEM, ECUDA. */
 int dpvo_ba_window_create(const dpvo_ba_window_params *params, dpvo_ba_window **out);
 
 /* Free the window's memory (after the work queued on its arrays). */
@@ -365,7 +368,10 @@ int dpvo_ba_window_destroy(dpvo_ba_window *w);
 
 /* Append a frame with n_new patches at DEVICE pixel centres new_xy [n_new][2]
  * (read).  Asynchronous on stream; the window's earlier work must be ordered
- * before it (same stream).  Errors: EINVAL (NULL, n_new outside
+ * before it (same stream).  Every argument is checked before the window
+ * changes: an EINVAL leaves it as it was.  If a launch fails (ECUDA) after the
+ * window's sizes have moved on, the window is marked unusable and every later
+ * call on it returns ECUDA.  Errors: EINVAL (NULL, n_new outside
  * [0, max_new_patches]), ECUDA. */
 int dpvo_ba_window_append(dpvo_ba_window *w, const float *new_xy, int n_new, void *stream);
 

@@ -17,7 +17,12 @@ from __future__ import annotations
 
 import numpy as np
 
-from paper_2208_04726_b300.corr_inputs import from_bf16
+
+def from_bf16(u) -> np.ndarray:
+    """bfloat16 bit patterns (uint16) widened exactly to float32: a bfloat16 is
+    the upper half of the float32 with the same sign, exponent and leading
+    mantissa bits."""
+    return (np.asarray(u, np.uint16).astype(np.uint32) << 16).view(np.float32)
 
 
 def _bilinear(F, x, y):

@@ -5,6 +5,7 @@ for sm_103a without a GPU.
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import subprocess
 import sys
@@ -14,6 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libdpvo_ba.so")
+STAMP = LIB + ".sha256"     # hash of the sources and flags the library was built from
 SOURCES = [os.path.join(CSRC, f) for f in ("dpvo_ba.cu", "pose_loss.cu", "window.cu", "corr.cu")]
 DEPENDS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")] + [
     os.path.join(ROOT, "include", "dpvo_ba.h")]
@@ -31,11 +33,24 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
+def source_hash() -> str:
+    """SHA-256 over the compiler flags and the bytes of every source and header
+    (file names included), so that a library built from other sources -- or
+    copied in with a newer timestamp -- is never taken as current."""
+    h = hashlib.sha256()
+    h.update(" ".join(NVCC_FLAGS).encode())
+    for f in sorted(DEPENDS):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in DEPENDS)
+    with open(STAMP) as fh:
+        return fh.read().strip() == source_hash()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -50,6 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         sys.stderr.write(res.stderr)
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(source_hash() + "\n")
     return LIB
 
 

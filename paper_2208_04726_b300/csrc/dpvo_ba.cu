@@ -298,10 +298,12 @@ static int grow_stage(dpvo_ba_handle *h, size_t need) {
     return DPVO_BA_OK;
 }
 
-static bool g_attr_set[64] = {false};
-
+// Kernel attributes belong to the current context, so they are set on every
+// call that needs them (a handle's creation, each allocation-free solve) rather
+// than cached per device: a context that is torn down and created again starts
+// without them.  Setting them is a host-side call that allocates nothing.
 static int set_kernel_attrs(int device) {
-    if (device >= 0 && device < 64 && g_attr_set[device]) return DPVO_BA_OK;
+    (void)device;
     if (cudaFuncSetAttribute(linearize_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024) != cudaSuccess ||
         cudaFuncSetAttribute(linearize_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -324,7 +326,6 @@ static int set_kernel_attrs(int device) {
     if (cudaFuncSetAttribute(bw_edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
         return DPVO_BA_ECUDA;
-    if (device >= 0 && device < 64) g_attr_set[device] = true;
     return DPVO_BA_OK;
 }
 
@@ -1070,11 +1071,9 @@ constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB per device
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Per-device set-up, done by the first call on each device: the device address
-// of g_noalloc_scratch (the host-side name is only a stand-in for it) and the
-// SM count.
-static char *g_noalloc_base[64] = {nullptr};
-static int g_noalloc_sms[64] = {0};
+// In host code g_noalloc_scratch names a host-side stand-in, not the device
+// array: every call asks the runtime for the array's device address in the
+// current context (cudaGetSymbolAddress) and passes that to the kernels.
 
 __global__ void noalloc_descriptors_kernel(Prob p, int n_items, Prob *dst_prob, Item *dst_items) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *dst_prob = p;
@@ -1090,22 +1089,25 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     cudaStream_t stream = (cudaStream_t)stream_;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DPVO_BA_ECUDA; }
-    if (dev < 0 || dev >= 64) return DPVO_BA_EINVAL;
-    if (!g_noalloc_base[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();   // an error left pending by earlier, unrelated work is not this call's
+    // Looked up on every call, with the caller's device current: the array's
+    // address belongs to the current context and moves if that context is torn
+    // down and created again; once the module is loaded the lookup allocates nothing.
+    char *base = nullptr;
+    {
+        void *q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_noalloc_scratch) != cudaSuccess || !q) {
             cudaGetLastError();
             return DPVO_BA_ECUDA;
         }
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return DPVO_BA_ECUDA;
-        }
-        if (set_kernel_attrs(dev)) return DPVO_BA_ECUDA;
-        g_noalloc_sms[dev] = sms;
-        g_noalloc_base[dev] = (char *)p;
+        base = (char *)q;
     }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DPVO_BA_ECUDA;
+    }
+    if (set_kernel_attrs(dev)) return DPVO_BA_ECUDA;
     const float damping = cfg ? cfg->damping : 1e-4f;
     const float z_min = cfg ? cfg->z_min : 0.1f;
     if (!(damping >= 0.f) || !(z_min == z_min)) return DPVO_BA_EINVAL;
@@ -1133,9 +1135,8 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.ks = tc ? 1 : k_split(nf);
     p.L = partial_len(nf);
     const int est_chunks = std::max(1, (d.n_patches + G_cap - 1) / G_cap);
-    p.n_items = std::max(1, std::min(2 * g_noalloc_sms[dev], est_chunks));
+    p.n_items = std::max(1, std::min(2 * sms, est_chunks));
     p.n_parts = p.n_items * p.ks;
-    char *base = g_noalloc_base[dev];
     size_t off = 0;
     auto take = [&](size_t bytes) { char *q = base + off; off = al256(off + bytes); return q; };
     p.seg = (int32_t *)take((size_t)(d.n_patches + 1) * 4);

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) append_edges_kernel(Batch B) {
 struct dpvo_ba_window {
     dpvo_ba_window_params prm{};
     int N = 0, P = 0, E = 0, cur = 0;
+    bool broken = false;                          // a launch failed after the mirror moved on: unusable
     std::vector<int> counts;                      // patches per frame, oldest first (host mirror)
     char *mem = nullptr;
     float *pose[2] = {nullptr, nullptr}, *patch[2] = {nullptr, nullptr};
@@ -200,6 +201,10 @@ struct dpvo_ba_window {
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The median of a new frame's inverse depth ranks the patches of the previous
+// 3 frames in shared memory (4 bytes each, at most 96 KiB).
+constexpr int kMaxNewPatches = 96 * 1024 / 4 / 3;
+
 static int edges_per_patch(int f, int N, int R) {
     const int lo = f - R < 0 ? 0 : f - R, hi = f + R > N - 1 ? N - 1 : f + R;
     return hi - lo + 1;
@@ -207,7 +212,7 @@ static int edges_per_patch(int f, int N, int R) {
 
 extern "C" int dpvo_ba_window_create(const dpvo_ba_window_params *p, dpvo_ba_window **out) {
     if (!p || !out || p->max_frames < 1 || p->max_frames > DPVO_BA_MAX_FRAMES || p->max_new_patches < 0 ||
-        p->radius < 0 || p->free_poses < 0 || p->n_iters < 1 || p->n_iters > DPVO_BA_MAX_ITERS)
+        p->max_new_patches > kMaxNewPatches || p->radius < 0 || p->free_poses < 0 || p->n_iters < 1 || p->n_iters > DPVO_BA_MAX_ITERS)
         return DPVO_BA_EINVAL;
     dpvo_ba_window *w = new (std::nothrow) dpvo_ba_window;
     if (!w) return DPVO_BA_ENOMEM;
@@ -313,13 +318,22 @@ static void plan_append(dpvo_ba_window *w, const float *new_xy, int n_new, dpvo_
 extern "C" int dpvo_ba_window_append_batch(dpvo_ba_window *const *ws, const float *const *new_xy, const int *n_new,
                                           int n, void *stream) {
     if (n < 0 || (n > 0 && (!ws || !new_xy || !n_new))) return DPVO_BA_EINVAL;
+    // every check comes before any window's host mirror moves on
     for (int b = 0; b < n; ++b) {
         const dpvo_ba_window *w = ws[b];
         if (!w || n_new[b] < 0 || n_new[b] > w->prm.max_new_patches || (n_new[b] > 0 && !new_xy[b]))
             return DPVO_BA_EINVAL;
+        if (w->broken) return DPVO_BA_ECUDA;
         for (int c = 0; c < b; ++c)
             if (ws[c] == w) return DPVO_BA_EINVAL;   // one append per window per call
     }
+    // the median candidates of any window fit in 96 KiB (max_new_patches is bounded at create)
+    if (n > 0 && cudaFuncSetAttribute(dpvo_win::append_state_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      96 * 1024) != cudaSuccess) {
+        cudaGetLastError();
+        return DPVO_BA_ECUDA;
+    }
+    cudaGetLastError();                            // report only this call's launch errors
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int b0 = 0; b0 < n; b0 += dpvo_win::kMaxBatch) {
         const int nb = n - b0 < dpvo_win::kMaxBatch ? n - b0 : dpvo_win::kMaxBatch;
@@ -331,15 +345,15 @@ extern "C" int dpvo_ba_window_append_batch(dpvo_ba_window *const *ws, const floa
             p_max = B.a[b].P2 > p_max ? B.a[b].P2 : p_max;
         }
         const size_t smem = (size_t)med_max * 4;
-        if (smem > 96 * 1024) return DPVO_BA_EINVAL;   // more than 24,576 candidate patches
-        if (smem > 48 * 1024 && cudaFuncSetAttribute(dpvo_win::append_state_kernel,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     96 * 1024) != cudaSuccess)
-            return DPVO_BA_ECUDA;
         dpvo_win::append_state_kernel<<<nb, dpvo_win::kThreads, smem, st>>>(B);
         const int ys = p_max > 0 ? (p_max + dpvo_win::kThreads - 1) / dpvo_win::kThreads : 1;
         dpvo_win::append_edges_kernel<<<dim3(nb, ys), dpvo_win::kThreads, 0, st>>>(B);
-        if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
+        if (cudaGetLastError() != cudaSuccess) {
+            // the mirrors of this sub-batch and of the ones before it have moved on
+            // while the device may not have: mark every window of the call unusable
+            for (int b = 0; b < n; ++b) ws[b]->broken = true;
+            return DPVO_BA_ECUDA;
+        }
     }
     return 0;
 }
@@ -350,6 +364,7 @@ extern "C" int dpvo_ba_window_append(dpvo_ba_window *w, const float *new_xy, int
 
 extern "C" int dpvo_ba_window_problem(const dpvo_ba_window *w, dpvo_ba_dims *dims, dpvo_ba_problem *prob) {
     if (!w || !dims || !prob || w->N == 0) return DPVO_BA_EINVAL;
+    if (w->broken) return DPVO_BA_ECUDA;
     // the last free_poses poses are free, but at least the first two stay fixed (gauge and
     // monocular scale), all of them while the window has fewer than three frames
     int t0 = w->N - w->prm.free_poses;

@@ -28,6 +28,13 @@ same shapes stand in for them):
   a fraction of edges are outliers displaced by U[5, 30] px in a uniform random
   direction.  Weights are U[0, 1] per component (outliers U[0, 0.05] unless
   ``outlier_weights_uniform``).
+* Near patches (``near_frac`` > 0, off in the benchmark workloads): that
+  fraction of the patches, drawn from a separate stream, is placed 0.15-0.4 m
+  in front of its source camera, so that cameras further along the path see
+  it from behind.  Their edges are kept only where the true homogeneous depth
+  is clearly on one side of the activity threshold (>= 0.5 or <= -0.5), so an
+  edge's part in the solve does not hinge on rounding; the patches then have
+  gaps in their frame lists.
 * Initial state: every free pose (index >= t0) is moved by a 2-degree rotation
   about a random axis and a 5 cm translation in a random direction (applied on
   the world->camera side); fixed poses stay at ground truth; inverse depths are
@@ -60,6 +67,7 @@ class SceneSpec:
     init_rot_deg: float = 2.0
     init_trans: float = 0.05
     noiseless: bool = False  # no pixel noise, no outliers, unit weights
+    near_frac: float = 0.0   # patches placed close to their source camera (see the module docstring)
 
     @property
     def n_patches(self) -> int:
@@ -207,6 +215,11 @@ def make_scene(spec: SceneSpec, seed: int, dtype=np.float32) -> Scene:
     xs, ys, zs = xs.reshape(-1), ys.reshape(-1), zs.reshape(-1)
     anchor = np.repeat(np.arange(n), ppf)
     P = xs.shape[0]
+    near = np.zeros(P, dtype=bool)
+    if spec.near_frac > 0:
+        nrng = np.random.Generator(np.random.PCG64(seed ^ 0x4EA2))
+        near = nrng.uniform(size=P) < spec.near_frac
+        zs[near] = nrng.uniform(0.15, 0.4, size=int(near.sum()))
 
     kk_list, jj_list = [], []
     for i in range(n):
@@ -216,6 +229,14 @@ def make_scene(spec: SceneSpec, seed: int, dtype=np.float32) -> Scene:
         jj_list.append(np.tile(frames, ppf))
     kk = np.concatenate(kk_list)
     jj = np.concatenate(jj_list)
+    if near.any():
+        # homogeneous depth of each edge at the true state: depth in frame j over depth in the source frame
+        pc = zs[:, None] * np.stack([(xs - CX) / FX, (ys - CY) / FY, np.ones(P)], axis=1)
+        pw = np.einsum('pab,pb->pa', R_cw[anchor], pc) + centres[anchor]
+        zj = np.einsum('eb,eb->e', R_wc[jj, 2, :], pw[kk]) + t_wc[jj, 2]
+        zh = zj / zs[kk]
+        keep = ~near[kk] | (zh >= 0.5) | (zh <= -0.5)
+        kk, jj = kk[keep], jj[keep]
     E = kk.shape[0]
 
     # render the true measurement of every edge with a world-point pinhole camera

@@ -11,7 +11,10 @@ oracle, that it becomes large.  The independent pieces written here:
   scipy rotations;
 * a Gauss-Newton step obtained by ``numpy.linalg.lstsq`` on the whitened,
   damped, finite-difference Jacobian (no normal equations, no Cholesky);
-* the minimiser of the objective found by ``scipy.optimize.least_squares``.
+* the minimiser of the objective found by ``scipy.optimize.least_squares``;
+* the set of edges behind (or nearly behind) the camera, found from the
+  world-point form's depth in frame j, and the same problem with those edges
+  deleted from the graph.
 """
 from __future__ import annotations
 
@@ -224,3 +227,54 @@ def update_error(scene):
     a_ = np.concatenate([out["poses"][t0:].ravel(), out["depths"]])
     b_ = np.concatenate([np.stack(ref).ravel(), d + dd])
     return np.linalg.norm(a_ - b_) / np.linalg.norm(b_ - np.concatenate([np.stack([np.concatenate([ts[a], Rotation.from_matrix(Rs[a]).as_quat()]) for a in range(t0, scene.n_frames)]).ravel(), d]))
+
+
+def wp_homogeneous_depth(scene):
+    """Third homogeneous coordinate of every edge's reprojected centre, in the
+    world-point form: depth of the back-projected point in frame j times the
+    patch's inverse depth (the point's depth in its source frame is 1 / d)."""
+    Rs, ts, d = _state(scene)
+    fx, fy, cx, cy = (float(v) for v in scene.intrinsics)
+    x, y = scene.patches[:, 0].astype(np.float64), scene.patches[:, 1].astype(np.float64)
+    pc = (1.0 / d)[:, None] * np.stack([(x - cx) / fx, (y - cy) / fy, np.ones_like(x)], 1)
+    i = scene.anchor
+    pw = np.einsum('pba,pb->pa', Rs[i], pc - ts[i])
+    k, j = scene.kk, scene.jj
+    zj = np.einsum('eb,eb->e', Rs[j][:, 2, :], pw[k]) + ts[j][:, 2]
+    return zj * d[k]
+
+
+def without_edges(scene, drop):
+    """The scene with the edges flagged in ``drop`` deleted from the graph."""
+    import dataclasses
+    keep = ~np.asarray(drop, bool)
+    kw = dict(kk=scene.kk[keep], jj=scene.jj[keep], target=scene.target[keep], weight=scene.weight[keep])
+    if scene.outlier is not None:
+        kw["outlier"] = scene.outlier[keep]
+    if scene.uv_true is not None:
+        kw["uv_true"] = scene.uv_true[keep]
+    return dataclasses.replace(scene, **kw)
+
+
+def inactive_edge_error(scene, z_min=dg.Z_MIN):
+    """An edge whose reprojected homogeneous depth is at most z_min takes no part
+    (the reading of Eq. 2-3's division by the third coordinate for points
+    behind or next to the camera): the oracle's first increment, its normal
+    equations restricted to the free variables and its cost on the scene must
+    equal those of the same scene with those edges deleted.  Returns the
+    largest relative difference and the number of such edges."""
+    drop = wp_homogeneous_depth(scene) <= z_min
+    sub = without_edges(scene, drop)
+    pa, pb = dg.Problem.from_scene(scene), dg.Problem.from_scene(sub)
+    Ha, ga = dg.normal_equations(pa, pa.T, pa.d)
+    Hb, gb = dg.normal_equations(pb, pb.T, pb.d)
+    idx = dg.free_index(pa)
+    eH = np.abs(Ha[np.ix_(idx, idx)] - Hb[np.ix_(idx, idx)]).max() / np.abs(Hb[np.ix_(idx, idx)]).max()
+    eg = np.abs(ga[idx] - gb[idx]).max() / np.abs(gb[idx]).max()
+    oa, ob = dg.solve_scene(scene, n_iters=1), dg.solve_scene(sub, n_iters=1)
+    xa = np.concatenate([oa["dxi"][0].ravel(), oa["dd"][0]])
+    xb = np.concatenate([ob["dxi"][0].ravel(), ob["dd"][0]])
+    ex = np.abs(xa - xb).max() / np.abs(xb).max()
+    ca, cb = dg.cost(pa, pa.T, pa.d), dg.cost(pb, pb.T, pb.d)
+    ec = abs(ca - cb) / cb
+    return max(eH, eg, ex, ec), int(drop.sum())

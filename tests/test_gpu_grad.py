@@ -17,7 +17,7 @@ from paper_2208_04726_b300 import ba
 from paper_2208_04726_b300 import scenes as S
 from oracle import dense_gn as dg
 from oracle import unrolled_grad as ug
-from tests.gpu_util import TOL_GRAD, rel
+from tests.gpu_util import TOL_GRAD, err
 
 pytestmark = pytest.mark.gpu
 
@@ -70,8 +70,8 @@ def test_backward_matches_autograd_twin(solver, spec, seed):
     sc = S.make_scene(spec, seed)
     gts, gws = gpu_gradients(solver, [sc])
     ref_t, ref_w, _ = ug.gradient(sc)
-    assert rel(gts[0], ref_t) < TOL_GRAD, rel(gts[0], ref_t)
-    assert rel(gws[0], ref_w) < TOL_GRAD, rel(gws[0], ref_w)
+    assert err(gts[0], ref_t) < TOL_GRAD, err(gts[0], ref_t)
+    assert err(gws[0], ref_w) < TOL_GRAD, err(gws[0], ref_w)
 
 
 def test_backward_batch_of_sixteen_problems(solver):
@@ -80,7 +80,7 @@ def test_backward_batch_of_sixteen_problems(solver):
     gts, gws = gpu_gradients(solver, scenes)
     for b in (0, 7, 15):
         ref_t, ref_w, _ = ug.gradient(scenes[b])
-        assert rel(gts[b], ref_t) < TOL_GRAD and rel(gws[b], ref_w) < TOL_GRAD, b
+        assert err(gts[b], ref_t) < TOL_GRAD and err(gws[b], ref_w) < TOL_GRAD, b
 
 
 def _oracle_loss(sc, target, weight):
@@ -126,7 +126,7 @@ def test_window_size_backward_matches_autograd_twin(solver):
     sc = S.make_scene(S.WINDOW_N22, 4)
     gts, gws = gpu_gradients(solver, [sc])
     ref_t, ref_w, _ = ug.gradient(sc)
-    assert rel(gts[0], ref_t) < TOL_GRAD and rel(gws[0], ref_w) < TOL_GRAD
+    assert err(gts[0], ref_t) < TOL_GRAD and err(gws[0], ref_w) < TOL_GRAD
 
 
 def test_autograd_function_gives_the_same_gradient(solver):
@@ -141,8 +141,8 @@ def test_autograd_function_gives_the_same_gradient(solver):
         (patches[:, 2] * torch.tensor(gd, dtype=torch.float32, device="cuda")).sum()
     g_t, g_w = torch.autograd.grad(L, [target, weight])
     ref_t, ref_w, _ = ug.gradient(sc)
-    assert rel(g_t.cpu().numpy(), ref_t) < TOL_GRAD
-    assert rel(g_w.cpu().numpy(), ref_w) < TOL_GRAD
+    assert err(g_t.cpu().numpy(), ref_t) < TOL_GRAD
+    assert err(g_w.cpu().numpy(), ref_w) < TOL_GRAD
 
 
 def test_tf32_schur_mode_gradient_matches_autograd_twin():
@@ -154,6 +154,6 @@ def test_tf32_schur_mode_gradient_matches_autograd_twin():
         sc = S.make_scene(S.WINDOW_N22, 8)
         gts, gws = gpu_gradients(s, [sc])
         ref_t, ref_w, _ = ug.gradient(sc)
-        assert rel(gts[0], ref_t) < TOL_GRAD and rel(gws[0], ref_w) < TOL_GRAD
+        assert err(gts[0], ref_t) < TOL_GRAD and err(gws[0], ref_w) < TOL_GRAD
     finally:
         s.close()

@@ -12,7 +12,7 @@ import torch
 
 from paper_2208_04726_b300 import ba
 from paper_2208_04726_b300 import scenes as S
-from tests.gpu_util import TOL_DEPTH, TOL_POSE, end_to_end_errors, rel, solve_gpu
+from tests.gpu_util import TOL_DEPTH, TOL_POSE, end_to_end_errors, err, solve_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -74,8 +74,8 @@ def test_default_fast_mix_batch_equals_windows_alone(solver):
             # alone the problem is split into more work items (other summation order): the
             # updates agree within the parity tolerance, not bit for bit
             assert int(p.status.item()) == 0
-            assert rel((pb - p0).cpu().numpy(), (p.poses - p0).cpu().numpy()) < TOL_POSE
-            assert rel((qb - q0)[:, 2].cpu().numpy(), (p.patches - q0)[:, 2].cpu().numpy()) < TOL_DEPTH
+            assert err((pb - p0).cpu().numpy(), (p.poses - p0).cpu().numpy()) < TOL_POSE
+            assert err((qb - q0)[:, 2].cpu().numpy(), (p.patches - q0)[:, 2].cpu().numpy()) < TOL_DEPTH
     finally:
         for w in ws:
             w.close()

@@ -171,6 +171,15 @@ def test_autograd_twin_forward_matches_oracle():
     assert np.abs(depths - out["depths"]).max() < 1e-10
 
 
+def test_autograd_twin_forward_matches_oracle_with_edges_behind_the_camera():
+    sc = S.make_scene(dataclasses.replace(S.PLAIN_N8, near_frac=0.1), 2)
+    assert (pins.wp_homogeneous_depth(sc) <= dg.Z_MIN).sum() >= 30
+    out = dg.solve_scene(sc)
+    poses, depths = ug.final_state(sc)
+    assert np.abs(poses - out["poses"]).max() < 1e-10
+    assert np.abs(depths - out["depths"]).max() < 1e-10
+
+
 def _oracle_loss(sc, target, weight, n_iters=2):
     sc2 = dataclasses.replace(sc, target=target, weight=weight)
     out = dg.solve_scene(sc2, n_iters=n_iters)
@@ -205,6 +214,23 @@ def test_autograd_twin_gradient_matches_central_differences():
             fd = (_oracle_loss(sc, tp, wp) - _oracle_loss(sc, tm, wm)) / (2 * h)
             scale = np.abs(grad).max()
             assert abs(fd - grad[e, c]) < 1e-6 * scale + 1e-9, (which, e, c, fd, grad[e, c])
+
+
+NEAR_N8 = dataclasses.replace(S.PLAIN_N8, near_frac=0.1)
+
+
+def test_edges_behind_the_camera_take_no_part():
+    """Seeded 8-frame scenes with patches close to their source camera: every
+    edge whose homogeneous depth (world-point form) is at most z_min contributes
+    nothing to H, g, the increment or the cost.  The scenes keep every edge at
+    least 0.25 away from the threshold, so the set does not hinge on rounding."""
+    for seed in (2, 4):
+        sc = S.make_scene(NEAR_N8, seed)
+        zh = pins.wp_homogeneous_depth(sc)
+        assert np.abs(zh - dg.Z_MIN).min() > 0.2
+        err, n_off = pins.inactive_edge_error(sc)
+        assert n_off >= 30, n_off
+        assert err < 1e-12, err
 
 
 # --------------------------------------------------------------- planted mistakes
@@ -268,3 +294,39 @@ def _normal_equations_without_damping(prob, T, d):
         return _true_normal_equations(prob, T, d)
     finally:
         prob.damping = saved
+
+
+def test_pins_catch_a_dropped_activity_mask(plant):
+    orig = dg.reproject
+
+    def rep(prob, T, d):
+        G, X, uv, active = orig(prob, T, d)
+        Z = X[:, 2]
+        uv = np.stack([prob.fx * X[:, 0] / Z + prob.cx, prob.fy * X[:, 1] / Z + prob.cy], axis=1)
+        return G, X, uv, np.ones_like(active)
+    plant.setattr(dg, "reproject", rep)
+    err, _ = pins.inactive_edge_error(S.make_scene(NEAR_N8, 2))
+    assert err > 1e-3
+
+
+def test_pins_catch_an_activity_mask_on_the_residual_only(plant):
+    orig = dg.linearize
+
+    def lin(prob, T, d):
+        r, Ji, Jj, Jd, act = orig(prob, T, d)
+        # Jacobians recomputed as if every edge took part
+        G, X, _, _ = dg.reproject(prob, T, d)
+        Z = X[:, 2]
+        Jpi = np.zeros((X.shape[0], 2, 3))
+        Jpi[:, 0, 0] = prob.fx / Z
+        Jpi[:, 0, 2] = -prob.fx * X[:, 0] / (Z * Z)
+        Jpi[:, 1, 1] = prob.fy / Z
+        Jpi[:, 1, 2] = -prob.fy * X[:, 1] / (Z * Z)
+        dXj = np.concatenate([X[:, 3, None, None] * np.eye(3)[None], -dg.skew(X[:, :3])], axis=2)
+        Jj2 = Jpi @ dXj
+        Ji2 = -Jj2 @ dg.adjoint(G)
+        Jd2 = np.einsum('eab,eb->ea', Jpi, G[:, :3, 3])
+        return r, Ji2, Jj2, Jd2, act
+    plant.setattr(dg, "linearize", lin)
+    err, _ = pins.inactive_edge_error(S.make_scene(NEAR_N8, 2))
+    assert err > 1e-3
