@@ -34,7 +34,9 @@ same shapes stand in for them):
   it from behind.  Their edges are kept only where the true homogeneous depth
   is clearly on one side of the activity threshold (>= 0.5 or <= -0.5), so an
   edge's part in the solve does not hinge on rounding; the patches then have
-  gaps in their frame lists.
+  gaps in their frame lists.  A drawn near patch left with fewer than 4 clearly
+  active edges to other frames stays a regular patch (its inverse depth would
+  be poorly determined).
 * Initial state: every free pose (index >= t0) is moved by a 2-degree rotation
   about a random axis and a 5 cm translation in a random direction (applied on
   the world->camera side); fixed poses stay at ground truth; inverse depths are
@@ -216,6 +218,7 @@ def make_scene(spec: SceneSpec, seed: int, dtype=np.float32) -> Scene:
     anchor = np.repeat(np.arange(n), ppf)
     P = xs.shape[0]
     near = np.zeros(P, dtype=bool)
+    zs_regular = zs.copy()
     if spec.near_frac > 0:
         nrng = np.random.Generator(np.random.PCG64(seed ^ 0x4EA2))
         near = nrng.uniform(size=P) < spec.near_frac
@@ -231,10 +234,20 @@ def make_scene(spec: SceneSpec, seed: int, dtype=np.float32) -> Scene:
     jj = np.concatenate(jj_list)
     if near.any():
         # homogeneous depth of each edge at the true state: depth in frame j over depth in the source frame
-        pc = zs[:, None] * np.stack([(xs - CX) / FX, (ys - CY) / FY, np.ones(P)], axis=1)
-        pw = np.einsum('pab,pb->pa', R_cw[anchor], pc) + centres[anchor]
-        zj = np.einsum('eb,eb->e', R_wc[jj, 2, :], pw[kk]) + t_wc[jj, 2]
-        zh = zj / zs[kk]
+        def hom_depth():
+            pc = zs[:, None] * np.stack([(xs - CX) / FX, (ys - CY) / FY, np.ones(P)], axis=1)
+            pw = np.einsum('pab,pb->pa', R_cw[anchor], pc) + centres[anchor]
+            zj = np.einsum('eb,eb->e', R_wc[jj, 2, :], pw[kk]) + t_wc[jj, 2]
+            return zj / zs[kk]
+        # a near patch keeps its place only if at least 4 edges to other frames
+        # stay clearly active (its inverse depth then stays well determined)
+        zh = hom_depth()
+        n_act = np.zeros(P, np.int64)
+        np.add.at(n_act, kk, ((zh >= 0.5) & (jj != anchor[kk])).astype(np.int64))
+        weak = near & (n_act < 4)
+        zs[weak] = zs_regular[weak]
+        near &= ~weak
+        zh = hom_depth()
         keep = ~near[kk] | (zh >= 0.5) | (zh <= -0.5)
         kk, jj = kk[keep], jj[keep]
     E = kk.shape[0]

@@ -31,11 +31,13 @@ MID16 = dataclasses.replace(S.WINDOW_N22, n_frames=24, patches_per_frame=48, rad
 MID25 = dataclasses.replace(S.STRESS_N64, n_frames=33, patches_per_frame=32, radius=16, t0=8, n_iters=2)
 
 
-@pytest.fixture(scope="module", params=[False, True], ids=["fp32-schur", "tf32-schur"])
+@pytest.fixture(scope="module", params=[0, 1], ids=["fp32-schur", "tf32-schur"])
 def solver(request):
+    """Beyond 15 free poses the default (0) assembles on the CUDA cores; mode 1
+    assembles on the tensor cores."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
-    s = ba.Solver(schur_tf32=request.param)
+    s = ba.Solver(schur_mode=request.param)
     yield s
     s.close()
 
@@ -73,10 +75,10 @@ def test_each_iteration_matches_oracle_step(solver, spec, seed):
 def test_edges_behind_the_camera_match_oracle(solver):
     """16 free poses (the assembly path) on a scene whose near patches are seen
     from behind by later cameras: those edges are left out on both paths."""
-    sc = S.make_scene(dataclasses.replace(MID16, near_frac=0.1), 1)
+    sc = S.make_scene(dataclasses.replace(MID16, near_frac=0.1), 4)
     pr = dg.Problem.from_scene(sc)
     Z = dg.reproject(pr, pr.T, pr.d)[1][:, 2]
-    assert (Z <= dg.Z_MIN).sum() >= 150 and np.abs(Z - dg.Z_MIN).min() > 0.1
+    assert (Z <= dg.Z_MIN).sum() >= 400 and np.abs(Z - dg.Z_MIN).min() > 0.1
     probs = solve_gpu(solver, [sc])
     assert int(probs[0].status.item()) == 0
     for t, (e_xi, e_dd) in enumerate(iteration_errors(solver, sc, 0, sc.n_iters)):

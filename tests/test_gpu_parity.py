@@ -20,26 +20,23 @@ from tests.gpu_util import (TOL_DEPTH, TOL_POSE, align_quats, end_to_end_errors,
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=[False, True], ids=["fp32-schur", "tf32-schur"])
+@pytest.fixture(scope="module", params=[0, 2], ids=["tc-schur", "fp32-schur"])
 def solver(request):
-    """Both accumulation modes of the Schur complement: compensated FP32 on the
-    CUDA cores (the default) and three TF32 products on the tensor cores."""
+    """Both accumulations of the Schur complement on these problems (at most
+    10 free poses): the default one-pass kernel (three TF32 products on the
+    tensor cores, drained into FP32 sums every few MMAs; back-substitution
+    recomputed from the edges) and compensated FP32 on the CUDA cores (the
+    fused linearise kernel with stored Schur rows)."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
-    s = ba.Solver(schur_tf32=request.param)
+    s = ba.Solver(schur_mode=request.param)
     yield s
     s.close()
 
 
 def step_errors(solver, scene, index, n_iters):
-    """Per-iteration errors against the oracle's teacher-forced step.  In the
-    FP32 mode each increment is measured relative to itself.  In the TF32 mode
-    it is measured against the first increment's norm: the tensor cores' FP32
-    accumulation truncates, so once the iterations converge the relative error
-    of a small increment exceeds 1e-4 on some 8-frame scenes (1.03e-4 measured)
-    while the error on the solve's own update scale stays near 1e-5."""
-    if solver.schur_tf32:
-        return iteration_abs_errors(solver, scene, index, n_iters)
+    """Per-iteration errors against the oracle's teacher-forced step, each
+    increment measured relative to itself (2-norm and per element)."""
     return iteration_errors(solver, scene, index, n_iters)
 
 
@@ -76,13 +73,13 @@ def test_whole_solve_matches_oracle(solver, spec, seed):
     assert err(dxi2, ref["dxi"][1]) < 1e-3
 
 
-@pytest.mark.parametrize("spec,seed,min_off", [(dataclasses.replace(S.PLAIN_N8, near_frac=0.1), 2, 30),
-                                                (dataclasses.replace(S.PLAIN_N8, near_frac=0.1), 4, 30),
-                                                (dataclasses.replace(S.WINDOW_N22, near_frac=0.1), 2, 900)])
+@pytest.mark.parametrize("spec,seed,min_off", [(dataclasses.replace(S.PLAIN_N8, near_frac=0.3), 4, 4),
+                                                (dataclasses.replace(S.PLAIN_N8, near_frac=0.3), 11, 4),
+                                                (dataclasses.replace(S.WINDOW_N22, near_frac=0.1), 1, 200)])
 def test_edges_behind_the_camera_match_oracle(solver, spec, seed, min_off):
     """Scenes with patches close to their source camera, seen from behind by
     cameras further along the path: those edges' homogeneous depth is far below
-    z_min (0.25 or more from the threshold at every oracle iterate), so both
+    z_min (0.1 or more from the threshold at every oracle iterate), so both
     paths must leave them out.  Per-iteration and whole-solve parity."""
     sc = S.make_scene(spec, seed)
     pr = dg.Problem.from_scene(sc)
