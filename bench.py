@@ -619,6 +619,50 @@ def parity_of(batch, scenes, refs):
     return out
 
 
+def plain_n8_bench(stream, n=200, warmup=10, seed=20_000):
+    """The 8-frame problem (8 frames x 64 patches, every patch connected to every
+    frame: 4,096 edges, poses 0-1 fixed, 2 GN iterations) solved one per call,
+    back to back: per-solve latency from CUDA events around each call on the
+    launching stream, and the split over the kernels of one call."""
+    import torch
+    from paper_2208_04726_b300 import ba
+    from paper_2208_04726_b300 import scenes as S
+    scenes = [S.make_scene(S.PLAIN_N8, seed + s) for s in range(8)]
+    batch = ba.PackedBatch(scenes, "cuda")
+    solver = ba.Solver()
+    solver.reserve(8, 512, 4096, 2, 1)
+    subsets = [batch.subset(b % len(scenes)) for b in range(n)]
+    for d_, p_ in subsets[:warmup]:
+        batch.reset()
+        solver.solve_arrays(d_, p_, 1, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for (a, b_), (d_, p_) in zip(ev, subsets):
+        a.record(stream)
+        solver.solve_arrays(d_, p_, 1, stream)
+        b_.record(stream)
+    torch.cuda.synchronize()
+    lat = np.array([a.elapsed_time(b_) for a, b_ in ev])
+    solver.set_timing(True)
+    solver.timing()
+    for d_, p_ in subsets[:20]:
+        solver.solve_arrays(d_, p_, 1, stream)
+    torch.cuda.synchronize()
+    launches = solver.timing(cap=256)
+    solver.set_timing(False)
+    solver.close()
+    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub"}
+    kinds = {}
+    for k, v in launches:
+        kinds.setdefault(names.get(int(k), str(k)), []).append(v)
+    return {"workload": "8 frames x 64 patches (512), all frames connected (4,096 edges), poses 0-1 fixed, "
+                        "2 GN iterations; one problem per call",
+            "solves": n, "latency_ms_p50": float(np.percentile(lat, 50)),
+            "latency_ms_p99": float(np.percentile(lat, 99)),
+            "kernel_ms_per_launch": {k: float(np.median(v)) for k, v in kinds.items()},
+            "kernel_launches_per_solve": {k: len(v) // 20 for k, v in kinds.items()}}
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -808,6 +852,7 @@ def main():
             fp32.update({k: par[k] for k in par if k != "problems_checked"})
         tsolver.close()
 
+    plain_n8 = plain_n8_bench(stream) if (rank == 0 and args.plain > 0) else None
     serving = serving_bench() if (rank == 0 and args.serving) else None
     stress = stress_bench(args.stress, 5, stream, load_peaks()[0]) if (rank == 0 and args.stress > 0) else None
     if stress is not None and args.tf32:
@@ -838,6 +883,7 @@ def main():
                         "latency_ms_p99": float(np.percentile(step_times, 99))},
             "plain": {"solves_per_s": plain_value, "latency_ms_p50": float(np.percentile(plain_lat, 50)),
                       "latency_ms_p99": float(np.percentile(plain_lat, 99)), "solves": args.plain},
+            "plain_n8": plain_n8,
             "kernels": kern,
             "roofline": roof,
             "parity": parity,
