@@ -32,10 +32,10 @@
 //          hi] . hi^T accumulates lo.hi^T (TMEM lanes 0-63) and hi.hi^T (lanes
 //          64-127) in FP32; rows 62/63 of hi carry C_k^-1/2 w_k in two halves,
 //          so v' comes out of the same product.  The tensor core truncates
-//          its FP32 accumulation, so the large hi.hi^T block is drained into
-//          FP32 sums in shared memory every kGpDrainEvery chunks (a fresh
-//          accumulation follows, which restarts both halves of D, so both are
-//          drained).
+//          its FP32 accumulation, so D is drained into FP32 sums in shared
+//          memory every kGpDrainEvery chunks (a fresh accumulation follows):
+//          A += hi.hi^T / 2 + lo.hi^T over the pose columns (then S's Schur
+//          term is A + A^T), and the w columns as v' needs them.
 //   Group end (the last chunk of an anchor's run): the per-frame sums M_j,
 //          v_j are combined over patch groups and the pose-pair blocks
 //          B_jj = M_j, B_ij = -Ad_ij^T M_j, B_ii = sum_j Ad_ij^T M_j Ad_ij go
@@ -59,7 +59,7 @@
 namespace dpvo {
 
 constexpr int kGpDrainEvery = 2;       // chunks of MMAs accumulated in TMEM before hi.hi^T is drained
-constexpr int kGpDaccLd = 68;          // row stride (floats) of the drained [lo.hi^T; hi.hi^T] sums
+constexpr int kGpDaccLd = 68;          // row stride (floats) of the drained sums A (64 rows)
 constexpr int kGpWin = 72;             // floats of window data per frame
 constexpr int kGpMpHalf = 14;          // frame sums (of 27) parked per thread at a time at a group end
 
@@ -67,8 +67,10 @@ constexpr int kGpMpHalf = 14;          // frame sums (of 27) parked per thread a
 struct GpSmem {
     int W, G, Gs, Gs1, Kc;
     uint32_t sbo;
-    size_t off_pnew, off_pold, off_dxs, off_win, off_rjj, off_rtg, off_rwt, off_rpx, off_rpy, off_rdep, off_rseg,
-        off_rcw, off_idx, off_u, off_sc1, off_pd, off_op, off_dacc, off_mc, bytes;
+    size_t off_pnew, off_pold, off_rot, off_dxs, off_win, off_stage, off_idx, off_u, off_sc1, off_pd, off_op,
+        off_dacc, off_mc, bytes;
+    // one chunk's staging buffers, offsets from a staging base
+    size_t st_rjj, st_rtg, st_rwt, st_rpx, st_rpy, st_rdep, st_rseg, st_rcw, st_bytes;
 };
 
 __host__ __device__ inline GpSmem gp_smem_layout(int W, int G, int n_max) {
@@ -81,19 +83,23 @@ __host__ __device__ inline GpSmem gp_smem_layout(int W, int G, int n_max) {
     s.sbo = (uint32_t)(s.Kc / 4) * 144u;
     const size_t EC = (size_t)W * G;
     const size_t slots4 = (size_t)W * s.Gs, slots1 = (size_t)W * s.Gs1;
+    size_t q = 0;
+    s.st_rjj = q;  q = align16(q + (EC + 8) * 4);
+    s.st_rtg = q;  q = align16(q + (EC + 2) * 8);
+    s.st_rwt = q;  q = align16(q + (EC + 2) * 8);
+    s.st_rpx = q;  q = align16(q + (size_t)G * 4);
+    s.st_rpy = q;  q = align16(q + (size_t)G * 4);
+    s.st_rdep = q; q = align16(q + (size_t)G * 4);
+    s.st_rseg = q; q = align16(q + (size_t)(G + 1) * 4);
+    s.st_rcw = q;  q = align16(q + (size_t)G * 8);
+    s.st_bytes = q;
     size_t o = 0;
     s.off_pnew = o; o = align16(o + (size_t)n_max * 7 * 4);
     s.off_pold = o; o = align16(o + (size_t)n_max * 7 * 4);
+    s.off_rot = o;  o = align16(o + (size_t)n_max * 18 * 4);
     s.off_dxs = o;  o = align16(o + (size_t)6 * kMaxFree * 4);
     s.off_win = o;  o = align16(o + (size_t)W * kGpWin * 4);
-    s.off_rjj = o;  o = align16(o + (EC + 8) * 4);
-    s.off_rtg = o;  o = align16(o + (EC + 2) * 8);
-    s.off_rwt = o;  o = align16(o + (EC + 2) * 8);
-    s.off_rpx = o;  o = align16(o + (size_t)G * 4);
-    s.off_rpy = o;  o = align16(o + (size_t)G * 4);
-    s.off_rdep = o; o = align16(o + (size_t)G * 4);
-    s.off_rseg = o; o = align16(o + (size_t)(G + 1) * 4);
-    s.off_rcw = o;  o = align16(o + (size_t)G * 8);
+    s.off_stage = o; o = align16(o + s.st_bytes);
     s.off_idx = o;  o = align16(o + slots4 * 2);
     // union: per-slot sums (sc4 float4 | sc1 float, the back-substitution
     // terms sharing sc1) during a chunk; at a group end one half of the
@@ -108,24 +114,52 @@ __host__ __device__ inline GpSmem gp_smem_layout(int W, int G, int n_max) {
     s.off_sc1 = o + align16(slots4 * 16);
     o = align16(o + u);
     s.off_pd = o;   o = align16(o + (size_t)G * 16);
+    // the operand and the drained sums are contiguous: the last launch (no
+    // linearisation) stages its next chunk there
     s.off_op = o;   o = align16(o + (size_t)16 * s.sbo);
-    s.off_dacc = o; o = align16(o + (size_t)2 * kTcRows * kGpDaccLd * 4);
+    s.off_dacc = o; o = align16(o + (size_t)kTcRows * kGpDaccLd * 4);
+    if (o - s.off_op < s.st_bytes) o = s.off_op + s.st_bytes;
     s.off_mc = o;   o = align16(o + (size_t)W * 27 * 4);
     s.bytes = o;
     return s;
 }
 
+// One chunk's staging buffers.
+struct GpStage {
+    int *rjj;
+    float2 *rtg, *rwt;
+    float *rpx, *rpy, *rdep;
+    int *rseg;
+    float2 *rcw;
+};
+
+__device__ __forceinline__ GpStage gp_stage(unsigned char *base, const GpSmem &L) {
+    GpStage g;
+    g.rjj = reinterpret_cast<int *>(base + L.st_rjj);
+    g.rtg = reinterpret_cast<float2 *>(base + L.st_rtg);
+    g.rwt = reinterpret_cast<float2 *>(base + L.st_rwt);
+    g.rpx = reinterpret_cast<float *>(base + L.st_rpx);
+    g.rpy = reinterpret_cast<float *>(base + L.st_rpy);
+    g.rdep = reinterpret_cast<float *>(base + L.st_rdep);
+    g.rseg = reinterpret_cast<int *>(base + L.st_rseg);
+    g.rcw = reinterpret_cast<float2 *>(base + L.st_rcw);
+    return g;
+}
+
+// TF32 (10 stored mantissa bits) nearest to x, ties away from zero, as bits:
+// the 13 dropped bits round the kept ones by an integer add and mask.
+__device__ __forceinline__ uint32_t gp_tf32(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+
 // Start copying one chunk's inputs: frames, targets and weights of its edges
 // (bulk copies on `bar` where aligned), its patches' centres and inverse
 // depths (depth_src), patch -> edge offsets, the previous pass's (C_k, w_k)
 // when cw != nullptr, and the descriptor of the chunk after it.
-__device__ __forceinline__ void gp_prefetch(const Prob &pr, const Chunk &ch, const float *depth_src, int *rjj,
-                                            float2 *rtg, float2 *rwt, float *rpx, float *rpy, float *rdep, int *rseg,
-                                            float2 *rcw, const Chunk *desc_src, Chunk *desc_dst, uint32_t bar) {
-    prefetch_chunk(pr, ch, depth_src, rjj, rtg, rwt, rpx, rpy, rdep, rseg, desc_src, desc_dst, bar);
-    if (rcw) {
+__device__ __forceinline__ void gp_prefetch(const Prob &pr, const Chunk &ch, const float *depth_src, const GpStage &g,
+                                            bool with_cw, const Chunk *desc_src, Chunk *desc_dst, uint32_t bar) {
+    prefetch_chunk(pr, ch, depth_src, g.rjj, g.rtg, g.rwt, g.rpx, g.rpy, g.rdep, g.rseg, desc_src, desc_dst, bar);
+    if (with_cw) {
         const float2 *cw = reinterpret_cast<const float2 *>(pr.cw);
-        for (int q = threadIdx.x; q < ch.count; q += kThreads) cp_async8(rcw + q, cw + ch.k0 + q);
+        for (int q = threadIdx.x; q < ch.count; q += kThreads) cp_async8(g.rcw + q, cw + ch.k0 + q);
         cp_async_commit();
     }
 }
@@ -134,36 +168,74 @@ __device__ __forceinline__ void gp_prefetch(const Prob &pr, const Chunk &ch, con
 //   [0, 12)  R_ij, t_ij at iterate t;   [12, 48) Ad(G_ij) at iterate t;
 //   [48, 60) R_ij, t_ij at iterate t-1; [60, 72) K_ij (row-major), h_ij of
 //   the back-substitution (iteration t-1's increment, zero for fixed poses).
-__device__ __forceinline__ void gp_window(const Prob &pr, const float *pnew, const float *pold, const float *dxs,
-                                          int anc, int jlo, int W, bool lin, bool bs, float *win) {
-    for (int jl = threadIdx.x; jl < W; jl += kThreads) {
+// Three threads per frame, one per row; rot holds each frame's rotation
+// matrix at iterates t (rot) and t-1 (rot + 9 N).
+// Step 1: R_ij = R_j R_i^T and t_ij = t_j - R_ij t_i.
+__device__ __forceinline__ void gp_window1(const float *pnew, const float *pold, const float *rot, int N, int anc,
+                                           int jlo, int W, bool lin, bool bs, float *win) {
+    for (int q = threadIdx.x; q < 3 * W; q += kThreads) {
+        const int jl = q / 3, r = q - 3 * jl, j = jlo + jl;
         float *wd = win + jl * kGpWin;
-        const int j = jlo + jl;
+#pragma unroll
+        for (int st = 0; st < 2; ++st) {
+            if (st == 0 ? !lin : !bs) continue;
+            const float *Rs = rot + st * 9 * N, *ps = st ? pold : pnew;
+            const float *Ri = Rs + 9 * anc, *Rj = Rs + 9 * j;
+            float R[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                R[c] = fmaf(Rj[3 * r + 2], Ri[3 * c + 2], fmaf(Rj[3 * r + 1], Ri[3 * c + 1], Rj[3 * r] * Ri[3 * c]));
+            float *o = wd + (st ? 48 : 0);
+            o[3 * r] = R[0];
+            o[3 * r + 1] = R[1];
+            o[3 * r + 2] = R[2];
+            const float *ti = ps + 7 * anc;
+            o[9 + r] = ps[7 * j + r] - fmaf(R[2], ti[2], fmaf(R[1], ti[1], R[0] * ti[0]));
+        }
+    }
+}
+
+// Step 2 (after a barrier): Ad(G_ij) rows r and r + 3; K_ij row r and h_ij[r]:
+//   K = [w_j]x R - R [w_i]x,  h = v_j + w_j x t - R v_i.
+__device__ __forceinline__ void gp_window2(const float *dxs, int t0, int anc, int jlo, int W, bool lin, bool bs,
+                                           float *win) {
+    for (int q = threadIdx.x; q < 3 * W; q += kThreads) {
+        const int jl = q / 3, r = q - 3 * jl, j = jlo + jl;
+        float *wd = win + jl * kGpWin;
+        const int r1 = r == 2 ? 0 : r + 1, r2 = r == 0 ? 2 : r - 1;
         if (lin) {
-            relative_pose(pnew + 7 * anc, pnew + 7 * j, wd, wd + 9);
-            adjoint6(wd, wd + 9, wd + 12);
+            const float *R = wd, *tt = wd + 9;
+            float *Ad = wd + 12;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Ad[6 * r + c] = R[3 * r + c];
+                // ([t]x R)_rc = t_{r+1} R_{r+2,c} - t_{r+2} R_{r+1,c}
+                Ad[6 * r + 3 + c] = fmaf(tt[r1], R[3 * r2 + c], -tt[r2] * R[3 * r1 + c]);
+                Ad[6 * (r + 3) + c] = 0.f;
+                Ad[6 * (r + 3) + 3 + c] = R[3 * r + c];
+            }
         }
         if (bs) {
-            float *R = wd + 48, *tt = wd + 57, *K = wd + 60, *h = wd + 69;
-            relative_pose(pold + 7 * anc, pold + 7 * j, R, tt);
+            const float *R = wd + 48, *tt = wd + 57;
+            float *K = wd + 60, *h = wd + 69;
             float vi[3] = {0.f, 0.f, 0.f}, wi[3] = {0.f, 0.f, 0.f}, vj[3] = {0.f, 0.f, 0.f}, wj[3] = {0.f, 0.f, 0.f};
-            if (anc >= pr.t0)
-                for (int m = 0; m < 3; ++m) { vi[m] = dxs[6 * (anc - pr.t0) + m]; wi[m] = dxs[6 * (anc - pr.t0) + 3 + m]; }
-            if (j >= pr.t0)
-                for (int m = 0; m < 3; ++m) { vj[m] = dxs[6 * (j - pr.t0) + m]; wj[m] = dxs[6 * (j - pr.t0) + 3 + m]; }
-            // K = [wj]x R - R [wi]x
-            for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 3; ++c) {
-                    // ([wj]x R)_rc = (wj x R_col c)_r
-                    const float a = wj[(r + 1) % 3] * R[3 * ((r + 2) % 3) + c] - wj[(r + 2) % 3] * R[3 * ((r + 1) % 3) + c];
-                    // (R [wi]x)_rc = sum_m R_rm ([wi]x)_mc, ([wi]x)_mc = eps_{m i c} wi_i
-                    const float b = R[3 * r + (c + 1) % 3] * wi[(c + 2) % 3] - R[3 * r + (c + 2) % 3] * wi[(c + 1) % 3];
-                    K[3 * r + c] = a - b;
-                }
-            // h = vj + wj x t - R vi
-            for (int r = 0; r < 3; ++r)
-                h[r] = vj[r] + (wj[(r + 1) % 3] * tt[(r + 2) % 3] - wj[(r + 2) % 3] * tt[(r + 1) % 3]) -
-                       (R[3 * r] * vi[0] + R[3 * r + 1] * vi[1] + R[3 * r + 2] * vi[2]);
+            if (anc >= t0)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) { vi[m] = dxs[6 * (anc - t0) + m]; wi[m] = dxs[6 * (anc - t0) + 3 + m]; }
+            if (j >= t0)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) { vj[m] = dxs[6 * (j - t0) + m]; wj[m] = dxs[6 * (j - t0) + 3 + m]; }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+                // ([wj]x R)_rc = wj_{r+1} R_{r+2,c} - wj_{r+2} R_{r+1,c}
+                const float a = fmaf(wj[r1], R[3 * r2 + c], -wj[r2] * R[3 * r1 + c]);
+                // (R [wi]x)_rc = R_{r,c+1} wi_{c+2} - R_{r,c+2} wi_{c+1}
+                const float b = fmaf(R[3 * r + c1], wi[c2], -R[3 * r + c2] * wi[c1]);
+                K[3 * r + c] = a - b;
+            }
+            h[r] = vj[r] + fmaf(wj[r1], tt[r2], -wj[r2] * tt[r1]) -
+                   fmaf(R[3 * r + 2], vi[2], fmaf(R[3 * r + 1], vi[1], R[3 * r] * vi[0]));
         }
     }
 }
@@ -187,24 +259,39 @@ __device__ __forceinline__ float gp_bs_term(const float *R, const float *K, floa
     return (iz * iz) * fmaf(w1 * fy2 * u1, g1, w0 * fx2 * u0 * g0);
 }
 
-// Add the TMEM accumulator D (128 lanes x 64 FP32 columns) into the FP32 sums
-// dacc [128][kGpDaccLd]: warp w reads lanes 32 (w % 4) .. + 31 (the quarter it
-// may access) and columns 32 (w / 4) .. + 31; a thread adds its row's 32
-// values with 16-byte shared-memory accesses (the padded stride keeps a
-// quarter warp's rows in distinct banks).
-__device__ __forceinline__ void gp_drain(uint32_t tmem, float *dacc, int warp, int lane) {
-    const int row = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);
-    float4 *dr = reinterpret_cast<float4 *>(dacc + row * kGpDaccLd + c0);
+// Drain D (128 TMEM lanes x 64 FP32 columns) into the FP32 sums A [64][kGpDaccLd]
+// in two passes (the two halves of D land on the same rows of A): first the
+// hi.hi^T rows (lanes 64-127: warps 2, 3, 6, 7), halved on the pose columns,
+// then, after a barrier, the lo.hi^T rows (lanes 0-63) without their column 63
+// (lo.lo of the w column).  Warp w reads lanes 32 (w % 4) .. + 31, the quarter
+// it may access, and columns 32 (w / 4) .. + 31.  All threads call it.
+__device__ __forceinline__ void gp_drain(uint32_t tmem, float *acc, int warp, int lane) {
+    const int q4 = warp & 3, c0 = 32 * (warp >> 2);
+    const int row = 32 * q4 + lane - (q4 >= 2 ? kTcRows : 0);
+    float4 *dr = reinterpret_cast<float4 *>(acc + row * kGpDaccLd + c0);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + 16 * h), v);
+    for (int pass = 0; pass < 2; ++pass) {
+        if ((q4 >= 2) == (pass == 0)) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float4 a = dr[4 * h + q];
-            a.x += v[4 * q]; a.y += v[4 * q + 1]; a.z += v[4 * q + 2]; a.w += v[4 * q + 3];
-            dr[4 * h + q] = a;
+            for (int h = 0; h < 2; ++h) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(c0 + 16 * h), v);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int col = c0 + 16 * h + 4 * q + e;
+                        float &x = v[4 * q + e];
+                        if (pass == 0) x = col < kTcRows - 2 ? 0.5f * x : x;   // hi.hi^T: halved pose columns
+                        else x = col == kTcRows - 1 ? 0.f : x;                  // lo.hi^T: no lo.lo of w
+                    }
+                    float4 a = dr[4 * h + q];
+                    a.x += v[4 * q]; a.y += v[4 * q + 1]; a.z += v[4 * q + 2]; a.w += v[4 * q + 3];
+                    dr[4 * h + q] = a;
+                }
+            }
         }
+        if (pass == 0) __syncthreads();
     }
 }
 
@@ -227,16 +314,14 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
     const GpSmem L = gp_smem_layout(W_cap, G_cap, n_max);
     float *pnew = reinterpret_cast<float *>(smem + L.off_pnew);
     float *pold = reinterpret_cast<float *>(smem + L.off_pold);
+    float *rot = reinterpret_cast<float *>(smem + L.off_rot);
     float *dxs = reinterpret_cast<float *>(smem + L.off_dxs);
     float *win = reinterpret_cast<float *>(smem + L.off_win);
-    int *rjj_s = reinterpret_cast<int *>(smem + L.off_rjj);
-    float2 *rtg_s = reinterpret_cast<float2 *>(smem + L.off_rtg);
-    float2 *rwt_s = reinterpret_cast<float2 *>(smem + L.off_rwt);
-    float *rpx = reinterpret_cast<float *>(smem + L.off_rpx);
-    float *rpy = reinterpret_cast<float *>(smem + L.off_rpy);
-    float *rdep = reinterpret_cast<float *>(smem + L.off_rdep);
-    int *rseg = reinterpret_cast<int *>(smem + L.off_rseg);
-    float2 *rcw = reinterpret_cast<float2 *>(smem + L.off_rcw);
+    // staging: one buffer; the last launch alternates with a second one in the
+    // (then unused) operand region, so that the next chunk's copies start as
+    // soon as the current chunk's have landed
+    unsigned char *const stage0 = smem + L.off_stage;
+    unsigned char *const stage1 = smem + (do_lin ? L.off_stage : L.off_op);
     short *sidx = reinterpret_cast<short *>(smem + L.off_idx);
     float4 *sc4 = reinterpret_cast<float4 *>(smem + L.off_u);
     float *sc1 = reinterpret_cast<float *>(smem + L.off_sc1);   // also the back-substitution terms
@@ -245,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
     float *Bp = reinterpret_cast<float *>(smem + L.off_u + align16((size_t)W_cap * 42 * 4));
     float4 *pd = reinterpret_cast<float4 *>(smem + L.off_pd);
     unsigned char *op = smem + L.off_op;
-    float *dacc = reinterpret_cast<float *>(smem + L.off_dacc);   // drained [lo.hi^T; hi.hi^T]
+    float *dacc = reinterpret_cast<float *>(smem + L.off_dacc);   // drained sums A
     float *Mc = reinterpret_cast<float *>(smem + L.off_mc);
     const int Gs = L.Gs, Gs1 = L.Gs1;
     const uint32_t sbo = L.sbo;
@@ -287,11 +372,16 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
     if (use_tc) {
         uint4 *o4 = reinterpret_cast<uint4 *>(op);
         for (int q = tid; q < (int)(16 * sbo / 16); q += kThreads) o4[q] = make_uint4(0u, 0u, 0u, 0u);
-        for (int q = tid; q < 2 * kTcRows * kGpDaccLd; q += kThreads) dacc[q] = 0.f;
+        for (int q = tid; q < kTcRows * kGpDaccLd; q += kThreads) dacc[q] = 0.f;
     }
     if (do_lin) {
         double *part = pr.partial + (size_t)itm.item * pr.L;
         for (int q = tid; q < pr.L; q += kThreads) part[q] = 0.0;
+    }
+    __syncthreads();                                 // poses staged
+    for (int j = tid; j < N; j += kThreads) {        // per-frame rotations at iterates t and t-1
+        if (do_lin) quat_to_rot(pnew + 7 * j + 3, rot + 9 * j);
+        if (do_bs) quat_to_rot(pold + 7 * j + 3, rot + 9 * N + 9 * j);
     }
     tc_fence_before();
     __syncthreads();
@@ -302,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
     if (c_begin < c_end) {
         if (tid == 0) s_ch[0] = pr.chunks[c_begin];
         __syncthreads();
-        gp_prefetch(pr, s_ch[0], depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg, do_bs ? rcw : nullptr,
+        gp_prefetch(pr, s_ch[0], depth_src, gp_stage(stage0, L), do_bs,
                     c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1], ldbar);
     }
 
@@ -319,16 +409,20 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
     for (int c = c_begin; c < c_end; ++c) {
         const Chunk ch = s_ch[cur];
         const bool have_next = c + 1 < c_end;
+        const GpStage g = gp_stage(cur ? stage1 : stage0, L);
         cp_async_wait_all();
         if (!mbar_wait(ldbar, (uint32_t)(c - c_begin) & 1u)) atomicOr(&s_bad, 1);
         // the previous chunk's MMAs read the operand, which this chunk rewrites
         if (use_tc && n_commit > 0 && !mbar_wait(mbar, (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_bad, 2);
         __syncthreads();
         if (s_bad) break;
-        int o_jj, o_tw;
-        staged_offsets(pr, ch, true, o_jj, o_tw);
         Chunk nx = ch;
         if (have_next) nx = s_ch[cur ^ 1];
+        if (!do_lin && have_next)   // the last launch: the next chunk's copies start now, into the other buffer
+            gp_prefetch(pr, nx, depth_src, gp_stage(cur ? stage0 : stage1, L), true,
+                        c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur], ldbar);
+        int o_jj, o_tw;
+        staged_offsets(pr, ch, true, o_jj, o_tw);
         const bool group_next = have_next && nx.anchor == ch.anchor && nx.jlo == ch.jlo && nx.jhi == ch.jhi;
         const int k0 = ch.k0, cnt = ch.count, e0 = ch.e0;
         const int anc = ch.anchor, jlo = ch.jlo;
@@ -345,16 +439,22 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
         const int LP = lanes_per_patch(cnt, &lp_sh);
         const int ps_sh = 8 - lp_sh, PSm = (1 << ps_sh) - 1;
 
-        // -- (0) slot -> staged edge table, patch data, window, cleared operand columns
+        // -- (0) the window at a group's first chunk (two steps), slot -> staged
+        // edge table, patch data, cleared operand columns
+        if (!group_open) {
+            gp_window1(pnew, pold, rot, N, anc, jlo, W, do_lin, do_bs, win);
+            __syncthreads();
+            gp_window2(dxs, t0, anc, jlo, W, do_lin, do_bs, win);
+        }
         {
             const int p = tid & PSm;
             if (p < cnt) {
-                const int a = rseg[p] - e0, b = rseg[p + 1] - e0;
+                const int a = g.rseg[p] - e0, b = g.rseg[p + 1] - e0;
                 int jf = 0, jz = -1;
                 bool contig = true;
                 if (b > a) {
-                    jf = rjj_s[o_jj + a];
-                    jz = rjj_s[o_jj + b - 1];
+                    jf = g.rjj[o_jj + a];
+                    jz = g.rjj[o_jj + b - 1];
                     contig = jz - jf + 1 == b - a;
                 }
                 for (int jl = tid >> ps_sh; jl < W; jl += kThreads >> ps_sh) {
@@ -367,9 +467,9 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                             int lo = a, hi = b - 1;
                             while (lo < hi) {
                                 const int mid = (lo + hi) >> 1;
-                                if (rjj_s[o_jj + mid] < j) lo = mid + 1; else hi = mid;
+                                if (g.rjj[o_jj + mid] < j) lo = mid + 1; else hi = mid;
                             }
-                            if (rjj_s[o_jj + lo] == j) idx = lo;
+                            if (g.rjj[o_jj + lo] == j) idx = lo;
                         }
                     }
                     sidx[jl * Gs + p] = (short)(idx >= 0 ? idx + o_tw : -1);
@@ -384,8 +484,7 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                     }
             }
             for (int q = tid; q < cnt; q += kThreads)
-                pd[q] = make_float4((rpx[q] - cx) * ifx, (rpy[q] - cy) * ify, rdep[q], 0.f);
-            if (!group_open) gp_window(pr, pnew, pold, dxs, anc, jlo, W, do_lin, do_bs, win);
+                pd[q] = make_float4((g.rpx[q] - cx) * ifx, (g.rpy[q] - cy) * ify, g.rdep[q], 0.f);
         }
         __syncthreads();
 
@@ -400,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                     float s = 0.f;
                     const int idx = sidx[my_jl * Gs + p];
                     if (pose_terms && idx >= 0) {
-                        const float2 wv = rwt_s[idx];
+                        const float2 wv = g.rwt[idx];
                         const float4 q = pd[p];
                         s = gp_bs_term(Rb, Kb, q.x, q.y, q.z, wv.x, wv.y, fx2, fy2, z_min);
                     }
@@ -416,18 +515,15 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                     for (int jl = sub; jl < W; jl += LP) s += sc1[jl * Gs1 + p];
                 s = lane_group_sum(s, LP);
                 if (sub == 0 && p < cnt) {
-                    const float2 cw = rcw[p];
-                    const float d = rdep[p] + (cw.y - s) / cw.x;
+                    const float2 cw = g.rcw[p];
+                    const float d = g.rdep[p] + (cw.y - s) / cw.x;
                     depth_t[k0 + p] = d;
                     pd[p].z = d;
                     if (!do_lin && !pr.no_writeback) pr.patches[3 * (k0 + p) + 2] = d;
                 }
             }
             __syncthreads();
-            if (!do_lin) {   // last launch: the staging buffers are free
-                if (have_next)
-                    gp_prefetch(pr, nx, depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg, rcw,
-                                c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur], ldbar);
+            if (!do_lin) {
                 group_open = group_next;
                 cur ^= 1;
                 continue;
@@ -436,12 +532,6 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
 
         // -- (C) linearise at iterate t
         if (edge_thread) {
-            if (!group_open) {
-#pragma unroll
-                for (int q = 0; q < 21; ++q) M[q] = 0.f;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) V[q] = 0.f;
-            }
             float Rr[12];
             const float *wd = win + my_jl * kGpWin;
 #pragma unroll
@@ -451,9 +541,9 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                 float Ce = 0.f, we = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
                 float4 elo = make_float4(0.f, 0.f, 0.f, 0.f), ehi = elo;
                 if (idx >= 0 && my_j != anc) {
-                    const float2 wv = rwt_s[idx];
+                    const float2 wv = g.rwt[idx];
                     if (wv.x != 0.f || wv.y != 0.f) {
-                        const float2 tv = rtg_s[idx];
+                        const float2 tv = g.rtg[idx];
                         const float4 q = pd[p];
                         EdgeLin E;
                         if (edge_linearize(Rr, Rr + 9, q.x, q.y, q.z, tv.x, tv.y, fx, fy, cx, cy, z_min, E)) {
@@ -500,15 +590,13 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
             }
         }
         __syncthreads();
-        // the staging buffers are free: start the next chunk's copies
+        // the staging buffer is free: start the next chunk's copies
         if (have_next)
-            gp_prefetch(pr, nx, depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg, do_bs ? rcw : nullptr,
-                        c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur], ldbar);
+            gp_prefetch(pr, nx, depth_src, gp_stage(stage0, L), do_bs, c + 2 < c_end ? pr.chunks + c + 2 : nullptr,
+                        &s_ch[cur], ldbar);
 
-        // drain D (lane = row: warp w reads lanes 32 (w % 4) .., columns 32 (w / 4) ..)
-        // before this chunk's MMAs start a fresh accumulation
-        const bool drain = use_tc && in_block >= kGpDrainEvery;
-        if (drain) {
+        // drain D before this chunk's MMAs start a fresh accumulation
+        if (use_tc && in_block >= kGpDrainEvery) {
             tc_fence_after();
             gp_drain(tmem, dacc, warp, lane);
             tc_fence_before();
@@ -560,8 +648,8 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                     uint32_t *hp = reinterpret_cast<uint32_t *>(op + off + (kTcRows / 8) * sbo);
                     float x = 0.f;
                     if (in) x = r < n6 ? __uint_as_float(*hp) * q : q * w;
-                    const uint32_t h = to_tf32(x);
-                    const uint32_t lo = to_tf32(x - __uint_as_float(h));
+                    const uint32_t h = gp_tf32(x);
+                    const uint32_t lo = gp_tf32(x - __uint_as_float(h));
                     if (r == kTcRows - 2) {          // hi rows 62, 63: hi and lo of C^-1/2 w
                         hp[0] = h;
                         hp[4] = lo;                  // row 63: 16 bytes on
@@ -609,10 +697,16 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                     }
                 }
                 __syncthreads();
+                if (h == 1) {   // the sums of the next group start from zero
+#pragma unroll
+                    for (int q = 0; q < 21; ++q) M[q] = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) V[q] = 0.f;
+                }
                 for (int q = tid; q < W * mn; q += kThreads) {
                     const int jl = q / mn, m = q - jl * mn;
                     float s = 0.f, cc = 0.f;
-                    for (int g = 0; g < NG; ++g) kahan_add(s, cc, Mp[(size_t)(jl * NG + g) * kGpMpHalf + m]);
+                    for (int g2 = 0; g2 < NG; ++g2) kahan_add(s, cc, Mp[(size_t)(jl * NG + g2) * kGpMpHalf + m]);
                     Mc[jl * 27 + m0 + m] = s - cc;
                 }
                 __syncthreads();
@@ -656,7 +750,8 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                 __syncthreads();
             }
             // each changed strip of the partial: per free pose f, its diagonal
-            // block (two strips), its v' strip, and its pair with the anchor
+            // block (two strips), its v' strip, and its pair with the anchor;
+            // the 18 (or 6) entries are loaded together, added, stored
             double *part = pr.partial + (size_t)itm.item * pr.L;
             const int fanc = anc - t0, nbs = 2 * n_block_pairs(nf);
             for (int it5 = tid; it5 < 5 * nf; it5 += kThreads) {
@@ -675,15 +770,22 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                 }
                 float add[18];
                 if (!strip_block_add(a2, b2, h2, vs, t0, anc, jlo, W, Mc, Aj, Bii, add)) continue;
-                if (vs) {
-                    double *o = part + 18 * nbs + 6 * a2;
+                const int n_e = vs ? 6 : 18;
+                double *o = vs ? part + 18 * nbs + 6 * a2
+                               : part + 18 * (2 * (a2 * nf - a2 * (a2 - 1) / 2 + (b2 - a2)) + h2);
+                double2 *o2 = reinterpret_cast<double2 *>(o);
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) o[q] += (double)add[q];
-                } else {
-                    const int st = 2 * (a2 * nf - a2 * (a2 - 1) / 2 + (b2 - a2)) + h2;
-                    double *o = part + 18 * st;
+                for (int q0 = 0; q0 < 9; q0 += 3) {      // three 16-byte loads in flight, then their stores
+                    if (2 * q0 >= n_e) break;
+                    double2 cur2[3];
 #pragma unroll
-                    for (int q = 0; q < 18; ++q) o[q] += (double)add[q];
+                    for (int q = 0; q < 3; ++q) cur2[q] = o2[q0 + q];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        cur2[q].x += (double)add[2 * (q0 + q)];
+                        cur2[q].y += (double)add[2 * (q0 + q) + 1];
+                        o2[q0 + q] = cur2[q];
+                    }
                 }
             }
             __syncthreads();   // Mp / Aj / Bp are read before the next chunk's slots overwrite them
@@ -708,13 +810,18 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
             if (tid == 0) atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
             have = false;
         }
+        __shared__ int s_have;
+        if (tid == 0) s_have = 1;
         __syncthreads();
+        if (!have) s_have = 0;
+        __syncthreads();
+        const bool have_all = s_have != 0;
         tc_fence_after();
-        if (have && in_block > 0) gp_drain(tmem, dacc, warp, lane);   // the last block
+        if (have_all && in_block > 0) gp_drain(tmem, dacc, warp, lane);   // the last block
         tc_fence_before();
         __syncthreads();
-        if (have) {
-            // S -= hi.hi^T + lo.hi^T + (lo.hi^T)^T;  v' -= the w columns (hi rows 62, 63)
+        if (have_all) {
+            // S -= A + A^T on the pose columns;  v' -= the w columns (62, 63)
             double *part = pr.partial + (size_t)itm.item * pr.L;
             const int nbs = 2 * n_block_pairs(nf);
             for (int q = tid; q < pr.L; q += kThreads) {
@@ -724,11 +831,10 @@ __global__ void __launch_bounds__(kThreads, 2) gn_pass_kernel(const Prob *__rest
                     int a, b;
                     decode_pair(st >> 1, nf, a, b);
                     const int m = 6 * a + 3 * (st & 1) + e / 6, n = 6 * b + e % 6;
-                    s = dacc[(kTcRows + m) * kGpDaccLd + n] + dacc[m * kGpDaccLd + n] + dacc[n * kGpDaccLd + m];
+                    s = dacc[m * kGpDaccLd + n] + dacc[n * kGpDaccLd + m];
                 } else {
                     const int m = q - 18 * nbs;
-                    s = dacc[(kTcRows + m) * kGpDaccLd + kTcRows - 2] + dacc[(kTcRows + m) * kGpDaccLd + kTcRows - 1] +
-                        dacc[m * kGpDaccLd + kTcRows - 2];
+                    s = dacc[m * kGpDaccLd + kTcRows - 2] + dacc[m * kGpDaccLd + kTcRows - 1];
                 }
                 part[q] -= (double)s;
             }
