@@ -203,21 +203,11 @@ def _stream_ptr(stream) -> int:
 class Solver:
     """A library handle (workspace + staging) on the current CUDA device."""
 
-    # Schur-complement accumulation (dpvo_ba_config.schur_tf32)
-    SCHUR_DEFAULT, SCHUR_TENSOR, SCHUR_FP32 = 0, 1, 2
-
     def __init__(self, damping: float = 1e-4, z_min: float = 0.1, mem_budget_bytes: int = 0,
-                 max_sessions: int = 0, schur_tf32: bool = False, schur_mode: Optional[int] = None):
-        """``schur_mode``: 0 the default (tensor cores with drained accumulation
-        up to 10 free poses, compensated FP32 on the CUDA cores beyond), 1
-        tensor cores wherever a kernel has them, 2 compensated FP32 on the CUDA
-        cores only.  ``schur_tf32=True`` is mode 1."""
+                 max_sessions: int = 0, schur_tf32: bool = False):
         self.lib = load()
-        if schur_mode is None:
-            schur_mode = self.SCHUR_TENSOR if schur_tf32 else self.SCHUR_DEFAULT
-        self.schur_mode = int(schur_mode)
-        self.schur_tf32 = self.schur_mode == self.SCHUR_TENSOR
-        cfg = Config(damping, z_min, mem_budget_bytes, max_sessions, self.schur_mode)
+        self.schur_tf32 = bool(schur_tf32)
+        cfg = Config(damping, z_min, mem_budget_bytes, max_sessions, 1 if schur_tf32 else 0)
         h = ctypes.c_void_p()
         _check(self.lib.dpvo_ba_create(ctypes.byref(cfg), ctypes.byref(h)), "dpvo_ba_create")
         self.h = h

@@ -54,7 +54,6 @@ struct Prob {
     double *partial;         // [n_parts][L] Schur partial sums (linearise CTAs, then assembly CTAs)
     double *sglob;           // [6nf (6nf + 1) / 2] FP64 reduced system, packed lower (more than kFusedMaxFree free poses)
     float *erow;             // [P][erow_len(nf)] scaled Schur row of each patch, last linearisation
-    float *cw;               // [P][2] C_k, w_k of the last linearisation (the one-pass kernel's back-substitution)
     // backward (adjoint) state; null / zero for a plain solve
     int store_factor;        // keep the factored reduced system of every iteration
     int no_writeback;        // leave the caller's poses and patches untouched

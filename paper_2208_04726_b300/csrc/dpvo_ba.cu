@@ -9,7 +9,6 @@
 #include "dpvo_ba.h"
 #include "ba_common.cuh"
 #include "kernels.cuh"
-#include "gn_pass.cuh"
 #include "solve_large.cuh"
 #include "assemble_tc.cuh"
 #include "assemble.cuh"
@@ -34,8 +33,7 @@ struct Layout {
     std::vector<Item> items;       // linearise work items, then assembly work items
     size_t bytes = 0, off_probs = 0, off_items = 0;
     int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0, n_max = 1;
-    bool gp = false;               // one-pass kernel (recomputed back-substitution, drained tensor-core Schur)
-    bool tc = false;               // Schur accumulation on the tensor cores (strip-free fused variant)
+    bool tc = false;               // Schur accumulation on the tensor cores
     bool ext = false;              // more than kFusedMaxFree free poses: assembly kernel, packed solve
     bool tc_asm = false;           // ext with the TF32 Schur mode: the assembly on the tensor cores
     int n_lin_items = 0, n_asm_items = 0;
@@ -109,9 +107,7 @@ static void launch_final(const Layout &L, int n, cudaStream_t stream, const Prob
 // One linearise launch, in the batch's variant.
 static void launch_linearize(const Layout &L, int grid, cudaStream_t stream, const Prob *probs, const Item *items,
                              int t, int adjoint_rhs) {
-    if (L.gp)
-        gn_pass_kernel<<<grid, kThreads, L.lin_smem, stream>>>(probs, items, t, L.W_cap, L.G_cap, L.n_max);
-    else if (L.tc)
+    if (L.tc)
         linearize_kernel<true, false><<<grid, kThreads, L.lin_smem, stream>>>(probs, items, t, L.W_cap, L.G_cap,
                                                                           L.nf_max, L.n_max, adjoint_rhs);
     else if (L.ext)
@@ -149,21 +145,14 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         L.iters_max = std::max(L.iters_max, dims[b].n_iters);
     }
     L.n_max = n_max;
-    // schur_tf32: 0 default, 1 tensor cores wherever available, 2 FP32 CUDA cores only
-    L.gp = !adjoint && cfg.schur_tf32 != 2 && use_tensor_cores(L.nf_max);
-    L.tc = !L.gp && cfg.schur_tf32 == 1 && use_tensor_cores(L.nf_max);
+    L.tc = cfg.schur_tf32 && use_tensor_cores(L.nf_max);
     L.W_cap = std::min(n_max, kMaxWindow);
     L.G_cap = 64;
-    if (L.gp) {
-        while (L.G_cap > 8 && gp_smem_layout(L.W_cap, L.G_cap, n_max).bytes > kLinSmemBudget) L.G_cap -= 8;
-        L.lin_smem = gp_smem_layout(L.W_cap, L.G_cap, n_max).bytes;
-    } else {
-        while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes > kLinSmemBudget)
-            L.G_cap -= 8;
-        L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
-    }
+    while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes > kLinSmemBudget)
+        L.G_cap -= 8;
+    L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
     L.ext = L.nf_max > kFusedMaxFree;
-    L.tc_asm = L.ext && cfg.schur_tf32 == 1;
+    L.tc_asm = L.ext && cfg.schur_tf32;
     L.solve_smem = L.ext ? solve_large_smem_bytes(L.nf_max) : solve_smem_bytes(L.nf_max);
     L.asm_smem = !L.ext ? 0
                  : L.tc_asm ? atc_smem_bytes(erow_len(L.nf_max))
@@ -185,7 +174,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.chunk_cap = L.G_cap;
         p.win_cap = L.W_cap;
         p.max_chunks = (d.n_patches + L.G_cap - 1) / L.G_cap + d.n_frames;
-        p.ks = (L.gp || L.tc || L.ext) ? 1 : k_split(p.nf);
+        p.ks = (L.tc || L.ext) ? 1 : k_split(p.nf);
         p.L = partial_len(p.nf);
         // work items: as many as fill one wave of the SMs (two linearise CTAs
         // per SM; one assembly CTA per SM), at least one per problem
@@ -216,8 +205,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
             const size_t n6 = 6 * (size_t)p.nf;
             p.sglob = (double *)(uintptr_t)take(n6 * (n6 + 1) / 2 * 8 + 8);
         }
-        p.erow = (float *)(uintptr_t)take(L.gp ? 16 : erow_bytes(L.tc, p, L.G_cap));
-        p.cw = (float *)(uintptr_t)take(L.gp ? (size_t)d.n_patches * 8 + 16 : 16);
+        p.erow = (float *)(uintptr_t)take(erow_bytes(L.tc, p, L.G_cap));
         if (adjoint) {
             const size_t n6 = 6 * (size_t)p.nf;
             p.store_factor = 1;
@@ -326,8 +314,6 @@ static int set_kernel_attrs(int device) {
         cudaFuncSetAttribute(linearize_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024) != cudaSuccess)
         return DPVO_BA_ECUDA;
-    if (cudaFuncSetAttribute(gn_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
-        return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
         return DPVO_BA_ECUDA;
@@ -370,7 +356,6 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         p.dxi = rebase(p.dxi, h->ws);
         p.partial = rebase(p.partial, h->ws);
         p.erow = rebase(p.erow, h->ws);
-        p.cw = rebase(p.cw, h->ws);
         if (p.sglob) p.sglob = rebase(p.sglob, h->ws);
     }
     h->last = L.probs;
@@ -405,7 +390,6 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     } else {
         for (int t = 0; t <= L.iters_max; ++t) {
             if (t < L.iters_max) rc = timed(1, [&] { launch_linearize(L, n_items, stream, d_probs, d_items, t, 0); });
-            else if (L.gp) rc = timed(4, [&] { launch_linearize(L, n_items, stream, d_probs, d_items, t, 0); });
             else rc = timed(4, [&] { launch_final(L, n, stream, d_probs, t); });
             if (rc) return rc;
             if (t < L.iters_max) {
@@ -453,7 +437,6 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
         p.dxi = rebase(p.dxi, h->ws);
         p.partial = rebase(p.partial, h->ws);
         p.erow = rebase(p.erow, h->ws);
-        p.cw = rebase(p.cw, h->ws);
         if (p.sglob) p.sglob = rebase(p.sglob, h->ws);
         p.ufac = rebase(p.ufac, h->ws);
         p.eps = rebase(p.eps, h->ws);
@@ -1136,7 +1119,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     const dpvo_ba_dims &d = *dims;
     const int nf = d.n_frames - d.t0;
     const int W_cap = std::min(d.n_frames, kMaxWindow);
-    const bool tc = cfg && cfg->schur_tf32 == 1 && use_tensor_cores(nf);
+    const bool tc = cfg && cfg->schur_tf32 && use_tensor_cores(nf);
     int G_cap = 64;
     while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes > kLinSmemBudget) G_cap -= 8;
     const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes;

@@ -31,13 +31,13 @@ MID16 = dataclasses.replace(S.WINDOW_N22, n_frames=24, patches_per_frame=48, rad
 MID25 = dataclasses.replace(S.STRESS_N64, n_frames=33, patches_per_frame=32, radius=16, t0=8, n_iters=2)
 
 
-@pytest.fixture(scope="module", params=[0, 1], ids=["fp32-schur", "tf32-schur"])
+@pytest.fixture(scope="module", params=[False, True], ids=["fp32-schur", "tf32-schur"])
 def solver(request):
-    """Beyond 15 free poses the default (0) assembles on the CUDA cores; mode 1
-    assembles on the tensor cores."""
+    """Beyond 15 free poses the default assembles on the CUDA cores; the opt-in
+    TF32 mode assembles on the tensor cores."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
-    s = ba.Solver(schur_mode=request.param)
+    s = ba.Solver(schur_tf32=request.param)
     yield s
     s.close()
 
