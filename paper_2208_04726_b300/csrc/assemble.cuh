@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kAsmMaxThreads, 1) schur_assembly_kernel(const
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (t >= pr.iters || *pr.status != 0) return;
+    if (t >= pr.iters || block_status(pr.status) != 0) return;
     __shared__ __align__(8) uint64_t s_full[kAsmStages], s_empty[kAsmStages];
     __shared__ int s_bad, s_issued;
     const int n_comp = (int)(blockDim.x >> 5) - 1;         // compute warps; warp n_comp produces

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kAtcThreads, 1) schur_assembly_tc_kernel(const
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (t >= pr.iters || *pr.status != 0) return;
+    if (t >= pr.iters || block_status(pr.status) != 0) return;
 
     const int nf = pr.nf, RS = erow_len(nf), np = n_block_pairs(nf), n6 = 6 * nf;
     const int k_lo = (int)(((long long)itm.item * pr.P) / pr.n_asm);

@@ -105,6 +105,16 @@ __host__ __device__ inline int k_split(int nf) {
     return k < 1 ? 1 : (k > kMaxKSplit ? kMaxKSplit : k);
 }
 
+// The problem's status bits as one thread of the block read them: every
+// thread of a kernel with block barriers must take the same early exit, and
+// another block may set a bit while this one starts.
+__device__ inline int block_status(const int32_t *status) {
+    __shared__ int s_status_once;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_status_once = *status;
+    __syncthreads();
+    return s_status_once;
+}
+
 // Decode the upper-triangle pair index of (a, b), a <= b.
 __host__ __device__ inline void decode_pair(int idx, int nf, int &a, int &b) {
     a = 0;

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) bw_init_kernel(const Prob *__restric
         pr.dL_dtarget[e] = 0.f;
         pr.dL_dweight[e] = 0.f;
     }
-    if (*pr.status != 0) return;
+    if (block_status(pr.status) != 0) return;
     const float *pose = pr.pose_it + (size_t)pr.iters * pr.N * 7;
     for (int a = tid; a < pr.N; a += kThreads) {
         double *ep = pr.eps + 6 * a;
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) bw_init_kernel(const Prob *__restric
 __global__ void __launch_bounds__(kSolveThreads) bw_retract_kernel(const Prob *__restrict__ probs, int t) {
     const Prob &pr = probs[blockIdx.x];
     const int tid = threadIdx.x;
-    if (t >= pr.iters || *pr.status != 0) return;
+    if (t >= pr.iters || block_status(pr.status) != 0) return;
     const int N = pr.N, t0 = pr.t0;
     if (t < pr.iters - 1) {
         for (int q = tid; q < N * 6; q += kSolveThreads) {
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kSolveThreads) bw_retract_kernel(const Prob *_
 __global__ void __launch_bounds__(kSolveThreads) bw_solve_kernel(const Prob *__restrict__ probs, int t) {
     const Prob &pr = probs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31;
-    if (t >= pr.iters || *pr.status != 0) return;
+    if (t >= pr.iters || block_status(pr.status) != 0) return;
     const int nf = pr.nf, n = 6 * nf;
     if (n == 0) return;
     __shared__ double b[6 * kMaxFree];
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 2) bw_edge_kernel(const Prob *__rest
     const Item itm = items[blockIdx.x];
     const Prob &pr = probs[itm.prob];
     const int tid = threadIdx.x;
-    if (t >= pr.iters || *pr.status != 0) return;
+    if (t >= pr.iters || block_status(pr.status) != 0) return;
     const BwSmem L = bw_smem_layout(W_cap, G_cap, n_max);
     float *spose = reinterpret_cast<float *>(smem + L.off_pose);
     int *rjj = reinterpret_cast<int *>(smem + L.off_rjj);

@@ -189,7 +189,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
             const int per = std::max(1, num_sms / (n * asm_slices_max));
             p.n_asm = std::max(1, std::min(per, est_chunks));
         }
-        p.n_parts = L.ext ? p.n_items + p.n_asm : p.n_items * p.ks;
+        p.n_parts = L.ext ? p.n_items + p.n_asm : p.n_items;   // one partial per linearise CTA
         // workspace offsets (rebased to device pointers later)
         auto take = [&](size_t bytes) { size_t o = off; off = al256(off + bytes); return o; };
         p.seg = (int32_t *)(uintptr_t)take((size_t)(d.n_patches + 1) * 4);
@@ -1139,7 +1139,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.L = partial_len(nf);
     const int est_chunks = std::max(1, (d.n_patches + G_cap - 1) / G_cap);
     p.n_items = std::max(1, std::min(2 * sms, est_chunks));
-    p.n_parts = p.n_items * p.ks;
+    p.n_parts = p.n_items;
     size_t off = 0;
     auto take = [&](size_t bytes) { char *q = base + off; off = al256(off + bytes); return q; };
     p.seg = (int32_t *)take((size_t)(d.n_patches + 1) * 4);
@@ -1150,7 +1150,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.pose_it = (float *)take((size_t)(d.n_iters + 1) * d.n_frames * 7 * 4);
     p.depth_it = (float *)take((size_t)(d.n_iters + 1) * d.n_patches * 4);
     p.dxi = (double *)take((size_t)d.n_iters * nf * 6 * 8 + 8);
-    p.partial = (double *)take((size_t)p.n_items * p.ks * p.L * 8 + 8);
+    p.partial = (double *)take((size_t)p.n_items * p.L * 8 + 8);
     p.erow = (float *)take(erow_bytes(tc, p, G_cap));
     Prob *d_prob = (Prob *)take(sizeof(Prob));
     Item *d_items = (Item *)take(sizeof(Item) * p.n_items);

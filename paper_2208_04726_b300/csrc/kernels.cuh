@@ -733,8 +733,11 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     // right-hand-side strips, for the adjoint solve of iteration t
     const bool do_bs = t > 0 && !adjoint_rhs;
     const bool final_pass = t == pr.iters && !adjoint_rhs;
-    {
-        const int st = *pr.status;
+    {   // read once: every thread takes the same exit (the kernel has block barriers)
+        __shared__ int s_st0;
+        if (tid == 0) s_st0 = *pr.status;
+        __syncthreads();
+        const int st = s_st0;
         if (final_pass && itm.item == 0 && tid == 0 && pr.status_user) *pr.status_user = st;
         if (st != 0) return;
     }
@@ -1498,18 +1501,43 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         }
     }
 
-    // write this CTA's partial of (S, v')
-    if (owns) {
-        double *out = pr.partial + ((size_t)itm.item * KS + my_ks) * pr.L;   // ks parts per item
-        if (!is_vstrip) {
-            double *o = out + 18 * my_strip;
+    // write this CTA's partial of (S, v'): with a patch-parity split (KS > 1,
+    // at most 10 free poses) the KS parts of each strip are first summed in
+    // FP64, in a fixed order, in the frame-sum buffer (dead here), so that the
+    // reduced solve reads one partial per CTA
+    double *out = pr.partial + (size_t)itm.item * pr.L;
+    if (KS == 1) {
+        if (owns) {
+            if (!is_vstrip) {
+                double *o = out + 18 * my_strip;
 #pragma unroll
-            for (int q = 0; q < 18; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
-        } else {
-            double *o = out + 18 * nbs + 6 * sa;
+                for (int q = 0; q < 18; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
+            } else {
+                double *o = out + 18 * nbs + 6 * sa;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
+                for (int q = 0; q < 6; ++q) o[q] = (double)acc_s[q] - (double)acc_c[q];
+            }
         }
+    } else {
+        double *buf = reinterpret_cast<double *>(smem + L.off_mp);
+        __syncthreads();
+        for (int q = tid; q < pr.L; q += kThreads) buf[q] = 0.0;
+        __syncthreads();
+        for (int r = 0; r < KS; ++r) {
+            if (owns && my_ks == r) {
+                if (!is_vstrip) {
+                    double *o = buf + 18 * my_strip;
+#pragma unroll
+                    for (int q = 0; q < 18; ++q) o[q] += (double)acc_s[q] - (double)acc_c[q];
+                } else {
+                    double *o = buf + 18 * nbs + 6 * sa;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) o[q] += (double)acc_s[q] - (double)acc_c[q];
+                }
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < pr.L; q += kThreads) out[q] = buf[q];
     }
 }
 
@@ -1533,7 +1561,7 @@ __global__ void __launch_bounds__(kThreads, TC ? 5 : 6) final_kernel(const Prob 
     const Prob &pr = probs[blockIdx.x];
     const int tid = threadIdx.x;
     if (t != pr.iters) return;
-    const int st = *pr.status;
+    const int st = block_status(pr.status);
     if (blockIdx.y == 0 && tid == 0 && pr.status_user) *pr.status_user = st;
     if (st != 0) return;
     const int N = pr.N;
