@@ -45,10 +45,7 @@ struct Layout {
 // the inverted diagonal blocks of the factor.
 static size_t solve_smem_bytes(int nf) {
     const size_t n = 6 * (size_t)nf, panels = (n + kPanel - 1) / kPanel;
-    // S, v, x (FP64); the FP32 factor, its right-hand side and inverted diagonal
-    // blocks; S as hi and lo floats and x as hi and lo floats (refinement residuals)
-    return n * (n + 1) * 8 + 2 * n * 8 + n * (n + 1) * 4 + n * 4 + panels * kPanel * kLinvLd * 4 +
-           2 * n * (n + 1) * 4 + 2 * n * 4 + 64;
+    return n * (n + 1) * 8 + 2 * n * 8 + n * (n + 1) * 4 + n * 4 + panels * kPanel * kLinvLd * 4 + 64;
 }
 
 // Stored Schur rows: one row per patch, or in the tensor-core variant one

@@ -1811,18 +1811,9 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         float *Sf = reinterpret_cast<float *>(x + n);
         float *bf = Sf + (size_t)n * ld;
         float *Linv = bf + n;                               // inverted diagonal blocks of the factor
-        // S as a pair of floats (S = Sh + Sl to about 2^-48) for the refinement
-        // residuals, which run on the FP32 pipes (B300's FP64 pipe is ~1/64 of them)
-        float *Sh = Linv + ((n + kPanel - 1) / kPanel) * kPanel * kLinvLd;
-        float *Sl = Sh + (size_t)n * ld;
-        float *xs = Sl + (size_t)n * ld;                    // x as hi (0..n-1) and lo (n..2n-1) floats
         for (int q = tid; q < n * n; q += kSolveThreads) {
             const int i = q / n, k = q - i * n;
-            const double sv = S[i * ld + k];
-            const float hi = (float)sv;
-            Sh[i * ld + k] = hi;
-            Sl[i * ld + k] = (float)(sv - (double)hi);
-            if (k <= i) Sf[i * ld + k] = hi;
+            if (k <= i) Sf[i * ld + k] = (float)S[i * ld + k];
         }
         for (int q = tid; q < n; q += kSolveThreads) {
             x[q] = 0.0;
@@ -1862,28 +1853,13 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
         __syncthreads();
         double prev = 0.0;
         for (int it = 0; it <= kMaxRefine && !s_use64; ++it) {
-            if (it > 0) {   // residual v - S x, four threads per row, S x in double-float arithmetic
-                for (int q = tid; q < n; q += kSolveThreads) {
-                    const float h = (float)x[q];
-                    xs[q] = h;
-                    xs[n + q] = (float)(x[q] - (double)h);
-                }
-                __syncthreads();
+            if (it > 0) {   // residual v - S x in FP64, four threads per row
                 const int qk = tid & 3;
                 for (int base = 0; base < n; base += kSolveThreads / 4) {
                     const int i = base + (tid >> 2);
-                    float hi = 0.f, lo = 0.f;
+                    double acc = 0.0;
                     if (i < n)
-                        for (int k = qk; k < n; k += 4) {
-                            const float a = Sh[i * ld + k], al = Sl[i * ld + k];
-                            const float xh = xs[k], xl = xs[n + k];
-                            const float pp = a * xh, pe = fmaf(a, xh, -pp);       // a xh = pp + pe exactly
-                            const float sm = hi + pp, bb = sm - hi;               // hi + pp = sm + se exactly
-                            const float se = (hi - (sm - bb)) + (pp - bb);
-                            hi = sm;
-                            lo += se + pe + fmaf(a, xl, al * xh);
-                        }
-                    double acc = (double)hi + (double)lo;
+                        for (int k = qk; k < n; k += 4) acc = fma(S[i * ld + k], x[k], acc);
                     acc += shfl_double(acc, lane ^ 1);
                     acc += shfl_double(acc, lane ^ 2);
                     if (i < n && qk == 0) bf[i] = (float)(v[i] - acc);
