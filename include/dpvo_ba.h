@@ -207,9 +207,13 @@ int dpvo_ba_session_close(dpvo_ba_handle *h, int64_t session_id);
  * may be NULL); waits up to 10 s for its request to finish.  Synchronous. */
 int dpvo_ba_session_read(dpvo_ba_handle *h, int64_t session_id, float *poses_out, float *patches_out);
 
-/* Queue a request on a session: target and weight are HOST arrays [E][2],
- * copied before the call returns.  EBUSY if the session's previous request has
- * not finished.  Errors: EINVAL, ENOTFOUND, EBUSY. */
+/* Queue a request on a session: target and weight are HOST arrays [E][2].
+ * Pageable buffers are copied before the call returns; page-locked ones
+ * (cudaMallocHost, cudaHostAlloc, cudaHostRegister) are read in place by the
+ * device when the batch runs, so they must stay unchanged until the request
+ * completes.  EBUSY if the session's previous request has not finished.
+ * Errors: EINVAL (also for a window session: see dpvo_ba_submit_frame),
+ * ENOTFOUND, EBUSY. */
 int dpvo_ba_submit(dpvo_ba_handle *h, int64_t session_id, const float *target, const float *weight,
                    uint64_t *ticket);
 
@@ -385,6 +389,49 @@ int dpvo_ba_window_append_batch(dpvo_ba_window *const *ws, const float *const *n
 /* The window's current problem: sizes (with t0, n_iters, intrinsics) and its
  * device arrays (status included).  Errors: EINVAL (NULL, empty window). */
 int dpvo_ba_window_problem(const dpvo_ba_window *w, dpvo_ba_dims *dims, dpvo_ba_problem *prob);
+
+/* ---- sliding-window serving sessions (Sec. 3.3 "Expansion" and
+ * "Optimization", served as in the calls above) ------------------------------
+ * A window session owns a window (semantics of dpvo_ba_window above, created
+ * empty) instead of a fixed graph.  Each request appends a frame and then
+ * solves the window: the VO system's per-frame step.  Requests of window and
+ * fixed-graph sessions are batched together.  dpvo_ba_poll, dpvo_ba_wait,
+ * dpvo_ba_session_read and dpvo_ba_session_close take window sessions too. */
+
+/* Open a window session.  Admitted against the memory budget by the window's
+ * device bytes; its largest problem (max_frames frames, max_frames x
+ * max_new_patches patches, the graph's edges, n_iters) must fit the max_dims
+ * given to dpvo_ba_serve_start.  Errors: EINVAL (parameters out of range or
+ * beyond max_dims), EBUSY (over the budget: not admitted), ENOMEM, ECUDA. */
+int dpvo_ba_session_open_window(dpvo_ba_handle *h, const dpvo_ba_window_params *params, int64_t *session_id);
+
+/* The number of edges E the session's window holds after appending a frame of
+ * n_new patches (from the host's frame counts; nothing runs on the device):
+ * the length of the arrays dpvo_ba_submit_frame takes.  Errors: EINVAL (not a
+ * window session, n_new out of range), ENOTFOUND, EBUSY (a request is pending:
+ * the count changes when it runs). */
+int dpvo_ba_session_frame_edges(dpvo_ba_handle *h, int64_t session_id, int n_new, int32_t *n_edges);
+
+/* The session's current sizes (a window's frames, patches, edges and t0; the
+ * fixed graph's dims).  Waits up to 10 s for its pending request.
+ * Errors: EINVAL, ENOTFOUND, ETIMEOUT. */
+int dpvo_ba_session_dims(dpvo_ba_handle *h, int64_t session_id, dpvo_ba_dims *dims);
+
+/* Queue a frame request on a window session (HOST arrays):
+ *   new_xy [n_new][2]  the new frame's patch centres (pixels), 0 <= n_new <= max_new_patches;
+ *   delta  [E][2]      revision of each edge's target, E = dpvo_ba_session_frame_edges(n_new):
+ *                      the target becomes the edge's reprojection at the window's
+ *                      current state plus delta (the flow revision of Eq. 5-6);
+ *   weight [E][2]      the edges' confidence weights.
+ * delta and weight are both given or both NULL (then targets stay the
+ * reprojections and weights 1).  When it runs: the frame is appended (as
+ * dpvo_ba_window_append), the factors set, and the window solved with its
+ * n_iters iterations.  Pageable buffers are copied before the call returns;
+ * page-locked ones are read in place when the batch runs (keep them unchanged
+ * until the request completes).  Errors: EINVAL (not a window session, bad
+ * sizes, one of delta / weight NULL), ENOTFOUND, EBUSY. */
+int dpvo_ba_submit_frame(dpvo_ba_handle *h, int64_t session_id, const float *new_xy, int n_new, const float *delta,
+                         const float *weight, uint64_t *ticket);
 
 /* ---- correlation features (Sec. 3.2 "Correlation", Eq. 4; Appendix
  * "Correlation Operation") -----------------------------------------------------

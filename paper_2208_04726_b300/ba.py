@@ -68,7 +68,9 @@ EXPORTS = ["dpvo_ba_create", "dpvo_ba_destroy", "dpvo_ba_reserve", "dpvo_ba_solv
            "dpvo_ba_serve_stop", "dpvo_ba_session_open", "dpvo_ba_session_close", "dpvo_ba_session_read",
            "dpvo_ba_submit", "dpvo_ba_poll", "dpvo_ba_wait", "dpvo_ba_strerror", "dpvo_ba_pose_loss",
            "dpvo_ba_window_create", "dpvo_ba_window_destroy", "dpvo_ba_window_append", "dpvo_ba_window_problem",
-           "dpvo_ba_window_append_batch", "dpvo_ba_correlation", "dpvo_ba_selftest_bounded_wait"]
+           "dpvo_ba_window_append_batch", "dpvo_ba_correlation", "dpvo_ba_selftest_bounded_wait",
+           "dpvo_ba_session_open_window", "dpvo_ba_session_frame_edges", "dpvo_ba_session_dims",
+           "dpvo_ba_submit_frame"]
 
 _lib = None
 
@@ -117,6 +119,10 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     lib.dpvo_ba_correlation.argtypes = [ctypes.POINTER(CorrDims), vp, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.dpvo_ba_window_append_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i32), i32, vp]
     lib.dpvo_ba_selftest_bounded_wait.argtypes = [vp, i32, i32, vp]
+    lib.dpvo_ba_session_open_window.argtypes = [vp, ctypes.POINTER(WindowParams), ctypes.POINTER(i64)]
+    lib.dpvo_ba_session_frame_edges.argtypes = [vp, i64, i32, ctypes.POINTER(ctypes.c_int32)]
+    lib.dpvo_ba_session_dims.argtypes = [vp, i64, ctypes.POINTER(Dims)]
+    lib.dpvo_ba_submit_frame.argtypes = [vp, i64, vp, i32, vp, vp, u64p]
     lib.dpvo_ba_strerror.argtypes = [i32]
     lib.dpvo_ba_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -340,11 +346,61 @@ class Solver:
                "dpvo_ba_session_read")
         return poses, patches
 
-    def submit(self, sid: int, target: np.ndarray, weight: np.ndarray) -> int:
-        t = np.ascontiguousarray(target, np.float32)
-        w = np.ascontiguousarray(weight, np.float32)
+    @staticmethod
+    def _host_ptr(a):
+        """(pointer, keep-alive) of a host float32 array: a page-locked torch tensor
+        is passed as is (the library reads it in place until the request
+        completes), anything else as a contiguous float32 numpy array."""
+        if isinstance(a, torch.Tensor):
+            a = a.detach()
+            if a.is_pinned() and a.dtype == torch.float32 and a.is_contiguous():
+                return a.data_ptr(), a
+            a = a.cpu().numpy()
+        a = np.ascontiguousarray(a, np.float32)
+        return a.ctypes.data, a
+
+    def submit(self, sid: int, target, weight) -> int:
+        """New factors for a fixed-graph session; ``target``, ``weight`` [E, 2]."""
+        pt, kt = self._host_ptr(target)
+        pw, kw = self._host_ptr(weight)
         tk = ctypes.c_uint64()
-        _check(self.lib.dpvo_ba_submit(self.h, sid, t.ctypes.data, w.ctypes.data, ctypes.byref(tk)), "dpvo_ba_submit")
+        _check(self.lib.dpvo_ba_submit(self.h, sid, pt, pw, ctypes.byref(tk)), "dpvo_ba_submit")
+        self._keep_alive(tk.value, (kt, kw))
+        return tk.value
+
+    def _keep_alive(self, ticket, objs):
+        if not hasattr(self, "_inflight"):
+            self._inflight = {}
+        self._inflight[ticket] = objs
+
+    def session_open_window(self, params: "WindowParams") -> int:
+        """Open a sliding-window session (empty window)."""
+        sid = ctypes.c_int64()
+        _check(self.lib.dpvo_ba_session_open_window(self.h, ctypes.byref(params), ctypes.byref(sid)),
+               "dpvo_ba_session_open_window")
+        return sid.value
+
+    def session_frame_edges(self, sid: int, n_new: int) -> int:
+        e = ctypes.c_int32()
+        _check(self.lib.dpvo_ba_session_frame_edges(self.h, sid, n_new, ctypes.byref(e)), "dpvo_ba_session_frame_edges")
+        return e.value
+
+    def session_dims(self, sid: int) -> "Dims":
+        d = Dims()
+        _check(self.lib.dpvo_ba_session_dims(self.h, sid, ctypes.byref(d)), "dpvo_ba_session_dims")
+        return d
+
+    def submit_frame(self, sid: int, new_xy, delta=None, weight=None) -> int:
+        """Append a frame (patch centres ``new_xy`` [n, 2]) to a window session and
+        solve it; ``delta``/``weight`` [E, 2] revise the regenerated targets and set
+        the weights (E from ``session_frame_edges``), or both None."""
+        n_new = int(new_xy.shape[0])
+        px, kx = self._host_ptr(new_xy)
+        pd, kd = self._host_ptr(delta) if delta is not None else (None, None)
+        pw, kw = self._host_ptr(weight) if weight is not None else (None, None)
+        tk = ctypes.c_uint64()
+        _check(self.lib.dpvo_ba_submit_frame(self.h, sid, px, n_new, pd, pw, ctypes.byref(tk)), "dpvo_ba_submit_frame")
+        self._keep_alive(tk.value, (kx, kd, kw))
         return tk.value
 
     def poll(self, ticket: int):
@@ -354,12 +410,14 @@ class Solver:
         if rc == EBUSY:
             return False, None, None
         _check(rc, "dpvo_ba_poll")
+        getattr(self, "_inflight", {}).pop(ticket, None)
         return True, st.value, lat.value
 
     def wait(self, ticket: int, timeout_ms: int = 10000):
         """(status, latency_ms); raises BAError(ETIMEOUT) when the bound runs out."""
         st, lat = ctypes.c_int32(), ctypes.c_double()
         _check(self.lib.dpvo_ba_wait(self.h, ticket, timeout_ms, ctypes.byref(st), ctypes.byref(lat)), "dpvo_ba_wait")
+        getattr(self, "_inflight", {}).pop(ticket, None)
         return st.value, lat.value
 
 

@@ -14,6 +14,7 @@
 #include "assemble.cuh"
 #include "backward.cuh"
 #include "serve.cuh"
+#include "window_host.h"
 
 using namespace dpvo;
 
@@ -730,6 +731,31 @@ static size_t session_bytes(const dpvo_ba_dims &d) {
     return al256(N * 28) + al256(P * 12) + al256(P * 4) + 2 * al256(E * 4) + 2 * al256(E * 8) + 256;
 }
 
+// Factors of every request of a batch, read in place from page-locked host
+// memory (jobs[b] for blockIdx.x = b, blocks strided over its edges).
+__global__ void serve_gather_kernel(const dpvo_serve::GatherJob *__restrict__ jobs) {
+    const dpvo_serve::GatherJob J = jobs[blockIdx.x];
+    if (J.mode == 2) return;
+    for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < J.n_edges; e += gridDim.y * blockDim.x) {
+        const float2 t = J.src_t[e], w = J.src_w[e];
+        if (J.mode == 0) {
+            J.dst_t[e] = t;
+        } else {
+            float2 d = J.dst_t[e];
+            d.x += t.x;
+            d.y += t.y;
+            J.dst_t[e] = d;
+        }
+        J.dst_w[e] = w;
+    }
+}
+
+// Every request's status to its page-locked slot (one thread per request).
+__global__ void serve_status_kernel(const dpvo_serve::GatherJob *__restrict__ jobs, int n) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n) *jobs[b].status_host = *jobs[b].status_dev;
+}
+
 static void CUDART_CB serve_batch_done(void *arg) {
     Slot *slot = static_cast<Slot *>(arg);
     Server *srv = slot->srv;
@@ -752,6 +778,57 @@ static void CUDART_CB serve_batch_done(void *arg) {
     srv->cv.notify_all();
 }
 
+// Launch one batch on a slot: the windows' appends, the factors, the solve, the
+// statuses.  Called without the server lock; the batch's sessions are busy, so
+// nothing else touches them.
+static int serve_launch(Slot *slot, const std::vector<Session *> &ss, const std::vector<Ticket> &tks) {
+    const int n = (int)ss.size();
+    cudaStream_t st = slot->stream;
+    std::vector<dpvo_ba_window *> wins;
+    std::vector<const float *> xys;
+    std::vector<int> nn;
+    for (int b = 0; b < n; ++b)
+        if (tks[b].kind == 1) {
+            wins.push_back(ss[b]->win);
+            xys.push_back(tks[b].src_xy);
+            nn.push_back(tks[b].n_new);
+        }
+    if (!wins.empty()) {
+        const int rc = dpvo_ba_window_append_batch(wins.data(), xys.data(), nn.data(), (int)wins.size(), st);
+        if (rc) return rc;
+    }
+    std::vector<dpvo_ba_dims> dims(n);
+    std::vector<dpvo_ba_problem> probs(n);
+    int e_max = 0;
+    for (int b = 0; b < n; ++b) {
+        Session *s = ss[b];
+        if (s->win) {
+            if (dpvo_ba_window_problem(s->win, &dims[b], &probs[b])) return DPVO_BA_ECUDA;
+        } else {
+            dims[b] = s->dims;
+            probs[b] = s->dev;
+        }
+        dpvo_serve::GatherJob &J = slot->jobs[b];
+        J.src_t = reinterpret_cast<const float2 *>(tks[b].src_t);
+        J.src_w = reinterpret_cast<const float2 *>(tks[b].src_w);
+        J.dst_t = reinterpret_cast<float2 *>(const_cast<float *>(probs[b].target));
+        J.dst_w = reinterpret_cast<float2 *>(const_cast<float *>(probs[b].weight));
+        J.n_edges = dims[b].n_edges;
+        J.mode = tks[b].kind == 0 ? 0 : (tks[b].src_t ? 1 : 2);
+        J.status_dev = probs[b].status;
+        J.status_host = s->pinned_status;
+        e_max = std::max(e_max, J.n_edges);
+    }
+    const int ys = std::max(1, std::min(64, (e_max + 255) / 256));
+    serve_gather_kernel<<<dim3(n, ys), 256, 0, st>>>(slot->jobs);
+    int rc = run_solve(slot->h, dims.data(), probs.data(), n, st, nullptr, nullptr);
+    if (rc) return rc;
+    serve_status_kernel<<<(n + 127) / 128, 128, 0, st>>>(slot->jobs, n);
+    if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;
+    if (cudaLaunchHostFunc(st, serve_batch_done, slot) != cudaSuccess) return DPVO_BA_ECUDA;
+    return DPVO_BA_OK;
+}
+
 static void serve_loop(Server *srv) {
     cudaSetDevice(srv->device);
     std::unique_lock<std::mutex> lk(srv->mu);
@@ -768,30 +845,17 @@ static void serve_loop(Server *srv) {
             batch.push_back(srv->pending.front());
             srv->pending.pop_front();
         }
-        std::vector<dpvo_ba_dims> dims;
-        std::vector<dpvo_ba_problem> probs;
         std::vector<Session *> ss;
+        std::vector<Ticket> tks;
         for (uint64_t tk : batch) {
-            Session *s = srv->sessions[srv->tickets[tk].session];
-            dims.push_back(s->dims);
-            probs.push_back(s->dev);
-            ss.push_back(s);
+            const Ticket &t = srv->tickets[tk];
+            ss.push_back(srv->sessions[t.session]);
+            tks.push_back(t);
         }
         slot->busy = true;
         slot->batch = batch;
         lk.unlock();
-        int rc = DPVO_BA_OK;
-        for (Session *s : ss) {
-            const size_t E = s->dims.n_edges;
-            if (E && (cudaMemcpyAsync((void *)s->dev.target, s->pinned_tw, E * 8, cudaMemcpyHostToDevice, slot->stream) ||
-                      cudaMemcpyAsync((void *)s->dev.weight, s->pinned_tw + 2 * E, E * 8, cudaMemcpyHostToDevice,
-                                      slot->stream)))
-                rc = DPVO_BA_ECUDA;
-        }
-        if (!rc) rc = run_solve(slot->h, dims.data(), probs.data(), (int)ss.size(), slot->stream, nullptr, nullptr);
-        for (Session *s : ss)
-            if (cudaMemcpyAsync(s->pinned_status, s->dev.status, 4, cudaMemcpyDeviceToHost, slot->stream)) rc = DPVO_BA_ECUDA;
-        if (cudaLaunchHostFunc(slot->stream, serve_batch_done, slot) != cudaSuccess) rc = DPVO_BA_ECUDA;
+        const int rc = serve_launch(slot, ss, tks);
         lk.lock();
         if (rc) {
             // could not launch: fail the batch's tickets on the host, free the slot
@@ -821,6 +885,7 @@ extern "C" int dpvo_ba_serve_start(dpvo_ba_handle *h, const dpvo_ba_dims *max_di
     srv->device = h->device;
     srv->max_batch = max_batch;
     srv->budget = h->cfg.mem_budget_bytes;
+    srv->max_dims = *max_dims;
     h->srv = srv;
     for (int i = 0; i < max_in_flight; ++i) {
         Slot *slot = new Slot();
@@ -828,7 +893,9 @@ extern "C" int dpvo_ba_serve_start(dpvo_ba_handle *h, const dpvo_ba_dims *max_di
         srv->slots.push_back(slot);
         if (dpvo_ba_create(&h->cfg, &slot->h) != DPVO_BA_OK ||
             cudaStreamCreateWithFlags(&slot->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMallocHost((void **)&slot->jobs, sizeof(dpvo_serve::GatherJob) * (size_t)max_batch) != cudaSuccess ||
             dpvo_ba_reserve(slot->h, max_dims, max_batch) != DPVO_BA_OK) {
+            cudaGetLastError();
             serve_stop_impl(h);
             return DPVO_BA_ENOMEM;
         }
@@ -853,11 +920,13 @@ static int serve_stop_impl(dpvo_ba_handle *h) {
             cudaStreamDestroy(slot->stream);
         }
         if (slot->h) dpvo_ba_destroy(slot->h);
+        if (slot->jobs) cudaFreeHost(slot->jobs);
         delete slot;
     }
     for (auto &kv : srv->sessions) {
         Session *s = kv.second;
         if (s->mem) cudaFree(s->mem);
+        if (s->win) dpvo_ba_window_destroy(s->win);
         if (s->pinned_tw) cudaFreeHost(s->pinned_tw);
         delete s;
     }
@@ -894,6 +963,7 @@ extern "C" int dpvo_ba_session_open(dpvo_ba_handle *h, const dpvo_ba_dims *dims,
     if (!rc && cudaMallocHost((void **)&s->pinned_tw, E * 16 + 16) != cudaSuccess) rc = DPVO_BA_ENOMEM;
     if (!rc) {
         s->pinned_status = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(s->pinned_tw) + E * 16);
+        s->max_edges = E;
         size_t o = 0;
         auto take = [&](size_t b) { char *p = s->mem + o; o += al256(b); return p; };
         s->dev.poses = (float *)take(N * 28);
@@ -955,7 +1025,8 @@ extern "C" int dpvo_ba_session_close(dpvo_ba_handle *h, int64_t session_id) {
     srv->sessions.erase(session_id);
     srv->used_bytes -= s->bytes;
     lk.unlock();
-    cudaFree(s->mem);
+    if (s->mem) cudaFree(s->mem);
+    if (s->win) dpvo_ba_window_destroy(s->win);
     cudaFreeHost(s->pinned_tw);
     delete s;
     return DPVO_BA_OK;
@@ -970,10 +1041,13 @@ extern "C" int dpvo_ba_session_read(dpvo_ba_handle *h, int64_t session_id, float
     if (!s) return rc;
     s->busy = true;        // hold it while copying
     lk.unlock();
-    if (poses_out && cudaMemcpy(poses_out, s->dev.poses, (size_t)s->dims.n_frames * 28, cudaMemcpyDeviceToHost))
+    dpvo_ba_dims d = s->dims;
+    dpvo_ba_problem p = s->dev;
+    if (s->win && dpvo_ba_window_problem(s->win, &d, &p) != DPVO_BA_OK) d.n_frames = d.n_patches = 0;
+    if (poses_out && d.n_frames && cudaMemcpy(poses_out, p.poses, (size_t)d.n_frames * 28, cudaMemcpyDeviceToHost))
         rc = DPVO_BA_ECUDA;
-    if (patches_out && s->dims.n_patches &&
-        cudaMemcpy(patches_out, s->dev.patches, (size_t)s->dims.n_patches * 12, cudaMemcpyDeviceToHost))
+    if (patches_out && d.n_patches &&
+        cudaMemcpy(patches_out, p.patches, (size_t)d.n_patches * 12, cudaMemcpyDeviceToHost))
         rc = DPVO_BA_ECUDA;
     lk.lock();
     s->busy = false;
@@ -981,38 +1055,180 @@ extern "C" int dpvo_ba_session_read(dpvo_ba_handle *h, int64_t session_id, float
     return rc;
 }
 
-extern "C" int dpvo_ba_submit(dpvo_ba_handle *h, int64_t session_id, const float *target, const float *weight,
-                              uint64_t *ticket) {
-    if (!h || !h->srv || !ticket) return DPVO_BA_EINVAL;
-    Server *srv = h->srv;
-    Session *s;
-    {
-        std::lock_guard<std::mutex> lk(srv->mu);
-        auto it = srv->sessions.find(session_id);
-        if (it == srv->sessions.end()) return DPVO_BA_ENOTFOUND;
-        s = it->second;
-        if (s->busy) return DPVO_BA_EBUSY;   // one request per session at a time
-        s->busy = true;
+// Host memory the device can read in place (page-locked: cudaMallocHost,
+// cudaHostAlloc or cudaHostRegister).
+static bool page_locked(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
     }
-    const size_t E = s->dims.n_edges;
-    if (E && (!target || !weight)) {
-        std::lock_guard<std::mutex> lk(srv->mu);
-        s->busy = false;
-        return DPVO_BA_EINVAL;
-    }
-    if (E) {
-        std::memcpy(s->pinned_tw, target, E * 8);
-        std::memcpy(s->pinned_tw + 2 * E, weight, E * 8);
-    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
+// Queue a ticket for an idle session marked busy by the caller.
+static uint64_t enqueue(Server *srv, Ticket tk) {
     std::lock_guard<std::mutex> lk(srv->mu);
     const uint64_t t = srv->next_ticket++;
-    Ticket tk;
-    tk.session = session_id;
     tk.submitted = Clock::now();
     srv->tickets[t] = tk;
     srv->pending.push_back(t);
     srv->cv.notify_all();
-    *ticket = t;
+    return t;
+}
+
+static Session *claim_session(Server *srv, int64_t id, bool window, int *rc) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->sessions.find(id);
+    if (it == srv->sessions.end()) { *rc = DPVO_BA_ENOTFOUND; return nullptr; }
+    Session *s = it->second;
+    if ((s->win != nullptr) != window) { *rc = DPVO_BA_EINVAL; return nullptr; }
+    if (s->busy) { *rc = DPVO_BA_EBUSY; return nullptr; }   // one request per session at a time
+    s->busy = true;
+    *rc = DPVO_BA_OK;
+    return s;
+}
+
+static void release_session(Server *srv, Session *s) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    s->busy = false;
+    srv->cv.notify_all();
+}
+
+extern "C" int dpvo_ba_submit(dpvo_ba_handle *h, int64_t session_id, const float *target, const float *weight,
+                              uint64_t *ticket) {
+    if (!h || !h->srv || !ticket) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    int rc;
+    Session *s = claim_session(srv, session_id, false, &rc);
+    if (!s) return rc;
+    const size_t E = s->dims.n_edges;
+    if (E && (!target || !weight)) {
+        release_session(srv, s);
+        return DPVO_BA_EINVAL;
+    }
+    Ticket tk;
+    tk.session = session_id;
+    tk.kind = 0;
+    tk.src_t = s->pinned_tw;
+    tk.src_w = s->pinned_tw + 2 * E;
+    if (E) {   // page-locked buffers are read in place; others are copied to the staging
+        if (page_locked(target)) tk.src_t = target;
+        else std::memcpy(s->pinned_tw, target, E * 8);
+        if (page_locked(weight)) tk.src_w = weight;
+        else std::memcpy(s->pinned_tw + 2 * E, weight, E * 8);
+    }
+    *ticket = enqueue(srv, tk);
+    return DPVO_BA_OK;
+}
+
+extern "C" int dpvo_ba_session_open_window(dpvo_ba_handle *h, const dpvo_ba_window_params *params,
+                                           int64_t *session_id) {
+    if (!h || !h->srv || !params || !session_id) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    const dpvo_ba_dims &mx = srv->max_dims;
+    const size_t max_p = (size_t)params->max_frames * (size_t)params->max_new_patches;
+    const size_t max_e = dpvo_win_host::max_edges(*params);
+    if (params->max_frames > mx.n_frames || max_p > (size_t)mx.n_patches || max_e > (size_t)mx.n_edges ||
+        params->n_iters > mx.n_iters)
+        return DPVO_BA_EINVAL;   // the slots' workspaces are reserved for max_dims
+    const size_t bytes = dpvo_win_host::device_bytes(*params);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->used_bytes + bytes > srv->budget) return DPVO_BA_EBUSY;   // not admitted: over the budget
+        srv->used_bytes += bytes;
+    }
+    Session *s = new Session();
+    s->bytes = bytes;
+    s->wprm = *params;
+    s->max_edges = max_e;
+    int rc = dpvo_ba_window_create(params, &s->win);
+    if (!rc && cudaMallocHost((void **)&s->pinned_tw, max_e * 16 + (size_t)params->max_new_patches * 8 + 16) !=
+                   cudaSuccess) {
+        cudaGetLastError();
+        rc = DPVO_BA_ENOMEM;
+    }
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (rc) {
+        if (s->win) dpvo_ba_window_destroy(s->win);
+        if (s->pinned_tw) cudaFreeHost(s->pinned_tw);
+        delete s;
+        srv->used_bytes -= bytes;
+        return rc;
+    }
+    s->pinned_xy = s->pinned_tw + 4 * max_e;
+    s->pinned_status = reinterpret_cast<int32_t *>(s->pinned_xy + 2 * (size_t)params->max_new_patches);
+    s->id = srv->next_session++;
+    srv->sessions[s->id] = s;
+    *session_id = s->id;
+    return DPVO_BA_OK;
+}
+
+extern "C" int dpvo_ba_session_frame_edges(dpvo_ba_handle *h, int64_t session_id, int n_new, int32_t *n_edges) {
+    if (!h || !h->srv || !n_edges) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->sessions.find(session_id);
+    if (it == srv->sessions.end()) return DPVO_BA_ENOTFOUND;
+    Session *s = it->second;
+    if (!s->win || n_new < 0 || n_new > s->wprm.max_new_patches) return DPVO_BA_EINVAL;
+    if (s->busy) return DPVO_BA_EBUSY;     // its frame count changes when the pending request runs
+    *n_edges = dpvo_win_host::edges_after(s->win, n_new);
+    return DPVO_BA_OK;
+}
+
+extern "C" int dpvo_ba_session_dims(dpvo_ba_handle *h, int64_t session_id, dpvo_ba_dims *dims) {
+    if (!h || !h->srv || !dims) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    int rc;
+    Session *s = find_idle_session(srv, session_id, lk, 10000, &rc);
+    if (!s) return rc;
+    if (!s->win) {
+        *dims = s->dims;
+        return DPVO_BA_OK;
+    }
+    dpvo_ba_problem p;
+    if (dpvo_ba_window_problem(s->win, dims, &p) != DPVO_BA_OK) {   // an empty window
+        int N, P, E;
+        dpvo_win_host::sizes(s->win, &N, &P, &E);
+        *dims = dpvo_ba_dims{N, P, E, 0, s->wprm.n_iters, s->wprm.fx, s->wprm.fy, s->wprm.cx, s->wprm.cy};
+    }
+    return DPVO_BA_OK;
+}
+
+extern "C" int dpvo_ba_submit_frame(dpvo_ba_handle *h, int64_t session_id, const float *new_xy, int n_new,
+                                    const float *delta, const float *weight, uint64_t *ticket) {
+    if (!h || !h->srv || !ticket || (delta == nullptr) != (weight == nullptr)) return DPVO_BA_EINVAL;
+    Server *srv = h->srv;
+    int rc;
+    Session *s = claim_session(srv, session_id, true, &rc);
+    if (!s) return rc;
+    if (n_new < 0 || n_new > s->wprm.max_new_patches || (n_new > 0 && !new_xy)) {
+        release_session(srv, s);
+        return DPVO_BA_EINVAL;
+    }
+    const size_t E = (size_t)dpvo_win_host::edges_after(s->win, n_new);   // the session is ours: mirror stable
+    Ticket tk;
+    tk.session = session_id;
+    tk.kind = 1;
+    tk.n_new = n_new;
+    tk.src_xy = s->pinned_xy;
+    if (n_new) {
+        if (page_locked(new_xy)) tk.src_xy = new_xy;
+        else std::memcpy(s->pinned_xy, new_xy, (size_t)n_new * 8);
+    }
+    if (delta) {
+        tk.src_t = s->pinned_tw;
+        tk.src_w = s->pinned_tw + 2 * E;
+        if (E) {
+            if (page_locked(delta)) tk.src_t = delta;
+            else std::memcpy(s->pinned_tw, delta, E * 8);
+            if (page_locked(weight)) tk.src_w = weight;
+            else std::memcpy(s->pinned_tw + 2 * E, weight, E * 8);
+        }
+    }
+    *ticket = enqueue(srv, tk);
     return DPVO_BA_OK;
 }
 

@@ -1,12 +1,18 @@
 // Serving runtime: many concurrent VO sessions with device-resident state,
 // requests batched continuously into the solve launches.
 //
-// A session holds one problem's graph (anchor, kk, jj), state (poses,
-// patches) and factor buffers (target, weight) in device memory owned by the
-// library, admitted against the handle's memory budget.  A request carries a
-// new set of factors (host memory) for one session; the scheduler thread packs
-// every pending request whose session is idle into one batched solve on one of
-// its in-flight slots (a stream with its own workspace), so requests that
+// A session holds one problem in device memory owned by the library, admitted
+// against the handle's memory budget: either a fixed graph (anchor, kk, jj)
+// with its state (poses, patches) and factor buffers (target, weight), or a
+// sliding window (Sec. 3.3, dpvo_ba_window) that grows by one frame per
+// request and drops its oldest frame when full.  A request carries new
+// factors for a fixed-graph session, or a new frame (patch centres) and the
+// revisions and weights of the window's edges after the append.  The scheduler
+// thread packs every pending request whose session is idle into one batch on
+// one of its in-flight slots (a stream with its own workspace): the windows'
+// appends (one batched call), one gather launch that reads every request's
+// factors in place from page-locked host memory, the batched solve, and one
+// launch that writes every status to page-locked memory.  Requests that
 // arrive while a batch runs go into the next batch and consecutive batches
 // overlap on the device.  Completion is timestamped by a host callback on the
 // slot's stream.  Every wait is bounded.
@@ -28,16 +34,34 @@ using Clock = std::chrono::steady_clock;
 struct Session {
     int64_t id = 0;
     dpvo_ba_dims dims{};
-    dpvo_ba_problem dev{};        // device arrays (library-owned)
-    char *mem = nullptr;          // one device allocation for all arrays
+    dpvo_ba_problem dev{};        // device arrays (library-owned); a window session's come from its window
+    char *mem = nullptr;          // one device allocation for all arrays (fixed-graph sessions)
+    dpvo_ba_window *win = nullptr;  // the sliding window (window sessions)
+    dpvo_ba_window_params wprm{};
     size_t bytes = 0;
-    float *pinned_tw = nullptr;   // pinned staging: target then weight of the pending request
+    size_t max_edges = 0;         // edges the staging holds
+    float *pinned_tw = nullptr;   // page-locked staging: target (or revision) then weight of the pending request
+    float *pinned_xy = nullptr;   // window sessions: the new frame's patch centres
     int32_t *pinned_status = nullptr;
     bool busy = false;            // a request is queued or running
 };
 
+// One request's device work in a batch: its factors, read in place from
+// page-locked host memory, and its status, written back to it.
+struct GatherJob {
+    const float2 *src_t, *src_w;  // host (page-locked): targets or revisions, weights
+    float2 *dst_t, *dst_w;        // device: the session's (or window's) factor arrays
+    int32_t n_edges;
+    int32_t mode;                 // 0 replace target and weight, 1 target += revision and set weight, 2 none
+    const int32_t *status_dev;
+    int32_t *status_host;
+};
+
 struct Ticket {
     int64_t session = 0;
+    int kind = 0;                 // 0 new factors, 1 new frame
+    int n_new = 0;                // frame requests: patches of the new frame
+    const float *src_t = nullptr, *src_w = nullptr, *src_xy = nullptr;   // page-locked sources
     Clock::time_point submitted;
     Clock::time_point done_at;
     bool done = false;
@@ -64,6 +88,7 @@ struct Server {
     size_t used_bytes = 0;
     size_t budget = 0;
     int launch_error = 0;
+    dpvo_ba_dims max_dims{};                           // bound of every session's sizes
 };
 
 struct Slot {
@@ -72,6 +97,7 @@ struct Slot {
     cudaStream_t stream = nullptr;
     bool busy = false;
     std::vector<uint64_t> batch;  // tickets in flight on this slot
+    GatherJob *jobs = nullptr;    // page-locked, max_batch entries, read by the gather and status launches
 };
 
 }  // namespace dpvo_serve

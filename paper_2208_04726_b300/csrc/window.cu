@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "dpvo_ba.h"
+#include "window_host.h"
 
 namespace dpvo_win {
 
@@ -210,6 +211,48 @@ static int edges_per_patch(int f, int N, int R) {
     return hi - lo + 1;
 }
 
+// Device layout of a window: offsets of its arrays (take() order) and total bytes.
+struct WinLayout {
+    size_t o_pose0, o_pose1, o_patch0, o_patch1, o_anc0, o_anc1, o_cnt0, o_cnt1, o_tab, o_kk, o_jj, o_tg, o_wt, o_st,
+        bytes, edges;
+};
+
+static WinLayout win_layout(const dpvo_ba_window_params &p) {
+    WinLayout L;
+    const size_t F = (size_t)p.max_frames, Pc = F * (size_t)p.max_new_patches;
+    const size_t span = (size_t)(2 * p.radius + 1) < F ? (size_t)(2 * p.radius + 1) : F;
+    const size_t Ec = Pc * span;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = al256(off + b); return o; };
+    L.o_pose0 = take(F * 28); L.o_pose1 = take(F * 28); L.o_patch0 = take(Pc * 12 + 4);
+    L.o_patch1 = take(Pc * 12 + 4); L.o_anc0 = take(Pc * 4 + 4); L.o_anc1 = take(Pc * 4 + 4);
+    L.o_cnt0 = take(F * 4); L.o_cnt1 = take(F * 4); L.o_tab = take((2 * F + 2) * 4);
+    L.o_kk = take(Ec * 4 + 4); L.o_jj = take(Ec * 4 + 4); L.o_tg = take(Ec * 8 + 8); L.o_wt = take(Ec * 8 + 8);
+    L.o_st = take(16);
+    L.bytes = off;
+    L.edges = Ec;
+    return L;
+}
+
+namespace dpvo_win_host {
+size_t device_bytes(const dpvo_ba_window_params &p) { return win_layout(p).bytes; }
+size_t max_edges(const dpvo_ba_window_params &p) { return win_layout(p).edges; }
+int edges_after(const dpvo_ba_window *w, int n_new) {
+    const int drop = w->N == w->prm.max_frames ? 1 : 0;
+    std::vector<int> cnt(w->counts.begin() + drop, w->counts.end());
+    cnt.push_back(n_new);
+    const int N2 = (int)cnt.size();
+    int E2 = 0;
+    for (int f = 0; f < N2; ++f) E2 += cnt[f] * edges_per_patch(f, N2, w->prm.radius);
+    return E2;
+}
+void sizes(const dpvo_ba_window *w, int *n_frames, int *n_patches, int *n_edges) {
+    *n_frames = w->N;
+    *n_patches = w->P;
+    *n_edges = w->E;
+}
+}  // namespace dpvo_win_host
+
 extern "C" int dpvo_ba_window_create(const dpvo_ba_window_params *p, dpvo_ba_window **out) {
     if (!p || !out || p->max_frames < 1 || p->max_frames > DPVO_BA_MAX_FRAMES || p->max_new_patches < 0 ||
         p->max_new_patches > kMaxNewPatches || p->radius < 0 || p->free_poses < 0 || p->n_iters < 1 || p->n_iters > DPVO_BA_MAX_ITERS)
@@ -217,16 +260,11 @@ extern "C" int dpvo_ba_window_create(const dpvo_ba_window_params *p, dpvo_ba_win
     dpvo_ba_window *w = new (std::nothrow) dpvo_ba_window;
     if (!w) return DPVO_BA_ENOMEM;
     w->prm = *p;
-    const size_t F = (size_t)p->max_frames, Pc = F * (size_t)p->max_new_patches;
-    const size_t span = (size_t)(2 * p->radius + 1) < F ? (size_t)(2 * p->radius + 1) : F;
-    const size_t Ec = Pc * span;
-    size_t off = 0;
-    auto take = [&](size_t b) { size_t o = off; off = al256(off + b); return o; };
-    const size_t o_pose0 = take(F * 28), o_pose1 = take(F * 28), o_patch0 = take(Pc * 12 + 4),
-                 o_patch1 = take(Pc * 12 + 4), o_anc0 = take(Pc * 4 + 4), o_anc1 = take(Pc * 4 + 4),
-                 o_cnt0 = take(F * 4), o_cnt1 = take(F * 4), o_tab = take((2 * F + 2) * 4),
-                 o_kk = take(Ec * 4 + 4), o_jj = take(Ec * 4 + 4), o_tg = take(Ec * 8 + 8), o_wt = take(Ec * 8 + 8),
-                 o_st = take(16);
+    const WinLayout WL = win_layout(*p);
+    const size_t off = WL.bytes;
+    const size_t o_pose0 = WL.o_pose0, o_pose1 = WL.o_pose1, o_patch0 = WL.o_patch0, o_patch1 = WL.o_patch1,
+                 o_anc0 = WL.o_anc0, o_anc1 = WL.o_anc1, o_cnt0 = WL.o_cnt0, o_cnt1 = WL.o_cnt1, o_tab = WL.o_tab,
+                 o_kk = WL.o_kk, o_jj = WL.o_jj, o_tg = WL.o_tg, o_wt = WL.o_wt, o_st = WL.o_st;
     if (cudaMalloc(&w->mem, off) != cudaSuccess) {
         delete w;
         return DPVO_BA_ENOMEM;

@@ -109,3 +109,76 @@ def test_one_request_per_session_and_unknown_tickets():
     finally:
         srv.serve_stop()
         srv.close()
+
+
+def test_sliding_window_sessions_equal_the_same_window_alone():
+    """Window sessions (the paper's Default and Fast shapes: 96 patches / 10
+    free poses and 48 / 7, radius 13, 22-frame windows) served together with
+    fixed-graph sessions.  Every request appends a frame (pixel centres, edge
+    revisions and weights from the client) and solves the window.  After each
+    frame, each session's state must equal the same frame appended to a window
+    of its own (dpvo_ba_window_append) and solved alone (dpvo_ba_solve).  The
+    reference window is reset to the served state before each frame, so every
+    comparison covers one append and one solve; 24 frames exercise the
+    dropping of the oldest frame once the window is full."""
+    _need_gpu()
+    rng = np.random.default_rng(3)
+    intr = (320.0, 320.0, 320.0, 240.0)
+    kinds = [(96, 10), (48, 7), (96, 10), (48, 7)]
+    srv = ba.Solver()
+    srv.serve_start(32, 3072, 66000, 2, max_batch=16, max_in_flight=2)
+    solo = ba.Solver()
+    graphs = S.make_serving_mix(2, base_seed=11)
+    refs = []
+    try:
+        sids = []
+        for m, f in kinds:
+            prm = ba.WindowParams(22, m, 13, f, 2, *intr)
+            sids.append(srv.session_open_window(prm))
+            refs.append(ba.Window(22, m, 13, f, intr))
+        gids = [srv.session_open(sc) for sc in graphs]
+        for frame in range(24):
+            reqs = []
+            for sid, (m, f) in zip(sids, kinds):
+                xy = rng.uniform([16, 16], [624, 464], (m, 2)).astype(np.float32)
+                E = srv.session_frame_edges(sid, m)
+                delta = rng.normal(scale=np.sqrt(0.5), size=(E, 2)).astype(np.float32)
+                weight = rng.uniform(0.0, 1.0, size=(E, 2)).astype(np.float32)
+                reqs.append((xy, delta, weight))
+            tickets = [srv.submit_frame(sid, *r) for sid, r in zip(sids, reqs)]
+            fresh = [S.refresh_factors(sc, 1000 * frame + b) for b, sc in enumerate(graphs)]
+            gts = [srv.submit(gid, r.target, r.weight) for gid, r in zip(gids, fresh)]
+            for tk in tickets + gts:
+                st, lat = srv.wait(tk, 20000)
+                assert st == 0 and lat > 0
+            for b, (sid, (xy, delta, weight)) in enumerate(zip(sids, reqs)):
+                w = refs[b]
+                w.append(torch.tensor(xy, device="cuda"))
+                p = w.problem()
+                p.target.add_(torch.tensor(delta, device="cuda"))
+                p.weight.copy_(torch.tensor(weight, device="cuda"))
+                p0, q0 = p.poses.clone(), p.patches.clone()     # the appended state, before the solve
+                solo.solve([p])
+                torch.cuda.synchronize()
+                assert int(p.status.item()) == 0
+                d = srv.session_dims(sid)
+                assert (d.n_frames, d.n_patches, d.n_edges) == tuple(p.poses.shape[:1]) + (p.patches.shape[0],
+                                                                                           p.kk.shape[0])
+                poses, patches = srv.session_read(sid, d.n_frames, d.n_patches)
+                t0 = d.t0
+                ref_p, ref_q = p.poses.cpu().numpy(), p.patches.cpu().numpy()
+                p0n, q0n = p0.cpu().numpy(), q0.cpu().numpy()
+                if d.n_frames > t0:
+                    assert err(poses[t0:] - p0n[t0:], ref_p[t0:] - p0n[t0:]) < TOL_POSE, (frame, b)
+                assert err(patches[:, 2] - q0n[:, 2], ref_q[:, 2] - q0n[:, 2]) < TOL_DEPTH, (frame, b)
+                # the next frame starts the reference from the served state
+                p.poses.copy_(torch.tensor(poses, device="cuda"))
+                p.patches.copy_(torch.tensor(patches, device="cuda"))
+        for sid in sids + gids:
+            srv.session_close(sid)
+    finally:
+        srv.serve_stop()
+        srv.close()
+        solo.close()
+        for w in refs:
+            w.close()
