@@ -18,7 +18,9 @@ Also measured and reported on the same JSON line:
   cpu_baseline  the FP64 oracle timed on this host's cores on a bounded sample
   serving   256 VO sessions (uneven shapes) with device-resident state, Poisson
             requests at 2000/s: p50/p99 latency and solves/s, continuous
-            batching vs one launch per solve, plus a saturated closed loop
+            batching vs one launch per solve, plus a saturated closed loop;
+            and the Default/Fast mix as 256 served sliding windows (a request
+            appends a frame and solves), the same measurements
   stress    64 large-window sessions (64 frames, 32 free poses, 4 iterations)
   grad      16 eight-frame problems: forward, the pose supervision loss of
             Sec. 3.4 on the device, and the backward to targets and weights
@@ -519,23 +521,32 @@ def serving_bench(n_sessions=256, distinct=32, rate=2000.0, duration=2.0, satura
     import time as _t
     from paper_2208_04726_b300 import ba
     from paper_2208_04726_b300 import scenes as S
+    import torch
     mix = S.make_serving_mix(distinct, base_seed=seed)
-    reqs = [[S.refresh_factors(sc, 10_000 + 10 * i + r) for r in range(3)] for i, sc in enumerate(mix)]
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.copy_(torch.from_numpy(np.ascontiguousarray(a, np.float32)))
+        return t
+
+    # each request's targets and weights sit in page-locked memory (read in place)
+    reqs = [[(pinned(f.target), pinned(f.weight)) for f in (S.refresh_factors(sc, 10_000 + 10 * i + r)
+                                                            for r in range(3))] for i, sc in enumerate(mix)]
     sess_of = [b % distinct for b in range(n_sessions)]
     max_n = max(sc.n_frames for sc in mix)
     max_p = max(sc.n_patches for sc in mix)
     max_e = max(sc.n_edges for sc in mix)
     out = {"sessions": n_sessions, "distinct_shapes": distinct, "poisson_rate": rate,
            "workload": "N~U{8..32} frames, {48,64,96} patches/frame, radius U{8..13}, last min(10, N-2) poses free, "
-                       "2 GN iterations, fresh targets and weights per request"}
+                       "2 GN iterations, fresh targets and weights per request (page-locked, read in place)"}
     for mode, (mb, mif) in (("batched", (n_sessions, 2)), ("plain", (1, 1))):
         srv = ba.Solver()
         srv.serve_start(max_n, max_p, max_e, 2, max_batch=mb, max_in_flight=mif)
         sids = [srv.session_open(mix[sess_of[b]]) for b in range(n_sessions)]
 
         def request(b, k):
-            r = reqs[sess_of[b]][k % 3]
-            return srv.submit(sids[b], r.target, r.weight)
+            t, w = reqs[sess_of[b]][k % 3]
+            return srv.submit(sids[b], t, w)
 
         for b in range(n_sessions):                     # warm-up: one request per session
             srv.wait(request(b, 0), 60000)
@@ -582,6 +593,101 @@ def serving_bench(n_sessions=256, distinct=32, rate=2000.0, duration=2.0, satura
             srv.wait(tk, 60000)
         res["saturated_solves_per_s"] = cnt / el
         out[mode] = res
+        srv.serve_stop()
+        srv.close()
+    return out
+
+
+def serving_slid_bench(n_default=128, n_fast=128, rate=2000.0, duration=2.0, saturate=1.0, seed=2):
+    """The paper's Default (96 patches/frame, 10 free poses) and Fast (48, 7)
+    configurations (Sec. 4) as served sliding-window sessions (radius 13,
+    22-frame windows, 2 GN iterations): every request appends a frame and
+    solves the window (Sec. 3.3).  The windows are first filled (22 frames
+    each); then a Poisson open loop (rate requests/s over all sessions) and a
+    saturated closed loop, for continuous batching and for one launch per
+    solve.  Each request's patch centres, edge revisions N(0, 0.5 px^2) and
+    weights U[0, 1] sit in page-locked memory and are read in place.  Latency
+    is the library's (submit to completion on the device)."""
+    import time as _t
+    import torch
+    from paper_2208_04726_b300 import ba
+    rng = np.random.default_rng(seed)
+    intr = (320.0, 320.0, 320.0, 240.0)
+    kinds = [(96, 10)] * n_default + [(48, 7)] * n_fast
+    n = len(kinds)
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.copy_(torch.from_numpy(a))
+        return t
+
+    xy = {m: [pinned(rng.uniform([16, 16], [624, 464], (m, 2)).astype(np.float32)) for _ in range(4)]
+          for m in (96, 48)}
+    out = {"sessions": n, "poisson_rate": rate,
+           "workload": f"{n_default} Default (96 patches/frame, 10 free poses) + {n_fast} Fast (48, 7) sliding "
+                       "windows, radius 13, 22 frames, 2 GN iterations; a request appends a frame and solves"}
+    for mode, (mb, mif) in (("batched", (n, 2)), ("plain", (1, 1))):
+        srv = ba.Solver()
+        srv.serve_start(22, 22 * 96, 22 * 96 * 22, 2, max_batch=mb, max_in_flight=mif)   # window capacities
+        sids = [srv.session_open_window(ba.WindowParams(22, m, 13, f, 2, *intr)) for m, f in kinds]
+        for f in range(22):                              # fill the windows (no revisions)
+            tks = [srv.submit_frame(sid, xy[m][f % 4]) for sid, (m, _) in zip(sids, kinds)]
+            for tk in tks:
+                srv.wait(tk, 60000)
+        E = {m: srv.session_frame_edges(sids[kinds.index((m, f))], m) for m, f in set(kinds)}
+        fac = {m: [(pinned(rng.normal(scale=np.sqrt(0.5), size=(E[m], 2)).astype(np.float32)),
+                    pinned(rng.uniform(0.0, 1.0, size=(E[m], 2)).astype(np.float32))) for _ in range(3)]
+               for m in E}
+
+        def request(b, k):
+            m = kinds[b][0]
+            d, w = fac[m][k % 3]
+            return srv.submit_frame(sids[b], xy[m][k % 4], d, w)
+
+        rng2 = np.random.default_rng(1)
+        arrivals = np.cumsum(rng2.exponential(1.0 / rate, size=int(rate * duration * 1.5) + 10))
+        arrivals = arrivals[arrivals < duration]
+        who = rng2.integers(0, n, size=arrivals.shape[0])
+        busy, queued = {}, {b: [] for b in range(n)}
+        lat, k, done, bad = [], 0, 0, 0
+        t0 = _t.perf_counter()
+        while done < arrivals.shape[0]:
+            now = _t.perf_counter() - t0
+            while k < arrivals.shape[0] and arrivals[k] <= now:
+                b = int(who[k])
+                if b in busy:
+                    queued[b].append(k)
+                else:
+                    busy[b] = request(b, k)
+                k += 1
+            for b, tk in list(busy.items()):
+                ok, st, ms = srv.poll(tk)
+                if ok:
+                    lat.append(ms)
+                    bad += int(st != 0)
+                    done += 1
+                    del busy[b]
+                    if queued[b]:
+                        busy[b] = request(b, queued[b].pop(0))
+        elapsed = _t.perf_counter() - t0
+        res = {"latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+               "completed": done, "solves_per_s": done / elapsed, "statuses_nonzero": bad}
+        busy = {b: request(b, 1) for b in range(n)}
+        cnt = 0
+        t0 = _t.perf_counter()
+        while _t.perf_counter() - t0 < saturate:
+            for b, tk in list(busy.items()):
+                ok, st, ms = srv.poll(tk)
+                if ok:
+                    cnt += 1
+                    busy[b] = request(b, cnt)
+        el = _t.perf_counter() - t0
+        for tk in busy.values():
+            srv.wait(tk, 60000)
+        res["saturated_solves_per_s"] = cnt / el
+        out[mode] = res
+        for sid in sids:
+            srv.session_close(sid)
         srv.serve_stop()
         srv.close()
     return out
@@ -861,6 +967,8 @@ def main():
 
     plain_n8 = plain_n8_bench(stream) if (rank == 0 and args.plain > 0) else None
     serving = serving_bench() if (rank == 0 and args.serving) else None
+    if serving is not None:
+        serving["slid_default_fast_mix"] = serving_slid_bench()
     stress = stress_bench(args.stress, 5, stream, load_peaks()[0]) if (rank == 0 and args.stress > 0) else None
     if stress is not None and args.tf32:
         st = stress_bench(args.stress, 5, stream, load_peaks()[0], tf32=True)

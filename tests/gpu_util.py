@@ -51,6 +51,25 @@ def err(a, b):
     return max(rel(a, b), max_rel(a, b))
 
 
+def err_update(x, ref, x0, tol=TOL_POSE):
+    """err() of the update x - x0 against ref - x0, where x and ref are FP32
+    states stored from the same start x0.  The reference scale of both measures
+    is at least 2 FP32 ulps of the state divided by ``tol``: a converged solve's
+    update can be smaller than the state's own storage resolution allows to
+    compare at ``tol`` (one ulp of a pose coordinate near 2.6 is 2.4e-7), and
+    two FP32 results that differ by an ulp are then the same result."""
+    x, ref, x0 = (np.asarray(a, np.float64) for a in (x, ref, x0))
+    du, dr = x - x0, ref - x0
+    floor = 2.0 * 2.0 ** -23 * np.abs(x0).max() / tol
+    n_ref = max(np.linalg.norm(dr), floor)
+    if du.ndim >= 2:
+        e_el = np.linalg.norm((du - dr).reshape(du.shape[0], -1), axis=1).max()
+        r_el = max(np.linalg.norm(dr.reshape(dr.shape[0], -1), axis=1).max(), floor)
+    else:
+        e_el, r_el = np.abs(du - dr).max(), max(np.abs(dr).max(), floor)
+    return float(max(np.linalg.norm(du - dr) / n_ref, e_el / r_el))
+
+
 def align_quats(poses, ref):
     out = np.asarray(poses, np.float64).copy()
     s = np.sign((out[:, 3:] * ref[:, 3:]).sum(1))

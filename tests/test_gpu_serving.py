@@ -12,7 +12,7 @@ import torch
 
 from paper_2208_04726_b300 import ba
 from paper_2208_04726_b300 import scenes as S
-from tests.gpu_util import TOL_DEPTH, TOL_POSE, err
+from tests.gpu_util import TOL_DEPTH, TOL_POSE, err, err_update
 
 pytestmark = pytest.mark.gpu
 
@@ -54,8 +54,8 @@ def test_results_alone_equal_results_in_the_mix():
                 ap, apt, ast = _alone(sc, state[b][0], state[b][1], r.target, r.weight)
                 assert ast == 0
                 t0 = sc.t0
-                assert err(poses[t0:] - state[b][0][t0:], ap[t0:] - state[b][0][t0:]) < TOL_POSE
-                assert err(patches[:, 2] - state[b][1][:, 2], apt[:, 2] - state[b][1][:, 2]) < TOL_DEPTH
+                assert err_update(poses[t0:], ap[t0:], state[b][0][t0:], TOL_POSE) < TOL_POSE
+                assert err_update(patches[:, 2], apt[:, 2], state[b][1][:, 2], TOL_DEPTH) < TOL_DEPTH
                 state[b] = (poses, patches)
         for sid in sids:
             srv.session_close(sid)
