@@ -45,8 +45,10 @@ struct Layout {
 // solve_kernel shared memory: S and its FP32 copy (n x (n+1)), v, x, the FP32 right-hand side,
 // the inverted diagonal blocks of the factor.
 static size_t solve_smem_bytes(int nf) {
-    const size_t n = 6 * (size_t)nf, panels = (n + kPanel - 1) / kPanel;
-    return n * (n + 1) * 8 + 2 * n * 8 + n * (n + 1) * 4 + n * 4 + panels * kPanel * kLinvLd * 4 + 64;
+    // S (FP64, n x (n+1)), v, x; the FP32 factor (rows padded to 4), the
+    // panel's scaled columns, the right-hand side
+    const size_t n = 6 * (size_t)nf, ldf = (n + 3) & ~(size_t)3;
+    return n * (n + 1) * 8 + 2 * n * 8 + n * ldf * 4 + n * kSolvePanel * 4 + n * 4 + 64;
 }
 
 // Stored Schur rows: one row per patch, or in the tensor-core variant one

@@ -1710,6 +1710,66 @@ struct RowMajorIdx {
     __device__ __forceinline__ int operator()(int i, int k) const { return i * ld + k; }
 };
 
+// ---- FP32 factorisation of the reduced system by panels (solve_kernel)
+constexpr int kSolvePanel = 8;          // columns per panel: two block barriers per panel
+
+// One warp: eliminate the nb x nb diagonal block at (J, J) of the FP32 copy Sf
+// (row stride ldf) in the square-root-free form (pivots d_j on the diagonal,
+// eliminated values a_ij below, a_ik -= a_ij a_kj / d_j), its pivot
+// reciprocals into rp[J..J+nb).  A pivot <= 0 or not finite sets *bad.
+__device__ __forceinline__ void factor_diag_block(float *Sf, int ldf, int J, int nb, float *rp, int lane,
+                                                  int *bad) {
+    for (int j = 0; j < nb; ++j) {
+        const float d = Sf[(J + j) * ldf + J + j];
+        const float r = 1.0f / d;
+        if (lane == 0) {
+            rp[J + j] = r;
+            if (!(d > 0.f) || !isfinite(r)) *bad = 1;
+        }
+        // elements (i, k), j < k <= i < nb, one per lane (at most 28)
+        const int m = nb - 1 - j;
+        for (int e = lane; e < m * (m + 1) / 2; e += 32) {
+            int c = 0, q = e;
+            while (q >= m - c) { q -= m - c; ++c; }      // column c of the trailing block, row c + q
+            const int k = J + j + 1 + c, i = k + q;
+            Sf[i * ldf + k] = fmaf(-Sf[i * ldf + J + j] * r, Sf[k * ldf + J + j], Sf[i * ldf + k]);
+        }
+        __syncwarp();
+    }
+}
+
+// One warp: solve (U D^-1 U^T) z = b for the factor above (l_ij = a_ij / d_j):
+// forward L y = b, w = D^-1 y, backward L^T z = w.  b in shared memory (n
+// entries), overwritten by z; each lane keeps rows lane, lane + 32, lane + 64.
+__device__ __forceinline__ void solve_ldl_warp(const float *Sf, int ldf, const float *rp, float *b, int n,
+                                               int lane) {
+    float x[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) x[t] = lane + 32 * t < n ? b[lane + 32 * t] : 0.f;
+    for (int j = 0; j < n; ++j) {                                   // forward
+        const float y = __shfl_sync(0xffffffffu, x[j >> 5], j & 31) * rp[j];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int r = lane + 32 * t;
+            if (r > j && r < n) x[t] = fmaf(-Sf[r * ldf + j], y, x[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+        if (lane + 32 * t < n) x[t] *= rp[lane + 32 * t];
+    for (int j = n - 1; j > 0; --j) {                               // backward
+        const float z = __shfl_sync(0xffffffffu, x[j >> 5], j & 31);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int r = lane + 32 * t;
+            if (r < j) x[t] = fmaf(-Sf[j * ldf + r] * rp[r], z, x[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+        if (lane + 32 * t < n) b[lane + 32 * t] = x[t];
+}
+
 constexpr int kMaxRefine = 4;          // FP64 refinement steps of the FP32 solution at most
 constexpr double kRefineTol = 1e-6;    // accept once the last correction is below this x max|x|
 
@@ -1808,52 +1868,97 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
     __syncthreads();
     if (!s_use64) {
         double *x = v + n;
-        float *Sf = reinterpret_cast<float *>(x + n);
-        float *bf = Sf + (size_t)n * ld;
-        float *Linv = bf + n;                               // inverted diagonal blocks of the factor
+        const int ldf = (n + 3) & ~3;
+        float *Sf = reinterpret_cast<float *>(x + n);          // [n][ldf] FP32 copy, factored in place
+        float *Lp = Sf + (size_t)n * ldf;                       // [n][kSolvePanel] a_im / d_m of the panel
+        float *bf = Lp + (size_t)n * kSolvePanel;               // [n] right-hand side, then the correction
+        __shared__ int s_next;                                  // 1: refine again, 0: done
         for (int q = tid; q < n * n; q += kSolveThreads) {
             const int i = q / n, k = q - i * n;
-            if (k <= i) Sf[i * ld + k] = (float)S[i * ld + k];
+            if (k <= i) Sf[i * ldf + k] = (float)S[i * ld + k];
         }
+        for (int q = tid; q < n * kSolvePanel; q += kSolveThreads) Lp[q] = 0.f;
         for (int q = tid; q < n; q += kSolveThreads) {
             x[q] = 0.0;
             bf[q] = (float)v[q];
         }
         __syncthreads();
-        if (tid == 0) {
-            const float p0 = Sf[0];
-            s_rpf[0] = p0 > 0.f ? 1.0f / p0 : -1.f;
-        }
+        // Panels of kSolvePanel columns: (1) the diagonal block by warp 0
+        // (the first one here, each next one at the end of (3)); (2) the
+        // panel's rows below the block, by forward substitution with the
+        // block's factor, one thread per row, with their scaled copies
+        // l_im = a_im / d_m; (3) the trailing triangle's rank-kSolvePanel
+        // update a_ik -= sum_m l_im a_km, every thread its own elements (the
+        // next diagonal block's by warp 0, which then eliminates it).
+        if (tid < 32) factor_diag_block(Sf, ldf, 0, min(kSolvePanel, n), s_rpf, lane, &s_use64);
         __syncthreads();
-        for (int j = 0; j < n; ++j) {
-            const float ip = s_rpf[j];
-            if (!(ip > 0.f) || !isfinite(ip)) {
-                if (tid == 0) s_use64 = 1;
-                break;
-            }
-            const int m = n - 1 - j, count = m * (m + 1) / 2, last = count - 1;
-            const float *colj = Sf + j;
-            if (count > 0 && tid == last % kSolveThreads) {
-                const int jn = j + 1;
-                const float pn = Sf[jn * ld + jn] - (colj[jn * ld] * ip) * colj[jn * ld];
-                Sf[jn * ld + jn] = pn;
-                s_rpf[jn] = pn > 0.f ? 1.0f / pn : -1.f;
-            }
+        for (int J = 0; J < n && !s_use64; J += kSolvePanel) {
+            const int nb = min(kSolvePanel, n - J), J2 = J + nb;
+            for (int i = J2 + tid; i < n; i += kSolveThreads) {
+                float a[kSolvePanel];
+                float *row = Sf + i * ldf + J;
 #pragma unroll
-            for (int u = 0; u < kSolveOwn; ++u) {
-                const int q = tid + kSolveThreads * u;
-                if (q >= last) break;
-                const int i = own[u] >> 16, k = own[u] & 0xffff;
-                Sf[i * ld + k] -= (colj[i * ld] * ip) * colj[k * ld];
+                for (int j = 0; j < kSolvePanel; ++j) {
+                    if (j >= nb) { a[j] = 0.f; continue; }
+                    float t = row[j];
+#pragma unroll
+                    for (int m = 0; m < j; ++m) t = fmaf(-a[m] * s_rpf[J + m], Sf[(J + j) * ldf + J + m], t);
+                    a[j] = t;
+                }
+#pragma unroll
+                for (int j = 0; j < kSolvePanel; ++j) {
+                    if (j < nb) row[j] = a[j];
+                    Lp[i * kSolvePanel + j] = j < nb ? a[j] * s_rpf[J + j] : 0.f;
+                }
             }
             __syncthreads();
+            if (J2 < n) {
+                const int m = n - J2, count = m * (m + 1) / 2;
+                const int nb2 = min(kSolvePanel, n - J2), blk_end = J2 + nb2;
+#pragma unroll
+                for (int u = 0; u < kSolveOwn; ++u) {
+                    const int q = tid + kSolveThreads * u;
+                    if (q >= count) break;
+                    const int i = own[u] >> 16, k = own[u] & 0xffff;
+                    if (i < blk_end) continue;                  // the next diagonal block: warp 0 below
+                    const float4 *li = reinterpret_cast<const float4 *>(Lp + i * kSolvePanel);
+                    const float4 *ak = reinterpret_cast<const float4 *>(Sf + k * ldf + J);
+                    const float4 l0 = li[0], l1 = li[1], a0 = ak[0], a1 = ak[1];
+                    float t = Sf[i * ldf + k];
+                    t = fmaf(-l0.x, a0.x, fmaf(-l0.y, a0.y, fmaf(-l0.z, a0.z, fmaf(-l0.w, a0.w, t))));
+                    t = fmaf(-l1.x, a1.x, fmaf(-l1.y, a1.y, fmaf(-l1.z, a1.z, fmaf(-l1.w, a1.w, t))));
+                    Sf[i * ldf + k] = t;
+                }
+                if (tid < 32) {
+                    for (int e = lane; e < nb2 * (nb2 + 1) / 2; e += 32) {   // the next block's trailing update
+                        int c = 0, q = e;
+                        while (q >= nb2 - c) { q -= nb2 - c; ++c; }
+                        const int k = J2 + c, i = k + q;
+                        const float4 *li = reinterpret_cast<const float4 *>(Lp + i * kSolvePanel);
+                        const float4 *ak = reinterpret_cast<const float4 *>(Sf + k * ldf + J);
+                        const float4 l0 = li[0], l1 = li[1], a0 = ak[0], a1 = ak[1];
+                        float t = Sf[i * ldf + k];
+                        t = fmaf(-l0.x, a0.x, fmaf(-l0.y, a0.y, fmaf(-l0.z, a0.z, fmaf(-l0.w, a0.w, t))));
+                        t = fmaf(-l1.x, a1.x, fmaf(-l1.y, a1.y, fmaf(-l1.z, a1.z, fmaf(-l1.w, a1.w, t))));
+                        Sf[i * ldf + k] = t;
+                    }
+                    __syncwarp();
+                    factor_diag_block(Sf, ldf, J2, nb2, s_rpf, lane, &s_use64);
+                }
+                __syncthreads();
+            }
         }
-        __syncthreads();
-        if (!s_use64) invert_diag_blocks(Sf, RowMajorIdx{ld}, s_rpf, Linv, n, tid);
+        // Solve and refine: the FP32 solve by warp 0, the FP64 residual v - S x
+        // by all threads.  Stop once a correction is below kRefineTol of the
+        // solution, or once the first correction is below 1e-4 of it (the
+        // refinement then contracts by about that ratio, so the next correction
+        // would be below 1e-8 of it); a correction that does not shrink to half
+        // the previous one, or kMaxRefine corrections, hand the system to FP64.
+        if (tid == 0) s_next = s_use64 ? 0 : 1;
         __syncthreads();
         double prev = 0.0;
-        for (int it = 0; it <= kMaxRefine && !s_use64; ++it) {
-            if (it > 0) {   // residual v - S x in FP64, four threads per row
+        for (int it = 0; it <= kMaxRefine && s_next; ++it) {
+            if (it > 0) {
                 const int qk = tid & 3;
                 for (int base = 0; base < n; base += kSolveThreads / 4) {
                     const int i = base + (tid >> 2);
@@ -1866,48 +1971,34 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const Prob *__rest
                 }
                 __syncthreads();
             }
-            solve_blocked_f32(Sf, RowMajorIdx{ld}, s_rpf, Linv, bf, n, tid);
-            double dmax = 0.0, xmax = 0.0;
-            for (int q = tid; q < n; q += kSolveThreads) {
-                const double d = (double)bf[q];
-                const double xn = x[q] + d;
-                x[q] = xn;
-                dmax = fmax(dmax, fabs(d));
-                xmax = fmax(xmax, fabs(xn));
-            }
+            if (tid < 32) {
+                solve_ldl_warp(Sf, ldf, s_rpf, bf, n, lane);
+                __syncwarp();
+                double dmax = 0.0, xmax = 0.0;
+                for (int q = lane; q < n; q += 32) {
+                    const double d = (double)bf[q];
+                    const double xn = x[q] + d;
+                    x[q] = xn;
+                    dmax = fmax(dmax, fabs(d));
+                    xmax = fmax(xmax, fabs(xn));
+                }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                dmax = fmax(dmax, shfl_double(dmax, lane ^ o));
-                xmax = fmax(xmax, shfl_double(xmax, lane ^ o));
+                for (int o = 16; o > 0; o >>= 1) {
+                    dmax = fmax(dmax, shfl_double(dmax, lane ^ o));
+                    xmax = fmax(xmax, shfl_double(xmax, lane ^ o));
+                }
+                if (lane == 0) {
+                    int next = 1;
+                    if (!(dmax <= 1e300)) { s_use64 = 1; next = 0; }                    // non-finite
+                    else if (it > 0 && (dmax <= kRefineTol * xmax || (it == 1 && dmax <= 1e-4 * xmax))) next = 0;
+                    else if (it > 1 && !(dmax <= 0.5 * prev)) { s_use64 = 1; next = 0; }   // not contracting
+                    else if (it == kMaxRefine) { s_use64 = 1; next = 0; }
+                    s_next = next;
+                }
+                prev = dmax;
             }
-            if (lane == 0) { s_red[tid >> 5][0] = dmax; s_red[tid >> 5][1] = xmax; }
-            __syncthreads();
-            dmax = 0.0; xmax = 0.0;
-#pragma unroll
-            for (int w = 0; w < kSolveThreads / 32; ++w) {
-                dmax = fmax(dmax, s_red[w][0]);
-                xmax = fmax(xmax, s_red[w][1]);
-            }
-            if (!(dmax <= 1e300)) {                                 // non-finite: hand to FP64
-                if (tid == 0) s_use64 = 1;
-                __syncthreads();
-                break;
-            }
-            if (it > 0 && dmax <= kRefineTol * xmax) break;         // converged (same in every thread)
-            if (it > 1 && !(dmax <= 0.5 * prev)) {                  // not contracting
-                if (tid == 0) s_use64 = 1;
-                __syncthreads();
-                break;
-            }
-            if (it == kMaxRefine) {
-                if (tid == 0) s_use64 = 1;
-                __syncthreads();
-                break;
-            }
-            prev = dmax;
             __syncthreads();
         }
-        __syncthreads();
         if (!s_use64)
             for (int q = tid; q < n; q += kSolveThreads) v[q] = x[q];
         __syncthreads();
