@@ -749,24 +749,31 @@ def plain_n8_bench(stream, n=200, warmup=10, seed=20_000):
         b_.record(stream)
     torch.cuda.synchronize()
     lat = np.array([a.elapsed_time(b_) for a, b_ in ev])
+    split = kernel_split(solver, subsets[:20], stream)
+    solver.close()
+    return {"workload": "8 frames x 64 patches (512), all frames connected (4,096 edges), poses 0-1 fixed, "
+                        "2 GN iterations; one problem per call",
+            "solves": n, "latency_ms_p50": float(np.percentile(lat, 50)),
+            "latency_ms_p99": float(np.percentile(lat, 99)), **split}
+
+
+def kernel_split(solver, subsets, stream):
+    """Median device time of each kernel kind over one-problem solves of
+    `subsets`, each launch bracketed by CUDA events on `stream`."""
+    import torch
     solver.set_timing(True)
     solver.timing()
-    for d_, p_ in subsets[:20]:
+    for d_, p_ in subsets:
         solver.solve_arrays(d_, p_, 1, stream)
     torch.cuda.synchronize()
-    launches = solver.timing(cap=256)
+    launches = solver.timing(cap=64 * len(subsets))
     solver.set_timing(False)
-    solver.close()
     names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub"}
     kinds = {}
     for k, v in launches:
         kinds.setdefault(names.get(int(k), str(k)), []).append(v)
-    return {"workload": "8 frames x 64 patches (512), all frames connected (4,096 edges), poses 0-1 fixed, "
-                        "2 GN iterations; one problem per call",
-            "solves": n, "latency_ms_p50": float(np.percentile(lat, 50)),
-            "latency_ms_p99": float(np.percentile(lat, 99)),
-            "kernel_ms_per_launch": {k: float(np.median(v)) for k, v in kinds.items()},
-            "kernel_launches_per_solve": {k: len(v) // 20 for k, v in kinds.items()}}
+    return {"kernel_ms_per_launch": {k: float(np.median(v)) for k, v in kinds.items()},
+            "kernel_launches_per_solve": {k: len(v) // len(subsets) for k, v in kinds.items()}}
 
 
 def main():
@@ -915,7 +922,8 @@ def main():
     tp1.record(stream)
     torch.cuda.synchronize()
     plain_lat = np.array([a.elapsed_time(b_) for a, b_ in ev])
-    plain_value = args.plain / (tp0.elapsed_time(tp1) / 1e3)
+    plain_value = args.plain / (tp0.elapsed_time(tp1) / 1e3) if args.plain > 0 else None
+    plain_split = kernel_split(solver, subsets[:20], stream) if args.plain > 0 else {}
 
     # ---- end to end through the host-buffer entry point
     hbatch = ba.PackedBatch(scenes, "pinned")
@@ -996,8 +1004,10 @@ def main():
                                  "device-to-device copy inside the timed region")},
             "batched": {"solves_per_s": value, "latency_ms_p50": float(np.percentile(step_times, 50)),
                         "latency_ms_p99": float(np.percentile(step_times, 99))},
-            "plain": {"solves_per_s": plain_value, "latency_ms_p50": float(np.percentile(plain_lat, 50)),
-                      "latency_ms_p99": float(np.percentile(plain_lat, 99)), "solves": args.plain},
+            "plain": ({"solves_per_s": plain_value, "latency_ms_p50": float(np.percentile(plain_lat, 50)),
+                       "latency_ms_p99": float(np.percentile(plain_lat, 99)), "solves": args.plain,
+                       **plain_split}
+                      if args.plain > 0 else None),
             "plain_n8": plain_n8,
             "kernels": kern,
             "roofline": roof,

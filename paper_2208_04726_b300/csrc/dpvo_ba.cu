@@ -10,6 +10,7 @@
 #include "ba_common.cuh"
 #include "kernels.cuh"
 #include "solve_large.cuh"
+#include "solve_warp.cuh"
 #include "assemble_tc.cuh"
 #include "assemble.cuh"
 #include "backward.cuh"
@@ -40,6 +41,7 @@ struct Layout {
     int n_lin_items = 0, n_asm_items = 0;
     int final_slices = 1;          // y extent of the last back-substitution's grid
     size_t lin_smem = 0, solve_smem = 0, asm_smem = 0;
+    size_t sw_smem = 0;            // solve_warp_kernel (forward solves of at most kFusedMaxFree free poses)
 };
 
 // solve_kernel shared memory: S and its FP32 copy (n x (n+1)), v, x, the FP32 right-hand side,
@@ -70,11 +72,19 @@ static void launch_assembly(const Layout &L, cudaStream_t stream, const Prob *pr
                                                                                erow_len(L.nf_max));
 }
 
+// The forward reduced solve of at most kFusedMaxFree free poses: one CTA per
+// problem, the rows per lane set by the largest problem (nf_max).
+static void launch_solve_warp(int nf_max, int n, cudaStream_t stream, const Prob *probs, int t, size_t smem) {
+    if (sw_rows(nf_max) == 2) solve_warp_kernel<2><<<n, kSwThreads, smem, stream>>>(probs, t);
+    else solve_warp_kernel<3><<<n, kSwThreads, smem, stream>>>(probs, t);
+}
+
 // Reduced solve launch, in the batch's variant.
 static void launch_solve(const Layout &L, int n, cudaStream_t stream, const Prob *probs, int t, double *S_out,
                          double *v_out) {
     if (L.ext) solve_large_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
-    else solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
+    else if (S_out) solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
+    else launch_solve_warp(L.nf_max, n, stream, probs, t, L.sw_smem);
 }
 
 // The bounded mbarrier wait of the pipelined kernels, on a phase that completes
@@ -154,6 +164,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     L.ext = L.nf_max > kFusedMaxFree;
     L.tc_asm = L.ext && cfg.schur_tf32;
     L.solve_smem = L.ext ? solve_large_smem_bytes(L.nf_max) : solve_smem_bytes(L.nf_max);
+    L.sw_smem = L.ext ? 0 : sw_smem_bytes(L.nf_max);
     L.asm_smem = !L.ext ? 0
                  : L.tc_asm ? atc_smem_bytes(erow_len(L.nf_max))
                             : asm_smem_bytes(erow_len(L.nf_max), asm_threads(L.nf_max));
@@ -319,6 +330,11 @@ static int set_kernel_attrs(int device) {
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(solve_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(solve_warp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sw_smem_bytes(kFusedMaxFree)) != cudaSuccess ||
+        cudaFuncSetAttribute(solve_warp_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sw_smem_bytes(kFusedMaxFree)) != cudaSuccess)
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(schur_assembly_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
@@ -1338,7 +1354,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     int G_cap = 64;
     while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes > kLinSmemBudget) G_cap -= 8;
     const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes;
-    const size_t solve_smem = solve_smem_bytes(nf);
+    const size_t solve_smem = sw_smem_bytes(nf);
     Prob p;
     std::memset(&p, 0, sizeof(Prob));
     p.poses = prob->poses; p.patches = prob->patches; p.anchor = prob->anchor; p.kk = prob->kk;
@@ -1383,7 +1399,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_prob);
     for (int t = 0; t < d.n_iters; ++t) {
         launch_linearize(lay, p.n_items, stream, d_prob, d_items, t, 0);
-        solve_kernel<<<1, kSolveThreads, solve_smem, stream>>>(d_prob, t, nullptr, nullptr);
+        launch_solve_warp(nf, 1, stream, d_prob, t, solve_smem);
     }
     launch_final(lay, 1, stream, d_prob, d.n_iters);
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;

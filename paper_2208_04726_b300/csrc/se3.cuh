@@ -1,5 +1,5 @@
 // Device-side SE(3) helpers: quaternion -> rotation, relative poses, the
-// group exponential in FP64 for the pose update.  Poses are world->camera,
+// group exponential for the pose update.  Poses are world->camera,
 // stored [tx ty tz qx qy qz qw]; increments are left twists (v, w).
 #pragma once
 
@@ -47,72 +47,72 @@ __device__ inline void adjoint6(const float *R, const float *t, float *Ad) {
         }
 }
 
-// T <- Exp(xi) T in FP64 for xi = (v, w):
+// T <- Exp(xi) T for xi = (v, w):
 //   Exp(xi) = [[R(w), V(w) v], [0, 1]],  R(w) = exp([w]x),
 //   V(w) = I + (1 - cos th)/th^2 [w]x + (th - sin th)/th^3 [w]x^2,  th = |w|;
-// quaternion of R(w) = (sin(th/2) w/th, cos(th/2)).
-// The scalar coefficients come from FP32 (sincosf, or Taylor series below
-// th = 0.1; (1 - cos th)/th^2 as 2 (sin(th/2)/th)^2, free of cancellation):
-// their rounding enters the pose only multiplied by th or th^2, and the
-// increment's quaternion is renormalised in FP64.  The composition is FP64.
+// quaternion of R(w) = q = (sin(th/2) w/th, cos(th/2)).
+// FP32, in increment form: every output coordinate is the stored coordinate
+// plus a correction that is small for a Gauss-Newton step and is formed with
+// FP32 relative accuracy, so the result is rounded once, as if the
+// composition were exact and then stored:
+//   t' = t + [(R - I) t + V v],  R - I from q without the "1 -" cancellation;
+//   q' = b + [(q - 1) (x) b - (eta/2) b],  q - 1 = (q_v, cos(th/2) - 1),
+// where eta = |q (x) b|^2 - 1 (the stored quaternion's norm error) makes q'
+// unit to first order.  The scalar coefficients are Taylor series below th =
+// 0.1, else from sincosf (cos(th/2) - 1 as -sin^2(th/2) / (1 + cos(th/2)),
+// free of cancellation).
 __device__ inline void se3_left_update(const double *xi, const float *pose_in, float *pose_out) {
-    const double v0 = xi[0], v1 = xi[1], v2 = xi[2];
-    const double w0 = xi[3], w1 = xi[4], w2 = xi[5];
-    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-    const float th2f = (float)th2, tf = sqrtf(th2f);
-    float hs, hc, bf;   // sin(th/2)/th, cos(th/2), (th - sin th)/th^3
+    const float v0 = (float)xi[0], v1 = (float)xi[1], v2 = (float)xi[2];
+    const float w0 = (float)xi[3], w1 = (float)xi[4], w2 = (float)xi[5];
+    const float th2 = w0 * w0 + w1 * w1 + w2 * w2, tf = sqrtf(th2);
+    float hs, hcm1, B;   // sin(th/2)/th, cos(th/2) - 1, (th - sin th)/th^3
     if (tf < 0.1f) {
-        hs = 0.5f + th2f * (-1.f / 48.f + th2f * (1.f / 3840.f - th2f * (1.f / 645120.f)));
-        hc = 1.f + th2f * (-1.f / 8.f + th2f * (1.f / 384.f - th2f * (1.f / 46080.f)));
-        bf = 1.f / 6.f + th2f * (-1.f / 120.f + th2f * (1.f / 5040.f - th2f * (1.f / 362880.f)));
+        hs = 0.5f + th2 * (-1.f / 48.f + th2 * (1.f / 3840.f - th2 * (1.f / 645120.f)));
+        hcm1 = th2 * (-1.f / 8.f + th2 * (1.f / 384.f - th2 * (1.f / 46080.f)));
+        B = 1.f / 6.f + th2 * (-1.f / 120.f + th2 * (1.f / 5040.f - th2 * (1.f / 362880.f)));
     } else {
         float s2, c2;
         sincosf(0.5f * tf, &s2, &c2);
         hs = s2 / tf;
-        hc = c2;
-        bf = (tf - 2.f * s2 * c2) / (th2f * tf);
+        hcm1 = -s2 * s2 / (1.f + c2);
+        B = (tf - 2.f * s2 * c2) / (th2 * tf);
     }
-    const double half_s0 = hs, half_c0 = hc, B = bf;
-    // renormalise (half_s0 w, half_c0): its squared norm is 1 to within FP32
-    // rounding, where 1.5 - s/2 approximates s^-1/2 to (3/8)(s - 1)^2
-    const double sn = half_s0 * half_s0 * th2 + half_c0 * half_c0;
-    const double nrm = 1.5 - 0.5 * sn;
-    const double half_s = half_s0 * nrm, half_c = half_c0 * nrm;
-    const double A = 2.0 * half_s * half_s;   // (1 - cos th)/th^2
-    // quaternion of the increment
-    const double qx = half_s * w0, qy = half_s * w1, qz = half_s * w2, qw = half_c;
-    // rotation matrix of the increment from its quaternion
-    double R[9];
-    R[0] = 1 - 2 * (qy * qy + qz * qz); R[1] = 2 * (qx * qy - qz * qw);     R[2] = 2 * (qx * qz + qy * qw);
-    R[3] = 2 * (qx * qy + qz * qw);     R[4] = 1 - 2 * (qx * qx + qz * qz); R[5] = 2 * (qy * qz - qx * qw);
-    R[6] = 2 * (qx * qz - qy * qw);     R[7] = 2 * (qy * qz + qx * qw);     R[8] = 1 - 2 * (qx * qx + qy * qy);
+    const float A = 2.f * hs * hs;   // (1 - cos th)/th^2
+    const float qx = hs * w0, qy = hs * w1, qz = hs * w2, qw = 1.f + hcm1;
+    // R - I of the increment (unit quaternion form)
+    const float E0 = -2.f * (qy * qy + qz * qz), E1 = 2.f * (qx * qy - qz * qw), E2 = 2.f * (qx * qz + qy * qw);
+    const float E3 = 2.f * (qx * qy + qz * qw), E4 = -2.f * (qx * qx + qz * qz), E5 = 2.f * (qy * qz - qx * qw);
+    const float E6 = 2.f * (qx * qz - qy * qw), E7 = 2.f * (qy * qz + qx * qw), E8 = -2.f * (qx * qx + qy * qy);
     // V v = v + A (w x v) + B (w x (w x v))
-    const double c0 = w1 * v2 - w2 * v1, c1 = w2 * v0 - w0 * v2, c2 = w0 * v1 - w1 * v0;
-    const double d0 = w1 * c2 - w2 * c1, d1 = w2 * c0 - w0 * c2, d2 = w0 * c1 - w1 * c0;
-    const double tv0 = v0 + A * c0 + B * d0, tv1 = v1 + A * c1 + B * d1, tv2 = v2 + A * c2 + B * d2;
-    const double t0 = pose_in[0], t1 = pose_in[1], t2 = pose_in[2];
-    const double nt0 = R[0] * t0 + R[1] * t1 + R[2] * t2 + tv0;
-    const double nt1 = R[3] * t0 + R[4] * t1 + R[5] * t2 + tv1;
-    const double nt2 = R[6] * t0 + R[7] * t1 + R[8] * t2 + tv2;
-    // q_new = q_inc (x) q_old  (Hamilton product, vector part first)
-    const double bx = pose_in[3], by = pose_in[4], bz = pose_in[5], bw = pose_in[6];
-    double nx = qw * bx + bw * qx + (qy * bz - qz * by);
-    double ny = qw * by + bw * qy + (qz * bx - qx * bz);
-    double nz = qw * bz + bw * qz + (qx * by - qy * bx);
-    double nw = qw * bw - (qx * bx + qy * by + qz * bz);
-    // the stored quaternion is unit to within FP32 rounding: one Newton step
-    // from 1.5 - s/2; other norms take the exact root
-    const double qs = nx * nx + ny * ny + nz * nz + nw * nw;
-    double inv;
-    if (fabs(qs - 1.0) < 1e-4) {
-        const double y = 1.5 - 0.5 * qs;
-        inv = y * (1.5 - 0.5 * qs * y * y);
-    } else {
-        inv = 1.0 / sqrt(qs);
+    const float c0 = w1 * v2 - w2 * v1, c1 = w2 * v0 - w0 * v2, c2 = w0 * v1 - w1 * v0;
+    const float d0 = w1 * c2 - w2 * c1, d1 = w2 * c0 - w0 * c2, d2 = w0 * c1 - w1 * c0;
+    const float t0 = pose_in[0], t1 = pose_in[1], t2 = pose_in[2];
+    pose_out[0] = t0 + (E0 * t0 + E1 * t1 + E2 * t2 + (v0 + A * c0 + B * d0));
+    pose_out[1] = t1 + (E3 * t0 + E4 * t1 + E5 * t2 + (v1 + A * c1 + B * d1));
+    pose_out[2] = t2 + (E6 * t0 + E7 * t1 + E8 * t2 + (v2 + A * c2 + B * d2));
+    // q' = q (x) b (Hamilton product, vector part first), as b + the correction
+    const float bx = pose_in[3], by = pose_in[4], bz = pose_in[5], bw = pose_in[6];
+    const float dx = hcm1 * bx + bw * qx + (qy * bz - qz * by);
+    const float dy = hcm1 * by + bw * qy + (qz * bx - qx * bz);
+    const float dz = hcm1 * bz + bw * qz + (qx * by - qy * bx);
+    const float dw = hcm1 * bw - (qx * bx + qy * by + qz * bz);
+    // eta = |b|^2 (1 + e) - 1, e = |q|^2 - 1 = th2 hs^2 + hcm1 (2 + hcm1)
+    const float e = th2 * hs * hs + hcm1 * (2.f + hcm1);
+    const float nb = fmaf(bx, bx, fmaf(by, by, fmaf(bz, bz, fmaf(bw, bw, -1.f))));
+    const float h = 0.5f * (nb + e + nb * e);
+    if (fabsf(h) < 1e-5f) {          // first order in eta: error below 3/8 eta^2
+        pose_out[3] = bx + (dx - h * bx);
+        pose_out[4] = by + (dy - h * by);
+        pose_out[5] = bz + (dz - h * bz);
+        pose_out[6] = bw + (dw - h * bw);
+    } else {                         // a stored quaternion far from unit norm
+        const float nx = bx + dx, ny = by + dy, nz = bz + dz, nw = bw + dw;
+        const float inv = 1.f / sqrtf(nx * nx + ny * ny + nz * nz + nw * nw);
+        pose_out[3] = nx * inv;
+        pose_out[4] = ny * inv;
+        pose_out[5] = nz * inv;
+        pose_out[6] = nw * inv;
     }
-    pose_out[0] = (float)nt0; pose_out[1] = (float)nt1; pose_out[2] = (float)nt2;
-    pose_out[3] = (float)(nx * inv); pose_out[4] = (float)(ny * inv);
-    pose_out[5] = (float)(nz * inv); pose_out[6] = (float)(nw * inv);
 }
 
 }  // namespace dpvo
