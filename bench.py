@@ -212,7 +212,8 @@ def stress_bench(n_sessions, steps, stream, hbm_peak, tf32=False):
     kinds = {}
     for k, v in launches:
         kinds.setdefault(int(k), []).append(v)
-    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub"}
+    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub",
+             5: "partials_sum"}
     kern = {names[k] + "_ms": float(np.mean(v)) for k, v in kinds.items() if k in names}
     kern.update({names[k] + "_launches_per_step": len(v) // steps for k, v in kinds.items() if k in names})
     sc = distinct[0]
@@ -768,7 +769,8 @@ def kernel_split(solver, subsets, stream):
     torch.cuda.synchronize()
     launches = solver.timing(cap=64 * len(subsets))
     solver.set_timing(False)
-    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub"}
+    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub",
+             5: "partials_sum"}
     kinds = {}
     for k, v in launches:
         kinds.setdefault(names.get(int(k), str(k)), []).append(v)
@@ -860,17 +862,18 @@ def main():
         t = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms = float(t.item())
-    n_launch_per_solve = 1 + 3 + 2
+    # one timing record per kernel launch: the launches of a step, and the
+    # kernels' device times by kind (0 plan, 1 linearise/Schur, 2 reduced
+    # solve, 4 last back-substitution, 5 partials summed into one)
+    n_launch_per_solve = len(launches) // args.steps
     value = world * B * args.steps / (elapsed_ms / 1e3)
-
-    # per-kernel times: per solve [plan, lin t0, solve, lin t1, solve, lin t2 (back-substitution only)]
-    lin_full, lin_bs, sol, plan = [], [], [], []
-    for s in range(len(launches) // n_launch_per_solve):
-        seq = launches[s * n_launch_per_solve:(s + 1) * n_launch_per_solve]
-        plan.append(seq[0][1]); lin_full += [seq[1][1], seq[3][1]]; sol += [seq[2][1], seq[4][1]]
-        lin_bs.append(seq[5][1])
-    kern = {"plan_ms": float(np.mean(plan)), "linearize_schur_ms": float(np.mean(lin_full)),
-            "backsub_final_ms": float(np.mean(lin_bs)), "reduce_cholesky_ms": float(np.mean(sol))}
+    by_kind = {}
+    for k, ms in launches:
+        by_kind.setdefault(k, []).append(ms)
+    kern = {"plan_ms": float(np.mean(by_kind[0])), "linearize_schur_ms": float(np.mean(by_kind[1])),
+            "backsub_final_ms": float(np.mean(by_kind[4])),
+            "reduce_cholesky_ms": float(np.mean(by_kind[2])) + (float(np.mean(by_kind[5])) if 5 in by_kind else 0.0),
+            "launches_per_step": n_launch_per_solve}
     step_ms = elapsed_ms / args.steps
     kern["share_linearize_schur"] = 2 * kern["linearize_schur_ms"] / step_ms
     kern["share_reduce_cholesky"] = 2 * kern["reduce_cholesky_ms"] / step_ms

@@ -35,6 +35,7 @@ struct Layout {
     std::vector<Item> items;       // linearise work items, then assembly work items
     size_t bytes = 0, off_probs = 0, off_items = 0;
     int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0, n_max = 1;
+    int max_parts = 1;             // Schur partials of the problem with the most
     bool tc = false;               // Schur accumulation on the tensor cores
     bool ext = false;              // more than kFusedMaxFree free poses: assembly kernel, packed solve
     bool tc_asm = false;           // ext with the TF32 Schur mode: the assembly on the tensor cores
@@ -72,8 +73,23 @@ static void launch_assembly(const Layout &L, cudaStream_t stream, const Prob *pr
                                                                                erow_len(L.nf_max));
 }
 
-// The forward reduced solve of at most kFusedMaxFree free poses: one CTA per
-// problem, the rows per lane set by the largest problem (nf_max).
+// The plan launch: more edge loads in flight per thread for batches smaller
+// than the SM count.
+static void launch_plan(int n, int num_sms, cudaStream_t stream, const Prob *probs) {
+    if (n >= num_sms) plan_kernel<1><<<n, kPlanThreads, 0, stream>>>(probs);
+    else plan_kernel<4><<<n, kPlanThreads, 0, stream>>>(probs);
+}
+
+// Whether the forward reduced solve needs its partials summed into one part
+// first (some problem has free poses and several partials), and that launch.
+static bool needs_reduce(bool ext, int max_parts, int nf_max) { return !ext && max_parts > 1 && nf_max > 0; }
+static void launch_reduce(int nf_max, int n, cudaStream_t stream, const Prob *probs, int t) {
+    const dim3 grid((partial_len(nf_max) + kPrThreads - 1) / kPrThreads, n);
+    partials_reduce_kernel<<<grid, kPrThreads, 0, stream>>>(probs, t);
+}
+
+// The forward reduced solve of at most kFusedMaxFree free poses, from summed
+// partials: one CTA per problem, the rows per lane set by the largest problem.
 static void launch_solve_warp(int nf_max, int n, cudaStream_t stream, const Prob *probs, int t, size_t smem) {
     if (sw_rows(nf_max) == 2) solve_warp_kernel<2><<<n, kSwThreads, smem, stream>>>(probs, t);
     else solve_warp_kernel<3><<<n, kSwThreads, smem, stream>>>(probs, t);
@@ -84,7 +100,7 @@ static void launch_solve(const Layout &L, int n, cudaStream_t stream, const Prob
                          double *v_out) {
     if (L.ext) solve_large_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
     else if (S_out) solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
-    else launch_solve_warp(L.nf_max, n, stream, probs, t, L.sw_smem);
+    else launch_solve_warp(L.nf_max, n, stream, probs, t, L.sw_smem);   // after launch_reduce
 }
 
 // The bounded mbarrier wait of the pipelined kernels, on a phase that completes
@@ -201,6 +217,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
             p.n_asm = std::max(1, std::min(per, est_chunks));
         }
         p.n_parts = L.ext ? p.n_items + p.n_asm : p.n_items;   // one partial per linearise CTA
+        L.max_parts = std::max(L.max_parts, p.n_parts);
         // workspace offsets (rebased to device pointers later)
         auto take = [&](size_t bytes) { size_t o = off; off = al256(off + bytes); return o; };
         p.seg = (int32_t *)(uintptr_t)take((size_t)(d.n_patches + 1) * 4);
@@ -248,16 +265,22 @@ T *rebase(T *off, char *base) { return reinterpret_cast<T *>(base + (uintptr_t)o
 
 }  // namespace
 
+constexpr int kStageRing = 4;
+
 struct dpvo_ba_handle {
     dpvo_ba_config cfg;
     int device = 0;
     int num_sms = 148;
     char *ws = nullptr;
     size_t ws_cap = 0;
-    char *stage = nullptr;          // pinned host staging for descriptors
-    size_t stage_cap = 0;
-    cudaEvent_t stage_done = nullptr;
-    bool stage_pending = false;
+    // page-locked host staging of the descriptors, a ring of buffers used in
+    // turn: a call waits only for the copy out of the buffer it reuses, so
+    // that the host can enqueue solves ahead of the device
+    char *stage[kStageRing] = {};
+    size_t stage_cap[kStageRing] = {};
+    cudaEvent_t stage_done[kStageRing] = {};
+    bool stage_pending[kStageRing] = {};
+    int stage_next = 0;
     char *io = nullptr;             // device staging for dpvo_ba_solve_host
     size_t io_cap = 0;
     std::vector<Prob> last;         // descriptors of the last solve (for dpvo_ba_iterate)
@@ -295,20 +318,34 @@ static int grow_device(char **buf, size_t *cap, size_t need) {
     return DPVO_BA_OK;
 }
 
-static int grow_stage(dpvo_ba_handle *h, size_t need) {
-    if (h->stage_pending) {
-        if (cudaEventSynchronize(h->stage_done) != cudaSuccess) return DPVO_BA_ECUDA;
-        h->stage_pending = false;
+// The next staging buffer of the ring, at least `need` bytes, once the copy
+// out of it (the call kStageRing calls ago) has completed.
+static int take_stage(dpvo_ba_handle *h, size_t need, char **out) {
+    const int i = h->stage_next;
+    if (h->stage_pending[i]) {
+        if (cudaEventSynchronize(h->stage_done[i]) != cudaSuccess) return DPVO_BA_ECUDA;
+        h->stage_pending[i] = false;
     }
-    if (need <= h->stage_cap) return DPVO_BA_OK;
-    if (h->stage) cudaFreeHost(h->stage);
-    h->stage = nullptr;
-    h->stage_cap = 0;
-    if (cudaMallocHost((void **)&h->stage, need * 2) != cudaSuccess) {
-        cudaGetLastError();
-        return DPVO_BA_ENOMEM;
+    if (need > h->stage_cap[i]) {
+        if (h->stage[i]) cudaFreeHost(h->stage[i]);
+        h->stage[i] = nullptr;
+        h->stage_cap[i] = 0;
+        if (cudaMallocHost((void **)&h->stage[i], need * 2) != cudaSuccess) {
+            cudaGetLastError();
+            return DPVO_BA_ENOMEM;
+        }
+        h->stage_cap[i] = need * 2;
     }
-    h->stage_cap = need * 2;
+    *out = h->stage[i];
+    return DPVO_BA_OK;
+}
+
+// After the copy out of the current staging buffer was enqueued on `stream`.
+static int release_stage(dpvo_ba_handle *h, cudaStream_t stream) {
+    const int i = h->stage_next;
+    if (cudaEventRecord(h->stage_done[i], stream) != cudaSuccess) return DPVO_BA_ECUDA;
+    h->stage_pending[i] = true;
+    h->stage_next = (i + 1) % kStageRing;
     return DPVO_BA_OK;
 }
 
@@ -355,7 +392,8 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     int rc = grow_device(&h->ws, &h->ws_cap, L.bytes);
     if (rc) return rc;
     const size_t desc_bytes = L.bytes - L.off_probs;
-    rc = grow_stage(h, desc_bytes);
+    char *stage = nullptr;
+    rc = take_stage(h, desc_bytes, &stage);
     if (rc) return rc;
     for (int b = 0; b < n; ++b) {
         Prob &p = L.probs[b];
@@ -375,12 +413,11 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         if (p.sglob) p.sglob = rebase(p.sglob, h->ws);
     }
     h->last = L.probs;
-    std::memcpy(h->stage, L.probs.data(), sizeof(Prob) * n);
-    std::memcpy(h->stage + (L.off_items - L.off_probs), L.items.data(), sizeof(Item) * L.items.size());
-    if (cudaMemcpyAsync(h->ws + L.off_probs, h->stage, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    std::memcpy(stage, L.probs.data(), sizeof(Prob) * n);
+    std::memcpy(stage + (L.off_items - L.off_probs), L.items.data(), sizeof(Item) * L.items.size());
+    if (cudaMemcpyAsync(h->ws + L.off_probs, stage, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return DPVO_BA_ECUDA;
-    if (cudaEventRecord(h->stage_done, stream) != cudaSuccess) return DPVO_BA_ECUDA;
-    h->stage_pending = true;
+    if ((rc = release_stage(h, stream))) return rc;
 
     const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
@@ -397,7 +434,7 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         }
         return DPVO_BA_OK;
     };
-    if ((rc = timed(0, [&] { plan_kernel<<<n, kPlanThreads, 0, stream>>>(d_probs); }))) return rc;
+    if ((rc = timed(0, [&] { launch_plan(n, h->num_sms, stream, d_probs); }))) return rc;
     const Item *d_asm_items = d_items + L.n_lin_items;
     if (S_out) {
         launch_linearize(L, n_items, stream, d_probs, d_items, 0, 0);
@@ -411,6 +448,10 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
             if (t < L.iters_max) {
                 if (L.ext) {
                     rc = timed(3, [&] { launch_assembly(L, stream, d_probs, d_asm_items, t); });
+                    if (rc) return rc;
+                }
+                if (needs_reduce(L.ext, L.max_parts, L.nf_max)) {
+                    rc = timed(5, [&] { launch_reduce(L.nf_max, n, stream, d_probs, t); });
                     if (rc) return rc;
                 }
                 rc = timed(2, [&] { launch_solve(L, n, stream, d_probs, t, nullptr, nullptr); });
@@ -432,7 +473,8 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
     int rc = grow_device(&h->ws, &h->ws_cap, L.bytes);
     if (rc) return rc;
     const size_t desc_bytes = L.bytes - L.off_probs;
-    rc = grow_stage(h, desc_bytes);
+    char *stage = nullptr;
+    rc = take_stage(h, desc_bytes, &stage);
     if (rc) return rc;
     for (int b = 0; b < n; ++b) {
         Prob &p = L.probs[b];
@@ -462,17 +504,16 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
         p.pgrad = rebase(p.pgrad, h->ws);
     }
     h->last = L.probs;
-    std::memcpy(h->stage, L.probs.data(), sizeof(Prob) * n);
-    std::memcpy(h->stage + (L.off_items - L.off_probs), L.items.data(), sizeof(Item) * L.items.size());
-    if (cudaMemcpyAsync(h->ws + L.off_probs, h->stage, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    std::memcpy(stage, L.probs.data(), sizeof(Prob) * n);
+    std::memcpy(stage + (L.off_items - L.off_probs), L.items.data(), sizeof(Item) * L.items.size());
+    if (cudaMemcpyAsync(h->ws + L.off_probs, stage, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return DPVO_BA_ECUDA;
-    if (cudaEventRecord(h->stage_done, stream) != cudaSuccess) return DPVO_BA_ECUDA;
-    h->stage_pending = true;
+    if ((rc = release_stage(h, stream))) return rc;
     const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
     const int n_items = L.n_lin_items;
     const size_t bw_smem = bw_smem_layout(L.W_cap, L.G_cap, L.n_max).bytes;
-    plan_kernel<<<n, kPlanThreads, 0, stream>>>(d_probs);
+    launch_plan(n, h->num_sms, stream, d_probs);
     for (int t = 0; t < L.iters_max; ++t) {
         launch_linearize(L, n_items, stream, d_probs, d_items, t, 0);
         solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
@@ -525,10 +566,19 @@ int dpvo_ba_create(const dpvo_ba_config *cfg, dpvo_ba_handle **out) {
     if (cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
         cudaGetLastError(); delete h; return DPVO_BA_ECUDA;
     }
-    if (cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError(); delete h; return DPVO_BA_ECUDA;
+    for (int i = 0; i < kStageRing; ++i) {
+        if (cudaEventCreateWithFlags(&h->stage_done[i], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            for (int k = 0; k < i; ++k) cudaEventDestroy(h->stage_done[k]);
+            delete h;
+            return DPVO_BA_ECUDA;
+        }
     }
-    if (set_kernel_attrs(h->device)) { cudaEventDestroy(h->stage_done); delete h; return DPVO_BA_ECUDA; }
+    if (set_kernel_attrs(h->device)) {
+        for (int i = 0; i < kStageRing; ++i) cudaEventDestroy(h->stage_done[i]);
+        delete h;
+        return DPVO_BA_ECUDA;
+    }
     *out = h;
     return DPVO_BA_OK;
 }
@@ -539,8 +589,10 @@ int dpvo_ba_destroy(dpvo_ba_handle *h) {
     cudaDeviceSynchronize();
     if (h->ws) cudaFree(h->ws);
     if (h->io) cudaFree(h->io);
-    if (h->stage) cudaFreeHost(h->stage);
-    if (h->stage_done) cudaEventDestroy(h->stage_done);
+    for (int i = 0; i < kStageRing; ++i) {
+        if (h->stage[i]) cudaFreeHost(h->stage[i]);
+        if (h->stage_done[i]) cudaEventDestroy(h->stage_done[i]);
+    }
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     delete h;
     return DPVO_BA_OK;
@@ -554,7 +606,12 @@ int dpvo_ba_reserve(dpvo_ba_handle *h, const dpvo_ba_dims *max_dims, int n_probl
     std::vector<dpvo_ba_dims> all(n_problems, d);
     Layout L = make_layout(all.data(), n_problems, h->num_sms, h->cfg);
     if (int rc = grow_device(&h->ws, &h->ws_cap, L.bytes)) return rc;
-    return grow_stage(h, L.bytes - L.off_probs);
+    for (int i = 0; i < kStageRing; ++i) {   // every buffer of the ring, in turn
+        char *stage = nullptr;
+        if (int rc = take_stage(h, L.bytes - L.off_probs, &stage)) return rc;
+        h->stage_next = (h->stage_next + 1) % kStageRing;
+    }
+    return DPVO_BA_OK;
 }
 
 int dpvo_ba_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs, int n_problems,
@@ -1396,9 +1453,10 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     lay.lin_smem = lin_smem;
     lay.final_slices = final_slices_of(tc, d.n_patches, p.max_chunks, 65535);
     noalloc_descriptors_kernel<<<1, kThreads, 0, stream>>>(p, p.n_items, d_prob, d_items);
-    plan_kernel<<<1, kPlanThreads, 0, stream>>>(d_prob);
+    launch_plan(1, sms, stream, d_prob);
     for (int t = 0; t < d.n_iters; ++t) {
         launch_linearize(lay, p.n_items, stream, d_prob, d_items, t, 0);
+        if (needs_reduce(false, p.n_parts, nf)) launch_reduce(nf, 1, stream, d_prob, t);
         launch_solve_warp(nf, 1, stream, d_prob, t, solve_smem);
     }
     launch_final(lay, 1, stream, d_prob, d.n_iters);

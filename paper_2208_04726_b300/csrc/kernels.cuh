@@ -104,9 +104,12 @@ __device__ __forceinline__ void anchor_terms(const EdgeLin &L, const float *Rij,
 // ----------------------------------------------------------------------------
 constexpr int kPlanThreads = 1024;
 constexpr int kPlanUnroll = 4;       // patches per thread with loads in flight together
-constexpr int kPlanQuads = 1;        // 4-edge groups per thread with loads in flight together
-
-__global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__restrict__ probs) {
+// QUADS: 4-edge groups per thread with loads in flight together.  One keeps
+// the kernel within 32 registers (two CTAs per SM, for batches of at least one
+// problem per SM); four take 64 registers and fewer memory round trips (small
+// batches).
+template <int QUADS>
+__global__ void __launch_bounds__(kPlanThreads, QUADS == 1 ? 2 : 1) plan_kernel(const Prob *__restrict__ probs) {
     const Prob &pr = probs[blockIdx.x];
     const int tid = threadIdx.x;
     const int N = pr.N, P = pr.P, E = pr.E;
@@ -184,11 +187,11 @@ __global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__res
         const int tail0 = head + 4 * Q;
         if (tid < head) edge_scalar(tid);
         else if (tid >= 32 && tid - 32 < E - tail0) edge_scalar(tail0 + tid - 32);
-        for (int base = 0; base < Q; base += kPlanQuads * kPlanThreads) {
-            int4 kv[kPlanQuads], jv[kPlanQuads];
-            int kq[kPlanQuads], jq[kPlanQuads];
+        for (int base = 0; base < Q; base += QUADS * kPlanThreads) {
+            int4 kv[QUADS], jv[QUADS];
+            int kq[QUADS], jq[QUADS];
 #pragma unroll
-            for (int u = 0; u < kPlanQuads; ++u) {   // loads of all unrolled quads first
+            for (int u = 0; u < QUADS; ++u) {   // loads of all unrolled quads first
                 const int q = base + u * kPlanThreads + tid;
                 kv[u] = make_int4(0, 0, 0, 0); jv[u] = kv[u]; kq[u] = -1; jq[u] = -1;
                 if (q < Q) {
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__res
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kPlanQuads; ++u) {
+            for (int u = 0; u < QUADS; ++u) {
                 const int q = base + u * kPlanThreads + tid;
                 const int ks = __shfl_up_sync(0xffffffffu, kv[u].w, 1);
                 const int js = __shfl_up_sync(0xffffffffu, jv[u].w, 1);

@@ -57,9 +57,9 @@ __host__ __device__ inline int sw_ldf(int n) { return ((((n + 7) & ~7) - 4 + 31)
 // Shared-memory layout for n = 6 nf (byte offsets, 16-byte aligned): S (FP64,
 // n x (n+1), both triangles), v' and x (FP64), the FP32 factor (n x ldf), the
 // pivot reciprocals, each diagonal block's inverse and its transpose, two
-// FP32 vectors of the solves.
+// FP32 vectors of the solves, each warp's copy of a panel's multipliers.
 struct SwLayout {
-    size_t S, v, x, Sf, rp, Minv, yb, zs, bytes;
+    size_t S, v, x, Sf, rp, Minv, yb, zs, Lc, bytes;
 };
 __host__ __device__ inline SwLayout sw_layout(int nf) {
     const size_t n = 6 * (size_t)nf, n8 = (n + 7) & ~size_t(7), nblk = n8 / kSwBlk;
@@ -72,7 +72,8 @@ __host__ __device__ inline SwLayout sw_layout(int nf) {
     L.Minv = L.rp + n8 * 4;
     L.yb = L.Minv + nblk * 2 * kSwMSize * 4;
     L.zs = L.yb + n8 * 4;
-    L.bytes = L.zs + n8 * 4;
+    L.Lc = L.zs + n8 * 4;
+    L.bytes = L.Lc + (kSwThreads / 32) * n8 * kSwBlk * 4;
     return L;
 }
 __host__ __device__ inline size_t sw_smem_bytes(int nf) { return sw_layout(nf).bytes; }
@@ -116,50 +117,64 @@ __device__ __forceinline__ float sw_rcp(float d) {
     return r;
 }
 
-// Rank-kSwBlk update of columns k..k+KK-1 of my rows in slots u >= KU (no
-// row in a lower slot reaches column k): a_ik -= sum_q a_{i,J+q} l_{k,J+q},
-// with the multipliers l_k of the trailing rows read as broadcast loads.  With
-// KK = 4 (k a multiple of 4) a row's four entries move as one 16-byte access;
-// entries above the diagonal in it are updated too and never read.
-template <int R, int KU, int KK>
-__device__ __forceinline__ void sw_trail_cols(float *Sf, int ldf, int J, int k, int n, int lane,
-                                              const float (&p)[R][kSwBlk]) {
-    float lk[KK][kSwBlk];
+// Rank-kSwBlk update of kw <= 4 consecutive columns k0.. (k0 a multiple of
+// 4) of my rows: a_ik -= sum_q a_{i,J+q} l_{k,J+q}, the multipliers l_k of the
+// trailing rows read from this warp's copy Lw (row k at Lw + kSwBlk k) as
+// broadcast loads.  A full group moves a row's four entries as one 16-byte
+// access; entries above the diagonal in it are updated too and never read.
+template <int R>
+__device__ __forceinline__ void sw_trail_group(float *Sf, int ldf, const float *Lw, int k0, int kw, int n,
+                                               int lane, const float (&p)[R][kSwBlk]) {
+    float lk[4][kSwBlk];
 #pragma unroll
-    for (int kk = 0; kk < KK; ++kk) sw_ld8(Sf + (k + kk) * ldf + J, lk[kk]);
+    for (int kk = 0; kk < 4; ++kk) {
+        if (kk < kw) {
+            sw_ld8(Lw + (k0 + kk) * kSwBlk, lk[kk]);
+        } else {
 #pragma unroll
-    for (int u = KU; u < R; ++u) {
+            for (int q = 0; q < kSwBlk; ++q) lk[kk][q] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
         const int i = lane + 32 * u;
-        if (i < k || i >= n) continue;
-        float *row = Sf + i * ldf + k;
-        float a[KK];
-        if constexpr (KK == 4) {
+        if (i < k0 || i >= n) continue;
+        float *row = Sf + i * ldf + k0;
+        float a[4];
+        if (kw == 4) {
             const float4 a4 = *reinterpret_cast<const float4 *>(row);
             a[0] = a4.x; a[1] = a4.y; a[2] = a4.z; a[3] = a4.w;
         } else {
 #pragma unroll
-            for (int kk = 0; kk < KK; ++kk) a[kk] = row[kk];
+            for (int kk = 0; kk < 4; ++kk) a[kk] = kk < kw ? row[kk] : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < kSwBlk; ++q)
 #pragma unroll
-            for (int kk = 0; kk < KK; ++kk) a[kk] = fmaf(-p[u][q], lk[kk][q], a[kk]);
-        if constexpr (KK == 4) {
+            for (int kk = 0; kk < 4; ++kk) a[kk] = fmaf(-p[u][q], lk[kk][q], a[kk]);
+        if (kw == 4) {
             *reinterpret_cast<float4 *>(row) = make_float4(a[0], a[1], a[2], a[3]);
         } else {
 #pragma unroll
-            for (int kk = 0; kk < KK; ++kk) row[kk] = a[kk];
+            for (int kk = 0; kk < 4; ++kk)
+                if (kk < kw) row[kk] = a[kk];
         }
     }
 }
 
-// Step 2, one warp.  Sf (row stride ldf; both triangles on entry, padding
-// columns zero) receives the multipliers l_ij below the diagonal blocks;
-// rp[j] = 1 / d_j; Minv holds, per diagonal block, its inverse M (row-major,
-// stride kSwMLd) and then M^T.  Returns false for a failed pivot (the factor
-// is then incomplete).
+// Step 2, all kSwThreads threads.  Sf (row stride ldf; both triangles on
+// entry, padding columns zero) receives the multipliers l_ij below the
+// diagonal blocks; rp[j] = 1 / d_j; Minv holds, per diagonal block, its
+// inverse M (row-major, stride kSwMLd) and then M^T.  Per panel: every warp
+// factors the diagonal block and eliminates the rows below it (lane l: rows
+// l, l + 32, l + 64), keeping the multipliers in a copy of its own (Lw); each
+// warp then updates every fourth group of 4 trailing columns; one block
+// barrier ends the panel.  Returns false, in every thread, for a failed pivot
+// (the factor is then incomplete).
 template <int R>
-__device__ bool sw_factor(float *Sf, int ldf, float *rp, float *Minv, int n, int lane) {
+__device__ bool sw_factor(float *Sf, int ldf, float *rp, float *Minv, float *Lcopies, int n, int tid) {
+    const int lane = tid & 31, warp = tid >> 5, n8 = (n + 7) & ~7;
+    float *Lw = Lcopies + warp * n8 * kSwBlk;
     for (int J = 0; J < n; J += kSwBlk) {
         const int nb = min(kSwBlk, n - J);
         // the diagonal block in every lane (rows past n padded with the identity)
@@ -186,9 +201,9 @@ __device__ bool sw_factor(float *Sf, int ldf, float *rp, float *Minv, int n, int
 #pragma unroll
                 for (int q2 = q + 1; q2 <= r2; ++q2) a[r2][q2] = fmaf(-a[r2][q], lb[q2][q], a[r2][q2]);
         }
-        if (!ok) return false;                   // the same decision in every lane
-        // my rows below the block: eliminate the panel's columns, store the multipliers
-        float p[R][kSwBlk];
+        if (!ok) return false;                   // the same decision in every thread
+        // my rows below the block: eliminate the panel's columns; multipliers into Lw
+        float p[R][kSwBlk], l[R][kSwBlk];
 #pragma unroll
         for (int u = 0; u < R; ++u) {
             const int i = lane + 32 * u;
@@ -198,51 +213,48 @@ __device__ bool sw_factor(float *Sf, int ldf, float *rp, float *Minv, int n, int
                 for (int q = 0; q < kSwBlk; ++q)
 #pragma unroll
                     for (int q2 = q + 1; q2 < kSwBlk; ++q2) p[u][q2] = fmaf(-p[u][q], lb[q2][q], p[u][q2]);
-                float l[kSwBlk];
 #pragma unroll
-                for (int q = 0; q < kSwBlk; ++q) l[q] = p[u][q] * rq[q];
-                sw_st8(Sf + i * ldf + J, l);
+                for (int q = 0; q < kSwBlk; ++q) l[u][q] = p[u][q] * rq[q];
+                sw_st8(Lw + i * kSwBlk, l[u]);
             } else {
 #pragma unroll
-                for (int q = 0; q < kSwBlk; ++q) p[u][q] = 0.f;
+                for (int q = 0; q < kSwBlk; ++q) p[u][q] = l[u][q] = 0.f;
             }
         }
-        if (lane == 0) sw_st8(rp + J, rq);       // rp is padded to a whole panel
-        if (lane < nb) {                         // column c = lane of the block's inverse
-            const int c = lane;
-            float m[kSwBlk];
+        if (warp == 0) {
+            if (lane == 0) sw_st8(rp + J, rq);   // rp is padded to a whole panel
+            if (lane < nb) {                     // column c = lane of the block's inverse
+                const int c = lane;
+                float m[kSwBlk];
 #pragma unroll
-            for (int r = 0; r < kSwBlk; ++r) {
-                float acc = r == c ? 1.f : 0.f;
+                for (int r = 0; r < kSwBlk; ++r) {
+                    float acc = r == c ? 1.f : 0.f;
 #pragma unroll
-                for (int q = 0; q < r; ++q)
-                    if (q >= c) acc = fmaf(-lb[r][q], m[q], acc);
-                m[r] = acc;
-            }
-            float *M = Minv + (J / kSwBlk) * 2 * kSwMSize;
+                    for (int q = 0; q < r; ++q)
+                        if (q >= c) acc = fmaf(-lb[r][q], m[q], acc);
+                    m[r] = acc;
+                }
+                float *M = Minv + (J / kSwBlk) * 2 * kSwMSize;
 #pragma unroll
-            for (int r = 0; r < kSwBlk; ++r) M[r * kSwMLd + c] = m[r];
-            sw_st8(M + kSwMSize + c * kSwMLd, m);   // row c of M^T
-        }
-        __syncwarp();
-        // rank-kSwBlk update of the trailing columns (only a full panel has any)
-#pragma unroll
-        for (int ku = 0; ku < R; ++ku) {
-            const int kbeg = max(J + kSwBlk, 32 * ku), kend = min(n, 32 * ku + 32);
-            int k = kbeg;
-            for (; k + 3 < kend; k += 4) {
-                if (ku == 0) sw_trail_cols<R, 0, 4>(Sf, ldf, J, k, n, lane, p);
-                else if (ku == 1) sw_trail_cols<R, 1, 4>(Sf, ldf, J, k, n, lane, p);
-                else sw_trail_cols<R, 2, 4>(Sf, ldf, J, k, n, lane, p);
-            }
-            for (; k < kend; ++k) {
-                if (ku == 0) sw_trail_cols<R, 0, 1>(Sf, ldf, J, k, n, lane, p);
-                else if (ku == 1) sw_trail_cols<R, 1, 1>(Sf, ldf, J, k, n, lane, p);
-                else sw_trail_cols<R, 2, 1>(Sf, ldf, J, k, n, lane, p);
+                for (int r = 0; r < kSwBlk; ++r) M[r * kSwMLd + c] = m[r];
+                sw_st8(M + kSwMSize + c * kSwMLd, m);   // row c of M^T
             }
         }
         __syncwarp();
+        // rank-kSwBlk update of the trailing columns, groups of 4 dealt to the warps in turn
+        for (int k0 = J + kSwBlk + 4 * warp; k0 < n; k0 += 16)
+            sw_trail_group<R>(Sf, ldf, Lw, k0, min(4, n - k0), n, lane, p);
+        __syncthreads();
+        // the multipliers into the factor (every warp has read this panel's columns)
+        if (warp == 0) {
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                const int i = lane + 32 * u;
+                if (i >= J + kSwBlk && i < n) sw_st8(Sf + i * ldf + J, l[u]);
+            }
+        }
     }
+    __syncwarp();
     return true;
 }
 
@@ -386,12 +398,40 @@ __device__ inline bool sw_solve_f64(double *S, double *v, int n, int ld, int lan
     return true;
 }
 
+// partials_reduce_kernel: a problem's Schur partials summed in place into part
+// 0, entry by entry in the parts' order (the FP64 sum every solve kernel
+// forms), so that the reduced solve reads one part.  Grid (entry slices,
+// problems); problems with one part are left as they are.
+constexpr int kPrThreads = 128;
+constexpr int kPrUnroll = 16;          // parts with loads in flight together
+
+__global__ void __launch_bounds__(kPrThreads) partials_reduce_kernel(const Prob *__restrict__ probs, int t) {
+    const Prob &pr = probs[blockIdx.y];
+    const int P = pr.n_parts, Lp = pr.L;
+    const int q = blockIdx.x * kPrThreads + threadIdx.x;
+    if (t >= pr.iters || P <= 1 || q >= Lp) return;
+    double *src = pr.partial + q;
+    double acc = src[0];
+    for (int part = 1; part < P; part += kPrUnroll) {   // loads of a group in flight together
+        double xv[kPrUnroll];
+#pragma unroll
+        for (int u = 0; u < kPrUnroll; ++u) xv[u] = part + u < P ? __ldg(src + (size_t)(part + u) * Lp) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kPrUnroll; ++u)
+            if (part + u < P) acc += xv[u];
+    }
+    src[0] = acc;
+}
+
 // One CTA of kSwThreads per problem; R = sw_rows(nf) of the batch's largest
-// problem.  Problems that keep the FP64 factor for the adjoint use solve_kernel.
+// problem.  Reads part 0 of the Schur partials only: partials_reduce_kernel
+// runs first wherever a problem has more than one.  Problems that keep the
+// FP64 factor for the adjoint use solve_kernel.
 template <int R>
 __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__restrict__ probs, int t) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_state;                      // 1: refine again, 0: x final, 2: FP64 elimination
+    __shared__ int s_status;
     const Prob &pr = probs[blockIdx.x];
     const int tid = threadIdx.x, lane = tid & 31;
     if (t >= pr.iters) return;
@@ -399,12 +439,6 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
     const float *pose_cur = pr.pose_it + (size_t)t * N * 7;
     float *pose_next = pr.pose_it + (size_t)(t + 1) * N * 7;
     double *dxi = pr.dxi + (size_t)t * nf * 6;
-    const int status_in = block_status(pr.status);
-    if (status_in != 0 || nf == 0) {
-        for (int q = tid; q < N * 7; q += kSwThreads) pose_next[q] = pose_cur[q];
-        for (int q = tid; q < nf * 6; q += kSwThreads) dxi[q] = 0.0;
-        return;
-    }
     const SwLayout lay = sw_layout(nf);
     const int ldf = sw_ldf(n);
     double *S = reinterpret_cast<double *>(smem + lay.S);
@@ -415,63 +449,74 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
     float *Minv = reinterpret_cast<float *>(smem + lay.Minv);
     float *yb = reinterpret_cast<float *>(smem + lay.yb);
     float *zs = reinterpret_cast<float *>(smem + lay.zs);
+    float *Lc = reinterpret_cast<float *>(smem + lay.Lc);
 
-    // -- 1. FP64 sum of the partials in the parts' order, a strip (3 x 6
-    // entries of block pair (a, b), a <= b) per thread; S both triangles and
-    // its FP32 copy; the FP32 copy's padding columns zeroed
-    {
-        const int Lp = pr.L, nparts = pr.n_parts, nbs = 2 * n_block_pairs(nf);
-        for (int st = tid; st < nbs; st += kSwThreads) {
+    // -- 1. the summed partial (S: strips of 3 x 6 entries of block pair (a,
+    // b), a <= b; then v'), a strip per thread, loaded while thread 0 reads
+    // the status.  S gets both triangles, the FP32 copy too; the FP32 copy's
+    // padding columns are zeroed.
+    const int nbs = 2 * n_block_pairs(nf);
+    float pin[7];                                // warp 0: pose `lane`, read now for the retraction
+    if (tid < 32 && lane < N)
+#pragma unroll
+        for (int q = 0; q < 7; ++q) pin[q] = pose_cur[7 * lane + q];
+    constexpr int kStrips = 2;                   // strips per thread with loads in flight together
+    for (int st0 = 0; st0 < max(nbs, 1); st0 += kStrips * kSwThreads) {
+        double2 d2[kStrips][9];
+#pragma unroll
+        for (int h = 0; h < kStrips; ++h) {
+            const int st = st0 + h * kSwThreads + tid;
+            if (st < nbs) {
+                const double2 *src = reinterpret_cast<const double2 *>(pr.partial + (size_t)st * 18);
+#pragma unroll
+                for (int e = 0; e < 9; ++e) d2[h][e] = src[e];
+            }
+        }
+        double vq = 0.0;
+        if (st0 == 0) {
+            if (tid < n) vq = pr.partial[18 * nbs + tid];
+            if (tid == 0) s_status = *pr.status;
+            __syncthreads();
+            if (s_status != 0 || nf == 0) {      // uniform: every thread passed the barrier
+                for (int q = tid; q < N * 7; q += kSwThreads) pose_next[q] = pose_cur[q];
+                for (int q = tid; q < nf * 6; q += kSwThreads) dxi[q] = 0.0;
+                return;
+            }
+            for (int q = tid; q < n; q += kSwThreads) {
+                v[q] = q == tid ? vq : pr.partial[18 * nbs + q];
+                for (int c = n; c < ldf; ++c) Sf[q * ldf + c] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < kStrips; ++h) {
+            const int st = st0 + h * kSwThreads + tid;
+            if (st >= nbs) continue;
             int a, b;
             decode_pair(st >> 1, nf, a, b);
             const int row0 = 6 * a + 3 * (st & 1), col0 = 6 * b;
-            double acc[18];
-            const double2 *src = reinterpret_cast<const double2 *>(pr.partial + (size_t)st * 18);
-#pragma unroll
-            for (int e = 0; e < 9; ++e) {
-                const double2 d2 = src[e];
-                acc[2 * e] = d2.x;
-                acc[2 * e + 1] = d2.y;
-            }
-            for (int part = 1; part < nparts; ++part) {
-                src += Lp / 2;
-                double2 d2[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) d2[e] = src[e];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) {
-                    acc[2 * e] += d2[e].x;
-                    acc[2 * e + 1] += d2[e].y;
-                }
-            }
 #pragma unroll
             for (int e = 0; e < 18; ++e) {
+                const double val = (e & 1) ? d2[h][e >> 1].y : d2[h][e >> 1].x;
                 const int row = row0 + e / 6, col = col0 + e % 6;
-                S[row * ld + col] = acc[e];
-                Sf[row * ldf + col] = (float)acc[e];
+                const float f = (float)val;
+                S[row * ld + col] = val;
+                Sf[row * ldf + col] = f;
                 if (a != b) {
-                    S[col * ld + row] = acc[e];
-                    Sf[col * ldf + row] = (float)acc[e];
+                    S[col * ld + row] = val;
+                    Sf[col * ldf + row] = f;
                 }
             }
         }
-        for (int q = tid; q < n; q += kSwThreads) {
-            const double *src = pr.partial + 18 * nbs + q;
-            double acc = src[0];
-            for (int part = 1; part < nparts; ++part) acc += src[(size_t)part * Lp];
-            v[q] = acc;
-        }
-        const int pad = ldf - n;
-        for (int q = tid; q < n * pad; q += kSwThreads) Sf[(q / pad) * ldf + n + q % pad] = 0.f;
     }
     __syncthreads();
 
-    // -- 2.-3. FP32 factor and the first solve (warp 0)
+    // -- 2. FP32 factor (all warps), 3. the first solve (warp 0)
+    const bool factored = sw_factor<R>(Sf, ldf, rp, Minv, Lc, n, tid);
     float y[R], xf[R];                           // warp 0: my rows' correction and FP32 view of x
     double prev = 0.0;
     if (tid < 32) {
         int state = 2;
-        if (sw_factor<R>(Sf, ldf, rp, Minv, n, lane)) {
+        if (factored) {
 #pragma unroll
             for (int u = 0; u < R; ++u) {
                 const int i = lane + 32 * u;
@@ -556,9 +601,15 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
     }
     for (int q = lane; q < n; q += 32) dxi[q] = v[q];
     for (int a = lane; a < N; a += 32) {
-        if (a >= t0) se3_left_update(v + 6 * (a - t0), pose_cur + 7 * a, pose_next + 7 * a);
-        else
-            for (int q = 0; q < 7; ++q) pose_next[7 * a + q] = pose_cur[7 * a + q];
+        if (a >= 32)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) pin[q] = pose_cur[7 * a + q];
+        if (a >= t0) {
+            se3_left_update(v + 6 * (a - t0), pin, pose_next + 7 * a);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 7; ++q) pose_next[7 * a + q] = pin[q];
+        }
     }
 }
 
