@@ -212,8 +212,7 @@ def stress_bench(n_sessions, steps, stream, hbm_peak, tf32=False):
     kinds = {}
     for k, v in launches:
         kinds.setdefault(int(k), []).append(v)
-    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub",
-             5: "partials_sum"}
+    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub"}
     kern = {names[k] + "_ms": float(np.mean(v)) for k, v in kinds.items() if k in names}
     kern.update({names[k] + "_launches_per_step": len(v) // steps for k, v in kinds.items() if k in names})
     sc = distinct[0]
@@ -769,8 +768,7 @@ def kernel_split(solver, subsets, stream):
     torch.cuda.synchronize()
     launches = solver.timing(cap=64 * len(subsets))
     solver.set_timing(False)
-    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub",
-             5: "partials_sum"}
+    names = {0: "plan", 1: "linearize", 2: "reduced_solve", 3: "schur_assembly", 4: "final_backsub"}
     kinds = {}
     for k, v in launches:
         kinds.setdefault(names.get(int(k), str(k)), []).append(v)
@@ -864,7 +862,7 @@ def main():
         elapsed_ms = float(t.item())
     # one timing record per kernel launch: the launches of a step, and the
     # kernels' device times by kind (0 plan, 1 linearise/Schur, 2 reduced
-    # solve, 4 last back-substitution, 5 partials summed into one)
+    # solve, 4 last back-substitution)
     n_launch_per_solve = len(launches) // args.steps
     value = world * B * args.steps / (elapsed_ms / 1e3)
     by_kind = {}
@@ -872,7 +870,7 @@ def main():
         by_kind.setdefault(k, []).append(ms)
     kern = {"plan_ms": float(np.mean(by_kind[0])), "linearize_schur_ms": float(np.mean(by_kind[1])),
             "backsub_final_ms": float(np.mean(by_kind[4])),
-            "reduce_cholesky_ms": float(np.mean(by_kind[2])) + (float(np.mean(by_kind[5])) if 5 in by_kind else 0.0),
+            "reduce_cholesky_ms": float(np.mean(by_kind[2])),
             "launches_per_step": n_launch_per_solve}
     step_ms = elapsed_ms / args.steps
     kern["share_linearize_schur"] = 2 * kern["linearize_schur_ms"] / step_ms

@@ -246,8 +246,7 @@ int dpvo_ba_iterate(dpvo_ba_handle *h, int index, int iter, float *poses_out, fl
  * dpvo_ba_timing() waits for the recorded events and writes, for each launch
  * since the previous read (all solves, in order), the elapsed milliseconds
  * (ms_out[i]) and the kernel (kind_out[i]: 0 plan, 1 linearise/Schur,
- * 2 reduce/Cholesky/retract, 3 Schur assembly, 4 last depth back-substitution,
- * 5 Schur partials summed into one, before kind 2 where a problem has several);
+ * 2 reduce/Cholesky/retract, 3 Schur assembly, 4 last depth back-substitution);
  * it returns the number of launches written
  * (<= cap) or a negative code, and starts a new record.  The record grows
  * while enabled: read it regularly. */

@@ -293,7 +293,7 @@ class Solver:
     def timing(self, cap: int = 4096):
         """[(kind, ms)] of every launch since the last read (kind 0 plan,
         1 linearise/Schur, 2 reduce/Cholesky/retract, 3 Schur assembly, 4 last
-        back-substitution, 5 Schur partials summed into one)."""
+        back-substitution)."""
         ms = np.zeros(cap, np.float32)
         kinds = np.zeros(cap, np.int32)
         n = self.lib.dpvo_ba_timing(self.h, ms.ctypes.data, kinds.ctypes.data, cap)

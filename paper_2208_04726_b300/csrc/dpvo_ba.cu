@@ -36,6 +36,7 @@ struct Layout {
     size_t bytes = 0, off_probs = 0, off_items = 0;
     int W_cap = 1, G_cap = 64, nf_max = 0, iters_max = 0, n_max = 1;
     int max_parts = 1;             // Schur partials of the problem with the most
+    int e_max = 0;                 // edges of the problem with the most
     bool tc = false;               // Schur accumulation on the tensor cores
     bool ext = false;              // more than kFusedMaxFree free poses: assembly kernel, packed solve
     bool tc_asm = false;           // ext with the TF32 Schur mode: the assembly on the tensor cores
@@ -73,26 +74,40 @@ static void launch_assembly(const Layout &L, cudaStream_t stream, const Prob *pr
                                                                                erow_len(L.nf_max));
 }
 
-// The plan launch: more edge loads in flight per thread for batches smaller
-// than the SM count.
-static void launch_plan(int n, int num_sms, cudaStream_t stream, const Prob *probs) {
-    if (n >= num_sms) plan_kernel<1><<<n, kPlanThreads, 0, stream>>>(probs);
-    else plan_kernel<4><<<n, kPlanThreads, 0, stream>>>(probs);
+// The plan launch: one CTA per problem for batches of at least one problem
+// per SM; smaller batches split each problem's edges into slices of at least
+// kPlanSliceEdges, up to two CTAs per SM over the batch.
+static void launch_plan(int n, int e_max, int num_sms, cudaStream_t stream, const Prob *probs) {
+    int slices = 1;
+    if (n < num_sms)
+        slices = std::max(1, std::min((e_max + kPlanSliceEdges - 1) / kPlanSliceEdges, 2 * num_sms / n));
+    plan_kernel<<<dim3(n, slices), kPlanThreads, 0, stream>>>(probs, slices);
 }
 
-// Whether the forward reduced solve needs its partials summed into one part
-// first (some problem has free poses and several partials), and that launch.
-static bool needs_reduce(bool ext, int max_parts, int nf_max) { return !ext && max_parts > 1 && nf_max > 0; }
-static void launch_reduce(int nf_max, int n, cudaStream_t stream, const Prob *probs, int t) {
-    const dim3 grid((partial_len(nf_max) + kPrThreads - 1) / kPrThreads, n);
-    partials_reduce_kernel<<<grid, kPrThreads, 0, stream>>>(probs, t);
-}
-
-// The forward reduced solve of at most kFusedMaxFree free poses, from summed
-// partials: one CTA per problem, the rows per lane set by the largest problem.
-static void launch_solve_warp(int nf_max, int n, cudaStream_t stream, const Prob *probs, int t, size_t smem) {
-    if (sw_rows(nf_max) == 2) solve_warp_kernel<2><<<n, kSwThreads, smem, stream>>>(probs, t);
-    else solve_warp_kernel<3><<<n, kSwThreads, smem, stream>>>(probs, t);
+// The forward reduced solve of at most kFusedMaxFree free poses: one CTA per
+// problem, or a cluster of kSwCluster CTAs per problem where some problem has
+// several Schur partials (they sum them); the rows per lane set by the
+// largest problem.
+static void launch_solve_warp(int nf_max, int max_parts, int n, cudaStream_t stream, const Prob *probs, int t,
+                              size_t smem) {
+    auto kernel = sw_rows(nf_max) == 2 ? solve_warp_kernel<2> : solve_warp_kernel<3>;
+    if (max_parts <= 1 || nf_max == 0) {
+        kernel<<<n, kSwThreads, smem, stream>>>(probs, t, 1);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n * kSwCluster);
+    cfg.blockDim = dim3(kSwThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSwCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, probs, t, (int)kSwCluster);
 }
 
 // Reduced solve launch, in the batch's variant.
@@ -100,7 +115,7 @@ static void launch_solve(const Layout &L, int n, cudaStream_t stream, const Prob
                          double *v_out) {
     if (L.ext) solve_large_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
     else if (S_out) solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(probs, t, S_out, v_out);
-    else launch_solve_warp(L.nf_max, n, stream, probs, t, L.sw_smem);   // after launch_reduce
+    else launch_solve_warp(L.nf_max, L.max_parts, n, stream, probs, t, L.sw_smem);
 }
 
 // The bounded mbarrier wait of the pipelined kernels, on a phase that completes
@@ -168,6 +183,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     for (int b = 0; b < n; ++b) {
         n_max = std::max(n_max, dims[b].n_frames);
         L.nf_max = std::max(L.nf_max, dims[b].n_frames - dims[b].t0);
+        L.e_max = std::max(L.e_max, dims[b].n_edges);
         L.iters_max = std::max(L.iters_max, dims[b].n_iters);
     }
     L.n_max = n_max;
@@ -434,7 +450,7 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         }
         return DPVO_BA_OK;
     };
-    if ((rc = timed(0, [&] { launch_plan(n, h->num_sms, stream, d_probs); }))) return rc;
+    if ((rc = timed(0, [&] { launch_plan(n, L.e_max, h->num_sms, stream, d_probs); }))) return rc;
     const Item *d_asm_items = d_items + L.n_lin_items;
     if (S_out) {
         launch_linearize(L, n_items, stream, d_probs, d_items, 0, 0);
@@ -448,10 +464,6 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
             if (t < L.iters_max) {
                 if (L.ext) {
                     rc = timed(3, [&] { launch_assembly(L, stream, d_probs, d_asm_items, t); });
-                    if (rc) return rc;
-                }
-                if (needs_reduce(L.ext, L.max_parts, L.nf_max)) {
-                    rc = timed(5, [&] { launch_reduce(L.nf_max, n, stream, d_probs, t); });
                     if (rc) return rc;
                 }
                 rc = timed(2, [&] { launch_solve(L, n, stream, d_probs, t, nullptr, nullptr); });
@@ -513,7 +525,7 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
     const int n_items = L.n_lin_items;
     const size_t bw_smem = bw_smem_layout(L.W_cap, L.G_cap, L.n_max).bytes;
-    launch_plan(n, h->num_sms, stream, d_probs);
+    launch_plan(n, L.e_max, h->num_sms, stream, d_probs);
     for (int t = 0; t < L.iters_max; ++t) {
         launch_linearize(L, n_items, stream, d_probs, d_items, t, 0);
         solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
@@ -1453,11 +1465,10 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     lay.lin_smem = lin_smem;
     lay.final_slices = final_slices_of(tc, d.n_patches, p.max_chunks, 65535);
     noalloc_descriptors_kernel<<<1, kThreads, 0, stream>>>(p, p.n_items, d_prob, d_items);
-    launch_plan(1, sms, stream, d_prob);
+    launch_plan(1, d.n_edges, sms, stream, d_prob);
     for (int t = 0; t < d.n_iters; ++t) {
         launch_linearize(lay, p.n_items, stream, d_prob, d_items, t, 0);
-        if (needs_reduce(false, p.n_parts, nf)) launch_reduce(nf, 1, stream, d_prob, t);
-        launch_solve_warp(nf, 1, stream, d_prob, t, solve_smem);
+        launch_solve_warp(nf, p.n_parts, 1, stream, d_prob, t, solve_smem);
     }
     launch_final(lay, 1, stream, d_prob, d.n_iters);
     if (cudaGetLastError() != cudaSuccess) return DPVO_BA_ECUDA;

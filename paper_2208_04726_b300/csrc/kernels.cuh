@@ -97,42 +97,103 @@ __device__ __forceinline__ void anchor_terms(const EdgeLin &L, const float *Rij,
 }
 
 // ----------------------------------------------------------------------------
-// plan_kernel: one CTA of kPlanThreads per problem.  One coalesced pass over
-// the anchors and one over the edges check the ordering and, at every change
-// of anchor (patch), record where each frame's patches (each patch's edges)
-// begin; no searches.
+// plan_kernel: grid (problems, edge slices), kPlanThreads per CTA.  Every CTA
+// checks one slice of a problem's edges (valid indices, sorted by patch and
+// then frame) and, at every change of patch, records where that patch's edges
+// begin; the last CTA of the problem to finish (a ticket in its descriptor)
+// then makes one pass over the anchors (where each frame's patches begin),
+// copies the initial state into iterate 0, builds the chunk table and writes
+// the status.  Coalesced passes, no searches.
 // ----------------------------------------------------------------------------
 constexpr int kPlanThreads = 1024;
 constexpr int kPlanUnroll = 4;       // patches per thread with loads in flight together
-// QUADS: 4-edge groups per thread with loads in flight together.  One keeps
-// the kernel within 32 registers (two CTAs per SM, for batches of at least one
-// problem per SM); four take 64 registers and fewer memory round trips (small
-// batches).
-template <int QUADS>
-__global__ void __launch_bounds__(kPlanThreads, QUADS == 1 ? 2 : 1) plan_kernel(const Prob *__restrict__ probs) {
+constexpr int kPlanSliceEdges = 4 * kPlanThreads;   // edges of one slice at least (one load round)
+
+__global__ void __launch_bounds__(kPlanThreads, 2) plan_kernel(const Prob *__restrict__ probs, int slices) {
     const Prob &pr = probs[blockIdx.x];
-    const int tid = threadIdx.x;
+    Prob *mp = const_cast<Prob *>(probs) + blockIdx.x;   // the ticket and the bad flag
+    const int tid = threadIdx.x, slice = blockIdx.y;
     const int N = pr.N, P = pr.P, E = pr.E;
-    __shared__ int s_bad;
+    __shared__ int s_bad, s_last;
     __shared__ int s_fstart[DPVO_BA_MAX_FRAMES + 1];
     __shared__ int s_choff[DPVO_BA_MAX_FRAMES + 1];
     if (tid == 0) s_bad = 0;
-    if (P == 0)
-        for (int i = tid; i <= N; i += kPlanThreads) s_fstart[i] = 0;
-    if (E == 0)
+    if (E == 0 && slice == 0)
         for (int k = tid; k <= P; k += kPlanThreads) pr.seg[k] = 0;
     __syncthreads();
 
     // Where kk and jj share their 16-byte phase the edges are read in groups
-    // of four by 16-byte loads.
+    // of four by 16-byte loads: a scalar head up to the 16-byte boundary and a
+    // scalar tail (slice 0), and this slice's range of quads.
     const uintptr_t ka = (uintptr_t)pr.kk, ja = (uintptr_t)pr.jj;
     const bool vec = (ka & 3) == 0 && (ka & 15) == (ja & 15);
     const int head = vec ? min(E, (int)(((16 - (ka & 15)) & 15) >> 2)) : 0;
     const int Q = vec ? (E - head) >> 2 : 0;
+    const int qs = (Q + slices - 1) / slices, q_lo = min(Q, slice * qs), q_hi = min(Q, q_lo + qs);
     const int4 *kk4 = reinterpret_cast<const int4 *>(pr.kk + head);
     const int4 *jj4 = reinterpret_cast<const int4 *>(pr.jj + head);
-
     int bad = 0;
+    // edge e = (k, j) after (kp, jp): valid and ordered, and patches (kp, k] start at e
+    auto edge = [&](int e, int k, int j, int kp, int jp) {
+        if (k < 0 || k >= P || j < 0 || j >= N || kp > k || (kp == k && jp >= j)) {
+            bad = 1;
+            return;
+        }
+        for (int q = max(kp + 1, 0); q <= k; ++q) pr.seg[q] = e;
+        if (e == E - 1)
+            for (int q = k + 1; q <= P; ++q) pr.seg[q] = E;
+    };
+    auto edge_scalar = [&](int e) {   // one edge with its own loads
+        edge(e, pr.kk[e], pr.jj[e], e > 0 ? pr.kk[e - 1] : -1, e > 0 ? pr.jj[e - 1] : -1);
+    };
+    const int lane = tid & 31, warp = tid >> 5;
+    if (vec) {
+        const int tail0 = head + 4 * Q;
+        if (slice == 0) {
+            if (tid < head) edge_scalar(tid);
+            else if (tid >= 32 && tid - 32 < E - tail0) edge_scalar(tail0 + tid - 32);
+        }
+        // four edges per thread per step; the previous edge of a quad is the
+        // neighbouring lane's last (a warp's first lane loads its own)
+        for (int q = q_lo + tid; q - tid < q_hi; q += kPlanThreads) {
+            int4 kv = make_int4(0, 0, 0, 0), jv = kv;
+            int kq = -1, jq = -1;
+            if (q < q_hi) {
+                kv = kk4[q];
+                jv = jj4[q];
+                if (lane == 0 && head + 4 * q > 0) {
+                    kq = pr.kk[head + 4 * q - 1];
+                    jq = pr.jj[head + 4 * q - 1];
+                }
+            }
+            const int ks = __shfl_up_sync(0xffffffffu, kv.w, 1);
+            const int js = __shfl_up_sync(0xffffffffu, jv.w, 1);
+            if (lane > 0) { kq = ks; jq = js; }
+            if (q >= q_hi) continue;
+            const int e = head + 4 * q;
+            edge(e, kv.x, jv.x, kq, jq);
+            edge(e + 1, kv.y, jv.y, kv.x, jv.x);
+            edge(e + 2, kv.z, jv.z, kv.y, jv.y);
+            edge(e + 3, kv.w, jv.w, kv.z, jv.z);
+        }
+    } else {
+        const int es = (E + slices - 1) / slices, e_lo = min(E, slice * es), e_hi = min(E, e_lo + es);
+        for (int e = e_lo + tid; e < e_hi; e += kPlanThreads) edge_scalar(e);
+    }
+    if (slices > 1) {                    // hand over to the last CTA of the problem
+        if (bad) atomicOr(&mp->plan_bad, 1);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(&mp->plan_ticket, 1) == slices - 1;
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        bad = tid == 0 ? atomicOr(&mp->plan_bad, 0) : 0;
+    }
+
+    // the anchors (where each frame's patches begin) and the initial state
+    if (P == 0)
+        for (int i = tid; i <= N; i += kPlanThreads) s_fstart[i] = 0;
     for (int i = tid; i < N * 7; i += kPlanThreads) {
         const float v = pr.poses[i];
         pr.pose_it[i] = v;
@@ -165,60 +226,6 @@ __global__ void __launch_bounds__(kPlanThreads, QUADS == 1 ? 2 : 1) plan_kernel(
                     for (int i = a + 1; i <= N; ++i) s_fstart[i] = P;
             }
         }
-    }
-    // edge e = (k, j) after (kp, jp): valid and ordered, and patches (kp, k] start at e
-    auto edge = [&](int e, int k, int j, int kp, int jp) {
-        if (k < 0 || k >= P || j < 0 || j >= N || kp > k || (kp == k && jp >= j)) {
-            bad = 1;
-            return;
-        }
-        for (int q = max(kp + 1, 0); q <= k; ++q) pr.seg[q] = e;
-        if (e == E - 1)
-            for (int q = k + 1; q <= P; ++q) pr.seg[q] = E;
-    };
-    auto edge_scalar = [&](int e) {   // one edge with its own loads
-        edge(e, pr.kk[e], pr.jj[e], e > 0 ? pr.kk[e - 1] : -1, e > 0 ? pr.jj[e - 1] : -1);
-    };
-    // Grouped read: a scalar head up to the 16-byte boundary, then four edges
-    // per thread per step (the previous edge of a group is the neighbouring
-    // lane's last; a warp's first lane loads its own), then a scalar tail.
-    const int lane = tid & 31, warp = tid >> 5;
-    if (vec) {
-        const int tail0 = head + 4 * Q;
-        if (tid < head) edge_scalar(tid);
-        else if (tid >= 32 && tid - 32 < E - tail0) edge_scalar(tail0 + tid - 32);
-        for (int base = 0; base < Q; base += QUADS * kPlanThreads) {
-            int4 kv[QUADS], jv[QUADS];
-            int kq[QUADS], jq[QUADS];
-#pragma unroll
-            for (int u = 0; u < QUADS; ++u) {   // loads of all unrolled quads first
-                const int q = base + u * kPlanThreads + tid;
-                kv[u] = make_int4(0, 0, 0, 0); jv[u] = kv[u]; kq[u] = -1; jq[u] = -1;
-                if (q < Q) {
-                    kv[u] = kk4[q];
-                    jv[u] = jj4[q];
-                    if (lane == 0 && head + 4 * q > 0) {
-                        kq[u] = pr.kk[head + 4 * q - 1];
-                        jq[u] = pr.jj[head + 4 * q - 1];
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < QUADS; ++u) {
-                const int q = base + u * kPlanThreads + tid;
-                const int ks = __shfl_up_sync(0xffffffffu, kv[u].w, 1);
-                const int js = __shfl_up_sync(0xffffffffu, jv[u].w, 1);
-                if (lane > 0) { kq[u] = ks; jq[u] = js; }
-                if (q >= Q) continue;
-                const int e = head + 4 * q;
-                edge(e, kv[u].x, jv[u].x, kq[u], jq[u]);
-                edge(e + 1, kv[u].y, jv[u].y, kv[u].x, jv[u].x);
-                edge(e + 2, kv[u].z, jv[u].z, kv[u].y, jv[u].y);
-                edge(e + 3, kv[u].w, jv[u].w, kv[u].z, jv[u].z);
-            }
-        }
-    } else {
-        for (int e = tid; e < E; e += kPlanThreads) edge_scalar(e);
     }
     if (bad) atomicOr(&s_bad, 1);
     __syncthreads();
@@ -258,8 +265,8 @@ __global__ void __launch_bounds__(kPlanThreads, QUADS == 1 ? 2 : 1) plan_kernel(
             Chunk ch;
             ch.k0 = k;
             ch.count = sz;
-            ch.e0 = pr.seg[k];
-            ch.e1 = pr.seg[k + sz];
+            ch.e0 = __ldcg(pr.seg + k);
+            ch.e1 = __ldcg(pr.seg + k + sz);
             ch.anchor = i;
             ch.jlo = i;          // window filled in below, one warp per chunk
             ch.jhi = i;
@@ -276,7 +283,7 @@ __global__ void __launch_bounds__(kPlanThreads, QUADS == 1 ? 2 : 1) plan_kernel(
         const Chunk ch = pr.chunks[c];
         int jlo = ch.anchor, jhi = ch.anchor;
         for (int q = ch.k0 + lane; q < ch.k0 + ch.count; q += 32) {
-            const int s0 = pr.seg[q], s1 = pr.seg[q + 1];
+            const int s0 = __ldcg(pr.seg + q), s1 = __ldcg(pr.seg + q + 1);
             if (s1 > s0) {
                 jlo = min(jlo, (int)pr.jj[s0]);
                 jhi = max(jhi, (int)pr.jj[s1 - 1]);

@@ -34,6 +34,7 @@
 //      of the free poses (se3_left_update).
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -398,41 +399,21 @@ __device__ inline bool sw_solve_f64(double *S, double *v, int n, int ld, int lan
     return true;
 }
 
-// partials_reduce_kernel: a problem's Schur partials summed in place into part
-// 0, entry by entry in the parts' order (the FP64 sum every solve kernel
-// forms), so that the reduced solve reads one part.  Grid (entry slices,
-// problems); problems with one part are left as they are.
-constexpr int kPrThreads = 128;
-constexpr int kPrUnroll = 16;          // parts with loads in flight together
+constexpr int kSwCluster = 8;          // CTAs summing the partials of a problem that has several
 
-__global__ void __launch_bounds__(kPrThreads) partials_reduce_kernel(const Prob *__restrict__ probs, int t) {
-    const Prob &pr = probs[blockIdx.y];
-    const int P = pr.n_parts, Lp = pr.L;
-    const int q = blockIdx.x * kPrThreads + threadIdx.x;
-    if (t >= pr.iters || P <= 1 || q >= Lp) return;
-    double *src = pr.partial + q;
-    double acc = src[0];
-    for (int part = 1; part < P; part += kPrUnroll) {   // loads of a group in flight together
-        double xv[kPrUnroll];
-#pragma unroll
-        for (int u = 0; u < kPrUnroll; ++u) xv[u] = part + u < P ? __ldg(src + (size_t)(part + u) * Lp) : 0.0;
-#pragma unroll
-        for (int u = 0; u < kPrUnroll; ++u)
-            if (part + u < P) acc += xv[u];
-    }
-    src[0] = acc;
-}
-
-// One CTA of kSwThreads per problem; R = sw_rows(nf) of the batch's largest
-// problem.  Reads part 0 of the Schur partials only: partials_reduce_kernel
-// runs first wherever a problem has more than one.  Problems that keep the
+// One CTA of kSwThreads per problem, or, where some problem of the batch has
+// more than one Schur partial, a cluster of csize = kSwCluster CTAs per
+// problem: each sums a slice of the partials' entries (in the parts' order)
+// into the shared memory of the cluster's first CTA, which then solves.
+// R = sw_rows(nf) of the batch's largest problem.  Problems that keep the
 // FP64 factor for the adjoint use solve_kernel.
 template <int R>
-__global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__restrict__ probs, int t) {
+__global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__restrict__ probs, int t, int csize) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_state;                      // 1: refine again, 0: x final, 2: FP64 elimination
     __shared__ int s_status;
-    const Prob &pr = probs[blockIdx.x];
+    const int b = blockIdx.x / csize, rank = blockIdx.x - b * csize;
+    const Prob &pr = probs[b];
     const int tid = threadIdx.x, lane = tid & 31;
     if (t >= pr.iters) return;
     const int N = pr.N, t0 = pr.t0, nf = pr.nf, n = 6 * nf, ld = n + 1;
@@ -461,7 +442,74 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
 #pragma unroll
         for (int q = 0; q < 7; ++q) pin[q] = pose_cur[7 * lane + q];
     constexpr int kStrips = 2;                   // strips per thread with loads in flight together
-    for (int st0 = 0; st0 < max(nbs, 1); st0 += kStrips * kSwThreads) {
+    if (csize > 1) {
+        // several partials: this CTA's slice of the entries, summed in the
+        // parts' order, into the first CTA's S, FP32 copy and v'
+        if (tid == 0) s_status = *pr.status;
+        __syncthreads();
+        if (s_status != 0 || nf == 0) {          // the same exit in every CTA of the cluster
+            if (rank == 0) {
+                for (int q = tid; q < N * 7; q += kSwThreads) pose_next[q] = pose_cur[q];
+                for (int q = tid; q < nf * 6; q += kSwThreads) dxi[q] = 0.0;
+            }
+            return;
+        }
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        double *S0 = cl.map_shared_rank(S, 0), *v0 = cl.map_shared_rank(v, 0);
+        float *Sf0 = cl.map_shared_rank(Sf, 0);
+        const int Lp = pr.L, P = pr.n_parts, per = (Lp + csize - 1) / csize;
+        const int q_lo = min(Lp, rank * per), q_hi = min(Lp, q_lo + per);
+        constexpr int kE = 2, kG = 8;            // entries per thread, parts per group of loads
+        for (int q0 = q_lo + tid; q0 < q_hi; q0 += kE * kSwThreads) {
+            double acc[kE];
+#pragma unroll
+            for (int e = 0; e < kE; ++e) {
+                const int q = q0 + e * kSwThreads;
+                acc[e] = q < q_hi ? __ldg(pr.partial + q) : 0.0;
+            }
+            for (int part = 1; part < P; part += kG) {
+                double xv[kE][kG];
+#pragma unroll
+                for (int e = 0; e < kE; ++e)
+#pragma unroll
+                    for (int u = 0; u < kG; ++u) {
+                        const int q = q0 + e * kSwThreads;
+                        xv[e][u] = q < q_hi && part + u < P ? __ldg(pr.partial + (size_t)(part + u) * Lp + q) : 0.0;
+                    }
+#pragma unroll
+                for (int u = 0; u < kG; ++u)
+#pragma unroll
+                    for (int e = 0; e < kE; ++e)
+                        if (part + u < P) acc[e] += xv[e][u];
+            }
+#pragma unroll
+            for (int e = 0; e < kE; ++e) {
+                const int q = q0 + e * kSwThreads;
+                if (q >= q_hi) continue;
+                if (q < 18 * nbs) {
+                    const int st = q / 18, e18 = q - 18 * st;
+                    int a, bb;
+                    decode_pair(st >> 1, nf, a, bb);
+                    const int row = 6 * a + 3 * (st & 1) + e18 / 6, col = 6 * bb + e18 % 6;
+                    const float f = (float)acc[e];
+                    S0[row * ld + col] = acc[e];
+                    Sf0[row * ldf + col] = f;
+                    if (a != bb) {
+                        S0[col * ld + row] = acc[e];
+                        Sf0[col * ldf + row] = f;
+                    }
+                } else {
+                    v0[q - 18 * nbs] = acc[e];
+                }
+            }
+        }
+        if (rank == 0)
+            for (int q = tid; q < n; q += kSwThreads)
+                for (int c = n; c < ldf; ++c) Sf[q * ldf + c] = 0.f;
+        cl.sync();
+        if (rank != 0) return;
+    }
+    for (int st0 = 0; csize == 1 && st0 < max(nbs, 1); st0 += kStrips * kSwThreads) {
         double2 d2[kStrips][9];
 #pragma unroll
         for (int h = 0; h < kStrips; ++h) {
