@@ -80,14 +80,26 @@ typedef struct {
     float z_min;            /* edge active iff reprojected homogeneous depth > z_min (0.1)*/
     size_t mem_budget_bytes;/* serving: device bytes sessions may hold (0 = 8 GiB)        */
     int32_t max_sessions;   /* serving: resident sessions (0 = 256)                       */
-    int32_t schur_tf32;     /* 0 (default): sum_k E_k C_k^-1 E_k^T accumulates in FP32
-                             * with compensated sums on the CUDA cores.  1: when every
-                             * problem of a batch has at most 10 free poses, it
-                             * accumulates on the tensor cores instead, each term as three
-                             * TF32 products (hi.hi + hi.lo + lo.hi); the tensor cores'
-                             * FP32 accumulation truncates, and on ill-conditioned reduced
-                             * systems the pose update error grows about 5x (measured
-                             * up to 1e-5 relative end to end, vs 1e-6 in FP32)          */
+    int32_t schur_tf32;     /* Where sum_k E_k C_k^-1 E_k^T accumulates.  Up to 15 free
+                             * poses (the Schur sums fused into the linearisation):
+                             * mode 0 (default) and 2 in FP32 with compensated sums on the
+                             * CUDA cores; mode 1, when every problem of the batch has at
+                             * most 10 free poses, on the tensor cores, each term as three
+                             * TF32 products (hi.hi + hi.lo + lo.hi).  Beyond 15 free poses
+                             * (a separate assembly launch): modes 0 and 1 on the tensor
+                             * cores (three TF32 products, the FP32 accumulation in TMEM
+                             * over at most 2048 patches, the ranges added in FP64), mode
+                             * 2 in compensated FP32 on the CUDA cores.  The tensor cores'
+                             * FP32 accumulation truncates: on the fused path's
+                             * ill-conditioned systems the pose update error grows about
+                             * 5x (measured up to 1e-5 relative end to end, vs 1e-6 in
+                             * FP32); on the wide windows both assemblies meet 1e-4 per
+                             * iteration against the FP64 oracle                           */
+    int32_t reduced_solve_f64; /* 0 (default): the reduced pose system is factored in FP32
+                             * and its solution refined against the FP64 system, with
+                             * FP64 elimination where an FP32 pivot fails or the
+                             * refinement stalls.  1: FP64 elimination always (slower;
+                             * the reference mode of the fallback path)                  */
 } dpvo_ba_config;
 
 /* One problem's device arrays (caller-owned).

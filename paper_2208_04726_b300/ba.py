@@ -27,7 +27,8 @@ class Dims(ctypes.Structure):
 
 class Config(ctypes.Structure):
     _fields_ = [("damping", ctypes.c_float), ("z_min", ctypes.c_float), ("mem_budget_bytes", ctypes.c_size_t),
-                ("max_sessions", ctypes.c_int32), ("schur_tf32", ctypes.c_int32)]
+                ("max_sessions", ctypes.c_int32), ("schur_tf32", ctypes.c_int32),
+                ("reduced_solve_f64", ctypes.c_int32)]
 
 
 class Grads(ctypes.Structure):
@@ -210,10 +211,16 @@ class Solver:
     """A library handle (workspace + staging) on the current CUDA device."""
 
     def __init__(self, damping: float = 1e-4, z_min: float = 0.1, mem_budget_bytes: int = 0,
-                 max_sessions: int = 0, schur_tf32: bool = False):
+                 max_sessions: int = 0, schur_tf32=False, reduced_solve_f64: bool = False):
+        """schur_tf32: the Schur mode of dpvo_ba_config (False / 0: the default,
+        True / 1: tensor cores on the fused path too, 2: FP32 CUDA cores
+        everywhere)."""
         self.lib = load()
-        self.schur_tf32 = bool(schur_tf32)
-        cfg = Config(damping, z_min, mem_budget_bytes, max_sessions, 1 if schur_tf32 else 0)
+        self.schur_mode = int(schur_tf32)
+        if self.schur_mode not in (0, 1, 2):
+            raise ValueError("schur_tf32 must be 0, 1 or 2")
+        self.schur_tf32 = self.schur_mode == 1
+        cfg = Config(damping, z_min, mem_budget_bytes, max_sessions, self.schur_mode, 1 if reduced_solve_f64 else 0)
         h = ctypes.c_void_p()
         _check(self.lib.dpvo_ba_create(ctypes.byref(cfg), ctypes.byref(h)), "dpvo_ba_create")
         self.h = h

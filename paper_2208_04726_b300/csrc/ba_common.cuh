@@ -77,6 +77,7 @@ struct Prob {
     int L;                   // doubles per partial
     int chunk_cap;           // patches per chunk at most
     int win_cap;             // frames per chunk window at most
+    int solve_f64;           // reduced solve by FP64 elimination only (no FP32 factor)
     int plan_ticket;         // plan CTAs of this problem done with their edge slices (0 on upload)
     int plan_bad;            // an edge slice found invalid input (0 on upload)
 };

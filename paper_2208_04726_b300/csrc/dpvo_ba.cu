@@ -187,14 +187,14 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         L.iters_max = std::max(L.iters_max, dims[b].n_iters);
     }
     L.n_max = n_max;
-    L.tc = cfg.schur_tf32 && use_tensor_cores(L.nf_max);
+    L.tc = cfg.schur_tf32 == 1 && use_tensor_cores(L.nf_max);
     L.W_cap = std::min(n_max, kMaxWindow);
     L.G_cap = 64;
     while (L.G_cap > 8 && lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes > kLinSmemBudget)
         L.G_cap -= 8;
     L.lin_smem = lin_smem_layout(L.W_cap, L.G_cap, L.nf_max, n_max, L.tc).bytes;
     L.ext = L.nf_max > kFusedMaxFree;
-    L.tc_asm = L.ext && cfg.schur_tf32;
+    L.tc_asm = L.ext && cfg.schur_tf32 != 2;   // beyond kFusedMaxFree: tensor cores unless FP32 is asked
     L.solve_smem = L.ext ? solve_large_smem_bytes(L.nf_max) : solve_smem_bytes(L.nf_max);
     L.sw_smem = L.ext ? 0 : sw_smem_bytes(L.nf_max);
     L.asm_smem = !L.ext ? 0
@@ -214,6 +214,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.nf = d.n_frames - d.t0;
         p.fx = d.fx; p.fy = d.fy; p.cx = d.cx; p.cy = d.cy;
         p.damping = cfg.damping; p.z_min = cfg.z_min;
+        p.solve_f64 = cfg.reduced_solve_f64 ? 1 : 0;
         p.chunk_cap = L.G_cap;
         p.win_cap = L.W_cap;
         p.max_chunks = (d.n_patches + L.G_cap - 1) / L.G_cap + d.n_frames;
@@ -568,6 +569,7 @@ int dpvo_ba_create(const dpvo_ba_config *cfg, dpvo_ba_handle **out) {
     h->cfg.mem_budget_bytes = (size_t)8 << 30;
     h->cfg.max_sessions = 256;
     h->cfg.schur_tf32 = 0;
+    h->cfg.reduced_solve_f64 = 0;
     if (cfg) {
         h->cfg = *cfg;
         if (h->cfg.mem_budget_bytes == 0) h->cfg.mem_budget_bytes = (size_t)8 << 30;
@@ -1419,7 +1421,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     const dpvo_ba_dims &d = *dims;
     const int nf = d.n_frames - d.t0;
     const int W_cap = std::min(d.n_frames, kMaxWindow);
-    const bool tc = cfg && cfg->schur_tf32 && use_tensor_cores(nf);
+    const bool tc = cfg && cfg->schur_tf32 == 1 && use_tensor_cores(nf);
     int G_cap = 64;
     while (G_cap > 8 && lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes > kLinSmemBudget) G_cap -= 8;
     const size_t lin_smem = lin_smem_layout(W_cap, G_cap, nf, d.n_frames, tc).bytes;
@@ -1432,6 +1434,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.N = d.n_frames; p.P = d.n_patches; p.E = d.n_edges; p.t0 = d.t0; p.iters = d.n_iters; p.nf = nf;
     p.fx = d.fx; p.fy = d.fy; p.cx = d.cx; p.cy = d.cy;
     p.damping = damping; p.z_min = z_min;
+    p.solve_f64 = cfg && cfg->reduced_solve_f64 ? 1 : 0;
     p.chunk_cap = G_cap;
     p.win_cap = W_cap;
     p.max_chunks = (d.n_patches + G_cap - 1) / G_cap + d.n_frames;

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
     float *PuT = Sp + panel_off(n);                        // a_ij at [j * ld + i]
     float *PwT = PuT + kPanel * ld;                        // a_ij / p_j at [j * ld + i]
     const int ty = tid >> 4, tx = tid & 15;
-    if (tid == 0) s_use64 = 0;
+    if (tid == 0) s_use64 = pr.solve_f64;
     for (int q = tid; q < n; q += kSolveThreads) {
         x[q] = 0.0;
         bf[q] = (float)(s_dsc[q] * v[q]);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
         PwT[j * ld + c] = 0.f;
     }
     __syncthreads();
-    for (int J = 0; J < n; J += kPanel) {
+    for (int J = 0; J < n && !s_use64; J += kPanel) {
         const int nb = min(kPanel, n - J), Rb = J + nb, m = n - Rb;
         if (tid < 32) {                                    // (1)
             const int ri = packed_index(J + lane, J);

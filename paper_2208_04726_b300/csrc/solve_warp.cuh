@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
     __syncthreads();
 
     // -- 2. FP32 factor (all warps), 3. the first solve (warp 0)
-    const bool factored = sw_factor<R>(Sf, ldf, rp, Minv, Lc, n, tid);
+    const bool factored = !pr.solve_f64 && sw_factor<R>(Sf, ldf, rp, Minv, Lc, n, tid);
     float y[R], xf[R];                           // warp 0: my rows' correction and FP32 view of x
     double prev = 0.0;
     if (tid < 32) {

@@ -31,10 +31,10 @@ MID16 = dataclasses.replace(S.WINDOW_N22, n_frames=24, patches_per_frame=48, rad
 MID25 = dataclasses.replace(S.STRESS_N64, n_frames=33, patches_per_frame=32, radius=16, t0=8, n_iters=2)
 
 
-@pytest.fixture(scope="module", params=[False, True], ids=["fp32-schur", "tf32-schur"])
+@pytest.fixture(scope="module", params=[0, 2], ids=["tc-assembly", "fp32-assembly"])
 def solver(request):
-    """Beyond 15 free poses the default assembles on the CUDA cores; the opt-in
-    TF32 mode assembles on the tensor cores."""
+    """Beyond 15 free poses the default (mode 0) assembles on the tensor cores;
+    mode 2 assembles in compensated FP32 on the CUDA cores."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     s = ba.Solver(schur_tf32=request.param)
@@ -46,7 +46,7 @@ def schur_tol(solver):
     """Reduced system against the oracle's: compensated FP32 sums reach 2e-6;
     the tensor cores' FP32 accumulation over up to 2048 patches per CTA is
     looser."""
-    return 2e-5 if solver.schur_tf32 else 2e-6
+    return 2e-6 if solver.schur_mode == 2 else 2e-5
 
 
 @pytest.mark.parametrize("spec,seed", [(MID32, 0), (MID16, 1), (MID25, 5)])
@@ -132,17 +132,18 @@ def test_stress_instance_matches_dense_oracle():
     """One full large-window instance: 64 frames, 256 patches each (16,384),
     radius 24 (649,216 edges), last 32 poses free, 4 iterations, 20% outliers,
     against the dense FP64 oracle (a 16,768-variable Cholesky per iteration),
-    with both assembly variants."""
+    with both assembly variants (the default on the tensor cores, mode 2 in
+    FP32 on the CUDA cores)."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     sc = S.make_scene(S.STRESS_N64, 1)
     assert sc.n_patches == 16384 and sc.n_edges == 649216
     ref = None
-    for tf32 in (False, True):
-        s = ba.Solver(schur_tf32=tf32)
+    for mode in (0, 2):
+        s = ba.Solver(schur_tf32=mode)
         probs = solve_gpu(s, [sc])
         s.close()
         assert int(probs[0].status.item()) == 0
         e_pose, e_depth, ref = end_to_end_errors(sc, probs[0], ref)
-        print("tf32" if tf32 else "fp32", "stress errors", e_pose, e_depth)
-        assert e_pose < TOL_POSE and e_depth < TOL_DEPTH, (tf32, e_pose, e_depth)
+        print("fp32" if mode == 2 else "tc", "stress errors", e_pose, e_depth)
+        assert e_pose < TOL_POSE and e_depth < TOL_DEPTH, (mode, e_pose, e_depth)

@@ -313,3 +313,30 @@ def test_invalid_arguments_return_einval(solver):
     assert e.value.code == ba.EINVAL
     with pytest.raises(ba.BAError):
         solver.solve([dataclasses.replace(p, t0=0, poses=torch.zeros(33, 7, device="cuda"))])   # 33 free > 32
+
+
+@pytest.mark.parametrize("spec,seed", [(S.PLAIN_N8, 31), (S.WINDOW_N22, 32)])
+def test_reduced_solve_f64_mode_matches_oracle_and_default(spec, seed):
+    """reduced_solve_f64 = 1 takes the FP64 elimination for every reduced
+    system, the path the default mode falls back to when an FP32 pivot fails
+    or the refinement stalls.  Per iteration it meets the oracle's step, and
+    its increments agree with the default mode's FP32 factor refined in FP64
+    (both solve the same FP64 system; the refinement stops within 1e-6 of
+    the solution, relative)."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    sc = S.make_scene(spec, seed)
+    f64 = ba.Solver(reduced_solve_f64=True)
+    dflt = ba.Solver()
+    try:
+        pf = solve_gpu(f64, [sc])
+        pd = solve_gpu(dflt, [sc])
+        assert int(pf[0].status.item()) == int(pd[0].status.item()) == 0
+        for t, (e_xi, e_dd) in enumerate(iteration_errors(f64, sc, 0, sc.n_iters)):
+            assert e_xi < TOL_POSE and e_dd < TOL_DEPTH, (t, e_xi, e_dd)
+        _, _, dxi_f = f64.iterate(0, 0, sc.n_frames, sc.n_patches, sc.t0)
+        _, _, dxi_d = dflt.iterate(0, 0, sc.n_frames, sc.n_patches, sc.t0)
+        assert err(dxi_d, dxi_f) < 1e-5
+    finally:
+        f64.close()
+        dflt.close()
