@@ -177,6 +177,21 @@ int check_problem(const dpvo_ba_dims &d, const dpvo_ba_problem &p) {
     return DPVO_BA_OK;
 }
 
+// Linearise work items per problem beyond kFusedMaxFree free poses (long
+// passes over thousands of patches): the count, up to twice the one-wave
+// count plus one, whose whole waves of two CTAs per SM are filled best.
+static int ext_items(int n, int target_ctas) {
+    const int k0 = std::max(1, target_ctas / n);
+    int best = k0;
+    double best_eff = 0.0;
+    for (int k = k0; k <= 2 * k0 + 1; ++k) {
+        const int ctas = n * k, waves = (ctas + target_ctas - 1) / target_ctas;
+        const double eff = (double)ctas / ((double)waves * target_ctas);
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = k; }
+    }
+    return best;
+}
+
 Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_config &cfg, bool adjoint = false) {
     Layout L;
     int n_max = 1;
@@ -224,6 +239,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         // per SM; one assembly CTA per SM), at least one per problem
         int est_chunks = std::max(1, (d.n_patches + L.G_cap - 1) / L.G_cap);
         int items = std::max(1, target_ctas / n);
+        if (L.ext) items = ext_items(n, target_ctas);
         p.n_items = std::max(1, std::min(items, est_chunks));
         if (L.tc_asm) {   // ranges of at most kAtcMaxPatches patches, at least one CTA per SM over the batch
             const int need = (d.n_patches + kAtcMaxPatches - 1) / kAtcMaxPatches;
