@@ -237,10 +237,12 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         p.L = partial_len(p.nf);
         // work items: as many as fill one wave of the SMs (two linearise CTAs
         // per SM; one assembly CTA per SM), at least one per problem
+        // at most one item per chunk: a frame's patches start a new chunk, so
+        // there are up to ceil(P / G) + N of them
         int est_chunks = std::max(1, (d.n_patches + L.G_cap - 1) / L.G_cap);
         int items = std::max(1, target_ctas / n);
         if (L.ext) items = ext_items(n, target_ctas);
-        p.n_items = std::max(1, std::min(items, est_chunks));
+        p.n_items = std::max(1, std::min(items, p.max_chunks));
         if (L.tc_asm) {   // ranges of at most kAtcMaxPatches patches, at least one CTA per SM over the batch
             const int need = (d.n_patches + kAtcMaxPatches - 1) / kAtcMaxPatches;
             const int stages = std::max(1, (d.n_patches + kAtcK - 1) / kAtcK);
@@ -1456,8 +1458,7 @@ extern "C" int dpvo_ba_solve_noalloc(const dpvo_ba_config *cfg, const dpvo_ba_di
     p.max_chunks = (d.n_patches + G_cap - 1) / G_cap + d.n_frames;
     p.ks = tc ? 1 : k_split(nf);
     p.L = partial_len(nf);
-    const int est_chunks = std::max(1, (d.n_patches + G_cap - 1) / G_cap);
-    p.n_items = std::max(1, std::min(2 * sms, est_chunks));
+    p.n_items = std::max(1, std::min(2 * sms, p.max_chunks));   // at most one item per chunk
     p.n_parts = p.n_items;
     size_t off = 0;
     auto take = [&](size_t bytes) { char *q = base + off; off = al256(off + bytes); return q; };
