@@ -150,7 +150,13 @@ int dpvo_ba_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_pro
 /* The same solve with every array in HOST memory (pageable or pinned): copies
  * the inputs to the handle's device staging area, solves, copies poses,
  * patches and status back, and synchronises before returning.  The pointers in
- * hprobs are host pointers with the layouts above.  Errors: as dpvo_ba_solve. */
+ * hprobs are host pointers with the layouts above.  A call of at least 64
+ * problems goes in up to 8 sub-batches of at least 32: each sub-batch's
+ * descriptors and inputs are copied on a stream of the handle's own (after the
+ * caller's prior work on `stream`), and each is solved on `stream` once its
+ * inputs have landed, so the solves run under the later copies.  Afterwards
+ * dpvo_ba_iterate sees the last sub-batch's problems only (index 0 = its
+ * first).  Errors: as dpvo_ba_solve. */
 int dpvo_ba_solve_host(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *hprobs,
                        int n_problems, void *stream);
 

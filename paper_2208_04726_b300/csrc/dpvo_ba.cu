@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
 #include <cstring>
 #include <vector>
 
@@ -301,6 +302,8 @@ T *rebase(T *off, char *base) { return reinterpret_cast<T *>(base + (uintptr_t)o
 }  // namespace
 
 constexpr int kStageRing = 4;
+constexpr int kHostSubBatches = 8;      // dpvo_ba_solve_host: sub-batches whose solves overlap the copies
+constexpr int kHostSubBatchMin = 32;    // problems per sub-batch at least
 
 struct dpvo_ba_handle {
     dpvo_ba_config cfg;
@@ -317,6 +320,10 @@ struct dpvo_ba_handle {
     bool stage_pending[kStageRing] = {};
     int stage_next = 0;
     char *io = nullptr;             // device staging for dpvo_ba_solve_host
+    cudaStream_t copy_stream = nullptr;              // dpvo_ba_solve_host: input copies of the sub-batches
+    char *ws_sub[kHostSubBatches] = {};              // ... and each sub-batch's own workspace
+    size_t ws_sub_cap[kHostSubBatches] = {};
+    cudaEvent_t copy_ev[kHostSubBatches + 1] = {};   // a sub-batch's inputs landed; the caller's prior work
     size_t io_cap = 0;
     std::vector<Prob> last;         // descriptors of the last solve (for dpvo_ba_iterate)
     bool timing = false;            // record events around launches
@@ -421,10 +428,18 @@ static int set_kernel_attrs(int device) {
 }
 
 // Upload descriptors and run plan + iterations.  dims/probs host arrays.
+// ws_slot >= 0 (dpvo_ba_solve_host's sub-batches): that sub-batch's own
+// workspace, its descriptors uploaded on `upload` (the copy stream), then
+// after_upload() (which enqueues the inputs there and orders `stream` after
+// them) before the kernels go to `stream`.
 static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs, int n,
-                     cudaStream_t stream, double *S_out, double *v_out) {
+                     cudaStream_t stream, double *S_out, double *v_out, int ws_slot = -1,
+                     cudaStream_t upload = nullptr, const std::function<int()> &after_upload = {}) {
     Layout L = make_layout(dims, n, h->num_sms, h->cfg);
-    int rc = grow_device(&h->ws, &h->ws_cap, L.bytes);
+    char *&ws = ws_slot >= 0 ? h->ws_sub[ws_slot] : h->ws;
+    size_t &ws_cap = ws_slot >= 0 ? h->ws_sub_cap[ws_slot] : h->ws_cap;
+    if (!upload) upload = stream;
+    int rc = grow_device(&ws, &ws_cap, L.bytes);
     if (rc) return rc;
     const size_t desc_bytes = L.bytes - L.off_probs;
     char *stage = nullptr;
@@ -436,26 +451,27 @@ static int run_solve(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
         p.poses = q.poses; p.patches = q.patches; p.anchor = q.anchor; p.kk = q.kk; p.jj = q.jj;
         p.target = q.target; p.weight = q.weight; p.status_user = q.status;
         p.bulk_edges = aligned16(q.jj, q.target, q.weight);
-        p.seg = rebase(p.seg, h->ws);
-        p.chunks = rebase(p.chunks, h->ws);
-        p.n_chunks = rebase(p.n_chunks, h->ws);
-        p.status = rebase(p.status, h->ws);
-        p.pose_it = rebase(p.pose_it, h->ws);
-        p.depth_it = rebase(p.depth_it, h->ws);
-        p.dxi = rebase(p.dxi, h->ws);
-        p.partial = rebase(p.partial, h->ws);
-        p.erow = rebase(p.erow, h->ws);
-        if (p.sglob) p.sglob = rebase(p.sglob, h->ws);
+        p.seg = rebase(p.seg, ws);
+        p.chunks = rebase(p.chunks, ws);
+        p.n_chunks = rebase(p.n_chunks, ws);
+        p.status = rebase(p.status, ws);
+        p.pose_it = rebase(p.pose_it, ws);
+        p.depth_it = rebase(p.depth_it, ws);
+        p.dxi = rebase(p.dxi, ws);
+        p.partial = rebase(p.partial, ws);
+        p.erow = rebase(p.erow, ws);
+        if (p.sglob) p.sglob = rebase(p.sglob, ws);
     }
     h->last = L.probs;
     std::memcpy(stage, L.probs.data(), sizeof(Prob) * n);
     std::memcpy(stage + (L.off_items - L.off_probs), L.items.data(), sizeof(Item) * L.items.size());
-    if (cudaMemcpyAsync(h->ws + L.off_probs, stage, desc_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    if (cudaMemcpyAsync(ws + L.off_probs, stage, desc_bytes, cudaMemcpyHostToDevice, upload) != cudaSuccess)
         return DPVO_BA_ECUDA;
-    if ((rc = release_stage(h, stream))) return rc;
+    if ((rc = release_stage(h, upload))) return rc;
+    if (after_upload && (rc = after_upload())) return rc;
 
-    const Prob *d_probs = reinterpret_cast<const Prob *>(h->ws + L.off_probs);
-    const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
+    const Prob *d_probs = reinterpret_cast<const Prob *>(ws + L.off_probs);
+    const Item *d_items = reinterpret_cast<const Item *>(ws + L.off_items);
     const int n_items = L.n_lin_items;
     // with timing on, bracket each launch with a pair of events on `stream`
     auto timed = [&](int kind, auto &&launch) -> int {
@@ -625,6 +641,11 @@ int dpvo_ba_destroy(dpvo_ba_handle *h) {
         if (h->stage[i]) cudaFreeHost(h->stage[i]);
         if (h->stage_done[i]) cudaEventDestroy(h->stage_done[i]);
     }
+    for (cudaEvent_t e : h->copy_ev)
+        if (e) cudaEventDestroy(e);
+    for (char *w : h->ws_sub)
+        if (w) cudaFree(w);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     delete h;
     return DPVO_BA_OK;
@@ -677,10 +698,12 @@ struct KindCopy {
     std::vector<size_t> bytes;      // bytes of problem b
 };
 
+// Copies of problems [b0, b1) of one kind, merged where consecutive
+// problems' host arrays are contiguous.
 int copy_runs(char *dev_base, const KindCopy &k, const std::vector<char *> &host, cudaMemcpyKind dir,
-              cudaStream_t s) {
-    const size_t n = host.size();
-    size_t b = 0;
+              cudaStream_t s, size_t b0 = 0, size_t b1 = SIZE_MAX) {
+    const size_t n = std::min(host.size(), b1);
+    size_t b = b0;
     while (b < n) {
         size_t e = b + 1, len = k.bytes[b];
         while (e < n && host[e] == host[e - 1] + k.bytes[e - 1]) { len += k.bytes[e]; ++e; }
@@ -742,19 +765,59 @@ int dpvo_ba_solve_host(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_b
         host[6].push_back((char *)hp[b].weight);
         host[7].push_back((char *)hp[b].status);
     }
-    for (int q = 0; q < 7; ++q)
-        if (int rc = copy_runs(h->io, k[q], host[q], cudaMemcpyHostToDevice, stream)) return rc;
-    if (int rc = run_solve(h, dims, dp.data(), n_problems, stream, nullptr, nullptr)) return rc;
-    for (int q : {0, 1})
-        if (int rc = copy_runs(h->io, k[q], host[q], cudaMemcpyDeviceToHost, stream)) return rc;
-    bool all_status = true;
-    for (int b = 0; b < n_problems; ++b) all_status = all_status && hp[b].status;
-    if (all_status) {
-        if (int rc = copy_runs(h->io, k[7], host[7], cudaMemcpyDeviceToHost, stream)) return rc;
-    } else {
-        for (int b = 0; b < n_problems; ++b)
-            if (hp[b].status && cudaMemcpyAsync(hp[b].status, dp[b].status, 4, cudaMemcpyDeviceToHost, stream))
+    // Large calls go in up to kHostSubBatches sub-batches: the inputs of
+    // every sub-batch are copied on the handle's copy stream, and each
+    // sub-batch is solved on the caller's stream once its inputs have landed,
+    // so that the solves run under the copies of the later sub-batches.
+    const int subs = std::max(1, std::min(kHostSubBatches, n_problems / kHostSubBatchMin));
+    cudaStream_t cs = stream;
+    if (subs > 1) {
+        if (!h->copy_stream) {
+            if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess) return DPVO_BA_ECUDA;
+            for (int s = 0; s <= kHostSubBatches; ++s)
+                if (cudaEventCreateWithFlags(&h->copy_ev[s], cudaEventDisableTiming) != cudaSuccess)
+                    return DPVO_BA_ECUDA;
+        }
+        cs = h->copy_stream;
+        if (cudaEventRecord(h->copy_ev[kHostSubBatches], stream) != cudaSuccess ||   // after the caller's work
+            cudaStreamWaitEvent(cs, h->copy_ev[kHostSubBatches], 0) != cudaSuccess)
+            return DPVO_BA_ECUDA;
+    }
+    auto range = [&](int s, int &b0, int &b1) {
+        b0 = (int)((long long)s * n_problems / subs);
+        b1 = (int)((long long)(s + 1) * n_problems / subs);
+    };
+    // Enqueued sub-batch by sub-batch: a solve's own descriptor upload is a
+    // host-to-device copy too, and it must not queue behind the later
+    // sub-batches' inputs on the copy engine.
+    for (int s = 0; s < subs; ++s) {
+        int b0, b1;
+        range(s, b0, b1);
+        auto inputs = [&]() -> int {                      // the sub-batch's inputs, on cs
+            for (int q = 0; q < 7; ++q)
+                if (int r = copy_runs(h->io, k[q], host[q], cudaMemcpyHostToDevice, cs, b0, b1)) return r;
+            if (subs > 1 && (cudaEventRecord(h->copy_ev[s], cs) != cudaSuccess ||
+                             cudaStreamWaitEvent(stream, h->copy_ev[s], 0) != cudaSuccess))
                 return DPVO_BA_ECUDA;
+            return DPVO_BA_OK;
+        };
+        // with sub-batches: its descriptors (its own workspace) go on cs ahead
+        // of its inputs, so that one copy queue holds them in order
+        int rc = subs > 1 ? run_solve(h, dims + b0, dp.data() + b0, b1 - b0, stream, nullptr, nullptr, s, cs, inputs)
+                          : (inputs() ? DPVO_BA_ECUDA
+                                      : run_solve(h, dims + b0, dp.data() + b0, b1 - b0, stream, nullptr, nullptr));
+        if (rc) return rc;
+        for (int q : {0, 1})
+            if (int rc = copy_runs(h->io, k[q], host[q], cudaMemcpyDeviceToHost, stream, b0, b1)) return rc;
+        bool all_status = true;
+        for (int b = b0; b < b1; ++b) all_status = all_status && hp[b].status;
+        if (all_status) {
+            if (int rc = copy_runs(h->io, k[7], host[7], cudaMemcpyDeviceToHost, stream, b0, b1)) return rc;
+        } else {
+            for (int b = b0; b < b1; ++b)
+                if (hp[b].status && cudaMemcpyAsync(hp[b].status, dp[b].status, 4, cudaMemcpyDeviceToHost, stream))
+                    return DPVO_BA_ECUDA;
+        }
     }
     if (cudaStreamSynchronize(stream) != cudaSuccess) return DPVO_BA_ECUDA;
     return DPVO_BA_OK;

@@ -305,6 +305,33 @@ def test_host_buffer_entry_point_matches_device_entry_point(solver):
     assert np.array_equal(h["patches"], dev.patches.cpu().numpy())
 
 
+def test_host_buffer_entry_point_in_sub_batches(solver):
+    """72 problems through the host-buffer entry point go in two sub-batches of
+    36 (inputs copied on the handle's copy stream, each sub-batch solved once
+    its inputs landed).  Every problem's result matches the same problem solved
+    from device buffers in one batch of 72, within the parity tolerance (the
+    batches split the Schur sums over different numbers of CTAs), and
+    afterwards the iterates of the last sub-batch are readable."""
+    scenes = [S.make_scene(S.PLAIN_N8, 700 + (b % 6)) for b in range(72)]
+    dev = solve_gpu(solver, scenes)
+    hs = [dict(poses=sc.poses.copy(), patches=sc.patches.copy(), anchor=sc.anchor.copy(), kk=sc.kk.copy(),
+               jj=sc.jj.copy(), target=sc.target.copy(), weight=sc.weight.copy(),
+               status=np.zeros(1, np.int32), intrinsics=sc.intrinsics, t0=sc.t0, n_iters=sc.n_iters)
+          for sc in scenes]
+    solver.solve_host(hs)
+    for b, (h, sc) in enumerate(zip(hs, scenes)):
+        assert h["status"][0] == 0, b
+        t0 = sc.t0
+        dp = dev[b].poses.cpu().numpy().astype(np.float64) - sc.poses
+        hp = h["poses"].astype(np.float64) - sc.poses
+        assert err(hp[t0:], dp[t0:]) < TOL_POSE, b
+        dd = dev[b].patches[:, 2].cpu().numpy().astype(np.float64) - sc.patches[:, 2]
+        hd = h["patches"][:, 2].astype(np.float64) - sc.patches[:, 2]
+        assert err(hd, dd) < TOL_DEPTH, b
+    poses, _, _ = solver.iterate(0, scenes[36].n_iters, scenes[36].n_frames, scenes[36].n_patches, scenes[36].t0)
+    assert np.array_equal(poses, hs[36]["poses"])
+
+
 def test_invalid_arguments_return_einval(solver):
     sc = S.make_scene(S.PLAIN_N8, 49)
     p = ba.problem_from_scene(sc)
