@@ -181,10 +181,12 @@ typedef struct {
  * Jacobian), linear solve (Schur complement with the kept factor), and the
  * per-edge residual and Jacobian terms including the Jacobian's own
  * derivative.  Inactive edges and self edges get zero gradient; a problem
- * whose status is not OK gets zero gradients.  Asynchronous on stream.
- * Errors: EINVAL (as dpvo_ba_solve, a NULL gradient buffer, or more than 15
- * free poses: the adjoint keeps the fused Schur path's FP64 factor), ENOMEM,
- * ECUDA. */
+ * whose status is not OK gets zero gradients.  Up to DPVO_BA_MAX_FREE free
+ * poses: beyond 15 the forward's reduced systems are eliminated in FP64 (their
+ * factors kept, n (n + 1) / 2 doubles per iteration) and the adjoint's
+ * right-hand side sum_k E_k C_k^-1 dbar_k is assembled from the rows of each
+ * adjoint linearisation, in the forward's Schur mode.  Asynchronous on stream.
+ * Errors: EINVAL (as dpvo_ba_solve, a NULL gradient buffer), ENOMEM, ECUDA. */
 int dpvo_ba_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_problem *probs,
                      const dpvo_ba_grads *grads, int n_problems, void *stream);
 

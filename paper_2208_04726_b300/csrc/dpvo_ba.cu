@@ -560,16 +560,25 @@ static int run_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_
     const Item *d_items = reinterpret_cast<const Item *>(h->ws + L.off_items);
     const int n_items = L.n_lin_items;
     const size_t bw_smem = bw_smem_layout(L.W_cap, L.G_cap, L.n_max).bytes;
+    const Item *d_asm_items = d_items + L.n_lin_items;
     launch_plan(n, L.e_max, h->num_sms, stream, d_probs);
     for (int t = 0; t < L.iters_max; ++t) {
         launch_linearize(L, n_items, stream, d_probs, d_items, t, 0);
-        solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+        if (L.ext) {   // beyond kFusedMaxFree: the assembly, then the packed solve keeping its FP64 factor
+            launch_assembly(L, stream, d_probs, d_asm_items, t);
+            solve_large_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+        } else {
+            solve_kernel<<<n, kSolveThreads, L.solve_smem, stream>>>(d_probs, t, nullptr, nullptr);
+        }
     }
     launch_final(L, n, stream, d_probs, L.iters_max);
     bw_init_kernel<<<n, kThreads, 0, stream>>>(d_probs);
     for (int t = L.iters_max - 1; t >= 0; --t) {
         bw_retract_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
         launch_linearize(L, n_items, stream, d_probs, d_items, t, 1);
+        // beyond kFusedMaxFree the right-hand side sum_k E_k C_k^-1 dbar_k comes
+        // from the assembly's v' part over the rows the adjoint pass stored
+        if (L.ext) launch_assembly(L, stream, d_probs, d_asm_items, t);
         bw_solve_kernel<<<n, kSolveThreads, 0, stream>>>(d_probs, t);
         bw_edge_kernel<<<n_items, kThreads, bw_smem, stream>>>(d_probs, d_items, t, L.W_cap, L.G_cap, L.n_max);
     }
@@ -585,7 +594,6 @@ int dpvo_ba_backward(dpvo_ba_handle *h, const dpvo_ba_dims *dims, const dpvo_ba_
     for (int b = 0; b < n_problems; ++b) {
         if (int rc = check_dims(dims[b])) return rc;
         if (int rc = check_problem(dims[b], probs[b])) return rc;
-        if (dims[b].n_frames - dims[b].t0 > kFusedMaxFree) return DPVO_BA_EINVAL;
         const dpvo_ba_grads &g = grads[b];
         if (!g.dL_dposes || (dims[b].n_patches > 0 && !g.dL_ddepth) ||
             (dims[b].n_edges > 0 && (!g.dL_dtarget || !g.dL_dweight)))

@@ -1170,7 +1170,9 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         if constexpr (!TC) {
             // this chunk's scaled rows to global memory: one bulk copy when the
             // shared row stride is the problem's, else one per row (warp 0)
-            if (warp == 0 && !adjoint_rhs) {
+            // (beyond kFusedMaxFree the adjoint right-hand side is summed from
+            // these rows too: they carry C_k^-1/2 dbar_k in place of C_k^-1/2 w_k)
+            if (warp == 0 && (EXT || !adjoint_rhs)) {
                 if (ES == RS) {
                     if (lane == 0) bulk_copy_s2g(pr.erow + (size_t)k0 * RS, Ec, (uint32_t)(cnt * RS * 4));
                 } else {

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
     float *PuT = Sp + panel_off(n);                        // a_ij at [j * ld + i]
     float *PwT = PuT + kPanel * ld;                        // a_ij / p_j at [j * ld + i]
     const int ty = tid >> 4, tx = tid & 15;
-    if (tid == 0) s_use64 = pr.solve_f64;
+    if (tid == 0) s_use64 = pr.solve_f64 || pr.store_factor;   // the adjoint keeps the FP64 factor
     for (int q = tid; q < n; q += kSolveThreads) {
         x[q] = 0.0;
         bf[q] = (float)(s_dsc[q] * v[q]);
@@ -375,6 +375,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_large_kernel(const Prob *
             __syncthreads();
         }
         __syncthreads();
+        if (!s_flag && pr.store_factor) {                   // U for the adjoint solve (packed lower)
+            double *u = pr.ufac + (size_t)t * np;
+            for (int q = tid; q < np; q += kSolveThreads) u[q] = Sd[q];
+        }
         if (!s_flag && tid < 32) {                          // U^T x = v'
             for (int j = n - 1; j >= 0; --j) {
                 const double xj = v[j] * s_rp[j];

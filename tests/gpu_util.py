@@ -142,3 +142,30 @@ def end_to_end_errors(scene, prob, ref=None):
     e_pose = err(poses[t0:] - p0[t0:], ref["poses"][t0:] - p0[t0:]) if scene.n_frames > t0 else 0.0
     e_depth = err(depths - scene.patches[:, 2], ref["depths"] - scene.patches[:, 2].astype(np.float64))
     return e_pose, e_depth, ref
+
+
+def loss_grads(scene, poses, depths):
+    """dL/dposes [N,7] and dL/ddepth [P] of the ground-truth loss at the given final state."""
+    gt = scene.poses_gt.astype(np.float64)
+    gp = np.zeros((scene.n_frames, 7))
+    for a in range(scene.t0, scene.n_frames):
+        q = poses[a, 3:].astype(np.float64)
+        s = 1.0 if np.dot(q, gt[a, 3:]) >= 0 else -1.0
+        gp[a, :3] = 2 * (poses[a, :3] - gt[a, :3])
+        gp[a, 3:] = 2 * (q - s * gt[a, 3:])
+    gd = 2 * (depths.astype(np.float64) - scene.depth_gt)
+    return gp, gd
+
+
+def oracle_loss(sc, target, weight):
+    """The ground-truth loss of the oracle's solve with the given targets and
+    weights (for central differences of the layer)."""
+    sc2 = dataclasses.replace(sc, target=target, weight=weight)
+    out = dg.solve_scene(sc2)
+    L = float(np.sum((out["depths"] - sc.depth_gt.astype(np.float64)) ** 2))
+    gt = sc.poses_gt.astype(np.float64)
+    for a in range(sc.t0, sc.n_frames):
+        q = out["poses"][a, 3:]
+        s = 1.0 if np.dot(q, gt[a, 3:]) >= 0 else -1.0
+        L += np.sum((out["poses"][a, :3] - gt[a, :3]) ** 2) + np.sum((q - s * gt[a, 3:]) ** 2)
+    return L

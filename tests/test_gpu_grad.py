@@ -17,7 +17,7 @@ from paper_2208_04726_b300 import ba
 from paper_2208_04726_b300 import scenes as S
 from oracle import dense_gn as dg
 from oracle import unrolled_grad as ug
-from tests.gpu_util import TOL_GRAD, err
+from tests.gpu_util import TOL_GRAD, err, loss_grads, oracle_loss
 
 pytestmark = pytest.mark.gpu
 
@@ -31,19 +31,6 @@ def solver():
     s = ba.Solver()
     yield s
     s.close()
-
-
-def loss_grads(scene, poses, depths):
-    """dL/dposes [N,7] and dL/ddepth [P] of the ground-truth loss at the given final state."""
-    gt = scene.poses_gt.astype(np.float64)
-    gp = np.zeros((scene.n_frames, 7))
-    for a in range(scene.t0, scene.n_frames):
-        q = poses[a, 3:].astype(np.float64)
-        s = 1.0 if np.dot(q, gt[a, 3:]) >= 0 else -1.0
-        gp[a, :3] = 2 * (poses[a, :3] - gt[a, :3])
-        gp[a, 3:] = 2 * (q - s * gt[a, 3:])
-    gd = 2 * (depths.astype(np.float64) - scene.depth_gt)
-    return gp, gd
 
 
 def gpu_gradients(solver, scenes):
@@ -83,18 +70,6 @@ def test_backward_batch_of_sixteen_problems(solver):
         assert err(gts[b], ref_t) < TOL_GRAD and err(gws[b], ref_w) < TOL_GRAD, b
 
 
-def _oracle_loss(sc, target, weight):
-    sc2 = dataclasses.replace(sc, target=target, weight=weight)
-    out = dg.solve_scene(sc2)
-    L = float(np.sum((out["depths"] - sc.depth_gt.astype(np.float64)) ** 2))
-    gt = sc.poses_gt.astype(np.float64)
-    for a in range(sc.t0, sc.n_frames):
-        q = out["poses"][a, 3:]
-        s = 1.0 if np.dot(q, gt[a, 3:]) >= 0 else -1.0
-        L += np.sum((out["poses"][a, :3] - gt[a, :3]) ** 2) + np.sum((q - s * gt[a, 3:]) ** 2)
-    return L
-
-
 def test_backward_matches_central_differences(solver):
     """FP64 central differences (h = 1e-6) of the oracle on 32 random coordinates."""
     sc = S.make_scene(SMALL, 3)
@@ -115,7 +90,7 @@ def test_backward_matches_central_differences(solver):
             t_p[e, c] += h; t_m[e, c] -= h
         else:
             w_p[e, c] += h; w_m[e, c] -= h
-        fd = (_oracle_loss(sc, t_p, w_p) - _oracle_loss(sc, t_m, w_m)) / (2 * h)
+        fd = (oracle_loss(sc, t_p, w_p) - oracle_loss(sc, t_m, w_m)) / (2 * h)
         g = gts[0][e, c] if which == "target" else gws[0][e, c]
         scale = scale_t if which == "target" else scale_w
         assert abs(g - fd) < TOL_GRAD * scale, (which, e, c, g, fd)

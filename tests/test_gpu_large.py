@@ -8,6 +8,7 @@ products on the tensor cores in the TF32 Schur mode); the solve factors S in
 FP32 and refines in FP64 (packed storage).  Sec. 3.1: the same Gauss-Newton
 step, compared with the FP64 oracle.
 """
+import ctypes
 import dataclasses
 
 import numpy as np
@@ -18,8 +19,9 @@ from paper_2208_04726_b300 import ba
 from paper_2208_04726_b300 import scenes as S
 from oracle import dense_gn as dg
 from oracle import schur
-from tests.gpu_util import (TOL_DEPTH, TOL_POSE, end_to_end_errors, iteration_abs_errors, iteration_errors, err,
-                            solve_gpu)
+from oracle import unrolled_grad as ug
+from tests.gpu_util import (TOL_DEPTH, TOL_GRAD, TOL_POSE, end_to_end_errors, iteration_abs_errors,
+                            iteration_errors, err, loss_grads, oracle_loss, solve_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -118,13 +120,71 @@ def test_bitwise_repeatable(solver):
     assert torch.equal(a.poses, b.poses) and torch.equal(a.patches, b.patches)
 
 
-def test_backward_and_no_alloc_paths_refuse_more_than_15_free_poses(solver):
+def test_no_alloc_path_refuses_more_than_15_free_poses():
+    """The allocation-free entry point has no assembly kernel: EINVAL beyond
+    15 free poses (the backward takes up to 32, tested below)."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
     sc = S.make_scene(MID16, 14)
     p = ba.problem_from_scene(sc)
-    g = torch.zeros_like(p.poses)
-    with pytest.raises(ba.BAError) as e:
-        solver.backward([p], [g], [torch.zeros_like(p.patches[:, 2])])
-    assert e.value.code == ba.EINVAL
+    d, c = p.dims(), p.cstruct()
+    rc = ba.load().dpvo_ba_solve_noalloc(None, ctypes.byref(d), ctypes.byref(c),
+                                         torch.cuda.current_stream().cuda_stream)
+    assert rc == ba.EINVAL
+
+
+def _grads(solver, sc):
+    """Forward solve for the final state, then the adjoint of the
+    ground-truth loss from the initial state (as tests/test_gpu_grad.py)."""
+    fwd = ba.problem_from_scene(sc)
+    solver.solve([fwd])
+    torch.cuda.synchronize()
+    gp, gd = loss_grads(sc, fwd.poses.cpu().numpy(), fwd.patches[:, 2].cpu().numpy())
+    start = ba.problem_from_scene(sc)
+    gts, gws = solver.backward([start], [torch.tensor(gp, dtype=torch.float32, device="cuda")],
+                               [torch.tensor(gd, dtype=torch.float32, device="cuda")])
+    torch.cuda.synchronize()
+    assert torch.equal(start.poses.cpu(), torch.as_tensor(sc.poses))
+    return gts[0].cpu().numpy(), gws[0].cpu().numpy()
+
+
+@pytest.mark.parametrize("spec,seed", [(MID16, 15), (MID32, 16)])
+def test_backward_beyond_15_free_poses_matches_autograd_twin(solver, spec, seed):
+    """The adjoint through the assembly path (16 and 32 free poses, both
+    assemblies): the forward keeps each iteration's FP64 factor, and the
+    right-hand side sum_k E_k C_k^-1 dbar_k is assembled from the adjoint
+    pass's rows.  Against the FP64 torch-autograd twin at 1e-3."""
+    sc = S.make_scene(spec, seed)
+    gt, gw = _grads(solver, sc)
+    ref_t, ref_w, _ = ug.gradient(sc)
+    assert err(gt, ref_t) < TOL_GRAD, err(gt, ref_t)
+    assert err(gw, ref_w) < TOL_GRAD, err(gw, ref_w)
+
+
+def test_backward_beyond_15_free_poses_matches_central_differences(solver):
+    """FP64 central differences (h = 1e-6) of the dense oracle on 12 random
+    target and weight coordinates of a 16-free-pose problem."""
+    sc = S.make_scene(dataclasses.replace(MID16, patches_per_frame=16), 17)
+    gt, gw = _grads(solver, sc)
+    rng = np.random.default_rng(7)
+    h, checked = 1e-6, 0
+    scale_t, scale_w = np.abs(gt).max(), np.abs(gw).max()
+    while checked < 12:
+        e, c = int(rng.integers(sc.n_edges)), int(rng.integers(2))
+        if sc.anchor[sc.kk[e]] == sc.jj[e]:
+            continue
+        which = "target" if checked % 2 == 0 else "weight"
+        tp, tm = sc.target.astype(np.float64).copy(), sc.target.astype(np.float64).copy()
+        wp, wm = sc.weight.astype(np.float64).copy(), sc.weight.astype(np.float64).copy()
+        if which == "target":
+            tp[e, c] += h; tm[e, c] -= h
+        else:
+            wp[e, c] += h; wm[e, c] -= h
+        fd = (oracle_loss(sc, tp, wp) - oracle_loss(sc, tm, wm)) / (2 * h)
+        g = gt[e, c] if which == "target" else gw[e, c]
+        scale = scale_t if which == "target" else scale_w
+        assert abs(g - fd) < TOL_GRAD * scale, (which, e, c, g, fd)
+        checked += 1
 
 
 @pytest.mark.slow
