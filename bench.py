@@ -599,7 +599,38 @@ def serving_bench(n_sessions=256, distinct=32, rate=2000.0, duration=2.0, satura
         out[mode] = res
         srv.serve_stop()
         srv.close()
+    out["full_batch_linearize_hbm"] = serving_batch_hbm([mix[sess_of[b]] for b in range(n_sessions)])
     return out
+
+
+def serving_batch_hbm(scenes):
+    """The linearise launch on one full batch of the serving mix (every
+    session's problem in one batched solve): its device time from the library's
+    launch events and its HBM fraction by the algorithmic bytes (24 per edge,
+    20 per patch), for comparison with the window batch's roofline."""
+    import torch
+    from paper_2208_04726_b300 import ba
+    batch = ba.PackedBatch(scenes, "cuda")
+    solver = ba.Solver()
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        batch.reset()
+        solver.solve_arrays(batch.dims, batch.probs, len(scenes), stream)
+    solver.set_timing(True)
+    solver.timing()
+    for _ in range(10):
+        batch.reset()
+        solver.solve_arrays(batch.dims, batch.probs, len(scenes), stream)
+    torch.cuda.synchronize()
+    lin = [ms for k, ms in solver.timing(cap=4096) if k == 1]
+    solver.set_timing(False)
+    solver.close()
+    t = float(np.median(lin))
+    bytes_ = float(sum(24.0 * sc.n_edges + 20.0 * sc.n_patches for sc in scenes))
+    peak, src = load_peaks()
+    gbs = bytes_ / (t / 1e3) / 1e9
+    return {"problems": len(scenes), "linearize_ms": t, "algorithmic_bytes": bytes_, "achieved_gbs": gbs,
+            "peak_gbs": peak, "frac": gbs / peak, "peak_source": src}
 
 
 def serving_slid_bench(n_default=128, n_fast=128, rate=2000.0, duration=2.0, saturate=1.0, seed=2):

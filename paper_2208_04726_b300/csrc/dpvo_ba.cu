@@ -220,6 +220,14 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
 
     const int target_ctas = 2 * num_sms;
     const int final_cap = std::max(1, (6 * num_sms + n - 1) / n);   // one wave of final_kernel CTAs
+    // a batch of unequal problems (serving mixes) deals the linearise CTAs in
+    // proportion to each problem's edges, so that the CTAs' work is even
+    double work_total = 0.0;
+    bool uniform = true;
+    for (int b = 0; b < n; ++b) {
+        work_total += (double)dims[b].n_edges + dims[b].n_patches;
+        uniform = uniform && dims[b].n_edges == dims[0].n_edges && dims[b].n_patches == dims[0].n_patches;
+    }
     size_t off = 0;
     L.probs.resize(n);
     for (int b = 0; b < n; ++b) {
@@ -243,6 +251,8 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         int est_chunks = std::max(1, (d.n_patches + L.G_cap - 1) / L.G_cap);
         int items = std::max(1, target_ctas / n);
         if (L.ext) items = ext_items(n, target_ctas);
+        else if (!uniform && work_total > 0.0)
+            items = std::max(1, (int)(target_ctas * ((double)d.n_edges + d.n_patches) / work_total));
         p.n_items = std::max(1, std::min(items, p.max_chunks));
         if (L.tc_asm) {   // ranges of at most kAtcMaxPatches patches, at least one CTA per SM over the batch
             const int need = (d.n_patches + kAtcMaxPatches - 1) / kAtcMaxPatches;
