@@ -86,13 +86,14 @@ static void launch_plan(int n, int e_max, int num_sms, cudaStream_t stream, cons
 }
 
 // The forward reduced solve of at most kFusedMaxFree free poses: one CTA per
-// problem, or a cluster of kSwCluster CTAs per problem where some problem has
-// several Schur partials (they sum them); the rows per lane set by the
-// largest problem.
+// problem, which sums the problem's Schur partials itself, or a cluster of
+// kSwCluster CTAs per problem where some problem has more than kSwDirectParts
+// partials (they sum them; a cluster grid of a large batch would take several
+// waves); the rows per lane set by the largest problem.
 static void launch_solve_warp(int nf_max, int max_parts, int n, cudaStream_t stream, const Prob *probs, int t,
                               size_t smem) {
     auto kernel = sw_rows(nf_max) == 2 ? solve_warp_kernel<2> : solve_warp_kernel<3>;
-    if (max_parts <= 1 || nf_max == 0) {
+    if (max_parts <= kSwDirectParts || nf_max == 0) {
         kernel<<<n, kSwThreads, smem, stream>>>(probs, t, 1);
         return;
     }

@@ -535,10 +535,12 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float s) {
     return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
 }
 
-// Relative poses of the window frames w.r.t. the anchor (and their adjoints).
+// Relative poses of the window frames w.r.t. the anchor (and their adjoints),
+// by threads tid0 .. kThreads - 1.
 __device__ __forceinline__ void window_poses(const float *poses, int anchor, int jlo, int W, float *rel,
-                                             float *adj) {
-    for (int jl = threadIdx.x; jl < W; jl += kThreads) {
+                                             float *adj, int tid0 = 0) {
+    for (int jl = (int)threadIdx.x - tid0; jl < W; jl += kThreads - tid0) {
+        if (jl < 0) break;
         float *R = rel + jl * 12;
         relative_pose(poses + 7 * anchor, poses + 7 * (jlo + jl), R, R + 9);
         if (adj) adjoint6(R, R + 9, adj + jl * 36);
@@ -1003,7 +1005,8 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 }
             }
         }
-        if (!group_open) window_poses(spn, anc, jlo, W, reln, adj);
+        // (the last warp, which has the fewest patches in this phase)
+        if (!group_open) window_poses(spn, anc, jlo, W, reln, adj, kThreads - 32);
         __syncthreads();
 
         // -- (b) linearise at the new state.  Each edge thread keeps its frame
@@ -1162,6 +1165,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             for (int q = tid; q < W * 27; q += kThreads) {
                 const int jl = q / 27, m = q - jl * 27;
                 float s = 0.f, cc = 0.f;
+#pragma unroll 4
                 for (int g = 0; g < NG; ++g) kahan_add(s, cc, Mp[(size_t)(jl * NG + g) * 27 + m]);
                 Mc[jl * 27 + m] = s - cc;
             }
@@ -1198,6 +1202,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             const int Kc = (cnt + 7) & ~7, n6 = 6 * nf;
             const int r8 = lane >> 2, k4 = lane & 3;
             float *eb = pr.erow + (size_t)c * kTcRows * kmax;
+#pragma unroll 4
             for (int idx = warp; idx < 2 * Kc; idx += kThreads / 32) {   // 8 row groups x Kc / 4 patch groups
                 const int rg = idx & 7, kg = idx >> 3;
                 const int r = 8 * rg + r8, k = 4 * kg + k4;

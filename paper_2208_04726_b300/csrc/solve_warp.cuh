@@ -400,11 +400,13 @@ __device__ inline bool sw_solve_f64(double *S, double *v, int n, int ld, int lan
 }
 
 constexpr int kSwCluster = 8;          // CTAs summing the partials of a problem that has several
+constexpr int kSwDirectParts = 4;      // partials per problem up to which one CTA sums them itself
 
-// One CTA of kSwThreads per problem, or, where some problem of the batch has
-// more than one Schur partial, a cluster of csize = kSwCluster CTAs per
-// problem: each sums a slice of the partials' entries (in the parts' order)
-// into the shared memory of the cluster's first CTA, which then solves.
+// One CTA of kSwThreads per problem, which sums the problem's Schur partials
+// itself, or, where some problem of the batch has more than kSwDirectParts
+// partials, a cluster of csize = kSwCluster CTAs per problem: each sums a
+// slice of the partials' entries into the shared memory of the cluster's
+// first CTA, which then solves.  Both sum the parts in their order.
 // R = sw_rows(nf) of the batch's largest problem.  Problems that keep the
 // FP64 factor for the adjoint use solve_kernel.
 template <int R>
@@ -509,6 +511,12 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
         cl.sync();
         if (rank != 0) return;
     }
+    const int n_parts = csize == 1 ? pr.n_parts : 1;
+    auto v_entry = [&](int q) {                  // entry q of v', summed over the parts
+        double s = pr.partial[18 * nbs + q];
+        for (int part = 1; part < n_parts; ++part) s += pr.partial[(size_t)part * pr.L + 18 * nbs + q];
+        return s;
+    };
     for (int st0 = 0; csize == 1 && st0 < max(nbs, 1); st0 += kStrips * kSwThreads) {
         double2 d2[kStrips][9];
 #pragma unroll
@@ -520,9 +528,29 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
                 for (int e = 0; e < 9; ++e) d2[h][e] = src[e];
             }
         }
+        for (int part = 1; part < n_parts; ++part) {
+            double2 p2[kStrips][9];
+#pragma unroll
+            for (int h = 0; h < kStrips; ++h) {
+                const int st = st0 + h * kSwThreads + tid;
+                if (st < nbs) {
+                    const double2 *src =
+                        reinterpret_cast<const double2 *>(pr.partial + (size_t)part * pr.L + (size_t)st * 18);
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) p2[h][e] = src[e];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < kStrips; ++h)
+#pragma unroll
+                for (int e = 0; e < 9; ++e) {
+                    d2[h][e].x += p2[h][e].x;
+                    d2[h][e].y += p2[h][e].y;
+                }
+        }
         double vq = 0.0;
         if (st0 == 0) {
-            if (tid < n) vq = pr.partial[18 * nbs + tid];
+            if (tid < n) vq = v_entry(tid);
             if (tid == 0) s_status = *pr.status;
             __syncthreads();
             if (s_status != 0 || nf == 0) {      // uniform: every thread passed the barrier
@@ -531,7 +559,7 @@ __global__ void __launch_bounds__(kSwThreads) solve_warp_kernel(const Prob *__re
                 return;
             }
             for (int q = tid; q < n; q += kSwThreads) {
-                v[q] = q == tid ? vq : pr.partial[18 * nbs + q];
+                v[q] = q == tid ? vq : v_entry(q);
                 for (int c = n; c < ldf; ++c) Sf[q * ldf + c] = 0.f;
             }
         }
