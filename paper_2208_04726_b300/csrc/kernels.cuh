@@ -865,63 +865,25 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     __shared__ __align__(8) uint64_t s_rowbar;   // stored-row staging (back-substitution): one phase per chunk
     __shared__ int s_ld_bad;
     const uint32_t ldbar = smem_u32(&s_ldbar), rowbar = smem_u32(&s_rowbar);
-    if (c_begin < c_end) {
-        if (tid == 0) {
-            s_ch[0] = pr.chunks[c_begin];
-            mbar_init(ldbar, 1);
-            mbar_init(rowbar, 1);
-            s_ld_bad = 0;
-        }
-        __syncthreads();
-        prefetch_chunk(pr, s_ch[0], depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg,
-                       c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1], ldbar);
-        if (do_bs) {
-            if constexpr (TC) prefetch_block(pr, c_begin, s_ch[0], kmax, srow);
-            else if (tid == 0) prefetch_rows_bulk(pr, s_ch[0], RS, srow, rowbar);
-        }
-    }
-    int cur = 0;
-    bool group_open = false;   // the previous chunk continues into this one
-
-    bool rows_pending = false;   // warp 0: a bulk row store may still read Ec
-    for (int c = c_begin; c < c_end; ++c) {
-        const Chunk ch = s_ch[cur];
-        const bool have_next = c + 1 < c_end;
-        if (rows_pending) {                                // Ec is rewritten after the next barrier
-            bulk_wait_read_all();
-            rows_pending = false;
-        }
-        cp_async_wait_all();
-        if (!mbar_wait(ldbar, (uint32_t)(c - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
-        if (!TC && do_bs && !mbar_wait(rowbar, (uint32_t)(c - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
-        __syncthreads();                                   // this chunk's inputs are in shared memory
-        if (s_ld_bad) break;                               // a bulk copy never landed: reported below
+    // Preparation of chunk pc (the pk-th of this CTA), from its staged inputs:
+    // the slot -> edge table, the patch data (after the back-substitution of
+    // the previous iteration from the staged rows), and, at the start of a
+    // group, the window poses (parts: 1 the slot table and window poses, 2 the
+    // patch data).  pc is read from shared memory (the descriptor slot stays
+    // valid until the copies of the chunk after next start).  It runs during the previous chunk's Schur products (and
+    // before the loop for the first chunk): it writes only buffers that chunk
+    // no longer reads.  Thread (p = tid mod PS, jl = tid /
+    // PS + (256 / PS) i) for the slots, PS = count rounded up to a power of
+    // two (at least 8).
+    auto prepare = [&](const Chunk &pc, int pk, bool new_group, int parts) {
         int o_jj, o_tw;                                    // alignment slack of the staged edge ranges
-        staged_offsets(pr, ch, true, o_jj, o_tw);
-        Chunk nx = ch;
-        if (have_next) nx = s_ch[cur ^ 1];
-        const bool group_next = have_next && nx.anchor == ch.anchor && nx.jlo == ch.jlo && nx.jhi == ch.jhi;
-        const int k0 = ch.k0, cnt = ch.count, e0 = ch.e0;
-        const int anc = ch.anchor, jlo = ch.jlo;
-        const int W = ch.jhi - jlo + 1;
-        const bool anc_free = anc >= t0;
-        const int NG = kThreads / W;
-        const int my_g = tid % NG, my_jl = tid / NG;       // consecutive lanes: consecutive patches of one frame
-        const int my_j = jlo + my_jl;
-        const bool edge_thread = my_jl < W;
-
-        // -- (0) slot -> edge table, patch data, window poses, cleared E columns.
-        // Thread (p = tid mod PS, jl = tid / PS + (256 / PS) i) for the slots,
-        // PS = cnt rounded up to a power of two (at least 8); LP lanes per
-        // patch for the per-patch phases.
-        int lp_sh = 2;                                     // 4 lanes per patch in the fused variants
+        staged_offsets(pr, pc, true, o_jj, o_tw);
+        const int cnt = pc.count, e0 = pc.e0, k0 = pc.k0, jlo = pc.jlo;
+        const int W = pc.jhi - jlo + 1;
+        int lp_sh = 2;
         const int LP = EXT ? lanes_per_patch(cnt, &lp_sh) : 4;
         const int ps_sh = 8 - lp_sh, PSm = (1 << ps_sh) - 1;
-        if constexpr (TC) {
-            // the previous chunk's MMAs read the operand: wait before rewriting it
-            if (n_commit > 0 && !mbar_wait(smem_u32(&s_mbar), (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_tc_bad, 1);
-        }
-        {
+        if (parts & 1) {
             const int p = tid & PSm;
             if (p < cnt) {
                 const int a = rseg[p] - e0, b = rseg[p + 1] - e0;
@@ -949,23 +911,9 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                     sidx[jl * Gs + p] = (short)(idx >= 0 ? idx + o_tw : -1);   // position in the staged target/weight
                 }
-                for (int f = tid >> ps_sh; f < nf; f += kThreads >> ps_sh) {   // E columns of free frames outside the window are zero
-                    const int fr = t0 + f;
-                    if (fr < jlo || fr > ch.jhi) {
-                        if constexpr (TC) {
-#pragma unroll
-                            for (int m = 0; m < 6; ++m)
-                                *reinterpret_cast<float *>(op + op_offset(kTcRows + 6 * f + m, p, sbo)) = 0.f;
-                        } else {
-                            float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * f);
-                            e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            e4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-                    }
-                }
             }
         }
-        {   // patch data, after the back-substitution of the previous iteration
+        if (parts & 2) {   // patch data, after the back-substitution of the previous iteration
             // from the staged rows (four lanes per patch)
             if constexpr (TC) {
                 // thread (group g = tid / 8, row slice tid % 8): 4 patches per group
@@ -986,6 +934,8 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     }
                 }
             } else {
+                // the staged rows completed on rowbar (each reader waits)
+                if (do_bs && !mbar_wait(rowbar, (uint32_t)pk & 1u)) atomicOr(&s_ld_bad, 1);
                 const int p = tid >> lp_sh, sub = tid & (LP - 1);
                 float s = 0.f;
                 if (do_bs && p < cnt) {
@@ -1006,8 +956,82 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
         }
         // (the last warp, which has the fewest patches in this phase)
-        if (!group_open) window_poses(spn, anc, jlo, W, reln, adj, kThreads - 32);
+        if ((parts & 1) && new_group) window_poses(spn, pc.anchor, jlo, W, reln, adj, kThreads - 32);
+    };
+
+    if (c_begin < c_end) {
+        if (tid == 0) {
+            s_ch[0] = pr.chunks[c_begin];
+            mbar_init(ldbar, 1);
+            mbar_init(rowbar, 1);
+            s_ld_bad = 0;
+        }
         __syncthreads();
+        prefetch_chunk(pr, s_ch[0], depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg,
+                       c_begin + 1 < c_end ? pr.chunks + c_begin + 1 : nullptr, &s_ch[1], ldbar);
+        if (do_bs) {
+            if constexpr (TC) prefetch_block(pr, c_begin, s_ch[0], kmax, srow);
+            else if (tid == 0) prefetch_rows_bulk(pr, s_ch[0], RS, srow, rowbar);
+        }
+        cp_async_wait_all();
+        if (!mbar_wait(ldbar, 0u)) atomicOr(&s_ld_bad, 1);
+        __syncthreads();                                   // the first chunk's inputs are in shared memory
+        if (!s_ld_bad) prepare(s_ch[0], 0, true, 3);
+        __syncthreads();
+    }
+    int cur = 0;
+    bool group_open = false;   // the previous chunk continues into this one
+
+    bool rows_pending = false;   // warp 0: a bulk row store may still read Ec
+    bool rows_issued = false;    // warp 0: bulk row stores to complete before the exit
+    for (int c = c_begin; c < c_end; ++c) {
+        // chunk c is prepared (slot table, patch data, window poses) and its
+        // edges are staged; the last barrier of the previous iteration (or
+        // the prologue's) orders all of it
+        if (s_ld_bad) break;                               // a bulk copy never landed: reported below
+        const Chunk ch = s_ch[cur];
+        const bool have_next = c + 1 < c_end;
+        Chunk nx = ch;
+        if (have_next) nx = s_ch[cur ^ 1];
+        const bool group_next = have_next && nx.anchor == ch.anchor && nx.jlo == ch.jlo && nx.jhi == ch.jhi;
+        const int k0 = ch.k0, cnt = ch.count, e0 = ch.e0;
+        const int anc = ch.anchor, jlo = ch.jlo;
+        const int W = ch.jhi - jlo + 1;
+        const bool anc_free = anc >= t0;
+        const int NG = kThreads / W;
+        const int my_g = tid % NG, my_jl = tid / NG;       // consecutive lanes: consecutive patches of one frame
+        const int my_j = jlo + my_jl;
+        const bool edge_thread = my_jl < W;
+
+        // lanes per patch of the per-patch phases (LP) and the slot layout
+        // (PS = 256 >> lp_sh patches by 256 / PS frame rows)
+        int lp_sh = 2;                                     // 4 lanes per patch in the fused variants
+        const int LP = EXT ? lanes_per_patch(cnt, &lp_sh) : 4;
+        const int ps_sh = 8 - lp_sh, PSm = (1 << ps_sh) - 1;
+        if constexpr (TC) {
+            // the previous chunk's MMAs read the operand: wait before rewriting it
+            if (n_commit > 0 && !mbar_wait(smem_u32(&s_mbar), (uint32_t)(n_commit - 1) & 1u)) atomicOr(&s_tc_bad, 1);
+        }
+        {   // E columns of free frames outside the window are zero (the edge
+            // threads write the others)
+            const int p = tid & PSm;
+            if (p < cnt)
+                for (int f = tid >> ps_sh; f < nf; f += kThreads >> ps_sh) {
+                    const int fr = t0 + f;
+                    if (fr < jlo || fr > ch.jhi) {
+                        if constexpr (TC) {
+#pragma unroll
+                            for (int m = 0; m < 6; ++m)
+                                *reinterpret_cast<float *>(op + op_offset(kTcRows + 6 * f + m, p, sbo)) = 0.f;
+                        } else {
+                            float4 *e4 = reinterpret_cast<float4 *>(Ec + p * ES + 8 * f);
+                            e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            e4[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
+                }
+        }
+
 
         // -- (b) linearise at the new state.  Each edge thread keeps its frame
         // sums (M_j, v_j) in its own Mp slot between the chunks of a group.
@@ -1170,6 +1194,10 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 Mc[jl * 27 + m] = s - cc;
             }
         }
+        if (!TC && have_next) {                            // the next chunk's inputs (copies started above)
+            cp_async_wait_all();
+            if (!mbar_wait(ldbar, (uint32_t)(c + 1 - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
+        }
         __syncthreads();
         if constexpr (!TC) {
             // this chunk's scaled rows to global memory: one bulk copy when the
@@ -1185,6 +1213,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 }
                 bulk_commit();
                 rows_pending = true;
+                rows_issued = true;
             }
         }
         // the per-slot sums are consumed: start copying the next chunk's stored rows
@@ -1230,6 +1259,9 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                     *lp = r < n6 ? lo : 0u;
                 }
             }
+            // the next chunk's inputs and stored rows, for its preparation
+            cp_async_wait_all();
+            if (have_next && !mbar_wait(ldbar, (uint32_t)(c + 1 - c_begin) & 1u)) atomicOr(&s_ld_bad, 1);
             fence_async_smem();
             __syncthreads();
             if (tid == 0) {
@@ -1285,6 +1317,13 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
             __syncthreads();
         }
+
+        // the next chunk's slot table, window poses and (without stored rows
+        // to wait for) patch data: none of them is read below (s_ld_bad was
+        // last written before a barrier).  The tensor-core variant, whose
+        // Schur products are not here, prepares after them instead.
+        const bool prep_next = have_next && !s_ld_bad;
+        if (!TC && prep_next) prepare(s_ch[cur ^ 1], c + 1 - c_begin, !group_next, do_bs ? 1 : 3);
 
         // -- (c) Schur accumulation over the chunk's patches, then the group's B blocks.
         // A strip with a frame outside the chunk's window would only add zeros
@@ -1443,12 +1482,19 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 }
             }
         }
+        // with a back-substitution the next chunk's patch data come last, so
+        // that its stored rows (started after the per-patch phase) have landed
+        if (prep_next && (TC || do_bs)) prepare(s_ch[cur ^ 1], c + 1 - c_begin, !group_next, TC ? 3 : 2);
+        if (rows_pending) {                                // Ec is rewritten after the barrier
+            bulk_wait_read_all();
+            rows_pending = false;
+        }
         __syncthreads();
         group_open = group_next;
         cur ^= 1;
     }
     cp_async_wait_all();
-    if (rows_pending) bulk_wait_all();                     // the stored rows are written
+    if (rows_issued) bulk_wait_all();                      // the stored rows are written
     if (c_begin < c_end && s_ld_bad) {
         // report, and give the copy that did not land one more bounded wait
         if (tid == 0) {
