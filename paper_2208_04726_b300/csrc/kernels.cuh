@@ -449,6 +449,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Role rotation of the in-loop prefetch: its first roles (the bulk copies,
+// the descriptor, the patch arrays) go to the last two warps, which hold no
+// patch of the per-patch phase that follows for chunks of up to 48 patches.
+constexpr int kPrefetchRot = 64;
+
 // Start copying one chunk's inputs -- frames, targets and weights of its
 // edges, its patches' centres and inverse depths, its patch -> edge offsets --
 // into the staging buffers.  With an mbarrier (bar != 0) and 16-byte aligned
@@ -468,16 +473,19 @@ __device__ __forceinline__ void staged_offsets(const Prob &pr, const Chunk &ch, 
 __device__ __forceinline__ void prefetch_chunk(const Prob &pr, const Chunk &ch, const float *depth_src, int *rjj,
                                                float2 *rtg, float2 *rwt, float *rpx, float *rpy, float *rdep,
                                                int *rseg, const Chunk *desc_src, Chunk *desc_dst,
-                                               uint32_t bar = 0) {
-    if (desc_src && threadIdx.x < 8)   // the descriptor of the chunk after this one
-        cp_async4(reinterpret_cast<int *>(desc_dst) + threadIdx.x, reinterpret_cast<const int *>(desc_src) + threadIdx.x);
+                                               uint32_t bar = 0, int rot = 0) {
+    // vt: the thread's role, rotated by rot so that the single-thread and
+    // low-index roles can fall on other warps than the first
+    const int vt = ((int)threadIdx.x + rot) & (kThreads - 1);
+    if (desc_src && vt < 8)   // the descriptor of the chunk after this one
+        cp_async4(reinterpret_cast<int *>(desc_dst) + vt, reinterpret_cast<const int *>(desc_src) + vt);
     const float2 *tg = reinterpret_cast<const float2 *>(pr.target);
     const float2 *wt = reinterpret_cast<const float2 *>(pr.weight);
     const int e0 = ch.e0, e1 = ch.e1;
     if (bar != 0 && pr.bulk_edges && e1 > e0) {
         const int a0 = e0 & ~3, a1 = min((e1 + 3) & ~3, pr.E & ~3);   // jj: 4 per 16 bytes
         const int b0 = e0 & ~1, b1 = min((e1 + 1) & ~1, pr.E & ~1);   // target, weight: 2 per 16 bytes
-        if (threadIdx.x == 0) {
+        if (vt == 0) {
             const uint32_t bj = a1 > a0 ? (uint32_t)(a1 - a0) * 4u : 0u;
             const uint32_t bt = b1 > b0 ? (uint32_t)(b1 - b0) * 8u : 0u;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bj + 2u * bt)
@@ -488,29 +496,29 @@ __device__ __forceinline__ void prefetch_chunk(const Prob &pr, const Chunk &ch, 
                 bulk_copy_g2s(rwt, wt + b0, bt, bar);
             }
         }
-        for (int e = max(e0, a1 > a0 ? a1 : e0) + (int)threadIdx.x; e < e1; e += kThreads)
+        for (int e = max(e0, a1 > a0 ? a1 : e0) + vt; e < e1; e += kThreads)
             cp_async4(rjj + (e - a0), pr.jj + e);
-        for (int e = max(e0, b1 > b0 ? b1 : e0) + (int)threadIdx.x; e < e1; e += kThreads) {
+        for (int e = max(e0, b1 > b0 ? b1 : e0) + vt; e < e1; e += kThreads) {
             cp_async8(rtg + (e - b0), tg + e);
             cp_async8(rwt + (e - b0), wt + e);
         }
     } else {
-        if (bar != 0 && threadIdx.x == 0)
+        if (bar != 0 && vt == 0)
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-        for (int q = threadIdx.x; q < e1 - e0; q += kThreads) {
+        for (int q = vt; q < e1 - e0; q += kThreads) {
             const int e = e0 + q;
             cp_async4(rjj + q, pr.jj + e);
             cp_async8(rtg + q, tg + e);
             cp_async8(rwt + q, wt + e);
         }
     }
-    for (int q = threadIdx.x; q < ch.count; q += kThreads) {
+    for (int q = vt; q < ch.count; q += kThreads) {
         const int k = ch.k0 + q;
         cp_async4(rpx + q, pr.patches + 3 * k);
         cp_async4(rpy + q, pr.patches + 3 * k + 1);
         cp_async4(rdep + q, depth_src + k);
     }
-    for (int q = threadIdx.x; q <= ch.count; q += kThreads) cp_async4(rseg + q, pr.seg + ch.k0 + q);
+    for (int q = vt; q <= ch.count; q += kThreads) cp_async4(rseg + q, pr.seg + ch.k0 + q);
     cp_async_commit();
 }
 
@@ -982,8 +990,8 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     int cur = 0;
     bool group_open = false;   // the previous chunk continues into this one
 
-    bool rows_pending = false;   // warp 0: a bulk row store may still read Ec
-    bool rows_issued = false;    // warp 0: bulk row stores to complete before the exit
+    bool rows_pending = false;   // last warp: a bulk row store may still read Ec
+    bool rows_issued = false;    // last warp: bulk row stores to complete before the exit
     for (int c = c_begin; c < c_end; ++c) {
         // chunk c is prepared (slot table, patch data, window poses) and its
         // edges are staged; the last barrier of the previous iteration (or
@@ -1114,7 +1122,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         // the staging buffers are free: start the next chunk's copies
         if (have_next)
             prefetch_chunk(pr, nx, depth_src, rjj_s, rtg_s, rwt_s, rpx, rpy, rdep, rseg,
-                           c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur], ldbar);
+                           c + 2 < c_end ? pr.chunks + c + 2 : nullptr, &s_ch[cur], ldbar, kPrefetchRot);
         {   // per-patch sums over the window by LP lanes: C_k, w_k, Y; then
             // C_k^-1/2, C_k^-1/2 w_k and the anchor column e_ik = -[d Y; pbar x Y]
             const int p = tid >> lp_sh, sub = tid & (LP - 1);
@@ -1185,8 +1193,10 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             }
         }
         if (!group_next && !adjoint_rhs) {
-            // combine the per-thread frame sums (M_j, v_j) over patch groups, compensated
-            for (int q = tid; q < W * 27; q += kThreads) {
+            // combine the per-thread frame sums (M_j, v_j) over patch groups,
+            // compensated; the entries start at the last two warps, which hold
+            // no patch above for chunks of up to 48 patches
+            for (int q = (tid + kPrefetchRot) & (kThreads - 1); q < W * 27; q += kThreads) {
                 const int jl = q / 27, m = q - jl * 27;
                 float s = 0.f, cc = 0.f;
 #pragma unroll 4
@@ -1201,10 +1211,11 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         __syncthreads();
         if constexpr (!TC) {
             // this chunk's scaled rows to global memory: one bulk copy when the
-            // shared row stride is the problem's, else one per row (warp 0)
+            // shared row stride is the problem's, else one per row (the last
+            // warp, which owns the fewest Schur strips)
             // (beyond kFusedMaxFree the adjoint right-hand side is summed from
             // these rows too: they carry C_k^-1/2 dbar_k in place of C_k^-1/2 w_k)
-            if (warp == 0 && (EXT || !adjoint_rhs)) {
+            if (warp == kThreads / 32 - 1 && (EXT || !adjoint_rhs)) {
                 if (ES == RS) {
                     if (lane == 0) bulk_copy_s2g(pr.erow + (size_t)k0 * RS, Ec, (uint32_t)(cnt * RS * 4));
                 } else {
@@ -1219,7 +1230,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         // the per-slot sums are consumed: start copying the next chunk's stored rows
         if (do_bs && have_next) {
             if constexpr (TC) prefetch_block(pr, c + 1, nx, kmax, srow);
-            else if (tid == 0) prefetch_rows_bulk(pr, nx, RS, srow, rowbar);
+            else if (tid == kThreads - 1) prefetch_rows_bulk(pr, nx, RS, srow, rowbar);
         }
         if constexpr (TC) {
             // Scale each pose column by C_k^-1/2, store the rows for the next
