@@ -949,6 +949,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 if (do_bs && p < cnt) {
                     const float4 *row = reinterpret_cast<const float4 *>(srow + p * RSS);
                     const float4 *dz4 = reinterpret_cast<const float4 *>(dxs);
+#pragma unroll 4
                     for (int q = sub; q < RS / 4; q += LP) s = dot4(row[q], dz4[q], s);
                 }
                 s = lane_group_sum(s, LP);
@@ -1128,6 +1129,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             const int p = tid >> lp_sh, sub = tid & (LP - 1);
             float C = sub == 0 ? lam : 0.f, w = 0.f, Y0 = 0.f, Y1 = 0.f, Y2 = 0.f;
             if (p < cnt)
+#pragma unroll 4
                 for (int jl = sub; jl < W; jl += LP) {
                     const float4 v = sc4[jl * Gs + p];
                     C += v.x;
@@ -1183,6 +1185,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 __syncwarp();
                 if (p < cnt) {
                     float4 *e4 = reinterpret_cast<float4 *>(e);
+#pragma unroll 4
                     for (int m = sub; m < 2 * nf; m += LP) {
                         float4 v = e4[m];
                         v.x *= sq; v.y *= sq; v.z *= sq;
