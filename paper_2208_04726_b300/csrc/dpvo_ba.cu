@@ -3,8 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <functional>
 #include <cstring>
+#include <queue>
 #include <vector>
 
 #include "dpvo_ba.h"
@@ -221,13 +223,41 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
 
     const int target_ctas = 2 * num_sms;
     const int final_cap = std::max(1, (6 * num_sms + n - 1) / n);   // one wave of final_kernel CTAs
-    // a batch of unequal problems (serving mixes) deals the linearise CTAs in
-    // proportion to each problem's edges, so that the CTAs' work is even
+    // a batch of unequal problems (serving mixes) deals the linearise CTAs of
+    // one wave so that the most work (edges + patches) any CTA carries is
+    // least: every problem starts with one CTA, and each further CTA goes to
+    // the problem whose CTAs carry the most, up to its chunk count (and, in a
+    // batch large enough that a cluster per problem would take several waves
+    // of the reduced solve, up to the partials one solve CTA sums itself)
     double work_total = 0.0;
     bool uniform = true;
     for (int b = 0; b < n; ++b) {
         work_total += (double)dims[b].n_edges + dims[b].n_patches;
         uniform = uniform && dims[b].n_edges == dims[0].n_edges && dims[b].n_patches == dims[0].n_patches;
+    }
+    std::vector<int> items_of(n, 1);
+    if (!L.ext && !uniform && work_total > 0.0 && n < target_ctas) {
+        const int part_cap = n * kSwCluster > target_ctas ? kSwDirectParts : 1 << 30;
+        std::priority_queue<std::pair<double, int>> heap;   // (work per CTA, problem)
+        for (int b = 0; b < n; ++b) heap.push({(double)dims[b].n_edges + dims[b].n_patches, b});
+        for (int left = target_ctas - n; left > 0 && !heap.empty();) {
+            const int b = heap.top().second;
+            heap.pop();
+            const int cap = std::min(part_cap, (dims[b].n_patches + L.G_cap - 1) / L.G_cap + dims[b].n_frames);
+            if (items_of[b] >= cap) continue;            // no further split of this one
+            ++items_of[b];
+            --left;
+            heap.push({((double)dims[b].n_edges + dims[b].n_patches) / items_of[b], b});
+        }
+        // then no more CTAs than that largest share needs: a split that does
+        // not lower it only adds a partial (e.g. some of many equal problems)
+        double most = 0.0;
+        for (int b = 0; b < n; ++b)
+            most = std::max(most, ((double)dims[b].n_edges + dims[b].n_patches) / items_of[b]);
+        for (int b = 0; b < n; ++b) {
+            const double need = std::ceil(((double)dims[b].n_edges + dims[b].n_patches) / most * (1.0 - 1e-12));
+            items_of[b] = std::max(1, std::min(items_of[b], (int)need));
+        }
     }
     size_t off = 0;
     L.probs.resize(n);
@@ -253,7 +283,7 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
         int items = std::max(1, target_ctas / n);
         if (L.ext) items = ext_items(n, target_ctas);
         else if (!uniform && work_total > 0.0)
-            items = std::max(1, (int)(target_ctas * ((double)d.n_edges + d.n_patches) / work_total));
+            items = items_of[b];
         p.n_items = std::max(1, std::min(items, p.max_chunks));
         if (L.tc_asm) {   // ranges of at most kAtcMaxPatches patches, at least one CTA per SM over the batch
             const int need = (d.n_patches + kAtcMaxPatches - 1) / kAtcMaxPatches;
