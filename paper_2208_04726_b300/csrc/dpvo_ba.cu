@@ -142,11 +142,29 @@ static int final_slices_of(bool tc, int n_patches, int max_chunks, int cap) {
 }
 
 // The last back-substitution (iteration t = the batch's last): n problems.
+// The row layout streams its stored rows through shared memory
+// (final_rows_kernel); the tensor-core layout reads them in place.
 static void launch_final(const Layout &L, int n, cudaStream_t stream, const Prob *probs, int t) {
     const dim3 grid(n, L.final_slices);
-    const size_t smem = 4 * (size_t)std::max(kTcRows, erow_len(L.nf_max));
-    if (L.tc) final_kernel<true><<<grid, kThreads, smem, stream>>>(probs, t, L.G_cap);
-    else final_kernel<false><<<grid, kThreads, smem, stream>>>(probs, t, L.G_cap);
+    if (L.tc) {
+        const size_t smem = 4 * (size_t)std::max(kTcRows, erow_len(L.nf_max));
+        final_kernel<true><<<grid, kThreads, smem, stream>>>(probs, t, L.G_cap);
+    } else {
+        const int rs = erow_len(L.nf_max);
+        final_rows_kernel<<<grid, kThreads, fr_smem_bytes(rs), stream>>>(probs, t, rs);
+    }
+}
+
+// CTAs of final_rows_kernel per problem that fill one wave of n problems.
+static int final_rows_cap(int n, int nf_max, int num_sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, final_rows_kernel, kThreads,
+                                                      fr_smem_bytes(erow_len(nf_max))) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return std::max(1, per_sm * num_sms / n);
 }
 
 // One linearise launch, in the batch's variant.
@@ -222,7 +240,8 @@ Layout make_layout(const dpvo_ba_dims *dims, int n, int num_sms, const dpvo_ba_c
     const int asm_slices_max = L.ext && !L.tc_asm ? asm_slices(L.nf_max) : 1;
 
     const int target_ctas = 2 * num_sms;
-    const int final_cap = std::max(1, (6 * num_sms + n - 1) / n);   // one wave of final_kernel CTAs
+    // one wave of the last back-substitution's CTAs
+    const int final_cap = L.tc ? std::max(1, (6 * num_sms + n - 1) / n) : final_rows_cap(n, L.nf_max, num_sms);
     // a batch of unequal problems (serving mixes) deals the linearise CTAs of
     // one wave so that the most work (edges + patches) any CTA carries is
     // least: every problem starts with one CTA, and each further CTA goes to
@@ -464,6 +483,9 @@ static int set_kernel_attrs(int device) {
         return DPVO_BA_ECUDA;
     if (cudaFuncSetAttribute(bw_edge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
         cudaSuccess)
+        return DPVO_BA_ECUDA;
+    if (cudaFuncSetAttribute(final_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fr_smem_bytes(erow_len(kMaxFree))) != cudaSuccess)
         return DPVO_BA_ECUDA;
     return DPVO_BA_OK;
 }

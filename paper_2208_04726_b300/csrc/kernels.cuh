@@ -1664,6 +1664,100 @@ __global__ void __launch_bounds__(kThreads, TC ? 5 : 6) final_kernel(const Prob 
 }
 
 // ----------------------------------------------------------------------------
+// final_rows_kernel: the last back-substitution in the row layout, streamed.
+// Grid (problems, CTAs per problem), one wave; each CTA takes the problem's
+// 64-patch slices blockIdx.y, blockIdx.y + gridDim.y, ... and brings each
+// slice's stored rows (64 consecutive rows, contiguous) into shared memory by
+// one bulk copy, kFrStages slices ahead, so that enough bytes are in flight
+// for the HBM rate; four lanes per patch then form the dot product from
+// shared memory in the order backsub_rows uses.  Every wait is bounded: a copy
+// that does not land marks TIMEOUT.  Dynamic shared memory: fr_smem_bytes.
+// ----------------------------------------------------------------------------
+constexpr int kFrPatches = kThreads / 4;   // patches per slice
+constexpr int kFrStages = 2;               // slices in flight per CTA
+
+__host__ __device__ inline size_t fr_smem_bytes(int rs_max) {
+    return align16((size_t)rs_max * 4) + (size_t)kFrStages * kFrPatches * rs_max * 4;
+}
+
+__global__ void __launch_bounds__(kThreads) final_rows_kernel(const Prob *__restrict__ probs, int t, int rs_max) {
+    extern __shared__ __align__(16) unsigned char fsm[];
+    __shared__ __align__(8) uint64_t s_full[kFrStages];
+    __shared__ int s_bad;
+    const Prob &pr = probs[blockIdx.x];
+    const int tid = threadIdx.x;
+    if (t != pr.iters) return;
+    const int st = block_status(pr.status);
+    if (blockIdx.y == 0 && tid == 0 && pr.status_user) *pr.status_user = st;
+    if (st != 0) return;
+    const int N = pr.N;
+    if (blockIdx.y == 0 && !pr.no_writeback) {
+        const float *pose_new = pr.pose_it + (size_t)t * N * 7;
+        for (int q = tid; q < N * 7; q += kThreads) pr.poses[q] = pose_new[q];
+    }
+    const int P = pr.P, nf = pr.nf, RS = erow_len(nf);
+    const int n_sl = (P + kFrPatches - 1) / kFrPatches;
+    if ((int)blockIdx.y >= n_sl) return;
+    const int n_mine = (n_sl - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y;
+    float *dxf = reinterpret_cast<float *>(fsm);
+    float *bufs = reinterpret_cast<float *>(fsm + align16((size_t)rs_max * 4));
+    const size_t buf_floats = (size_t)kFrPatches * rs_max;
+    if (tid == 0) {
+        for (int b = 0; b < kFrStages; ++b) mbar_init(smem_u32(&s_full[b]), 1);
+        s_bad = 0;
+    }
+    stage_dxi<false>(pr, t, dxf, tid, kThreads);
+    __syncthreads();
+    // thread 0: the i-th of this CTA's slices into buffer i % kFrStages
+    auto issue = [&](int i) {
+        const int k0 = ((int)blockIdx.y + i * (int)gridDim.y) * kFrPatches;
+        const int cnt = min(kFrPatches, P - k0);
+        const uint32_t bar = smem_u32(&s_full[i % kFrStages]);
+        const uint32_t bytes = (uint32_t)(cnt * RS * 4);   // a multiple of 16: RS = 8 nf + 4
+        fence_async_smem();                                // the buffer's earlier reads come first
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+        bulk_copy_g2s(bufs + (i % kFrStages) * buf_floats, pr.erow + (size_t)k0 * RS, bytes, bar);
+    };
+    if (tid == 0)
+        for (int i = 0; i < min(kFrStages, n_mine); ++i) issue(i);
+    const float *depth_old = pr.depth_it + (size_t)(t - 1) * P;
+    float *depth_new = pr.depth_it + (size_t)t * P;
+    const float4 *dz4 = reinterpret_cast<const float4 *>(dxf);
+    const int p = tid >> 2, sub = tid & 3;
+    for (int i = 0; i < n_mine; ++i) {
+        const int k0 = ((int)blockIdx.y + i * (int)gridDim.y) * kFrPatches;
+        const int cnt = min(kFrPatches, P - k0), k = k0 + p;
+        const float d_old = p < cnt && sub == 0 ? depth_old[k] : 0.f;
+        const bool landed = mbar_wait(smem_u32(&s_full[i % kFrStages]), (uint32_t)(i / kFrStages) & 1u);
+        if (!landed) s_bad = 1;
+        const float *row = bufs + (i % kFrStages) * buf_floats + (size_t)p * RS;
+        float s = 0.f;
+        if (landed && p < cnt) {
+            const float4 *row4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll 4
+            for (int q = sub; q < RS / 4; q += 4) s = dot4(row4[q], dz4[q], s);
+        }
+        s = quad_sum(s);
+        if (landed && p < cnt && sub == 0) {
+            const float dnew = d_old + row[8 * nf + 1] * (row[8 * nf] - s);
+            depth_new[k] = dnew;
+            if (!pr.no_writeback) pr.patches[3 * k + 2] = dnew;
+        }
+        __syncthreads();                                   // the buffer is read
+        if (s_bad) break;                                  // read after the barrier: the same in every thread
+        if (tid == 0 && i + kFrStages < n_mine) issue(i + kFrStages);
+    }
+    if (s_bad && tid == 0) {
+        // report, and give the copies still in flight one more bounded wait
+        atomicOr(pr.status, DPVO_BA_STATUS_TIMEOUT);
+        for (int b = 0; b < kFrStages; ++b) {
+            mbar_wait(smem_u32(&s_full[b]), 0u);
+            mbar_wait(smem_u32(&s_full[b]), 1u);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
 // solve_kernel: one CTA of kSolveThreads per problem.  Sums the Schur partials
 // in FP64 (fixed order), factors the reduced pose system by Cholesky in its
 // square-root-free form S = U D^-1 U^T (U lower, D = diag U) with the right-
