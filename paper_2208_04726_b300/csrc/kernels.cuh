@@ -449,6 +449,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// TMEM columns of the strip running sums per linearise CTA (FP32 fused
+// variant): two warps per lane quarter, 36 columns each, rounded up to a
+// power of two.  Two CTAs per SM take 256 of the 512.
+constexpr uint32_t kSumsTmemCols = 128;
+
 // Role rotation of the in-loop prefetch: its first roles (the bulk copies,
 // the descriptor, the patch arrays) go to the last two warps, which hold no
 // patch of the per-patch phase that follows for chunks of up to 48 patches.
@@ -840,9 +845,13 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
             sa = sb = my_strip - nbs;
         }
     }
-    float acc_s[18], acc_c[18], blk[18];
+    // the strip's compensated running sums (s, c); in the FP32 fused variant
+    // they wait in TMEM between the chunks' Schur phases, which leaves their
+    // registers to the other phases
+    constexpr bool kSumsInTmem = !TC && !EXT;
+    float acc_s[18], acc_c[18];
 #pragma unroll
-    for (int q = 0; q < 18; ++q) { acc_s[q] = 0.f; acc_c[q] = 0.f; blk[q] = 0.f; }
+    for (int q = 0; q < 18; ++q) { acc_s[q] = 0.f; acc_c[q] = 0.f; }
 
     for (int q = tid; q < N * 7; q += kThreads) spn[q] = pose_new[q];
     if constexpr (EXT) {
@@ -866,6 +875,20 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         __syncthreads();
         tc_fence_after();
         tmem = s_tmem;
+    }
+
+    // TMEM for the running sums: warp w uses lanes 32 (w % 4) .. + 31,
+    // columns 36 (w / 4) .. + 35 (s, then c)
+    __shared__ uint32_t s_sums_tmem;
+    uint32_t tsums = 0;
+    constexpr bool sums_tmem = kSumsInTmem;
+    if (sums_tmem) {
+        if (warp == 0) tmem_alloc(&s_sums_tmem, kSumsTmemCols);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        tsums = s_sums_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(36 * (warp >> 2));
+        tmem_st_sums36(tsums, acc_s, acc_c);                 // zeros
     }
 
     __shared__ __align__(16) Chunk s_ch[2];
@@ -1342,7 +1365,11 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         // -- (c) Schur accumulation over the chunk's patches, then the group's B blocks.
         // A strip with a frame outside the chunk's window would only add zeros
         // (those columns of E are zero): its owner skips the chunk's products.
+        if (sums_tmem) tmem_ld_sums36(tsums, acc_s, acc_c);   // whole warps
         if (owns) {
+            float blk[18];                                 // FP32 block sum of up to kFlushEvery patches
+#pragma unroll
+            for (int q = 0; q < 18; ++q) blk[q] = 0.f;
             int since = 0;
             const int fa_s = t0 + sa, fb_s = t0 + sb;
             const bool s_on = fa_s >= jlo && fa_s <= ch.jhi && fb_s >= jlo && fb_s <= ch.jhi;
@@ -1459,6 +1486,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 }
             }
         }
+        if (sums_tmem) tmem_st_sums36(tsums, acc_s, acc_c);   // whole warps
         if constexpr (EXT) if (!group_next && !adjoint_rhs) {
             // more strips than threads: each pose-pair block goes straight into
             // this CTA's FP64 partial (it owns the partial; groups are
@@ -1582,6 +1610,15 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     // at most 10 free poses) the KS parts of each strip are first summed in
     // FP64, in a fixed order, in the frame-sum buffer (dead here), so that the
     // reduced solve reads one partial per CTA
+    if (sums_tmem) {
+        tmem_ld_sums36(tsums, acc_s, acc_c);
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc_fence_after();
+            tmem_dealloc(s_sums_tmem, kSumsTmemCols);
+        }
+    }
     double *out = pr.partial + (size_t)itm.item * pr.L;
     if (KS == 1) {
         if (owns) {

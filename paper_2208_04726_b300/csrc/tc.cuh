@@ -150,4 +150,56 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// A thread's 18 + 18 FP32 running sums (s, then c) kept in 36 consecutive
+// TMEM columns of its lane between uses: loaded into registers and stored
+// back by the whole warp (every lane takes part).  Each wait names the
+// registers it guards, so that no use of them moves above it.
+__device__ __forceinline__ void tmem_ld_sums36(uint32_t taddr, float *s, float *c) {
+    uint32_t r[16];
+    float v[36];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr + 16u * h));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                       "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                       "+r"(r[15])
+                     :
+                     : "memory");
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[16 * h + q] = __uint_as_float(r[q]);
+    }
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr + 32u));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[32 + q] = __uint_as_float(r[q]);
+#pragma unroll
+    for (int q = 0; q < 18; ++q) { s[q] = v[q]; c[q] = v[18 + q]; }
+}
+
+__device__ __forceinline__ void tmem_st_sums36(uint32_t taddr, const float *s, const float *c) {
+    uint32_t v[36];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) { v[q] = __float_as_uint(s[q]); v[18 + q] = __float_as_uint(c[q]); }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t *r = v + 16 * h;
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
+            ::"r"(taddr + 16u * h), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+            "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+            : "memory");
+    }
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(taddr + 32u), "r"(v[32]),
+                 "r"(v[33]), "r"(v[34]), "r"(v[35])
+                 : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
 }  // namespace dpvo
