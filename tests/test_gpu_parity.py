@@ -367,3 +367,51 @@ def test_reduced_solve_f64_mode_matches_oracle_and_default(spec, seed):
     finally:
         f64.close()
         dflt.close()
+
+
+def test_ill_conditioned_reduced_system_takes_the_fp64_elimination(solver):
+    """The default reduced solve (FP32 factor, FP64 refinement) must hand a
+    system it cannot refine to its FP64 elimination.  The last free pose of an
+    8-frame scene keeps four observations, two at full weight and two at 1e-6
+    (every other edge touching it weightless), so that some of its directions
+    are pinned only by the weak pair: the reduced system is SPD with condition
+    number ~1.7e10, beyond what the FP32 factor's refinement contracts (at
+    weight 1e-5, condition ~1.6e9, it still converges; at 1e-8 the system is no
+    longer SPD in FP64 and both modes report NOT_SPD).  Checked three ways:
+    status OK; the increment is bit for bit that of reduced_solve_f64 (which
+    always eliminates in FP64) on the same inputs, so the FP64 elimination
+    produced it; and it solves the device's own reduced system (S, v') to
+    within 1e-5 relative of numpy's dense solve of that system (measured
+    ~4e-7; S's two triangles differ by ~7e-9 of its largest entry, which at
+    this condition number alone allows differences of that size).  At this
+    condition number the FP32 linearisation moves the solution by far more
+    than 1e-4 in the weak directions, so the oracle's FP64 step is no
+    yardstick here."""
+    sc = S.make_scene(S.PLAIN_N8, 7)
+    last = sc.n_frames - 1
+    w = sc.weight.copy()
+    w[(sc.jj == last) | (sc.anchor[sc.kk] == last)] = 0.0
+    cand = np.flatnonzero((sc.jj == last) & (sc.anchor[sc.kk] != last))
+    pick = np.random.default_rng(0).choice(cand, 4, replace=False)
+    w[pick[:2]] = 1.0
+    w[pick[2:]] = 1e-6
+    sc = dataclasses.replace(sc, weight=w.astype(np.float32))
+    S_dev, v_dev = solver.reduced_system(ba.problem_from_scene(sc))
+    torch.cuda.synchronize()
+    Sm, vm = S_dev.cpu().numpy(), v_dev.cpu().numpy()
+    assert np.abs(Sm - Sm.T).max() <= 1e-7 * np.abs(Sm).max()
+    assert np.linalg.eigvalsh(0.5 * (Sm + Sm.T)).min() > 0
+    cond = np.linalg.cond(Sm)
+    assert 1e9 < cond < 1e11, cond
+    f64 = ba.Solver(schur_tf32=solver.schur_mode, reduced_solve_f64=True)   # the same Schur mode
+    try:
+        pd = solve_gpu(solver, [sc])
+        pf = solve_gpu(f64, [sc])
+        assert int(pd[0].status.item()) == int(pf[0].status.item()) == 0
+        _, _, dxi_d = solver.iterate(0, 0, sc.n_frames, sc.n_patches, sc.t0)
+        _, _, dxi_f = f64.iterate(0, 0, sc.n_frames, sc.n_patches, sc.t0)
+        assert np.array_equal(dxi_d, dxi_f)
+        x = np.linalg.solve(Sm, vm)
+        assert np.linalg.norm(dxi_d.reshape(-1) - x) <= 1e-5 * np.linalg.norm(x), cond
+    finally:
+        f64.close()
