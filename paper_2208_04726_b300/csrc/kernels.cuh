@@ -881,8 +881,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     // columns 36 (w / 4) .. + 35 (s, then c)
     __shared__ uint32_t s_sums_tmem;
     uint32_t tsums = 0;
-    constexpr bool sums_tmem = kSumsInTmem;
-    if (sums_tmem) {
+    if constexpr (kSumsInTmem) {
         if (warp == 0) tmem_alloc(&s_sums_tmem, kSumsTmemCols);
         tc_fence_before();
         __syncthreads();
@@ -901,11 +900,11 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     // the previous iteration from the staged rows), and, at the start of a
     // group, the window poses (parts: 1 the slot table and window poses, 2 the
     // patch data).  pc is read from shared memory (the descriptor slot stays
-    // valid until the copies of the chunk after next start).  It runs during the previous chunk's Schur products (and
-    // before the loop for the first chunk): it writes only buffers that chunk
-    // no longer reads.  Thread (p = tid mod PS, jl = tid /
-    // PS + (256 / PS) i) for the slots, PS = count rounded up to a power of
-    // two (at least 8).
+    // valid until the copies of the chunk after next start).  It runs during
+    // the previous chunk's Schur products (and before the loop for the first
+    // chunk): it writes only buffers that chunk no longer reads.  Thread
+    // (p = tid mod PS, jl = tid / PS + (256 / PS) i) for the slots, PS = count
+    // rounded up to a power of two (at least 8).
     auto prepare = [&](const Chunk &pc, int pk, bool new_group, int parts) {
         int o_jj, o_tw;                                    // alignment slack of the staged edge ranges
         staged_offsets(pr, pc, true, o_jj, o_tw);
@@ -1365,7 +1364,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
         // -- (c) Schur accumulation over the chunk's patches, then the group's B blocks.
         // A strip with a frame outside the chunk's window would only add zeros
         // (those columns of E are zero): its owner skips the chunk's products.
-        if (sums_tmem) tmem_ld_sums36(tsums, acc_s, acc_c);   // whole warps
+        if constexpr (kSumsInTmem) tmem_ld_sums36(tsums, acc_s, acc_c);   // whole warps
         if (owns) {
             float blk[18];                                 // FP32 block sum of up to kFlushEvery patches
 #pragma unroll
@@ -1486,7 +1485,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
                 }
             }
         }
-        if (sums_tmem) tmem_st_sums36(tsums, acc_s, acc_c);   // whole warps
+        if constexpr (kSumsInTmem) tmem_st_sums36(tsums, acc_s, acc_c);   // whole warps
         if constexpr (EXT) if (!group_next && !adjoint_rhs) {
             // more strips than threads: each pose-pair block goes straight into
             // this CTA's FP64 partial (it owns the partial; groups are
@@ -1610,7 +1609,7 @@ __global__ void __launch_bounds__(kThreads, 2) linearize_kernel(const Prob *__re
     // at most 10 free poses) the KS parts of each strip are first summed in
     // FP64, in a fixed order, in the frame-sum buffer (dead here), so that the
     // reduced solve reads one partial per CTA
-    if (sums_tmem) {
+    if constexpr (kSumsInTmem) {
         tmem_ld_sums36(tsums, acc_s, acc_c);
         tc_fence_before();
         __syncthreads();
