@@ -271,6 +271,10 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ 
         Plan &P = s_plan[slot];
         const int mode = P.mode;
         float *out = A.corr + (size_t)e * 2 * kQ * 49;
+        // warp 0 plans the next edge now, while this edge's boxes land (its
+        // plan slot was freed by the last barrier of the previous edge)
+        const int en = e + gridDim.x;
+        if (en < A.E && warp == 0) plan_edge(A, en, s_plan[slot ^ 1], lane, tma_ok);
         if (mode == kFast) {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             if (!dpvo::mbar_wait(tbar, (uint32_t)(n_tma - 1) & 1u)) atomicOr(&s_bad, 1);
@@ -369,10 +373,8 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ 
                 __syncthreads();
             }
         }
-        // plan the next edge and start its copies (they fly during this epilogue)
-        const int en = e + gridDim.x;
+        // start the next edge's copies (they fly during this epilogue)
         if (en < A.E) {
-            if (warp == 0) plan_edge(A, en, s_plan[slot ^ 1], lane, tma_ok);
             dpvo::fence_async_smem();                    // this CTA's generic writes before the next copies
             __syncthreads();
             if (s_plan[slot ^ 1].mode == kFast && s_bad == 0) issue_fast(s_plan[slot ^ 1]);
