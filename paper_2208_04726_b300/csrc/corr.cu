@@ -46,17 +46,33 @@ constexpr size_t kSmemBytes = kAbytes + kA1bytes + kBbytes + (size_t)(kChunk + k
 static_assert(kA1bytes + kBbytes + (size_t)(kChunk + kRows1) * kDld * 4 >= kAbytes,
               "the level-1 GEMM's 128 operand rows stay inside the allocation");
 // Fast edges load their footprints by TMA: one fixed box per level (level 0
-// 11 x 11 pixels, level 1 9 x 9) per 8-channel group, written as a slab of
-// box-pixel rows of 16 bytes (row t = y * width + x), the slabs of a level
-// kSlab0 / kSlab1 bytes apart: a K-major operand whose core matrices (8 rows x
-// 16 bytes) are 128 contiguous bytes, 8-row groups 128 bytes apart and
-// K-adjacent core matrices one slab apart.  Out-of-map pixels read as zero.
+// 11 x 11 pixels, level 1 9 x 9) per 64-channel half, with 128-byte swizzling:
+// box-pixel rows of 128 bytes (row t = y * width + x), 16-byte pieces permuted
+// within each 1024-byte group of 8 rows -- the canonical K-major operand with
+// 128-byte swizzling, whose 8-row groups are 1024 bytes apart.  A level's two
+// halves (channels 0-63, 64-127) are kHalf0 / kHalf1 bytes apart; an MMA's
+// K = 16 slice starts 32 bytes further along the row.  The fast operands sit
+// in the first kAbytes + kA1bytes of shared memory (A0f at 0, A1f at kA1f),
+// which must then start on 1024 bytes.  Out-of-map pixels read as zero.
 constexpr int kBoxW0 = 11, kBoxH0 = 11, kBoxW1 = 9, kBoxH1 = 9;
-constexpr uint32_t kSlab0 = kChunk * 16, kSlab1 = kRows1 * 16;
-constexpr uint32_t kTmaBytes = (kD / 8) * 16 * (kBoxW0 * kBoxH0 + kBoxW1 * kBoxH1);
+constexpr int kHalfC = 64;                                  // channels per box
+constexpr uint32_t kHalf0 = kChunk * 128, kHalf1 = kRows1 * 128, kA1f = 2 * kHalf0;
+constexpr uint32_t kTmaBytes = 2 * kHalfC * 2 * (kBoxW0 * kBoxH0 + kBoxW1 * kBoxH1);
 static_assert(kBoxW0 * kBoxH0 <= kChunk && kBoxW1 * kBoxH1 <= kRows1, "boxes fit their operands");
-static_assert((kD / 8) * kSlab0 <= kAbytes && (kD / 8 - 1) * kSlab1 + kChunk * 16 <= kA1bytes,
-              "TMA slabs and the level-1 GEMM's 128 rows stay inside A0 and A1");
+static_assert(kHalf1 % 1024 == 0 && kA1f % 1024 == 0, "the swizzled halves start on 1024 bytes");
+static_assert(kA1f + kHalf1 + kChunk * 128 <= kAbytes + kA1bytes,
+              "the level-1 GEMM's 128 rows of either half stay inside A0 and A1");
+
+// Shared-memory descriptor of a K-major operand with 128-byte swizzling:
+// 8-row groups 1024 bytes apart (the leading offset is unused), version 1.
+__device__ __forceinline__ uint64_t swz128_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kChunk >> 4) << 24);   // FP32 D, BF16 A and B, K-major, 128 x 16
 constexpr float kCoordMax = 1e4f;
@@ -217,7 +233,7 @@ __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *tm, int
 }
 
 __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ Args A) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *opA0 = smem, *opA1 = smem + kAbytes, *opB = smem + kAbytes + kA1bytes;
     float *Dfast = reinterpret_cast<float *>(smem + kAbytes + kA1bytes + kBbytes);   // rows 0..127 level 0, then level 1
     float *Dgen = reinterpret_cast<float *>(opA1);   // general path (up to kMaxChunks x 128 rows), over A1 .. copies
@@ -228,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t aA0 = smem_u32(opA0), aA1 = smem_u32(opA1), aB = smem_u32(opB), mbar = smem_u32(&s_mbar);
     const uint32_t tbar = smem_u32(&s_tma);
-    const bool tma_ok = A.use_tma && (aA0 & 127u) == 0 && (aA1 & 127u) == 0;   // box destinations 128-byte aligned
+    const bool tma_ok = A.use_tma && (aA0 & 1023u) == 0;   // the swizzled box destinations start on 1024 bytes
     if (warp == 0) dpvo::tmem_alloc(&s_tmem, 32);
     if (tid == 0) {
         dpvo::mbar_init(mbar, 1);
@@ -251,9 +267,9 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ 
         if (tid == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tbar), "r"(kTmaBytes)
                          : "memory");
-            for (int g = 0; g < kD / 8; ++g) {
-                tma_box(aA0 + g * kSlab0, &A.tm[0], 8 * g, P.box[0][0], P.box[0][1], P.j, tbar);
-                tma_box(aA1 + g * kSlab1, &A.tm[1], 8 * g, P.box[1][0], P.box[1][1], P.j, tbar);
+            for (int h = 0; h < 2; ++h) {
+                tma_box(aA0 + h * kHalf0, &A.tm[0], kHalfC * h, P.box[0][0], P.box[0][1], P.j, tbar);
+                tma_box(aA0 + kA1f + h * kHalf1, &A.tm[1], kHalfC * h, P.box[1][0], P.box[1][1], P.j, tbar);
             }
         }
         ++n_tma;
@@ -284,11 +300,11 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ 
             if (s_bad == 0) {
                 if (tid == 0) {
                     dpvo::tc_fence_after();
-                    for (int ks = 0; ks < kD / 16; ++ks)
-                        mma_bf16(tmem, dpvo::smem_desc(aA0 + ks * 2 * kSlab0, kSlab0, 128),
+                    for (int ks = 0; ks < kD / 16; ++ks)   // K slice ks: half ks / 4, 32 bytes per slice
+                        mma_bf16(tmem, swz128_desc(aA0 + (ks >> 2) * kHalf0 + (ks & 3) * 32),
                                  dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
                     for (int ks = 0; ks < kD / 16; ++ks)
-                        mma_bf16(tmem + kN, dpvo::smem_desc(aA1 + ks * 2 * kSlab1, kSlab1, 128),
+                        mma_bf16(tmem + kN, swz128_desc(aA0 + kA1f + (ks >> 2) * kHalf1 + (ks & 3) * 32),
                                  dpvo::smem_desc(aB + ks * 2 * kLbo, kLbo, kSbo), ks > 0 ? 1 : 0);
                     dpvo::mma_commit(mbar);
                 }
@@ -414,8 +430,9 @@ __global__ void __launch_bounds__(kThreads) corr_kernel(const __grid_constant__ 
 }
 
 // Host: the tensor maps of both levels ([N][H][W][128] bfloat16, 16-byte
-// aligned: checked by the entry point), boxes of 8 channels x the level's
-// fixed box; false if the driver entry point is missing or rejects them.
+// aligned: checked by the entry point), boxes of 64 channels x the level's
+// fixed box with 128-byte swizzling; false if the driver entry point is
+// missing or rejects them.
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -439,10 +456,11 @@ static bool encode_maps(Args &A) {
         const cuuint64_t W = (cuuint64_t)A.W[l], H = (cuuint64_t)A.H[l];
         const cuuint64_t dims[4] = {(cuuint64_t)kD, W, H, (cuuint64_t)A.N};
         const cuuint64_t strides[3] = {(cuuint64_t)kD * 2, W * kD * 2, H * W * kD * 2};
-        const cuuint32_t box[4] = {8, (cuuint32_t)(l == 0 ? kBoxW0 : kBoxW1), (cuuint32_t)(l == 0 ? kBoxH0 : kBoxH1), 1};
+        const cuuint32_t box[4] = {(cuuint32_t)kHalfC, (cuuint32_t)(l == 0 ? kBoxW0 : kBoxW1),
+                                   (cuuint32_t)(l == 0 ? kBoxH0 : kBoxH1), 1};
         const cuuint32_t estr[4] = {1, 1, 1, 1};
         if (encode(&A.tm[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(A.fmap[l]), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }
